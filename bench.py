@@ -1,0 +1,368 @@
+"""Benchmark of the ventilation-flow time step on GB300: Gcell-updates/s and fraction of the HBM roofline.
+
+Workload (one step = every row of the hot path: RK4 stages, divergence, 4 iterations of the FFT Poisson solve,
+projection, filter, FP64 reductions): the single room of 256 x 128 x 128 cells (10 x 5 x 5 m, 2-cell walls, a
+5x5-cell inlet duct forced to 1 m/s and the opposite outlet), FP32 bulk with FP64 reductions every step.  The
+state (about 0.3 GB) is larger than L2, so no flush is needed between steps.
+
+Our arm prints one JSON line with the device-timed throughput, the end-to-end throughput through the C ABI with
+host buffers, the roofline of the dominant kernel (per-kernel CUDA-event times from vf_profile_steps), the FP64
+form's throughput, clocks sampled during the timed region and the oracle timed on the host cores.
+
+``--impl reference`` times the FP64 CPU oracle as it stands on the host cores (the only other place this script
+runs it), on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gcell-updates/s per step & % HBM roofline"
+UNIT = "Gcell-updates/s"
+
+# Algorithmic bytes per cell of each kernel phase in FP32 (F = 4 bytes per value, 1 byte of mask per pass that
+# reads it): what each launch must read and write at least once.
+F32 = 4
+PHASE_BYTES_PER_CELL = {
+    "stage1": 12 * F32 + 1,      # read q (4), write acc (4), q2 (4), mask
+    "stage2": 20 * F32 + 1,      # read q_s, q_n, acc; write acc, q_next; mask
+    "stage3": 20 * F32 + 1,
+    "stage4": 12 * F32 + 1,      # read q_s, acc; write q*; mask
+    "div": 4 * F32,              # read u*, v*, w*; write r
+    "fft_x_fwd": 3 * F32 + 1,    # read r, p, mask; write the half spectrum (N/2 complex = N F bytes)
+    "fft_y_fwd": 2 * F32,        # read + write the spectrum
+    "fft_z_solve": 2 * F32,
+    "fft_y_inv": 2 * F32,
+    "fft_x_inv": 2 * F32,        # read the spectrum, write p
+    "project": 7 * F32 + 1,      # read u*, v*, w*, p, mask; write u, v, w
+    "filter": 8 * F32 + 1,       # read u, v, w, c, mask; write 4 fields
+    "reduce": 4 * F32 + 1,       # read u, v, w, c, mask
+}
+# Model of one step with the kernels fused as far as the method allows (RK4 121F+9 with n = 4): the survey's
+# algorithmic minimum, used for the step-level roofline fraction.
+STEP_MODEL_BYTES_PER_CELL_FP32 = 121 * F32 + 9
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu_index = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.gpu_index)],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is None:
+            return
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if os.environ.get("VF_BENCH_GLOO") is None else "gloo")
+    return world, rank, local
+
+
+def dist_max(value, world):
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device="cuda" if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def dist_barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def traffic_record(kernel):
+    """DRAM bytes per launch of ``kernel`` from the committed ncu summary, if taken on the current source."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        rec = json.load(f)
+    entry = rec.get("kernels", {}).get(kernel)
+    if not entry:
+        return None
+    src = os.path.join(ROOT, entry["source"])
+    if not os.path.exists(src):
+        return None
+    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    if digest != entry.get("source_sha256"):
+        return None
+    scale = entry.get("scale_to_full", 1.0)
+    return entry["dram_bytes_per_launch"] * scale
+
+
+def cpu_baseline_oracle(room, precision_note, steps=1):
+    """The FP64 oracle timed on the host cores over ``steps`` full steps of the same room."""
+    from oracle import flow as F
+    from paper_2204_02107_gb300 import rooms
+    prm = F.Params(nx=room.nx, ny=room.ny, nz=room.nz, lx=room.lx, ly=room.ly, lz=room.lz, nu=rooms.NU_AIR,
+                   dt=room.dt, u_set=(room.u_in, 0.0, 0.0), c_set=0.0, filter=True, n_pressure_iters=4)
+    geom = F.Geometry(room.beta, room.S, room.room)
+    st = F.zero_state(prm, c=room.initial_c())
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        st, _ = F.step(st, geom, prm)
+    dt = time.perf_counter() - t0
+    return {"value": room.cells * steps / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{steps} full FP64 step(s) of the {room.nx}x{room.ny}x{room.nz} room ({precision_note}); "
+                      f"numpy element-wise ops and numpy.fft run on one core"}
+
+
+def run_reference(args):
+    """--impl reference: the oracle on the host cores, on a bounded sample of the workload."""
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return 0
+    from oracle import flow as F
+    from paper_2204_02107_gb300 import rooms
+    room = rooms.single_room(128, 64, 64)
+    prm = F.Params(nx=room.nx, ny=room.ny, nz=room.nz, lx=room.lx, ly=room.ly, lz=room.lz, nu=rooms.NU_AIR,
+                   dt=room.dt, u_set=(room.u_in, 0.0, 0.0), c_set=0.0, filter=True, n_pressure_iters=4)
+    geom = F.Geometry(room.beta, room.S, room.room)
+    st = F.zero_state(prm, c=room.initial_c())
+    for _ in range(args.warmup):
+        st, _ = F.step(st, geom, prm)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        st, _ = F.step(st, geom, prm)
+    el = time.perf_counter() - t0
+    value = room.cells * args.steps / el / 1e9
+    sample = ("each step one full FP64 oracle step of the same room construction at 128x64x64 (1/8 of the cells "
+              "of the 256x128x128 room), numpy on one host core")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3 / max(1, args.steps),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": "single room 256x128x128 (sampled at 128x64x64)",
+                                            "cells": room.cells, "parallelism": "none (host oracle)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def e2e_run(room, precision, steps, stream):
+    """End to end through the C ABI with pinned host buffers: grid creation, mask / inflow / region / scalar
+    upload, ``steps`` steps with a reduction record each, then the records and all five fields read back."""
+    import torch
+    from paper_2204_02107_gb300 import native
+    n = room.cells
+
+    def pinned(arr, dtype):
+        t = torch.empty(arr.size, dtype=dtype, pin_memory=True)
+        t.numpy()[:] = arr.ravel()
+        return t.numpy()
+
+    beta = pinned(room.beta, torch.uint8)
+    S = pinned(room.S, torch.uint8)
+    region = pinned(room.room, torch.uint8)
+    c0 = pinned(room.initial_c().astype(np.float32), torch.float32)
+    outs = [torch.empty(n, dtype=torch.float32, pin_memory=True).numpy() for _ in range(5)]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g = native.Grid(room.nx, room.ny, room.nz, room.lx, room.ly, room.lz, nu=1.6e-5, dt=room.dt,
+                    precision=precision, stream=stream.cuda_stream, history_capacity=max(16, steps))
+    g.set_mask(beta)
+    g.set_inflow(S, (room.u_in, 0.0, 0.0), 0.0)
+    g.set_region(region)
+    g.set_field("c", c0)
+    g.step(steps, reduce_every=1)
+    hist = g.history(steps)
+    for name, out in zip(("u", "v", "w", "c", "p"), outs):
+        native.lib().vf_read_field(g._h, native.FIELDS[name], native.C.c_void_p(out.ctypes.data), 0,
+                                   native.VF_HOST)
+    g.sync()
+    el = time.perf_counter() - t0
+    g.close()
+    h2d = 3 * n + 4 * n
+    d2h = 5 * 4 * n + len(hist) * native.C.sizeof(native.VfReduce)
+    return {"value": n * steps / el / 1e9, "unit": UNIT, "h2d_bytes_per_step": h2d / steps,
+            "d2h_bytes_per_step": d2h / steps, "seconds": el,
+            "what": "create grid + upload mask, forcing region, room region, scalar (pinned host) + steps with "
+                    "per-step FP64 reductions + read back the reduction records and u, v, w, c, p"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fp64-steps", type=int, default=100)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    from paper_2204_02107_gb300 import native, rooms
+    native.lib()
+
+    room = rooms.single_room(256, 128, 128)
+    stream = torch.cuda.Stream()
+    g = native.room_grid(room, precision="fp32", stream=stream.cuda_stream)
+    cells = room.cells
+    launches_per_step = 4 + 1 + 5 * 4 + 1 + 1 + 2
+
+    g.step(args.warmup, reduce_every=1)
+    g.sync()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    gpu_index = int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0]) if \
+        os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0].isdigit() else local
+    with ClockSampler(gpu_index) as clocks:
+        time.sleep(0.3)
+        dist_barrier(world)
+        torch.cuda.synchronize()
+        start.record(stream)
+        g.step(args.steps, reduce_every=1)
+        end.record(stream)
+        end.synchronize()
+        torch.cuda.synchronize()
+        dist_barrier(world)
+    ms = start.elapsed_time(end)
+    ms_max = dist_max(ms, world)
+    hist = g.history(16)
+    value = world * cells * args.steps / (ms_max / 1e3) / 1e9
+
+    # per-kernel durations (CUDA events after every launch on the grid's stream)
+    prof_steps = max(3, min(args.steps, 20))
+    phases = g.profile_steps(prof_steps, reduce_every=1)
+    peak, peak_kind = measured_peaks()
+    per_kernel = {}
+    for name, (tot_ms, nl) in phases.items():
+        avg_s = tot_ms / nl / 1e3
+        b = PHASE_BYTES_PER_CELL[name] * cells
+        per_kernel[name] = {"launches": nl, "avg_us": avg_s * 1e6, "share": None,
+                            "algorithmic_gb_s": b / avg_s / 1e9}
+    total_ms = sum(t for t, _ in phases.values())
+    for name, (tot_ms, _) in phases.items():
+        per_kernel[name]["share"] = tot_ms / total_ms
+    dominant = max(phases, key=lambda k: phases[k][0])
+    dom_avg_s = phases[dominant][0] / phases[dominant][1] / 1e3
+    achieved = PHASE_BYTES_PER_CELL[dominant] * cells / dom_avg_s / 1e9
+    traffic = traffic_record(dominant)
+    step_s = ms_max / 1e3 / args.steps
+    step_gbs = STEP_MODEL_BYTES_PER_CELL_FP32 * cells / step_s / 1e9
+
+    # FP64 form of the same step (parity path)
+    g64 = native.room_grid(room, precision="fp64", stream=stream.cuda_stream)
+    g64.step(3, reduce_every=1)
+    g64.sync()
+    s64, e64 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s64.record(stream)
+    g64.step(args.fp64_steps, reduce_every=1)
+    e64.record(stream)
+    e64.synchronize()
+    fp64_ms = s64.elapsed_time(e64)
+    g64.close()
+
+    e2e = e2e_run(room, "fp32", args.steps, stream)
+    g.close()
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "single room 256x128x128 (10x5x5 m, 2-cell walls, 5x5 duct, U_in = 1 m/s), "
+                               "FP32 bulk + FP64 reductions every step, filter on, 4 pressure iterations",
+                   "cells": cells, "global_cells": cells * world, "precision": "fp32_mixed",
+                   "l2": "state 0.3 GB > 126 MB L2: inputs larger than L2, no flush",
+                   "parallelism": "one independent room per GPU" if world > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                     "bytes_per_cell": PHASE_BYTES_PER_CELL[dominant]},
+        "step_roofline": {"model_bytes_per_cell": STEP_MODEL_BYTES_PER_CELL_FP32, "achieved_gb_s": step_gbs,
+                          "frac": step_gbs / peak, "peak_kind": peak_kind},
+        "kernels": per_kernel,
+        "fp64": {"value": cells * args.fp64_steps / (fp64_ms / 1e3) / 1e9, "unit": UNIT,
+                 "ms_per_step": fp64_ms / args.fp64_steps, "steps": args.fp64_steps},
+        "e2e": e2e,
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clocks.summary(),
+        "last_record": {k: hist[-1][k] for k in ("step", "ke", "c_room", "div_max", "u_max")} if hist else None,
+    }
+    if world == 1 and rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_oracle(room, "FP64, filter on, 4 pressure iterations")
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

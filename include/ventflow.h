@@ -1,0 +1,225 @@
+/*
+ * ventflow.h -- C ABI of the GB300 incompressible-flow time step of DNSLABIB
+ * (Korhonen, Laitinen, Ersavas Isitman, Jimenez, Vuorinen: "A GPU-accelerated computational fluid dynamics
+ * solver for assessing shear-driven indoor airflow and virus transmission by scale-resolved simulations",
+ * arXiv 2204.02107).
+ *
+ * One grid is a uniform periodic Cartesian box of nx*ny*nz cells (cell centres x_i = i*lx/nx, ...).  A time step
+ * (Sec. 2.1-2.2) is:
+ *   1. classic RK4 of u, v, w and the passive scalar c: skew-symmetric central convection, central diffusion,
+ *      relaxation forcing S (u_set - u) / tau_f, body force b; every stage right-hand side is multiplied by the
+ *      binary mask beta (Eqs. 2-4), no pressure term inside the stages;
+ *   2. the divergence r = D u* by central differences;
+ *   3. n iterations of  L p^{k+1} = D((1 - beta) G p^k) + r / dt  (Eq. 9), each a forward 3D FFT, a division by
+ *      the eigenvalues of L = D o G, lambda = -sum_j sin^2(2 pi k_j / n_j) / h_j^2 (zero on the eight null
+ *      modes), and an inverse 3D FFT; p^0 is the previous step's pressure.  p is the pressure divided by
+ *      density: the paper's Eq. 8 has no dt, so its p is dt times this one;
+ *   4. the projection u = beta (u* - dt G p) (Eq. 8);
+ *   5. the sixth-order filter q <- beta (q + pi^-6 sum_j S6_j q), S6 = (1,-6,15,-20,15,-6,1), on u, v, w, c (Eq. 6);
+ *   6. optional FP64 reductions (energy, divergence, scalar inventory, 64-bin histogram) (Sec. 3.3).
+ *
+ * Memory layout: every field is one array of nx*ny*nz values, x fastest: index = x + nx*(y + ny*z).
+ * Precision: VF_FP64 computes everything in double; VF_FP32_MIXED keeps fields, stencils and FFTs in float and
+ * accumulates every reduction in double (per-thread compensated float sums, double across threads).
+ *
+ * Errors: every call returns VF_OK (0) or a negative VF_E* code.  A failing call on a grid records a message
+ * (vf_last_error) and, for CUDA failures, a sticky status that later calls on that grid return.  Calls never
+ * throw.  Device kernels never trap: bounded waits and checks report through status words read by the host.
+ *
+ * Ownership: the caller owns every buffer it passes; the library copies from it (stream-ordered) before the call
+ * returns and never keeps the pointer.  The library owns all device memory it allocates for a grid, through the
+ * optional allocator callback, until vf_destroy.
+ *
+ * Threading: a grid may be used from one host thread at a time.
+ */
+#ifndef VENTFLOW_H
+#define VENTFLOW_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------------------------------------------- */
+#define VF_OK 0
+#define VF_EINVAL (-1)      /* bad argument (null pointer, bad enum, non-positive length, ...) */
+#define VF_ESIZE (-2)       /* grid size not even, < 8, or with a prime factor other than 2, 3, 5 */
+#define VF_ENOMEM (-3)      /* allocation failed, or a batch is over its memory budget */
+#define VF_ECUDA (-4)       /* a CUDA runtime call failed (sticky for the grid) */
+#define VF_ESTATE (-5)      /* call not valid in the current state (e.g. step before set_mask) */
+#define VF_ENONFINITE (-6)  /* a reduction found a NaN or Inf in the fields */
+#define VF_ETIMEOUT (-7)    /* a bounded device wait expired */
+
+typedef enum { VF_FP64 = 0, VF_FP32_MIXED = 1 } vf_precision;
+typedef enum { VF_U = 0, VF_V = 1, VF_W = 2, VF_C = 3, VF_P = 4 } vf_field;
+typedef enum { VF_HOST = 0, VF_DEVICE = 1 } vf_mem;
+
+/* Optional device allocator.  alloc returns a device pointer of at least `bytes` (256-byte aligned) usable on
+ * `stream` (a cudaStream_t), or NULL on failure; free releases it.  NULL allocator -> cudaMallocAsync/FreeAsync. */
+typedef struct vf_allocator {
+    void* (*alloc)(size_t bytes, void* stream, void* ctx);
+    void (*free)(void* ptr, void* stream, void* ctx);
+    void* ctx;
+} vf_allocator;
+
+/* Grid description (Sec. 2.4: the case parameters).  Fill with vf_grid_desc_default, then override. */
+typedef struct vf_grid_desc {
+    int32_t nx, ny, nz;          /* cells per axis: each even, >= 8, of the form 2^a 3^b 5^c */
+    double lx, ly, lz;           /* box lengths [m]; h_j = l_j / n_j */
+    double nu;                   /* kinematic viscosity [m^2/s] */
+    double alpha_c;              /* scalar diffusivity [m^2/s]; < 0 -> nu */
+    double dt;                   /* fixed time step [s], > 0 */
+    double tau_f;                /* forcing relaxation time [s]; <= 0 -> dt */
+    double body_force[3];        /* b [m/s^2] */
+    int32_t n_pressure_iters;    /* iterations of Eq. 9 per step (paper: 4); grids without solid cells use 1,
+                                    which gives the same result because (1 - beta) G p vanishes */
+    int32_t filter;              /* 1: apply the Eq. 6 filter after the projection; 0: skip it */
+    int32_t precision;           /* vf_precision */
+    int32_t history_capacity;    /* number of per-step reduction records kept on the device (ring buffer) */
+    void* cuda_stream;           /* cudaStream_t the grid works on; NULL -> a stream the grid creates */
+    const vf_allocator* alloc;   /* NULL -> cudaMallocAsync */
+} vf_grid_desc;
+
+/* FP64 reductions of one state (Sec. 3.3 diagnostics).  dV = hx*hy*hz.  Room cells are those flagged by
+ * vf_set_region (default: all fluid cells). */
+typedef struct vf_reduce {
+    double t;                    /* simulated time of the state [s] */
+    int64_t step;                /* steps taken to reach it */
+    double ke;                   /* 1/2 sum dV |u|^2 */
+    double div_max;              /* max |D u| */
+    double div_l2;               /* sqrt(sum dV (D u)^2) */
+    double u_max;                /* max over cells and components of |u_i| */
+    double c_total;              /* sum dV c over all cells */
+    double c_room;               /* sum dV c over room cells */
+    double c2_room;              /* sum dV c^2 over room cells */
+    double v_room;               /* sum dV over room cells */
+    int64_t hist[64];            /* room cells with c in [b/64, (b+1)/64) (c == 1 in bin 63) */
+    int64_t hist_under;          /* room cells with c < 0 */
+    int64_t hist_over;           /* room cells with c > 1 */
+} vf_reduce;
+
+typedef struct vf_grid vf_grid;
+
+/* ---- grid lifecycle ------------------------------------------------------------------------------------- */
+
+/* Fill *d with defaults: 64^3 unit box, nu = 1.6e-5, alpha_c = nu, dt = 1e-3, tau_f = dt, no body force,
+ * 4 pressure iterations, filter on, FP32_MIXED, 4096 history records, own stream, default allocator. */
+int vf_grid_desc_default(vf_grid_desc* d);
+
+/* Validate *d, allocate every device buffer of the grid on the current CUDA device, build the FFT twiddle and
+ * eigenvalue tables (Sec. 2.2) and zero all fields.  The mask starts as all-fluid with no forcing region; the
+ * grid is ready to step once vf_set_mask has been called.  *out receives the handle (NULL on failure). */
+int vf_create_grid(const vf_grid_desc* d, vf_grid** out);
+
+/* Release everything the grid owns (waits for its stream first).  NULL is accepted. */
+int vf_destroy(vf_grid* g);
+
+/* ---- inputs (Sec. 2.1: beta, S, u_set, c_set; Sec. 3.3: the room region) ----------------------------------- */
+
+/* beta: nx*ny*nz bytes in `mem`, nonzero = fluid, 0 = solid.  Fields are re-masked (set to zero in solids). */
+int vf_set_mask(vf_grid* g, const uint8_t* beta, int mem);
+
+/* S: nx*ny*nz bytes, nonzero = forcing region (cells outside the fluid are ignored); u_set[3] and c_set are the
+ * targets of the relaxation terms S (u_set - u) / tau_f and S (c_set - c) / tau_f (Eqs. 2-3).  S may be NULL to
+ * keep the current region and only change the set point. */
+int vf_set_inflow(vf_grid* g, const uint8_t* S, const double u_set[3], double c_set, int mem);
+
+/* room: nx*ny*nz bytes, nonzero = counted in c_room, c2_room, v_room and the histogram. */
+int vf_set_region(vf_grid* g, const uint8_t* room, int mem);
+
+/* Overwrite one field from nx*ny*nz values (double if is_fp64, else float) in `mem`.  VF_P takes the pressure
+ * divided by density p/rho (the warm start of the next pressure solve); u, v, w, c are multiplied by beta on the
+ * way in. */
+int vf_set_field(vf_grid* g, int field, const void* src, int is_fp64, int mem);
+
+/* Set the simulated time and step counter of the current state (used when restoring a saved state). */
+int vf_set_time(vf_grid* g, double t, int64_t step);
+
+/* ---- stepping -------------------------------------------------------------------------------------------- */
+
+/* Enqueue n time steps on the grid's stream and return without waiting.  Every `reduce_every`-th step (counted
+ * from step 0; 0 = never) also records the reductions of the new state into the device history.  Steps replay a
+ * captured CUDA graph of one step unless the environment variable VF_NO_GRAPH is set. */
+int vf_step(vf_grid* g, int64_t n, int32_t reduce_every);
+
+/* Wait for all work enqueued on the grid. */
+int vf_sync(vf_grid* g);
+
+/* ---- outputs --------------------------------------------------------------------------------------------- */
+
+/* Copy one field (nx*ny*nz values, double if as_fp64 else float) into dst in `mem`, after all enqueued steps.
+ * VF_P is the pressure divided by density, p/rho [m^2/s^2]; the library stores exactly this value, so reading
+ * and writing it back restores the state bit for bit. */
+int vf_read_field(vf_grid* g, int field, void* dst, int as_fp64, int mem);
+
+/* Compute the reductions of the current state (waits).  Returns VF_ENONFINITE if a field holds NaN/Inf. */
+int vf_reductions(vf_grid* g, vf_reduce* out);
+
+/* Copy the per-step reduction records taken by vf_step (oldest first, at most max_records of the most recent)
+ * into out[]; *count receives the number copied.  Waits for enqueued steps. */
+int vf_history(vf_grid* g, vf_reduce* out, int64_t max_records, int64_t* count);
+
+/* Forget the recorded history. */
+int vf_clear_history(vf_grid* g);
+
+/* Simulated time, step count, cell count and bytes of device memory held by the grid. */
+int vf_info(const vf_grid* g, double* t, int64_t* step, int64_t* cells, int64_t* device_bytes);
+
+/* Solve L p = f once with the grid's FFT Poisson solver (Sec. 2.2, one pass of steps a6-a8): forward 3D FFT,
+ * division by lambda (null modes -> 0), inverse 3D FFT.  f and p are device arrays of nx*ny*nz values in the
+ * grid's precision (double for VF_FP64, float otherwise); they may alias.  Uses the grid's spectrum buffer as
+ * scratch; stream-ordered on the grid's stream, returns without waiting. */
+int vf_poisson_solve(vf_grid* g, const void* f, void* p);
+
+/* ---- measurement ----------------------------------------------------------------------------------------- */
+
+/* Kernel phases of one step, in launch order. */
+#define VF_PHASE_STAGE1 0       /* RK4 stage 1: k1, acc = q + dt/6 k1, q2 = q + dt/2 k1 */
+#define VF_PHASE_STAGE2 1       /* RK4 stage 2 */
+#define VF_PHASE_STAGE3 2       /* RK4 stage 3 */
+#define VF_PHASE_STAGE4 3       /* RK4 stage 4: q* = acc + dt/6 k4 */
+#define VF_PHASE_DIV 4          /* r = D u* / dt */
+#define VF_PHASE_FFT_X_FWD 5    /* Eq. 9 right-hand side + real-to-complex FFT along x */
+#define VF_PHASE_FFT_Y_FWD 6    /* FFT along y */
+#define VF_PHASE_FFT_Z_SOLVE 7  /* FFT along z, division by lambda, inverse FFT along z */
+#define VF_PHASE_FFT_Y_INV 8    /* inverse FFT along y */
+#define VF_PHASE_FFT_X_INV 9    /* complex-to-real inverse FFT along x -> p */
+#define VF_PHASE_PROJECT 10     /* u = beta (u* - dt G p) */
+#define VF_PHASE_FILTER 11      /* Eq. 6 filter */
+#define VF_PHASE_REDUCE 12      /* FP64 reductions (partials + final) */
+#define VF_N_PHASES 13
+
+/* Run n steps like vf_step but with direct launches bracketed by CUDA events on the grid's stream; adds the
+ * elapsed milliseconds of every phase to phase_ms[VF_N_PHASES] and its launch count to launches[VF_N_PHASES]
+ * (both caller-owned, not cleared).  Waits for completion. */
+int vf_profile_steps(vf_grid* g, int64_t n, int32_t reduce_every, double* phase_ms, int64_t* launches);
+
+/* Name of a phase id ("stage1", "fft_z_solve", ...), or "unknown". */
+const char* vf_phase_name(int phase);
+
+/* ---- status ---------------------------------------------------------------------------------------------- */
+
+const char* vf_status_string(int status);
+const char* vf_last_error(const vf_grid* g);
+
+/* ---- host-side ventilation metrics (Sec. 3.3.2, 3.4), from a reduction series -------------------------------- */
+
+/* ACH [1/h] from the least-squares slope of ln c(t) (fresh air c = 0): ACH = -3600 d ln c / dt, t in seconds. */
+int vf_ach_log_slope(const double* t_seconds, const double* c_mean, int64_t n, double* ach_per_hour);
+
+/* Three-parameter fit c(t) = C0 exp(-ACH t) + C1 (Sec. 3.3.2): ACH [1/h], C0, C1. */
+int vf_ach_fit3(const double* t_seconds, const double* c_mean, int64_t n, double* ach_per_hour, double* c0,
+                double* c1);
+
+/* Time-dependent Wells-Riley (Eqs. 17-18): dose Q(t) = (C0 p / ACH)(1 - exp(-ACH t)) and P = 1 - exp(-Q).
+ * c0 [quanta/m^3], breathing p [m^3/h], ach [1/h] (0 allowed), t [h]. */
+int vf_wells_riley(double c0, double breathing_m3_h, double ach_per_hour, double t_hours, double* dose,
+                   double* probability);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VENTFLOW_H */

@@ -1,0 +1,803 @@
+// Step engine and C ABI of the ventilation-flow library (declared in include/ventflow.h).
+//
+// A grid owns every device buffer of one room: the state q = (u, v, w, c), two RK4 stage states and the RK4
+// accumulator, the pressure p / rho (kept between steps as the warm start of Eq. 9; the paper's p carries a factor
+// dt, so the solver works on D u* / dt and the projection subtracts dt G p), the divergence r, the half
+// spectrum, a staging buffer for host/device transfers, the packed mask and the FFT tables.  A step is a fixed
+// sequence of kernel launches on the grid's stream; it is captured once into a CUDA graph and replayed.
+#include <cuda_runtime_api.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "vf_internal.h"
+
+using vf::FftAxis;
+using vf::FlowConsts;
+using vf::Kernels;
+using vf::PoissonArgs;
+using vf::StageArgs;
+
+struct vf_grid {
+    vf_grid_desc d{};
+    bool fp64 = false;
+    size_t N = 0, esz = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cudaStream_t cap_stream = nullptr;
+    vf_allocator alloc{};
+    bool have_alloc = false;
+    std::vector<void*> allocs;
+    size_t bytes = 0;
+    int alloc_count = 0;
+    int fail_alloc_at = 0;       // fault injection: the n-th allocation of this grid fails (0 = off)
+
+    void* q[4]{};
+    void* acc[4]{};
+    void* qa[4]{};
+    void* qb[4]{};
+    void* p = nullptr;
+    void* r = nullptr;
+    void* spec = nullptr;
+    void* staging = nullptr;     // N * 8 bytes
+    uint8_t* mask = nullptr;
+    void* twx = nullptr;
+    void* twy = nullptr;
+    void* twz = nullptr;
+    void* twr = nullptr;
+    void* lamx = nullptr;
+    void* lamy = nullptr;
+    void* lamz = nullptr;
+
+    double* red_partial = nullptr;
+    int* hist_partial = nullptr;
+    vf_reduce* red_out = nullptr;
+    vf_reduce* history = nullptr;
+    long long* dev_counters = nullptr;   // [0] history count, [1] step counter
+    int* nonfinite = nullptr;
+    unsigned long long* solid_count = nullptr;
+    int nred = 0;
+
+    FftAxis ax{}, ay{}, az{};
+    int rows_per_block = 1, cols_per_block = 16;
+
+    cudaGraphExec_t gexec[2]{nullptr, nullptr};
+    bool graph_ok = false;
+    bool use_graph = true;
+
+    int status = VF_OK;
+    std::string err;
+    bool mask_set = false;
+    bool has_solid = false;
+    double uset[3]{0, 0, 0};
+    double cset = 0;
+    int64_t step = 0;
+    double t0 = 0;
+};
+
+namespace {
+
+const char* kStatusNames[] = {"VF_OK", "VF_EINVAL", "VF_ESIZE", "VF_ENOMEM", "VF_ECUDA", "VF_ESTATE",
+                              "VF_ENONFINITE", "VF_ETIMEOUT"};
+
+int set_err(vf_grid* g, int code, const std::string& msg)
+{
+    if (g) g->err = msg;
+    return code;
+}
+
+int fail_cuda(vf_grid* g, cudaError_t e, const char* what)
+{
+    if (g) {
+        g->status = VF_ECUDA;
+        g->err = std::string(what) + ": " + cudaGetErrorString(e);
+    }
+    return VF_ECUDA;
+}
+
+#define VF_CK(call)                                                  \
+    do {                                                             \
+        cudaError_t e_ = (call);                                     \
+        if (e_ != cudaSuccess) return fail_cuda(g, e_, #call);       \
+    } while (0)
+
+bool smooth235_even(int n)
+{
+    if (n < 8 || n % 2) return false;
+    for (int p : {2, 3, 5})
+        while (n % p == 0) n /= p;
+    return n == 1;
+}
+
+// Radix schedule: powers of two in as many radix-8 passes as possible (a remainder of 2 becomes 4 x 4 or a 4),
+// then the factors 3 and 5.
+FftAxis make_axis(int n)
+{
+    FftAxis a{};
+    a.n = n;
+    int m = n, twos = 0;
+    while (m % 2 == 0) { m /= 2; ++twos; }
+    int eights = twos / 3, rem = twos % 3;
+    std::vector<int> rad;
+    if (rem == 1 && eights > 0) { --eights; rad.push_back(4); rad.push_back(4); }
+    else if (rem == 1) rad.push_back(2);
+    else if (rem == 2) rad.push_back(4);
+    for (int i = 0; i < eights; ++i) rad.push_back(8);
+    while (m % 3 == 0) { m /= 3; rad.push_back(3); }
+    while (m % 5 == 0) { m /= 5; rad.push_back(5); }
+    a.nstages = (int)rad.size();
+    for (int i = 0; i < a.nstages && i < vf::kMaxRadixStages; ++i) a.radix[i] = rad[i];
+    return a;
+}
+
+void* galloc(vf_grid* g, size_t bytes)
+{
+    ++g->alloc_count;
+    if (g->fail_alloc_at > 0 && g->alloc_count == g->fail_alloc_at) return nullptr;
+    void* p = nullptr;
+    bytes = (bytes + 255) & ~(size_t)255;
+    if (g->have_alloc) {
+        p = g->alloc.alloc(bytes, (void*)g->stream, g->alloc.ctx);
+    } else if (cudaMallocAsync(&p, bytes, g->stream) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    if (p) {
+        g->allocs.push_back(p);
+        g->bytes += bytes;
+        if (cudaMemsetAsync(p, 0, bytes, g->stream) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+    }
+    return p;
+}
+
+void release_all(vf_grid* g)
+{
+    for (int i = 0; i < 2; ++i)
+        if (g->gexec[i]) { cudaGraphExecDestroy(g->gexec[i]); g->gexec[i] = nullptr; }
+    g->graph_ok = false;
+    for (void* p : g->allocs) {
+        if (g->have_alloc) g->alloc.free(p, (void*)g->stream, g->alloc.ctx);
+        else cudaFreeAsync(p, g->stream);
+    }
+    g->allocs.clear();
+    if (g->stream) cudaStreamSynchronize(g->stream);
+}
+
+template <typename T>
+FlowConsts<T> flow_consts(const vf_grid* g)
+{
+    FlowConsts<T> k{};
+    const vf_grid_desc& d = g->d;
+    k.nx = d.nx; k.ny = d.ny; k.nz = d.nz;
+    const double h[3] = {d.lx / d.nx, d.ly / d.ny, d.lz / d.nz};
+    for (int j = 0; j < 3; ++j) {
+        k.i2h[j] = (T)(1.0 / (2.0 * h[j]));
+        k.i2h_div[j] = (T)(1.0 / (2.0 * h[j] * d.dt));
+        k.i2h_dt[j] = (T)(d.dt / (2.0 * h[j]));
+        k.q4h[j] = (T)(1.0 / (4.0 * h[j]));
+        k.ih[j] = (T)(1.0 / h[j]);
+        k.ih2[j] = (T)(1.0 / (h[j] * h[j]));
+        k.bf[j] = (T)d.body_force[j];
+        k.uset[j] = (T)g->uset[j];
+    }
+    const double tau = d.tau_f > 0 ? d.tau_f : d.dt;
+    k.nu = (T)d.nu;
+    k.alpha = (T)(d.alpha_c < 0 ? d.nu : d.alpha_c);
+    k.inv_tau = (T)(1.0 / tau);
+    k.dt = (T)d.dt;
+    k.dt2 = (T)(d.dt / 2.0);
+    k.dt3 = (T)(d.dt / 3.0);
+    k.dt6 = (T)(d.dt / 6.0);
+    k.cset = (T)g->cset;
+    k.filt = (T)(1.0 / std::pow(M_PI, 6));
+    return k;
+}
+
+template <typename T>
+PoissonArgs<T> poisson_args(const vf_grid* g, const T* r, T* p, int use_mask)
+{
+    PoissonArgs<T> a{};
+    const vf_grid_desc& d = g->d;
+    a.nx = d.nx; a.ny = d.ny; a.nz = d.nz; a.M = d.nx / 2;
+    a.r = r; a.p = p; a.mask = g->mask; a.use_mask = use_mask;
+    a.spec = g->spec;
+    a.twx = g->twx; a.twy = g->twy; a.twz = g->twz; a.twr = g->twr;
+    a.lamx = (const T*)g->lamx; a.lamy = (const T*)g->lamy; a.lamz = (const T*)g->lamz;
+    const double h[3] = {d.lx / d.nx, d.ly / d.ny, d.lz / d.nz};
+    for (int j = 0; j < 3; ++j) a.i2h2[j] = (T)(1.0 / (4.0 * h[j] * h[j]));
+    a.invN = (T)(1.0 / ((double)d.nx * d.ny * d.nz));
+    a.ax = g->ax; a.ay = g->ay; a.az = g->az;
+    a.rows_per_block = g->rows_per_block;
+    a.cols_per_block = g->cols_per_block;
+    return a;
+}
+
+vf::ReduceArgsDev reduce_args(const vf_grid* g)
+{
+    vf::ReduceArgsDev r{};
+    r.partial = g->red_partial;
+    r.hist_partial = g->hist_partial;
+    r.out = g->red_out;
+    r.history = g->history;
+    r.hist_count = g->dev_counters;
+    r.step_counter = g->dev_counters + 1;
+    r.nonfinite = g->nonfinite;
+    r.history_capacity = g->d.history_capacity;
+    r.dV = (g->d.lx / g->d.nx) * (g->d.ly / g->d.ny) * (g->d.lz / g->d.nz);
+    r.dt = g->d.dt;
+    r.t0 = g->t0;
+    return r;
+}
+
+int pressure_iters(const vf_grid* g)
+{
+    if (g->d.n_pressure_iters <= 0) return 0;
+    return g->has_solid ? g->d.n_pressure_iters : 1;
+}
+
+template <typename T>
+cudaError_t enqueue_step_t(vf_grid* g, cudaStream_t st, bool with_reduce, const vf::LaunchHook* hook)
+{
+    auto mark = [&](int phase) { if (hook) (*hook)(phase); };
+    const FlowConsts<T> k = flow_consts<T>(g);
+    T* q[4];
+    T* acc[4];
+    T* qa[4];
+    T* qb[4];
+    for (int f = 0; f < 4; ++f) {
+        q[f] = (T*)g->q[f]; acc[f] = (T*)g->acc[f]; qa[f] = (T*)g->qa[f]; qb[f] = (T*)g->qb[f];
+    }
+    StageArgs<T> a{};
+    a.mask = g->mask;
+    auto set = [&](T* const* qs, T* const* out) {
+        for (int f = 0; f < 4; ++f) { a.qs[f] = qs[f]; a.qn[f] = q[f]; a.acc[f] = acc[f]; a.out[f] = out[f]; }
+    };
+    cudaError_t e;
+    set(q, qa);
+    if ((e = Kernels<T>::stage(1, a, k, st)) != cudaSuccess) return e;
+    mark(VF_PHASE_STAGE1);
+    set(qa, qb);
+    if ((e = Kernels<T>::stage(2, a, k, st)) != cudaSuccess) return e;
+    mark(VF_PHASE_STAGE2);
+    set(qb, qa);
+    if ((e = Kernels<T>::stage(3, a, k, st)) != cudaSuccess) return e;
+    mark(VF_PHASE_STAGE3);
+    set(qa, qb);
+    if ((e = Kernels<T>::stage(4, a, k, st)) != cudaSuccess) return e;
+    mark(VF_PHASE_STAGE4);
+    const int iters = pressure_iters(g);
+    if (iters > 0) {
+        if ((e = Kernels<T>::divergence(qb[0], qb[1], qb[2], (T*)g->r, k, st)) != cudaSuccess) return e;
+        mark(VF_PHASE_DIV);
+        const PoissonArgs<T> pa = poisson_args<T>(g, (const T*)g->r, (T*)g->p, g->has_solid ? 1 : 0);
+        for (int it = 0; it < iters; ++it)
+            if ((e = Kernels<T>::poisson_iteration(pa, st, hook)) != cudaSuccess) return e;
+    }
+    const T* us[3] = {qb[0], qb[1], qb[2]};
+    long long* step_counter = g->dev_counters + 1;
+    if (g->d.filter) {
+        T* out[4] = {acc[0], acc[1], acc[2], qb[3]};
+        if ((e = Kernels<T>::project(us, qb[3], (const T*)g->p, out, g->mask, step_counter, k, st)) != cudaSuccess)
+            return e;
+        mark(VF_PHASE_PROJECT);
+        const T* in[4] = {acc[0], acc[1], acc[2], qb[3]};
+        if ((e = Kernels<T>::filter(in, q, g->mask, k, st)) != cudaSuccess) return e;
+        mark(VF_PHASE_FILTER);
+    } else {
+        if ((e = Kernels<T>::project(us, qb[3], (const T*)g->p, q, g->mask, step_counter, k, st)) != cudaSuccess)
+            return e;
+        mark(VF_PHASE_PROJECT);
+    }
+    if (with_reduce) {
+        const T* qq[4] = {q[0], q[1], q[2], q[3]};
+        if ((e = Kernels<T>::reduce(qq, g->mask, k, reduce_args(g), 1, st)) != cudaSuccess) return e;
+        mark(VF_PHASE_REDUCE);
+    }
+    return cudaSuccess;
+}
+
+cudaError_t enqueue_step(vf_grid* g, cudaStream_t st, bool with_reduce, const vf::LaunchHook* hook = nullptr)
+{
+    return g->fp64 ? enqueue_step_t<double>(g, st, with_reduce, hook)
+                   : enqueue_step_t<float>(g, st, with_reduce, hook);
+}
+
+// Event recorder behind vf_profile_steps: one event after every launch, tagged with its phase.
+struct PhaseRecorder {
+    cudaStream_t stream;
+    std::vector<cudaEvent_t> events;
+    std::vector<int> phases;
+    cudaError_t err = cudaSuccess;
+    static void hook(void* ctx, int phase)
+    {
+        PhaseRecorder* r = (PhaseRecorder*)ctx;
+        cudaEvent_t ev;
+        cudaError_t e = cudaEventCreate(&ev);
+        if (e == cudaSuccess) e = cudaEventRecord(ev, r->stream);
+        if (e != cudaSuccess) { r->err = e; return; }
+        r->events.push_back(ev);
+        r->phases.push_back(phase);
+    }
+};
+
+void drop_graphs(vf_grid* g)
+{
+    for (int i = 0; i < 2; ++i)
+        if (g->gexec[i]) { cudaGraphExecDestroy(g->gexec[i]); g->gexec[i] = nullptr; }
+    g->graph_ok = false;
+}
+
+int capture_graphs(vf_grid* g)
+{
+    drop_graphs(g);
+    for (int i = 0; i < 2; ++i) {
+        cudaGraph_t graph = nullptr;
+        VF_CK(cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeRelaxed));
+        cudaError_t e = enqueue_step(g, g->cap_stream, i == 1);
+        cudaError_t e2 = cudaStreamEndCapture(g->cap_stream, &graph);
+        if (e != cudaSuccess) { if (graph) cudaGraphDestroy(graph); return fail_cuda(g, e, "capture step"); }
+        if (e2 != cudaSuccess) return fail_cuda(g, e2, "cudaStreamEndCapture");
+        e = cudaGraphInstantiate(&g->gexec[i], graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return fail_cuda(g, e, "cudaGraphInstantiate");
+    }
+    g->graph_ok = true;
+    return VF_OK;
+}
+
+template <typename T>
+int build_tables_t(vf_grid* g)
+{
+    const vf_grid_desc& d = g->d;
+    const int M = d.nx / 2;
+    struct C2 { T x, y; };
+    auto roots = [](int n, int count) {
+        std::vector<C2> t(count);
+        for (int m = 0; m < count; ++m) {
+            const double a = 2.0 * M_PI * (double)m / (double)n;
+            t[m].x = (T)std::cos(a);
+            t[m].y = (T)(-std::sin(a));
+        }
+        return t;
+    };
+    auto lam = [](int n, int count, double h) {
+        std::vector<T> t(count);
+        for (int k = 0; k < count; ++k) {
+            const double s = (k == 0 || 2 * k == n) ? 0.0 : std::sin(2.0 * M_PI * (double)k / (double)n);
+            t[k] = (T)(s * s / (h * h));
+        }
+        return t;
+    };
+    const std::vector<C2> tx = roots(M, M), ty = roots(d.ny, d.ny), tz = roots(d.nz, d.nz), tr = roots(d.nx, M + 1);
+    const std::vector<T> lx = lam(d.nx, M, d.lx / d.nx), ly = lam(d.ny, d.ny, d.ly / d.ny),
+                         lz = lam(d.nz, d.nz, d.lz / d.nz);
+    struct Up { void** dst; const void* src; size_t bytes; };
+    const Up ups[] = {{&g->twx, tx.data(), tx.size() * sizeof(C2)}, {&g->twy, ty.data(), ty.size() * sizeof(C2)},
+                      {&g->twz, tz.data(), tz.size() * sizeof(C2)}, {&g->twr, tr.data(), tr.size() * sizeof(C2)},
+                      {&g->lamx, lx.data(), lx.size() * sizeof(T)}, {&g->lamy, ly.data(), ly.size() * sizeof(T)},
+                      {&g->lamz, lz.data(), lz.size() * sizeof(T)}};
+    for (const Up& u : ups) {
+        *u.dst = galloc(g, u.bytes);
+        if (!*u.dst) return set_err(g, VF_ENOMEM, "table allocation failed");
+        VF_CK(cudaMemcpyAsync(*u.dst, u.src, u.bytes, cudaMemcpyHostToDevice, g->stream));
+    }
+    VF_CK(cudaStreamSynchronize(g->stream));   // host vectors die here
+    const PoissonArgs<T> pa = poisson_args<T>(g, nullptr, nullptr, 0);
+    VF_CK(Kernels<T>::poisson_prepare(pa));
+    return VF_OK;
+}
+
+int check(const vf_grid* g)
+{
+    if (!g) return VF_EINVAL;
+    return g->status;
+}
+
+// Copy `bytes` from the caller (host or device) into device memory the grid can read, returning the pointer.
+const void* stage_input(vf_grid* g, const void* src, size_t bytes, int mem, int* rc)
+{
+    *rc = VF_OK;
+    if (mem == VF_DEVICE) return src;
+    cudaError_t e = cudaMemcpyAsync(g->staging, src, bytes, cudaMemcpyHostToDevice, g->stream);
+    if (e != cudaSuccess) { *rc = fail_cuda(g, e, "cudaMemcpyAsync(staging)"); return nullptr; }
+    return g->staging;
+}
+
+template <typename T>
+cudaError_t mask_fields(vf_grid* g)
+{
+    for (int f = 0; f < 4; ++f) {
+        cudaError_t e = Kernels<T>::apply_mask((T*)g->q[f], g->mask, g->N, g->stream);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" {
+
+int vf_grid_desc_default(vf_grid_desc* d)
+{
+    if (!d) return VF_EINVAL;
+    std::memset(d, 0, sizeof(*d));
+    d->nx = d->ny = d->nz = 64;
+    d->lx = d->ly = d->lz = 1.0;
+    d->nu = 1.6e-5;
+    d->alpha_c = -1.0;
+    d->dt = 1e-3;
+    d->tau_f = 0.0;
+    d->n_pressure_iters = 4;
+    d->filter = 1;
+    d->precision = VF_FP32_MIXED;
+    d->history_capacity = 4096;
+    d->cuda_stream = nullptr;
+    d->alloc = nullptr;
+    return VF_OK;
+}
+
+int vf_create_grid(const vf_grid_desc* d, vf_grid** out)
+{
+    if (!d || !out) return VF_EINVAL;
+    *out = nullptr;
+    if (!smooth235_even(d->nx) || !smooth235_even(d->ny) || !smooth235_even(d->nz)) return VF_ESIZE;
+    if (!(d->lx > 0) || !(d->ly > 0) || !(d->lz > 0) || !(d->dt > 0) || !(d->nu >= 0)) return VF_EINVAL;
+    if (d->precision != VF_FP64 && d->precision != VF_FP32_MIXED) return VF_EINVAL;
+    if (d->n_pressure_iters < 0 || d->history_capacity < 1) return VF_EINVAL;
+    if ((long long)d->nx * d->ny * d->nz > (1LL << 31)) return VF_ESIZE;
+
+    vf_grid* g = new vf_grid();
+    g->d = *d;
+    g->fp64 = d->precision == VF_FP64;
+    g->esz = g->fp64 ? 8 : 4;
+    g->N = (size_t)d->nx * d->ny * d->nz;
+    if (d->alloc) { g->alloc = *d->alloc; g->have_alloc = g->alloc.alloc && g->alloc.free; }
+    if (const char* s = std::getenv("VF_FAULT_ALLOC_AT")) g->fail_alloc_at = std::atoi(s);
+    if (std::getenv("VF_NO_GRAPH")) g->use_graph = false;
+
+    auto fail = [&](int code) {
+        release_all(g);
+        if (g->own_stream && g->stream) cudaStreamDestroy(g->stream);
+        if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
+        delete g;
+        return code;
+    };
+    if (d->cuda_stream) {
+        g->stream = (cudaStream_t)d->cuda_stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking) != cudaSuccess) return fail(VF_ECUDA);
+        g->own_stream = true;
+    }
+    if (cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking) != cudaSuccess) return fail(VF_ECUDA);
+
+    const int M = d->nx / 2;
+    {
+        // every FFT pass keeps two tiles of its batch in shared memory (at most 227 KB per CTA)
+        const size_t cplx = g->fp64 ? 16 : 8, tb = g->fp64 ? 8 : 16, limit = 227 * 1024;
+        if (2 * tb * (size_t)std::max(d->ny, d->nz) * cplx > limit || 2 * (size_t)M * cplx > limit)
+            return fail(VF_ESIZE);
+    }
+    g->ax = make_axis(M);
+    g->ay = make_axis(d->ny);
+    g->az = make_axis(d->nz);
+    const int target = g->fp64 ? 1024 : 2048;   // complex values per CTA in the x passes
+    g->rows_per_block = std::max(1, target / M);
+    g->cols_per_block = g->fp64 ? 8 : 16;
+
+    const size_t fb = g->N * g->esz;
+    void** fields[] = {&g->q[0], &g->q[1], &g->q[2], &g->q[3], &g->acc[0], &g->acc[1], &g->acc[2], &g->acc[3],
+                       &g->qa[0], &g->qa[1], &g->qa[2], &g->qa[3], &g->qb[0], &g->qb[1], &g->qb[2], &g->qb[3],
+                       &g->p, &g->r, &g->spec};
+    for (void** f : fields)
+        if (!(*f = galloc(g, fb))) return fail(VF_ENOMEM);
+    if (!(g->staging = galloc(g, g->N * 8))) return fail(VF_ENOMEM);
+    if (!(g->mask = (uint8_t*)galloc(g, g->N))) return fail(VF_ENOMEM);
+
+    const FlowConsts<float> kf = flow_consts<float>(g);
+    g->nred = Kernels<float>::reduce_blocks(kf);
+    if (!(g->red_partial = (double*)galloc(g, (size_t)g->nred * vf::kRedSlots * sizeof(double)))) return fail(VF_ENOMEM);
+    if (!(g->hist_partial = (int*)galloc(g, (size_t)g->nred * (vf::kHistBins + 2) * sizeof(int)))) return fail(VF_ENOMEM);
+    if (!(g->red_out = (vf_reduce*)galloc(g, sizeof(vf_reduce)))) return fail(VF_ENOMEM);
+    if (!(g->history = (vf_reduce*)galloc(g, (size_t)d->history_capacity * sizeof(vf_reduce)))) return fail(VF_ENOMEM);
+    if (!(g->dev_counters = (long long*)galloc(g, 2 * sizeof(long long)))) return fail(VF_ENOMEM);
+    if (!(g->nonfinite = (int*)galloc(g, sizeof(int)))) return fail(VF_ENOMEM);
+    if (!(g->solid_count = (unsigned long long*)galloc(g, sizeof(unsigned long long)))) return fail(VF_ENOMEM);
+
+    int rc = g->fp64 ? build_tables_t<double>(g) : build_tables_t<float>(g);
+    if (rc != VF_OK) return fail(rc == VF_ECUDA ? VF_ECUDA : rc);
+    // all-fluid mask, every cell in the room region
+    if (vf::mask_fill(g->mask, vf::kBitBeta | vf::kBitRoom, g->N, g->stream) != cudaSuccess) return fail(VF_ECUDA);
+    if (cudaStreamSynchronize(g->stream) != cudaSuccess) return fail(VF_ECUDA);
+    *out = g;
+    return VF_OK;
+}
+
+int vf_destroy(vf_grid* g)
+{
+    if (!g) return VF_OK;
+    if (g->stream) cudaStreamSynchronize(g->stream);
+    release_all(g);
+    if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
+    if (g->own_stream && g->stream) cudaStreamDestroy(g->stream);
+    delete g;
+    return VF_OK;
+}
+
+int vf_set_mask(vf_grid* g, const uint8_t* beta, int mem)
+{
+    int rc = check(g);
+    if (rc) return rc;
+    if (!beta || (mem != VF_HOST && mem != VF_DEVICE)) return set_err(g, VF_EINVAL, "vf_set_mask: bad argument");
+    const void* src = stage_input(g, beta, g->N, mem, &rc);
+    if (rc) return rc;
+    VF_CK(vf::mask_merge(g->mask, (const uint8_t*)src, vf::kBitBeta, g->N, g->stream));
+    VF_CK(g->fp64 ? mask_fields<double>(g) : mask_fields<float>(g));
+    VF_CK(vf::mask_count_solid(g->mask, g->N, g->solid_count, g->stream));
+    unsigned long long solids = 0;
+    VF_CK(cudaMemcpyAsync(&solids, g->solid_count, sizeof(solids), cudaMemcpyDeviceToHost, g->stream));
+    VF_CK(cudaStreamSynchronize(g->stream));
+    g->has_solid = solids > 0;
+    g->mask_set = true;
+    drop_graphs(g);
+    return VF_OK;
+}
+
+int vf_set_inflow(vf_grid* g, const uint8_t* S, const double u_set[3], double c_set, int mem)
+{
+    int rc = check(g);
+    if (rc) return rc;
+    if (!u_set || (mem != VF_HOST && mem != VF_DEVICE)) return set_err(g, VF_EINVAL, "vf_set_inflow: bad argument");
+    if (S) {
+        const void* src = stage_input(g, S, g->N, mem, &rc);
+        if (rc) return rc;
+        VF_CK(vf::mask_merge(g->mask, (const uint8_t*)src, vf::kBitS, g->N, g->stream));
+        VF_CK(cudaStreamSynchronize(g->stream));
+    }
+    for (int j = 0; j < 3; ++j) g->uset[j] = u_set[j];
+    g->cset = c_set;
+    drop_graphs(g);
+    return VF_OK;
+}
+
+int vf_set_region(vf_grid* g, const uint8_t* room, int mem)
+{
+    int rc = check(g);
+    if (rc) return rc;
+    if (!room || (mem != VF_HOST && mem != VF_DEVICE)) return set_err(g, VF_EINVAL, "vf_set_region: bad argument");
+    const void* src = stage_input(g, room, g->N, mem, &rc);
+    if (rc) return rc;
+    VF_CK(vf::mask_merge(g->mask, (const uint8_t*)src, vf::kBitRoom, g->N, g->stream));
+    VF_CK(cudaStreamSynchronize(g->stream));
+    return VF_OK;
+}
+
+int vf_set_field(vf_grid* g, int field, const void* src, int is_fp64, int mem)
+{
+    int rc = check(g);
+    if (rc) return rc;
+    if (!src || field < VF_U || field > VF_P || (mem != VF_HOST && mem != VF_DEVICE))
+        return set_err(g, VF_EINVAL, "vf_set_field: bad argument");
+    const size_t bytes = g->N * (is_fp64 ? 8 : 4);
+    const void* dsrc = stage_input(g, src, bytes, mem, &rc);
+    if (rc) return rc;
+    void* dst = field == VF_P ? g->p : g->q[field];
+    const double scale = 1.0;
+    const uint8_t* mask = field == VF_P ? nullptr : g->mask;
+    if (g->fp64) VF_CK(Kernels<double>::convert_in(dsrc, is_fp64, (double*)dst, g->N, scale, mask, g->stream));
+    else VF_CK(Kernels<float>::convert_in(dsrc, is_fp64, (float*)dst, g->N, scale, mask, g->stream));
+    VF_CK(cudaStreamSynchronize(g->stream));
+    return VF_OK;
+}
+
+int vf_set_time(vf_grid* g, double t, int64_t step)
+{
+    int rc = check(g);
+    if (rc) return rc;
+    if (step < 0) return set_err(g, VF_EINVAL, "vf_set_time: negative step");
+    VF_CK(cudaStreamSynchronize(g->stream));
+    g->step = step;
+    g->t0 = t - (double)step * g->d.dt;
+    long long s = step;
+    VF_CK(cudaMemcpyAsync(g->dev_counters + 1, &s, sizeof(s), cudaMemcpyHostToDevice, g->stream));
+    VF_CK(cudaStreamSynchronize(g->stream));
+    drop_graphs(g);   // t0 is baked into the reduction launch
+    return VF_OK;
+}
+
+int vf_step(vf_grid* g, int64_t n, int32_t reduce_every)
+{
+    int rc = check(g);
+    if (rc) return rc;
+    if (n < 0 || reduce_every < 0) return set_err(g, VF_EINVAL, "vf_step: negative count");
+    if (!g->mask_set) return set_err(g, VF_ESTATE, "vf_step: call vf_set_mask first");
+    if (g->use_graph && !g->graph_ok) {
+        rc = capture_graphs(g);
+        if (rc) return rc;
+    }
+    for (int64_t i = 0; i < n; ++i) {
+        const int64_t s = g->step + 1;
+        const bool red = reduce_every > 0 && (s % reduce_every) == 0;
+        if (g->use_graph) VF_CK(cudaGraphLaunch(g->gexec[red ? 1 : 0], g->stream));
+        else VF_CK(enqueue_step(g, g->stream, red));
+        g->step = s;
+    }
+    return VF_OK;
+}
+
+int vf_sync(vf_grid* g)
+{
+    int rc = check(g);
+    if (rc) return rc;
+    VF_CK(cudaStreamSynchronize(g->stream));
+    return VF_OK;
+}
+
+int vf_read_field(vf_grid* g, int field, void* dst, int as_fp64, int mem)
+{
+    int rc = check(g);
+    if (rc) return rc;
+    if (!dst || field < VF_U || field > VF_P || (mem != VF_HOST && mem != VF_DEVICE))
+        return set_err(g, VF_EINVAL, "vf_read_field: bad argument");
+    const void* src = field == VF_P ? g->p : g->q[field];
+    const double scale = 1.0;
+    void* out = mem == VF_DEVICE ? dst : g->staging;
+    if (g->fp64) VF_CK(Kernels<double>::convert_out((const double*)src, out, as_fp64, g->N, scale, g->stream));
+    else VF_CK(Kernels<float>::convert_out((const float*)src, out, as_fp64, g->N, scale, g->stream));
+    if (mem == VF_HOST)
+        VF_CK(cudaMemcpyAsync(dst, g->staging, g->N * (as_fp64 ? 8 : 4), cudaMemcpyDeviceToHost, g->stream));
+    VF_CK(cudaStreamSynchronize(g->stream));
+    return VF_OK;
+}
+
+int vf_reductions(vf_grid* g, vf_reduce* out)
+{
+    int rc = check(g);
+    if (rc) return rc;
+    if (!out) return set_err(g, VF_EINVAL, "vf_reductions: null output");
+    const vf::ReduceArgsDev r = reduce_args(g);
+    if (g->fp64) {
+        const FlowConsts<double> k = flow_consts<double>(g);
+        const double* q[4] = {(double*)g->q[0], (double*)g->q[1], (double*)g->q[2], (double*)g->q[3]};
+        VF_CK(Kernels<double>::reduce(q, g->mask, k, r, 0, g->stream));
+    } else {
+        const FlowConsts<float> k = flow_consts<float>(g);
+        const float* q[4] = {(float*)g->q[0], (float*)g->q[1], (float*)g->q[2], (float*)g->q[3]};
+        VF_CK(Kernels<float>::reduce(q, g->mask, k, r, 0, g->stream));
+    }
+    int bad = 0;
+    VF_CK(cudaMemcpyAsync(out, g->red_out, sizeof(vf_reduce), cudaMemcpyDeviceToHost, g->stream));
+    VF_CK(cudaMemcpyAsync(&bad, g->nonfinite, sizeof(int), cudaMemcpyDeviceToHost, g->stream));
+    VF_CK(cudaStreamSynchronize(g->stream));
+    if (bad) {
+        VF_CK(cudaMemsetAsync(g->nonfinite, 0, sizeof(int), g->stream));
+        VF_CK(cudaStreamSynchronize(g->stream));
+        return set_err(g, VF_ENONFINITE, "vf_reductions: a field holds NaN or Inf");
+    }
+    return VF_OK;
+}
+
+int vf_history(vf_grid* g, vf_reduce* out, int64_t max_records, int64_t* count)
+{
+    int rc = check(g);
+    if (rc) return rc;
+    if (!count || (max_records > 0 && !out) || max_records < 0) return set_err(g, VF_EINVAL, "vf_history: bad argument");
+    long long total = 0;
+    VF_CK(cudaMemcpyAsync(&total, g->dev_counters, sizeof(total), cudaMemcpyDeviceToHost, g->stream));
+    VF_CK(cudaStreamSynchronize(g->stream));
+    const long long cap = g->d.history_capacity;
+    const long long n = std::min<long long>(std::min<long long>(total, cap), max_records);
+    const long long first = total - n;
+    long long done = 0;
+    while (done < n) {
+        const long long slot = (first + done) % cap;
+        const long long run = std::min(n - done, cap - slot);
+        VF_CK(cudaMemcpyAsync(out + done, g->history + slot, run * sizeof(vf_reduce), cudaMemcpyDeviceToHost,
+                              g->stream));
+        done += run;
+    }
+    VF_CK(cudaStreamSynchronize(g->stream));
+    *count = n;
+    return VF_OK;
+}
+
+int vf_clear_history(vf_grid* g)
+{
+    int rc = check(g);
+    if (rc) return rc;
+    VF_CK(cudaMemsetAsync(g->dev_counters, 0, sizeof(long long), g->stream));
+    VF_CK(cudaStreamSynchronize(g->stream));
+    return VF_OK;
+}
+
+int vf_info(const vf_grid* g, double* t, int64_t* step, int64_t* cells, int64_t* device_bytes)
+{
+    if (!g) return VF_EINVAL;
+    if (t) *t = g->t0 + (double)g->step * g->d.dt;
+    if (step) *step = g->step;
+    if (cells) *cells = (int64_t)g->N;
+    if (device_bytes) *device_bytes = (int64_t)g->bytes;
+    return VF_OK;
+}
+
+int vf_poisson_solve(vf_grid* g, const void* f, void* p)
+{
+    int rc = check(g);
+    if (rc) return rc;
+    if (!f || !p) return set_err(g, VF_EINVAL, "vf_poisson_solve: null pointer");
+    if (g->fp64) {
+        const PoissonArgs<double> a = poisson_args<double>(g, (const double*)f, (double*)p, 0);
+        VF_CK(Kernels<double>::poisson_iteration(a, g->stream));
+    } else {
+        const PoissonArgs<float> a = poisson_args<float>(g, (const float*)f, (float*)p, 0);
+        VF_CK(Kernels<float>::poisson_iteration(a, g->stream));
+    }
+    return VF_OK;
+}
+
+int vf_profile_steps(vf_grid* g, int64_t n, int32_t reduce_every, double* phase_ms, int64_t* launches)
+{
+    int rc = check(g);
+    if (rc) return rc;
+    if (n < 0 || reduce_every < 0 || !phase_ms || !launches) return set_err(g, VF_EINVAL, "vf_profile_steps: bad argument");
+    if (!g->mask_set) return set_err(g, VF_ESTATE, "vf_profile_steps: call vf_set_mask first");
+    for (int64_t i = 0; i < n; ++i) {
+        PhaseRecorder rec;
+        rec.stream = g->stream;
+        cudaEvent_t start;
+        VF_CK(cudaEventCreate(&start));
+        VF_CK(cudaEventRecord(start, g->stream));
+        const vf::LaunchHook hook{&PhaseRecorder::hook, &rec};
+        const int64_t s = g->step + 1;
+        const bool red = reduce_every > 0 && (s % reduce_every) == 0;
+        cudaError_t e = enqueue_step(g, g->stream, red, &hook);
+        g->step = s;
+        if (e == cudaSuccess) e = rec.err;
+        if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+        cudaEvent_t prev = start;
+        for (size_t k = 0; e == cudaSuccess && k < rec.events.size(); ++k) {
+            float ms = 0.f;
+            e = cudaEventElapsedTime(&ms, prev, rec.events[k]);
+            const int ph = rec.phases[k];
+            if (e == cudaSuccess && ph >= 0 && ph < VF_N_PHASES) {
+                phase_ms[ph] += ms;
+                launches[ph] += 1;
+            }
+            prev = rec.events[k];
+        }
+        cudaEventDestroy(start);
+        for (cudaEvent_t ev : rec.events) cudaEventDestroy(ev);
+        if (e != cudaSuccess) return fail_cuda(g, e, "vf_profile_steps");
+    }
+    return VF_OK;
+}
+
+const char* vf_phase_name(int phase)
+{
+    static const char* names[VF_N_PHASES] = {"stage1", "stage2", "stage3", "stage4", "div", "fft_x_fwd",
+                                             "fft_y_fwd", "fft_z_solve", "fft_y_inv", "fft_x_inv", "project",
+                                             "filter", "reduce"};
+    if (phase < 0 || phase >= VF_N_PHASES) return "unknown";
+    return names[phase];
+}
+
+const char* vf_status_string(int status)
+{
+    if (status > 0 || status < VF_ETIMEOUT) return "VF_UNKNOWN";
+    return kStatusNames[-status];
+}
+
+const char* vf_last_error(const vf_grid* g)
+{
+    if (!g) return "null grid";
+    return g->err.c_str();
+}
+
+}  // extern "C"

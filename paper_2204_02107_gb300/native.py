@@ -1,0 +1,326 @@
+"""ctypes binding of ``libventflow.so`` (declared in ``include/ventflow.h``): argument marshalling only.
+
+Every computation runs in the library's CUDA kernels.  If the library has not been built, every entry point
+raises ``VentflowUnavailable``; there is no CPU fallback.
+
+Host arrays are numpy arrays (C-contiguous, the dtype the call needs); device arrays are CUDA torch tensors,
+passed by pointer.  Shapes follow the library layout: (nz, ny, nx), x fastest.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libventflow.so")
+
+VF_OK, VF_EINVAL, VF_ESIZE, VF_ENOMEM, VF_ECUDA, VF_ESTATE, VF_ENONFINITE, VF_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6, -7
+VF_FP64, VF_FP32_MIXED = 0, 1
+VF_HOST, VF_DEVICE = 0, 1
+FIELDS = {"u": 0, "v": 1, "w": 2, "c": 3, "p": 4}
+N_PHASES = 13
+PRECISIONS = {"fp64": VF_FP64, "fp32": VF_FP32_MIXED, "fp32_mixed": VF_FP32_MIXED}
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
+
+
+class VfAllocator(C.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("ctx", C.c_void_p)]
+
+
+class VfGridDesc(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
+                ("lx", C.c_double), ("ly", C.c_double), ("lz", C.c_double),
+                ("nu", C.c_double), ("alpha_c", C.c_double), ("dt", C.c_double), ("tau_f", C.c_double),
+                ("body_force", C.c_double * 3),
+                ("n_pressure_iters", C.c_int32), ("filter", C.c_int32), ("precision", C.c_int32),
+                ("history_capacity", C.c_int32),
+                ("cuda_stream", C.c_void_p), ("alloc", C.POINTER(VfAllocator))]
+
+
+class VfReduce(C.Structure):
+    _fields_ = [("t", C.c_double), ("step", C.c_int64), ("ke", C.c_double), ("div_max", C.c_double),
+                ("div_l2", C.c_double), ("u_max", C.c_double), ("c_total", C.c_double), ("c_room", C.c_double),
+                ("c2_room", C.c_double), ("v_room", C.c_double), ("hist", C.c_int64 * 64),
+                ("hist_under", C.c_int64), ("hist_over", C.c_int64)]
+
+    def to_dict(self):
+        d = {name: getattr(self, name) for name, _ in self._fields_ if name != "hist"}
+        d["hist"] = np.array(self.hist[:], dtype=np.int64)
+        return d
+
+
+class VentflowUnavailable(RuntimeError):
+    pass
+
+
+class VentflowError(RuntimeError):
+    def __init__(self, code, message):
+        super().__init__(f"{status_string(code)} ({code}): {message}")
+        self.code = code
+
+
+_lib = None
+
+_SIGNATURES = {
+    "vf_grid_desc_default": (C.c_int, [C.POINTER(VfGridDesc)]),
+    "vf_create_grid": (C.c_int, [C.POINTER(VfGridDesc), C.POINTER(C.c_void_p)]),
+    "vf_destroy": (C.c_int, [C.c_void_p]),
+    "vf_set_mask": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
+    "vf_set_inflow": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_double), C.c_double, C.c_int]),
+    "vf_set_region": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
+    "vf_set_field": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int]),
+    "vf_set_time": (C.c_int, [C.c_void_p, C.c_double, C.c_int64]),
+    "vf_step": (C.c_int, [C.c_void_p, C.c_int64, C.c_int32]),
+    "vf_sync": (C.c_int, [C.c_void_p]),
+    "vf_read_field": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int]),
+    "vf_reductions": (C.c_int, [C.c_void_p, C.POINTER(VfReduce)]),
+    "vf_history": (C.c_int, [C.c_void_p, C.POINTER(VfReduce), C.c_int64, C.POINTER(C.c_int64)]),
+    "vf_clear_history": (C.c_int, [C.c_void_p]),
+    "vf_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                          C.POINTER(C.c_int64)]),
+    "vf_poisson_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "vf_profile_steps": (C.c_int, [C.c_void_p, C.c_int64, C.c_int32, C.POINTER(C.c_double),
+                                   C.POINTER(C.c_int64)]),
+    "vf_phase_name": (C.c_char_p, [C.c_int]),
+    "vf_status_string": (C.c_char_p, [C.c_int]),
+    "vf_last_error": (C.c_char_p, [C.c_void_p]),
+    "vf_ach_log_slope": (C.c_int, [C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_int64,
+                                   C.POINTER(C.c_double)]),
+    "vf_ach_fit3": (C.c_int, [C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_int64, C.POINTER(C.c_double),
+                              C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "vf_wells_riley": (C.c_int, [C.c_double, C.c_double, C.c_double, C.c_double, C.POINTER(C.c_double),
+                                 C.POINTER(C.c_double)]),
+}
+
+
+def lib():
+    """The loaded library (loads it on first use)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise VentflowUnavailable(f"{LIB_PATH} is not built; run paper_2204_02107_gb300.build.build()")
+        handle = C.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGNATURES.items():
+            fn = getattr(handle, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = handle
+    return _lib
+
+
+def status_string(code):
+    return lib().vf_status_string(int(code)).decode()
+
+
+def _dptr(arr):
+    return C.cast(arr.ctypes.data, C.POINTER(C.c_double))
+
+
+def _is_tensor(x):
+    return type(x).__module__.startswith("torch")
+
+
+def _pointer(x, dtype, n):
+    """(pointer, mem, keepalive) for a numpy array (host) or CUDA torch tensor (device) of n values."""
+    if _is_tensor(x):
+        if not x.is_cuda:
+            x = x.detach().cpu().numpy()
+        else:
+            if not x.is_contiguous() or x.numel() != n:
+                raise ValueError(f"device array must be contiguous with {n} elements")
+            return C.c_void_p(x.data_ptr()), VF_DEVICE, x
+    a = np.ascontiguousarray(x, dtype=dtype)
+    if a.size != n:
+        raise ValueError(f"array must have {n} elements, got {a.size}")
+    return C.c_void_p(a.ctypes.data), VF_HOST, a
+
+
+def default_desc():
+    d = VfGridDesc()
+    lib().vf_grid_desc_default(C.byref(d))
+    return d
+
+
+class Grid:
+    """One room grid on the current CUDA device (``vf_create_grid``).  Sizes (nx, ny, nz) must be even, >= 8 and
+    2-3-5 smooth.  ``precision`` is 'fp64' or 'fp32' (FP32 fields, FP64 reductions)."""
+
+    def __init__(self, nx, ny, nz, lx, ly, lz, nu, dt, alpha_c=None, tau_f=0.0, body_force=(0.0, 0.0, 0.0),
+                 n_pressure_iters=4, filter=True, precision="fp32", history_capacity=4096, stream=None):
+        d = default_desc()
+        d.nx, d.ny, d.nz = nx, ny, nz
+        d.lx, d.ly, d.lz = lx, ly, lz
+        d.nu = nu
+        d.alpha_c = -1.0 if alpha_c is None else alpha_c
+        d.dt = dt
+        d.tau_f = tau_f
+        for j in range(3):
+            d.body_force[j] = body_force[j]
+        d.n_pressure_iters = n_pressure_iters
+        d.filter = 1 if filter else 0
+        d.precision = PRECISIONS[precision]
+        d.history_capacity = history_capacity
+        d.cuda_stream = C.c_void_p(stream) if stream else None
+        h = C.c_void_p()
+        rc = lib().vf_create_grid(C.byref(d), C.byref(h))
+        if rc != VF_OK:
+            raise VentflowError(rc, "vf_create_grid")
+        self._h = h
+        self.desc = d
+        self.shape = (nz, ny, nx)
+        self.n = nx * ny * nz
+        self.precision = precision
+
+    # -- lifecycle
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().vf_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _check(self, rc, what):
+        if rc != VF_OK:
+            msg = lib().vf_last_error(self._h)
+            raise VentflowError(rc, f"{what}: {msg.decode() if msg else ''}")
+
+    # -- inputs
+    def set_mask(self, beta):
+        ptr, mem, _keep = _pointer(beta, np.uint8, self.n)
+        self._check(lib().vf_set_mask(self._h, ptr, mem), "vf_set_mask")
+
+    def set_inflow(self, S, u_set, c_set):
+        us = (C.c_double * 3)(*u_set)
+        if S is None:
+            self._check(lib().vf_set_inflow(self._h, None, us, float(c_set), VF_HOST), "vf_set_inflow")
+            return
+        ptr, mem, _keep = _pointer(S, np.uint8, self.n)
+        self._check(lib().vf_set_inflow(self._h, ptr, us, float(c_set), mem), "vf_set_inflow")
+
+    def set_region(self, room):
+        ptr, mem, _keep = _pointer(room, np.uint8, self.n)
+        self._check(lib().vf_set_region(self._h, ptr, mem), "vf_set_region")
+
+    def set_field(self, name, values):
+        if _is_tensor(values) and values.is_cuda:
+            import torch
+            is64 = values.dtype == torch.float64
+            ptr, mem, _keep = _pointer(values, None, self.n)
+        else:
+            arr = np.asarray(values)
+            is64 = arr.dtype != np.float32
+            ptr, mem, _keep = _pointer(arr, np.float64 if is64 else np.float32, self.n)
+        self._check(lib().vf_set_field(self._h, FIELDS[name], ptr, 1 if is64 else 0, mem), "vf_set_field")
+
+    def set_time(self, t, step):
+        self._check(lib().vf_set_time(self._h, float(t), int(step)), "vf_set_time")
+
+    # -- stepping
+    def step(self, n=1, reduce_every=0):
+        self._check(lib().vf_step(self._h, int(n), int(reduce_every)), "vf_step")
+
+    def sync(self):
+        self._check(lib().vf_sync(self._h), "vf_sync")
+
+    # -- outputs
+    def read_field(self, name, as_fp64=True):
+        out = np.empty(self.shape, dtype=np.float64 if as_fp64 else np.float32)
+        self._check(lib().vf_read_field(self._h, FIELDS[name], C.c_void_p(out.ctypes.data), 1 if as_fp64 else 0,
+                                        VF_HOST), "vf_read_field")
+        return out
+
+    def read_field_into(self, name, tensor):
+        """Device-to-device read into a contiguous CUDA tensor (float64 or float32)."""
+        import torch
+        ptr, mem, _keep = _pointer(tensor, None, self.n)
+        self._check(lib().vf_read_field(self._h, FIELDS[name], ptr, 1 if tensor.dtype == torch.float64 else 0, mem),
+                    "vf_read_field")
+
+    def reductions(self):
+        r = VfReduce()
+        self._check(lib().vf_reductions(self._h, C.byref(r)), "vf_reductions")
+        return r.to_dict()
+
+    def history(self, max_records=None):
+        if max_records is None:
+            max_records = self.desc.history_capacity
+        buf = (VfReduce * max(1, max_records))()
+        count = C.c_int64()
+        self._check(lib().vf_history(self._h, buf, int(max_records), C.byref(count)), "vf_history")
+        return [buf[i].to_dict() for i in range(count.value)]
+
+    def clear_history(self):
+        self._check(lib().vf_clear_history(self._h), "vf_clear_history")
+
+    def info(self):
+        t, s, cells, nbytes = C.c_double(), C.c_int64(), C.c_int64(), C.c_int64()
+        self._check(lib().vf_info(self._h, C.byref(t), C.byref(s), C.byref(cells), C.byref(nbytes)), "vf_info")
+        return dict(t=t.value, step=s.value, cells=cells.value, device_bytes=nbytes.value)
+
+    def profile_steps(self, n, reduce_every=0):
+        """n steps with CUDA events after every launch: {phase name: (total ms, launches)}."""
+        ms = (C.c_double * N_PHASES)()
+        cnt = (C.c_int64 * N_PHASES)()
+        self._check(lib().vf_profile_steps(self._h, int(n), int(reduce_every), ms, cnt), "vf_profile_steps")
+        return {lib().vf_phase_name(i).decode(): (ms[i], cnt[i]) for i in range(N_PHASES) if cnt[i] > 0}
+
+    def poisson_solve(self, f, p):
+        """Solve L p = f on the device (f, p: contiguous CUDA tensors in the grid's precision)."""
+        self._check(lib().vf_poisson_solve(self._h, C.c_void_p(f.data_ptr()), C.c_void_p(p.data_ptr())),
+                    "vf_poisson_solve")
+
+
+# -- host-side ventilation metrics
+def ach_log_slope(t_seconds, c_mean):
+    t = np.ascontiguousarray(t_seconds, dtype=np.float64)
+    c = np.ascontiguousarray(c_mean, dtype=np.float64)
+    out = C.c_double()
+    rc = lib().vf_ach_log_slope(_dptr(t), _dptr(c), t.size, C.byref(out))
+    if rc != VF_OK:
+        raise VentflowError(rc, "vf_ach_log_slope")
+    return out.value
+
+
+def ach_fit3(t_seconds, c_mean):
+    t = np.ascontiguousarray(t_seconds, dtype=np.float64)
+    c = np.ascontiguousarray(c_mean, dtype=np.float64)
+    a, c0, c1 = C.c_double(), C.c_double(), C.c_double()
+    rc = lib().vf_ach_fit3(_dptr(t), _dptr(c), t.size, C.byref(a), C.byref(c0), C.byref(c1))
+    if rc != VF_OK:
+        raise VentflowError(rc, "vf_ach_fit3")
+    return a.value, c0.value, c1.value
+
+
+def wells_riley(c0, breathing_m3_h, ach_per_hour, t_hours):
+    q, p = C.c_double(), C.c_double()
+    rc = lib().vf_wells_riley(float(c0), float(breathing_m3_h), float(ach_per_hour), float(t_hours), C.byref(q),
+                              C.byref(p))
+    if rc != VF_OK:
+        raise VentflowError(rc, "vf_wells_riley")
+    return q.value, p.value
+
+
+def room_grid(room, precision="fp32", filter=True, n_pressure_iters=4, nu=1.6e-5, dt=None, **kw):
+    """A Grid set up for a ``rooms.Room``: mask, forcing region (u_set = (U_in, 0, 0), c_set = 0), room region
+    and the stale-air initial scalar."""
+    g = Grid(room.nx, room.ny, room.nz, room.lx, room.ly, room.lz, nu=nu, dt=room.dt if dt is None else dt,
+             filter=filter, n_pressure_iters=n_pressure_iters, precision=precision, **kw)
+    g.set_mask(room.beta)
+    g.set_inflow(room.S, (room.u_in, 0.0, 0.0), 0.0)
+    g.set_region(room.room)
+    g.set_field("c", room.initial_c())
+    return g

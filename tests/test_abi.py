@@ -1,0 +1,96 @@
+"""The C ABI without a GPU: the library loads, exports every function the header declares, validates sizes
+before touching the device, and its host-side metrics agree with the oracle's."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import ventilation as V
+from paper_2204_02107_gb300 import build as B
+from paper_2204_02107_gb300 import native
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    srcs = [os.path.join(B.CSRC, f) for f in os.listdir(B.CSRC)] + [os.path.join(B.INCLUDE, "ventflow.h")]
+    if not os.path.exists(B.LIB_PATH) or os.path.getmtime(B.LIB_PATH) < max(os.path.getmtime(s) for s in srcs):
+        B.build()
+    return native.lib()
+
+
+def declared_functions():
+    names = []
+    for header in os.listdir(os.path.join(ROOT, "include")):
+        text = open(os.path.join(ROOT, "include", header)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names += re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\*?\s*(vf_[a-z0-9_]+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 20
+    raw = ctypes.CDLL(B.LIB_PATH)
+    missing = [n for n in names if not hasattr(raw, n)]
+    assert not missing
+
+
+def test_binding_covers_header(lib):
+    assert set(declared_functions()) <= set(native._SIGNATURES)
+
+
+def test_struct_sizes_match_header(lib):
+    # vf_reduce: 10 scalars + 64 + 2 counters, all 8 bytes
+    assert ctypes.sizeof(native.VfReduce) == 8 * (10 + 64 + 2)
+    d = native.default_desc()
+    assert (d.nx, d.ny, d.nz) == (64, 64, 64) and d.n_pressure_iters == 4 and d.filter == 1
+    assert d.precision == native.VF_FP32_MIXED and d.alpha_c < 0
+
+
+def test_status_strings(lib):
+    assert native.status_string(0) == "VF_OK"
+    assert native.status_string(native.VF_ESIZE) == "VF_ESIZE"
+    assert native.status_string(-99) == "VF_UNKNOWN"
+
+
+@pytest.mark.parametrize("n", [7, 9, 14, 22, 6, 0, -8])
+def test_bad_sizes_rejected_before_any_device_call(lib, n):
+    d = native.default_desc()
+    d.nx = n
+    h = ctypes.c_void_p()
+    assert lib.vf_create_grid(ctypes.byref(d), ctypes.byref(h)) == native.VF_ESIZE
+    assert not h.value
+
+
+def test_bad_arguments_rejected(lib):
+    d = native.default_desc()
+    d.dt = 0.0
+    h = ctypes.c_void_p()
+    assert lib.vf_create_grid(ctypes.byref(d), ctypes.byref(h)) == native.VF_EINVAL
+    d = native.default_desc()
+    d.precision = 7
+    assert lib.vf_create_grid(ctypes.byref(d), ctypes.byref(h)) == native.VF_EINVAL
+    assert lib.vf_create_grid(None, ctypes.byref(h)) == native.VF_EINVAL
+    assert lib.vf_destroy(None) == native.VF_OK
+
+
+def test_host_metrics_match_oracle(lib):
+    t = np.linspace(0, 600, 121)
+    c = 0.9 * np.exp(-4.5 * t / 3600)
+    assert native.ach_log_slope(t, c) == pytest.approx(V.ach_log_slope(t, c), rel=1e-12)
+    t = np.linspace(0, 3600, 300)
+    c = 0.55 * np.exp(-3.3 * t / 3600) + 0.31
+    a, c0, c1 = native.ach_fit3(t, c)
+    ra, rc0, rc1 = V.ach_fit3(t, c)
+    assert a == pytest.approx(3.3, rel=1e-7) and a == pytest.approx(ra, rel=1e-7)
+    assert c0 == pytest.approx(rc0, rel=1e-6) and c1 == pytest.approx(rc1, rel=1e-6)
+    for ach in (0.0, 1e-9, 3.48, 67.6):
+        q, p = native.wells_riley(100 / 192, 1.2, ach, 0.5)
+        assert q == pytest.approx(V.wells_riley_dose(100 / 192, 1.2, ach, 0.5), rel=1e-12)
+        assert p == pytest.approx(V.infection_probability(q), rel=1e-12)
+    with pytest.raises(native.VentflowError):
+        native.wells_riley(1.0, 1.2, -1.0, 0.5)
