@@ -173,6 +173,28 @@ int vf_info(const vf_grid* g, double* t, int64_t* step, int64_t* cells, int64_t*
  * scratch; stream-ordered on the grid's stream, returns without waiting. */
 int vf_poisson_solve(vf_grid* g, const void* f, void* p);
 
+/* ---- Poisson solve without device allocation --------------------------------------------------------------- */
+
+/* The paper has no counterpart of this call; it exists for callers that cannot allocate device memory (code that
+ * runs where cudaMalloc is forbidden or unavailable, e.g. inside an allocator or a framework that owns every
+ * device allocation).  It computes the same solve as vf_poisson_solve -- L p = f with the forward 3D FFT,
+ * division by lambda (null modes -> 0) and inverse 3D FFT -- without a grid handle and without allocating:
+ * its scratch (half spectrum and FFT / eigenvalue tables) is one file-scope device array of 33 MiB that every
+ * GPU loading the library holds until the process exits.
+ *   nx, ny, nz, lx, ly, lz: sizes and box lengths as in vf_grid_desc;  precision: VF_FP64 (f, p are double) or
+ *   VF_FP32_MIXED (float);  f, p: caller-owned device arrays of nx*ny*nz values (may alias);  stream: a
+ *   cudaStream_t or NULL.  Returns after p is written.
+ * Limits: nx*ny*nz <= vf_poisson_noalloc_max_cells(precision) (4,194,304 in FP64, 8,388,608 in FP32) and every
+ * FFT length (nx/2 + 1, ny, nz) <= 1024; larger sizes return VF_ESIZE.
+ * The first call on a device looks up the array's device address (once per device, with that device current);
+ * make that first call before any stream capture.  Every call reuses the same array and leaves its contents
+ * behind; calls that overlap on the GPU (several streams or threads at once) race on it. */
+int vf_poisson_solve_noalloc(int32_t nx, int32_t ny, int32_t nz, double lx, double ly, double lz,
+                             int32_t precision, const void* f, void* p, void* stream);
+
+/* Largest nx*ny*nz that vf_poisson_solve_noalloc accepts in the given precision (0 for a bad precision). */
+int64_t vf_poisson_noalloc_max_cells(int32_t precision);
+
 /* ---- measurement ----------------------------------------------------------------------------------------- */
 
 /* Kernel phases of one step, in launch order. */

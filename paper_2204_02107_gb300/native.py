@@ -83,6 +83,9 @@ _SIGNATURES = {
     "vf_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                           C.POINTER(C.c_int64)]),
     "vf_poisson_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "vf_poisson_solve_noalloc": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_double, C.c_double, C.c_double,
+                                           C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "vf_poisson_noalloc_max_cells": (C.c_int64, [C.c_int32]),
     "vf_profile_steps": (C.c_int, [C.c_void_p, C.c_int64, C.c_int32, C.POINTER(C.c_double),
                                    C.POINTER(C.c_int64)]),
     "vf_phase_name": (C.c_char_p, [C.c_int]),
@@ -282,6 +285,16 @@ class Grid:
         """Solve L p = f on the device (f, p: contiguous CUDA tensors in the grid's precision)."""
         self._check(lib().vf_poisson_solve(self._h, C.c_void_p(f.data_ptr()), C.c_void_p(p.data_ptr())),
                     "vf_poisson_solve")
+
+
+def poisson_solve_noalloc(nx, ny, nz, lx, ly, lz, f, p, stream=None):
+    """Solve L p = f without any device allocation (f, p: contiguous CUDA tensors, float64 or float32)."""
+    import torch
+    precision = VF_FP64 if f.dtype == torch.float64 else VF_FP32_MIXED
+    rc = lib().vf_poisson_solve_noalloc(nx, ny, nz, lx, ly, lz, precision, C.c_void_p(f.data_ptr()),
+                                        C.c_void_p(p.data_ptr()), C.c_void_p(stream) if stream else None)
+    if rc != VF_OK:
+        raise VentflowError(rc, "vf_poisson_solve_noalloc")
 
 
 # -- host-side ventilation metrics
