@@ -46,6 +46,8 @@ PHASE_BYTES_PER_CELL = {
     "fft_z_solve": 2 * F32,
     "fft_y_inv": 2 * F32,
     "fft_x_inv": 2 * F32,        # read the spectrum, write p
+    "fft_yz_solve": 2 * F32,     # read + write the spectrum once (y, z transforms and division in shared memory)
+    "poisson_rhs": None,         # touches only the cells next to solids (about 1 in 9 here): not a roofline row
     "project": 7 * F32 + 1,      # read u*, v*, w*, p, mask; write u, v, w
     "filter": 8 * F32 + 1,       # read u, v, w, c, mask; write 4 fields
     "reduce": 4 * F32 + 1,       # read u, v, w, c, mask
@@ -275,7 +277,7 @@ def main():
     stream = torch.cuda.Stream()
     g = native.room_grid(room, precision="fp32", stream=stream.cuda_stream)
     cells = room.cells
-    launches_per_step = 4 + 1 + 5 * 4 + 1 + 1 + 2
+    launches_per_step = None   # counted from the profiled steps below
 
     g.step(args.warmup, reduce_every=1)
     g.sync()
@@ -304,13 +306,13 @@ def main():
     per_kernel = {}
     for name, (tot_ms, nl) in phases.items():
         avg_s = tot_ms / nl / 1e3
-        b = PHASE_BYTES_PER_CELL[name] * cells
+        bpc = PHASE_BYTES_PER_CELL.get(name)
         per_kernel[name] = {"launches": nl, "avg_us": avg_s * 1e6, "share": None,
-                            "algorithmic_gb_s": b / avg_s / 1e9}
+                            "algorithmic_gb_s": None if bpc is None else bpc * cells / avg_s / 1e9}
     total_ms = sum(t for t, _ in phases.values())
     for name, (tot_ms, _) in phases.items():
         per_kernel[name]["share"] = tot_ms / total_ms
-    dominant = max(phases, key=lambda k: phases[k][0])
+    dominant = max((k for k in phases if PHASE_BYTES_PER_CELL.get(k) is not None), key=lambda k: phases[k][0])
     dom_avg_s = phases[dominant][0] / phases[dominant][1] / 1e3
     achieved = PHASE_BYTES_PER_CELL[dominant] * cells / dom_avg_s / 1e9
     traffic = traffic_record(dominant)
@@ -350,7 +352,7 @@ def main():
         "fp64": {"value": cells * args.fp64_steps / (fp64_ms / 1e3) / 1e9, "unit": UNIT,
                  "ms_per_step": fp64_ms / args.fp64_steps, "steps": args.fp64_steps},
         "e2e": e2e,
-        "gpu_launches": launches_per_step * args.steps,
+        "gpu_launches": int(round(sum(n for _, n in phases.values()) / prof_steps)) * args.steps,
         "clocks": clocks.summary(),
         "last_record": {k: hist[-1][k] for k in ("step", "ke", "c_room", "div_max", "u_max")} if hist else None,
     }

@@ -203,15 +203,17 @@ int64_t vf_poisson_noalloc_max_cells(int32_t precision);
 #define VF_PHASE_STAGE3 2       /* RK4 stage 3 */
 #define VF_PHASE_STAGE4 3       /* RK4 stage 4: q* = acc + dt/6 k4 */
 #define VF_PHASE_DIV 4          /* r = D u* / dt */
-#define VF_PHASE_FFT_X_FWD 5    /* Eq. 9 right-hand side + real-to-complex FFT along x */
+#define VF_PHASE_FFT_X_FWD 5    /* real-to-complex FFT along x of the Eq. 9 right-hand side */
 #define VF_PHASE_FFT_Y_FWD 6    /* FFT along y */
 #define VF_PHASE_FFT_Z_SOLVE 7  /* FFT along z, division by lambda, inverse FFT along z */
 #define VF_PHASE_FFT_Y_INV 8    /* inverse FFT along y */
 #define VF_PHASE_FFT_X_INV 9    /* complex-to-real inverse FFT along x -> p */
 #define VF_PHASE_PROJECT 10     /* u = beta (u* - dt G p) */
 #define VF_PHASE_FILTER 11      /* Eq. 6 filter */
-#define VF_PHASE_REDUCE 12      /* FP64 reductions (partials + final) */
-#define VF_N_PHASES 13
+#define VF_PHASE_REDUCE 12      /* FP64 reductions */
+#define VF_PHASE_POISSON_RHS 13 /* Eq. 9 correction D((1 - beta) G p) at the cells next to solids */
+#define VF_PHASE_FFT_YZ_SOLVE 14 /* per-kx plane: y, z FFTs, division by lambda, inverse z, y FFTs */
+#define VF_N_PHASES 15
 
 /* Run n steps like vf_step but with direct launches bracketed by CUDA events on the grid's stream; adds the
  * elapsed milliseconds of every phase to phase_ms[VF_N_PHASES] and its launch count to launches[VF_N_PHASES]

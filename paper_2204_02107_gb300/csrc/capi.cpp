@@ -37,13 +37,17 @@ struct vf_grid {
     int alloc_count = 0;
     int fail_alloc_at = 0;       // fault injection: the n-th allocation of this grid fails (0 = off)
 
-    void* q[4]{};
-    void* acc[4]{};
-    void* qa[4]{};
-    void* qb[4]{};
+    void* q = nullptr;           // state (u, v, w, c) per cell as a 4-vector
+    void* acc = nullptr;         // RK4 accumulator
+    void* qa = nullptr;          // RK4 stage states
+    void* qb = nullptr;
     void* p = nullptr;
-    void* r = nullptr;
+    void* f = nullptr;           // right-hand side of Eq. 9: D u* / dt, plus the correction next to solids
     void* spec = nullptr;
+    int* near_list = nullptr;    // cells with a solid axis neighbour, ascending (capacity N)
+    void* near_r = nullptr;      // D u* / dt at those cells (capacity N)
+    int n_near = 0;
+    bool plane_layout = false;
     void* staging = nullptr;     // N * 8 bytes
     uint8_t* mask = nullptr;
     void* twx = nullptr;
@@ -53,9 +57,12 @@ struct vf_grid {
     void* lamx = nullptr;
     void* lamy = nullptr;
     void* lamz = nullptr;
+    int* krev_y = nullptr;       // digit-reversal tables of the in-place y and z transforms
+    int* krev_z = nullptr;
 
     double* red_partial = nullptr;
-    int* hist_partial = nullptr;
+    unsigned long long* hist_accum = nullptr;
+    unsigned int* red_done = nullptr;
     vf_reduce* red_out = nullptr;
     vf_reduce* history = nullptr;
     long long* dev_counters = nullptr;   // [0] history count, [1] step counter
@@ -112,27 +119,6 @@ bool smooth235_even(int n)
     for (int p : {2, 3, 5})
         while (n % p == 0) n /= p;
     return n == 1;
-}
-
-// Radix schedule: powers of two in as many radix-8 passes as possible (a remainder of 2 becomes 4 x 4 or a 4),
-// then the factors 3 and 5.
-FftAxis make_axis(int n)
-{
-    FftAxis a{};
-    a.n = n;
-    int m = n, twos = 0;
-    while (m % 2 == 0) { m /= 2; ++twos; }
-    int eights = twos / 3, rem = twos % 3;
-    std::vector<int> rad;
-    if (rem == 1 && eights > 0) { --eights; rad.push_back(4); rad.push_back(4); }
-    else if (rem == 1) rad.push_back(2);
-    else if (rem == 2) rad.push_back(4);
-    for (int i = 0; i < eights; ++i) rad.push_back(8);
-    while (m % 3 == 0) { m /= 3; rad.push_back(3); }
-    while (m % 5 == 0) { m /= 5; rad.push_back(5); }
-    a.nstages = (int)rad.size();
-    for (int i = 0; i < a.nstages && i < vf::kMaxRadixStages; ++i) a.radix[i] = rad[i];
-    return a;
 }
 
 void* galloc(vf_grid* g, size_t bytes)
@@ -202,19 +188,25 @@ FlowConsts<T> flow_consts(const vf_grid* g)
 }
 
 template <typename T>
-PoissonArgs<T> poisson_args(const vf_grid* g, const T* r, T* p, int use_mask)
+PoissonArgs<T> poisson_args(const vf_grid* g, T* f, T* p, int use_mask)
 {
     PoissonArgs<T> a{};
     const vf_grid_desc& d = g->d;
     a.nx = d.nx; a.ny = d.ny; a.nz = d.nz; a.M = d.nx / 2;
-    a.r = r; a.p = p; a.mask = g->mask; a.use_mask = use_mask;
+    a.f = f; a.p = p; a.mask = g->mask;
+    a.near_list = g->near_list;
+    a.near_r = (T*)g->near_r;
+    a.n_near = use_mask ? g->n_near : 0;
+    a.plane_layout = g->plane_layout ? 1 : 0;
     a.spec = g->spec;
     a.twx = g->twx; a.twy = g->twy; a.twz = g->twz; a.twr = g->twr;
     a.lamx = (const T*)g->lamx; a.lamy = (const T*)g->lamy; a.lamz = (const T*)g->lamz;
+    a.krev_y = g->krev_y; a.krev_z = g->krev_z;
     const double h[3] = {d.lx / d.nx, d.ly / d.ny, d.lz / d.nz};
     for (int j = 0; j < 3; ++j) a.i2h2[j] = (T)(1.0 / (4.0 * h[j] * h[j]));
     a.invN = (T)(1.0 / ((double)d.nx * d.ny * d.nz));
     a.ax = g->ax; a.ay = g->ay; a.az = g->az;
+    a.ny_div = vf::make_fast_div((uint32_t)d.ny);
     a.rows_per_block = g->rows_per_block;
     a.cols_per_block = g->cols_per_block;
     return a;
@@ -224,7 +216,8 @@ vf::ReduceArgsDev reduce_args(const vf_grid* g)
 {
     vf::ReduceArgsDev r{};
     r.partial = g->red_partial;
-    r.hist_partial = g->hist_partial;
+    r.hist_accum = g->hist_accum;
+    r.done = g->red_done;
     r.out = g->red_out;
     r.history = g->history;
     r.hist_count = g->dev_counters;
@@ -248,57 +241,44 @@ cudaError_t enqueue_step_t(vf_grid* g, cudaStream_t st, bool with_reduce, const 
 {
     auto mark = [&](int phase) { if (hook) (*hook)(phase); };
     const FlowConsts<T> k = flow_consts<T>(g);
-    T* q[4];
-    T* acc[4];
-    T* qa[4];
-    T* qb[4];
-    for (int f = 0; f < 4; ++f) {
-        q[f] = (T*)g->q[f]; acc[f] = (T*)g->acc[f]; qa[f] = (T*)g->qa[f]; qb[f] = (T*)g->qb[f];
-    }
     StageArgs<T> a{};
     a.mask = g->mask;
-    auto set = [&](T* const* qs, T* const* out) {
-        for (int f = 0; f < 4; ++f) { a.qs[f] = qs[f]; a.qn[f] = q[f]; a.acc[f] = acc[f]; a.out[f] = out[f]; }
-    };
+    a.qn = g->q;
+    a.acc = g->acc;
     cudaError_t e;
-    set(q, qa);
+    // stage s reads q_s with the stencil: q, qa, qb, qa; writes the next stage state: qa, qb, qa, then q* in qb
+    a.qs = g->q; a.out = g->qa;
     if ((e = Kernels<T>::stage(1, a, k, st)) != cudaSuccess) return e;
     mark(VF_PHASE_STAGE1);
-    set(qa, qb);
+    a.qs = g->qa; a.out = g->qb;
     if ((e = Kernels<T>::stage(2, a, k, st)) != cudaSuccess) return e;
     mark(VF_PHASE_STAGE2);
-    set(qb, qa);
+    a.qs = g->qb; a.out = g->qa;
     if ((e = Kernels<T>::stage(3, a, k, st)) != cudaSuccess) return e;
     mark(VF_PHASE_STAGE3);
-    set(qa, qb);
+    a.qs = g->qa; a.out = g->qb;
     if ((e = Kernels<T>::stage(4, a, k, st)) != cudaSuccess) return e;
     mark(VF_PHASE_STAGE4);
     const int iters = pressure_iters(g);
     if (iters > 0) {
-        if ((e = Kernels<T>::divergence(qb[0], qb[1], qb[2], (T*)g->r, k, st)) != cudaSuccess) return e;
+        if ((e = Kernels<T>::divergence(g->qb, (T*)g->f, k, st)) != cudaSuccess) return e;
         mark(VF_PHASE_DIV);
-        const PoissonArgs<T> pa = poisson_args<T>(g, (const T*)g->r, (T*)g->p, g->has_solid ? 1 : 0);
+        const PoissonArgs<T> pa = poisson_args<T>(g, (T*)g->f, (T*)g->p, g->has_solid ? 1 : 0);
         for (int it = 0; it < iters; ++it)
-            if ((e = Kernels<T>::poisson_iteration(pa, st, hook)) != cudaSuccess) return e;
+            if ((e = Kernels<T>::poisson_iteration(pa, it == 0, st, hook)) != cudaSuccess) return e;
     }
-    const T* us[3] = {qb[0], qb[1], qb[2]};
     long long* step_counter = g->dev_counters + 1;
+    // projection into acc (then filtered into q) or straight into q
+    void* proj_out = g->d.filter ? g->acc : g->q;
+    if ((e = Kernels<T>::project(g->qb, (const T*)g->p, proj_out, g->mask, step_counter, k, st)) != cudaSuccess)
+        return e;
+    mark(VF_PHASE_PROJECT);
     if (g->d.filter) {
-        T* out[4] = {acc[0], acc[1], acc[2], qb[3]};
-        if ((e = Kernels<T>::project(us, qb[3], (const T*)g->p, out, g->mask, step_counter, k, st)) != cudaSuccess)
-            return e;
-        mark(VF_PHASE_PROJECT);
-        const T* in[4] = {acc[0], acc[1], acc[2], qb[3]};
-        if ((e = Kernels<T>::filter(in, q, g->mask, k, st)) != cudaSuccess) return e;
+        if ((e = Kernels<T>::filter(g->acc, g->q, g->mask, k, st)) != cudaSuccess) return e;
         mark(VF_PHASE_FILTER);
-    } else {
-        if ((e = Kernels<T>::project(us, qb[3], (const T*)g->p, q, g->mask, step_counter, k, st)) != cudaSuccess)
-            return e;
-        mark(VF_PHASE_PROJECT);
     }
     if (with_reduce) {
-        const T* qq[4] = {q[0], q[1], q[2], q[3]};
-        if ((e = Kernels<T>::reduce(qq, g->mask, k, reduce_args(g), 1, st)) != cudaSuccess) return e;
+        if ((e = Kernels<T>::reduce(g->q, g->mask, k, reduce_args(g), 1, st)) != cudaSuccess) return e;
         mark(VF_PHASE_REDUCE);
     }
     return cudaSuccess;
@@ -379,17 +359,23 @@ int build_tables_t(vf_grid* g)
     const std::vector<C2> tx = roots(M, M), ty = roots(d.ny, d.ny), tz = roots(d.nz, d.nz), tr = roots(d.nx, M + 1);
     const std::vector<T> lx = lam(d.nx, M, d.lx / d.nx), ly = lam(d.ny, d.ny, d.ly / d.ny),
                          lz = lam(d.nz, d.nz, d.lz / d.nz);
+    std::vector<int> ry(d.ny), rz(d.nz);
+    vf::digit_reversal(g->ay, ry.data());
+    vf::digit_reversal(g->az, rz.data());
     struct Up { void** dst; const void* src; size_t bytes; };
     const Up ups[] = {{&g->twx, tx.data(), tx.size() * sizeof(C2)}, {&g->twy, ty.data(), ty.size() * sizeof(C2)},
                       {&g->twz, tz.data(), tz.size() * sizeof(C2)}, {&g->twr, tr.data(), tr.size() * sizeof(C2)},
                       {&g->lamx, lx.data(), lx.size() * sizeof(T)}, {&g->lamy, ly.data(), ly.size() * sizeof(T)},
-                      {&g->lamz, lz.data(), lz.size() * sizeof(T)}};
+                      {&g->lamz, lz.data(), lz.size() * sizeof(T)},
+                      {(void**)&g->krev_y, ry.data(), ry.size() * sizeof(int)},
+                      {(void**)&g->krev_z, rz.data(), rz.size() * sizeof(int)}};
     for (const Up& u : ups) {
         *u.dst = galloc(g, u.bytes);
         if (!*u.dst) return set_err(g, VF_ENOMEM, "table allocation failed");
         VF_CK(cudaMemcpyAsync(*u.dst, u.src, u.bytes, cudaMemcpyHostToDevice, g->stream));
     }
     VF_CK(cudaStreamSynchronize(g->stream));   // host vectors die here
+    g->plane_layout = Kernels<T>::plane_fits(d.ny, d.nz) && !std::getenv("VF_TILE_FFT");
     const PoissonArgs<T> pa = poisson_args<T>(g, nullptr, nullptr, 0);
     VF_CK(Kernels<T>::poisson_prepare(pa));
     return VF_OK;
@@ -414,11 +400,7 @@ const void* stage_input(vf_grid* g, const void* src, size_t bytes, int mem, int*
 template <typename T>
 cudaError_t mask_fields(vf_grid* g)
 {
-    for (int f = 0; f < 4; ++f) {
-        cudaError_t e = Kernels<T>::apply_mask((T*)g->q[f], g->mask, g->N, g->stream);
-        if (e != cudaSuccess) return e;
-    }
-    return cudaSuccess;
+    return Kernels<T>::apply_mask(g->q, g->mask, g->N, g->stream);
 }
 
 }  // namespace
@@ -480,31 +462,36 @@ int vf_create_grid(const vf_grid_desc* d, vf_grid** out)
 
     const int M = d->nx / 2;
     {
-        // every FFT pass keeps two tiles of its batch in shared memory (at most 227 KB per CTA)
+        // the FFT passes keep up to three tiles of their batch and a twiddle table in shared memory (at most
+        // 227 KB per CTA): ny, nz <= 593 in FP32 and <= 581 in FP64
         const size_t cplx = g->fp64 ? 16 : 8, tb = g->fp64 ? 8 : 16, limit = 227 * 1024;
-        if (2 * tb * (size_t)std::max(d->ny, d->nz) * cplx > limit || 2 * (size_t)M * cplx > limit)
-            return fail(VF_ESIZE);
+        const size_t n = (size_t)std::max(d->ny, d->nz);
+        if ((3 * tb * n + n) * cplx > limit || 4 * (size_t)M * cplx > limit) return fail(VF_ESIZE);
     }
-    g->ax = make_axis(M);
-    g->ay = make_axis(d->ny);
-    g->az = make_axis(d->nz);
+    g->ax = vf::make_fft_axis(M);
+    g->ay = vf::make_fft_axis(d->ny);
+    g->az = vf::make_fft_axis(d->nz);
     const int target = g->fp64 ? 1024 : 2048;   // complex values per CTA in the x passes
     g->rows_per_block = std::max(1, target / M);
     g->cols_per_block = g->fp64 ? 8 : 16;
 
     const size_t fb = g->N * g->esz;
-    void** fields[] = {&g->q[0], &g->q[1], &g->q[2], &g->q[3], &g->acc[0], &g->acc[1], &g->acc[2], &g->acc[3],
-                       &g->qa[0], &g->qa[1], &g->qa[2], &g->qa[3], &g->qb[0], &g->qb[1], &g->qb[2], &g->qb[3],
-                       &g->p, &g->r, &g->spec};
-    for (void** f : fields)
+    void** states[] = {&g->q, &g->acc, &g->qa, &g->qb};
+    for (void** f : states)
+        if (!(*f = galloc(g, 4 * fb))) return fail(VF_ENOMEM);
+    void** scalars[] = {&g->p, &g->f, &g->spec, &g->near_r};
+    for (void** f : scalars)
         if (!(*f = galloc(g, fb))) return fail(VF_ENOMEM);
+    if (!(g->near_list = (int*)galloc(g, g->N * sizeof(int)))) return fail(VF_ENOMEM);
     if (!(g->staging = galloc(g, g->N * 8))) return fail(VF_ENOMEM);
     if (!(g->mask = (uint8_t*)galloc(g, g->N))) return fail(VF_ENOMEM);
 
     const FlowConsts<float> kf = flow_consts<float>(g);
     g->nred = Kernels<float>::reduce_blocks(kf);
     if (!(g->red_partial = (double*)galloc(g, (size_t)g->nred * vf::kRedSlots * sizeof(double)))) return fail(VF_ENOMEM);
-    if (!(g->hist_partial = (int*)galloc(g, (size_t)g->nred * (vf::kHistBins + 2) * sizeof(int)))) return fail(VF_ENOMEM);
+    if (!(g->hist_accum = (unsigned long long*)galloc(g, (vf::kHistBins + 2) * sizeof(unsigned long long))))
+        return fail(VF_ENOMEM);
+    if (!(g->red_done = (unsigned int*)galloc(g, sizeof(unsigned int)))) return fail(VF_ENOMEM);
     if (!(g->red_out = (vf_reduce*)galloc(g, sizeof(vf_reduce)))) return fail(VF_ENOMEM);
     if (!(g->history = (vf_reduce*)galloc(g, (size_t)d->history_capacity * sizeof(vf_reduce)))) return fail(VF_ENOMEM);
     if (!(g->dev_counters = (long long*)galloc(g, 2 * sizeof(long long)))) return fail(VF_ENOMEM);
@@ -539,7 +526,27 @@ int vf_set_mask(vf_grid* g, const uint8_t* beta, int mem)
     const void* src = stage_input(g, beta, g->N, mem, &rc);
     if (rc) return rc;
     VF_CK(vf::mask_merge(g->mask, (const uint8_t*)src, vf::kBitBeta, g->N, g->stream));
+    VF_CK(vf::mask_mark_near_solid(g->mask, g->d.nx, g->d.ny, g->d.nz, g->stream));
     VF_CK(g->fp64 ? mask_fields<double>(g) : mask_fields<float>(g));
+    {
+        // ordered list of the cells next to a solid: per-chunk counts, host exclusive scan, fill
+        const size_t chunks = (g->N + vf::kListChunk - 1) / vf::kListChunk;
+        int* d_counts = (int*)g->staging;
+        VF_CK(vf::mask_near_counts(g->mask, g->N, d_counts, g->stream));
+        std::vector<int> counts(chunks);
+        VF_CK(cudaMemcpyAsync(counts.data(), d_counts, chunks * sizeof(int), cudaMemcpyDeviceToHost, g->stream));
+        VF_CK(cudaStreamSynchronize(g->stream));
+        int total = 0;
+        for (size_t c = 0; c < chunks; ++c) {
+            const int n = counts[c];
+            counts[c] = total;
+            total += n;
+        }
+        VF_CK(cudaMemcpyAsync(d_counts, counts.data(), chunks * sizeof(int), cudaMemcpyHostToDevice, g->stream));
+        VF_CK(vf::mask_near_fill(g->mask, g->N, d_counts, g->near_list, g->stream));
+        VF_CK(cudaStreamSynchronize(g->stream));
+        g->n_near = total;
+    }
     VF_CK(vf::mask_count_solid(g->mask, g->N, g->solid_count, g->stream));
     unsigned long long solids = 0;
     VF_CK(cudaMemcpyAsync(&solids, g->solid_count, sizeof(solids), cudaMemcpyDeviceToHost, g->stream));
@@ -588,11 +595,11 @@ int vf_set_field(vf_grid* g, int field, const void* src, int is_fp64, int mem)
     const size_t bytes = g->N * (is_fp64 ? 8 : 4);
     const void* dsrc = stage_input(g, src, bytes, mem, &rc);
     if (rc) return rc;
-    void* dst = field == VF_P ? g->p : g->q[field];
-    const double scale = 1.0;
+    void* dst = field == VF_P ? g->p : g->q;
+    const int comp = field == VF_P ? -1 : field;
     const uint8_t* mask = field == VF_P ? nullptr : g->mask;
-    if (g->fp64) VF_CK(Kernels<double>::convert_in(dsrc, is_fp64, (double*)dst, g->N, scale, mask, g->stream));
-    else VF_CK(Kernels<float>::convert_in(dsrc, is_fp64, (float*)dst, g->N, scale, mask, g->stream));
+    if (g->fp64) VF_CK(Kernels<double>::convert_in(dsrc, is_fp64, dst, comp, g->N, 1.0, mask, g->stream));
+    else VF_CK(Kernels<float>::convert_in(dsrc, is_fp64, dst, comp, g->N, 1.0, mask, g->stream));
     VF_CK(cudaStreamSynchronize(g->stream));
     return VF_OK;
 }
@@ -646,11 +653,11 @@ int vf_read_field(vf_grid* g, int field, void* dst, int as_fp64, int mem)
     if (rc) return rc;
     if (!dst || field < VF_U || field > VF_P || (mem != VF_HOST && mem != VF_DEVICE))
         return set_err(g, VF_EINVAL, "vf_read_field: bad argument");
-    const void* src = field == VF_P ? g->p : g->q[field];
-    const double scale = 1.0;
+    const void* src = field == VF_P ? g->p : g->q;
+    const int comp = field == VF_P ? -1 : field;
     void* out = mem == VF_DEVICE ? dst : g->staging;
-    if (g->fp64) VF_CK(Kernels<double>::convert_out((const double*)src, out, as_fp64, g->N, scale, g->stream));
-    else VF_CK(Kernels<float>::convert_out((const float*)src, out, as_fp64, g->N, scale, g->stream));
+    if (g->fp64) VF_CK(Kernels<double>::convert_out(src, comp, out, as_fp64, g->N, 1.0, g->stream));
+    else VF_CK(Kernels<float>::convert_out(src, comp, out, as_fp64, g->N, 1.0, g->stream));
     if (mem == VF_HOST)
         VF_CK(cudaMemcpyAsync(dst, g->staging, g->N * (as_fp64 ? 8 : 4), cudaMemcpyDeviceToHost, g->stream));
     VF_CK(cudaStreamSynchronize(g->stream));
@@ -663,15 +670,8 @@ int vf_reductions(vf_grid* g, vf_reduce* out)
     if (rc) return rc;
     if (!out) return set_err(g, VF_EINVAL, "vf_reductions: null output");
     const vf::ReduceArgsDev r = reduce_args(g);
-    if (g->fp64) {
-        const FlowConsts<double> k = flow_consts<double>(g);
-        const double* q[4] = {(double*)g->q[0], (double*)g->q[1], (double*)g->q[2], (double*)g->q[3]};
-        VF_CK(Kernels<double>::reduce(q, g->mask, k, r, 0, g->stream));
-    } else {
-        const FlowConsts<float> k = flow_consts<float>(g);
-        const float* q[4] = {(float*)g->q[0], (float*)g->q[1], (float*)g->q[2], (float*)g->q[3]};
-        VF_CK(Kernels<float>::reduce(q, g->mask, k, r, 0, g->stream));
-    }
+    if (g->fp64) VF_CK(Kernels<double>::reduce(g->q, g->mask, flow_consts<double>(g), r, 0, g->stream));
+    else VF_CK(Kernels<float>::reduce(g->q, g->mask, flow_consts<float>(g), r, 0, g->stream));
     int bad = 0;
     VF_CK(cudaMemcpyAsync(out, g->red_out, sizeof(vf_reduce), cudaMemcpyDeviceToHost, g->stream));
     VF_CK(cudaMemcpyAsync(&bad, g->nonfinite, sizeof(int), cudaMemcpyDeviceToHost, g->stream));
@@ -733,11 +733,11 @@ int vf_poisson_solve(vf_grid* g, const void* f, void* p)
     if (rc) return rc;
     if (!f || !p) return set_err(g, VF_EINVAL, "vf_poisson_solve: null pointer");
     if (g->fp64) {
-        const PoissonArgs<double> a = poisson_args<double>(g, (const double*)f, (double*)p, 0);
-        VF_CK(Kernels<double>::poisson_iteration(a, g->stream));
+        const PoissonArgs<double> a = poisson_args<double>(g, (double*)f, (double*)p, 0);
+        VF_CK(Kernels<double>::poisson_iteration(a, 1, g->stream));
     } else {
-        const PoissonArgs<float> a = poisson_args<float>(g, (const float*)f, (float*)p, 0);
-        VF_CK(Kernels<float>::poisson_iteration(a, g->stream));
+        const PoissonArgs<float> a = poisson_args<float>(g, (float*)f, (float*)p, 0);
+        VF_CK(Kernels<float>::poisson_iteration(a, 1, g->stream));
     }
     return VF_OK;
 }
@@ -783,7 +783,7 @@ const char* vf_phase_name(int phase)
 {
     static const char* names[VF_N_PHASES] = {"stage1", "stage2", "stage3", "stage4", "div", "fft_x_fwd",
                                              "fft_y_fwd", "fft_z_solve", "fft_y_inv", "fft_x_inv", "project",
-                                             "filter", "reduce"};
+                                             "filter", "reduce", "poisson_rhs", "fft_yz_solve"};
     if (phase < 0 || phase >= VF_N_PHASES) return "unknown";
     return names[phase];
 }

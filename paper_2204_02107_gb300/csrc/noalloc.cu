@@ -56,23 +56,6 @@ bool smooth235_even(int n)
     return n == 1;
 }
 
-vf::FftAxis axis_plan(int n)
-{
-    vf::FftAxis a{};
-    a.n = n;
-    int m = n, twos = 0;
-    while (m % 2 == 0) { m /= 2; ++twos; }
-    int eights = twos / 3, rem = twos % 3, k = 0;
-    if (rem == 1 && eights > 0) { --eights; a.radix[k++] = 4; a.radix[k++] = 4; }
-    else if (rem == 1) a.radix[k++] = 2;
-    else if (rem == 2) a.radix[k++] = 4;
-    for (int i = 0; i < eights; ++i) a.radix[k++] = 8;
-    while (m % 3 == 0) { m /= 3; a.radix[k++] = 3; }
-    while (m % 5 == 0) { m /= 5; a.radix[k++] = 5; }
-    a.nstages = k;
-    return a;
-}
-
 template <typename T>
 int solve(int nx, int ny, int nz, double lx, double ly, double lz, const void* f, void* p, cudaStream_t st)
 {
@@ -82,7 +65,8 @@ int solve(int nx, int ny, int nz, double lx, double ly, double lz, const void* f
     if (cells * sizeof(T) > kSpectrumBytes) return VF_ESIZE;
     if (M + 1 > kMaxAxis || ny > kMaxAxis || nz > kMaxAxis) return VF_ESIZE;
     const size_t tb = sizeof(T) == 8 ? 8 : 16;
-    if (2 * tb * (size_t)(ny > nz ? ny : nz) * sizeof(C2) > 227 * 1024) return VF_ESIZE;
+    const size_t nmax = (size_t)(ny > nz ? ny : nz);
+    if ((3 * tb * nmax + nmax) * sizeof(C2) > 227 * 1024) return VF_ESIZE;
 
     void* base = nullptr;
     if (scratch_on_current_device(&base) != cudaSuccess || !base) return VF_ECUDA;
@@ -121,10 +105,11 @@ int solve(int nx, int ny, int nz, double lx, double ly, double lz, const void* f
 
     vf::PoissonArgs<T> a{};
     a.nx = nx; a.ny = ny; a.nz = nz; a.M = M;
-    a.r = static_cast<const T*>(f);
+    a.f = const_cast<T*>(static_cast<const T*>(f));   // only read: no correction runs without a mask
     a.p = static_cast<T*>(p);
     a.mask = nullptr;
-    a.use_mask = 0;
+    a.n_near = 0;
+    a.plane_layout = 0;
     a.spec = spectrum;
     a.twx = dtw;
     a.twy = dtw + kMaxAxis;
@@ -135,14 +120,15 @@ int solve(int nx, int ny, int nz, double lx, double ly, double lz, const void* f
     a.lamz = dlam + 2 * kMaxAxis;
     for (int j = 0; j < 3; ++j) a.i2h2[j] = (T)(1.0 / (4.0 * h[j] * h[j]));
     a.invN = (T)(1.0 / (double)cells);
-    a.ax = axis_plan(M);
-    a.ay = axis_plan(ny);
-    a.az = axis_plan(nz);
+    a.ax = vf::make_fft_axis(M);
+    a.ay = vf::make_fft_axis(ny);
+    a.az = vf::make_fft_axis(nz);
+    a.ny_div = vf::make_fast_div((uint32_t)ny);
     const int per_cta = sizeof(T) == 8 ? 1024 : 2048;   // complex values per CTA in the x passes
     a.rows_per_block = per_cta / M > 0 ? per_cta / M : 1;
     a.cols_per_block = (int)tb;
     if (vf::Kernels<T>::poisson_prepare(a) != cudaSuccess) return VF_ECUDA;
-    if (vf::Kernels<T>::poisson_iteration(a, st) != cudaSuccess) return VF_ECUDA;
+    if (vf::Kernels<T>::poisson_iteration(a, 1, st) != cudaSuccess) return VF_ECUDA;
     // the stack tables must stay alive until their copies have been consumed
     if (cudaStreamSynchronize(st) != cudaSuccess) return VF_ECUDA;
     return VF_OK;

@@ -14,10 +14,12 @@ namespace vf {
 constexpr int kHistBins = 64;
 constexpr int kMaxRadixStages = 16;
 
-// Mask byte of a cell: bit 0 beta (fluid), bit 1 S (forcing region), bit 2 room region.
+// Mask byte of a cell: bit 0 beta (fluid), bit 1 S (forcing region), bit 2 room region, bit 3 "a neighbour
+// along some axis is solid" (derived from beta by vf_set_mask; the Eq. 9 correction is zero without it).
 constexpr uint8_t kBitBeta = 1u;
 constexpr uint8_t kBitS = 2u;
 constexpr uint8_t kBitRoom = 4u;
+constexpr uint8_t kBitNearSolid = 8u;
 
 // Constants of the flow kernels, in the compute precision T.
 template <typename T>
@@ -37,32 +39,98 @@ struct FlowConsts {
     T filt;       // pi^-6
 };
 
-// Pointers of one RK4 stage: q_s (stencil input), q_n, the accumulator and the output state.
+// Pointers of one RK4 stage.  Every state array holds one 4-vector (u, v, w, c) of T per cell (16 bytes for
+// float, 32 for double): q_s (stencil input), q_n, the accumulator and the output state.
 template <typename T>
 struct StageArgs {
-    const T* qs[4];
-    const T* qn[4];
-    T* acc[4];
-    T* out[4];
+    const void* qs;
+    const void* qn;
+    void* acc;
+    void* out;
     const uint8_t* mask;
 };
 
-// One FFT axis: length and radix schedule (product of radix[] == n).
+// Division by a run-time invariant d by multiply and shift (Granlund-Montgomery), exact for n < 2^31.
+struct FastDiv {
+    uint32_t d, m, s;
+};
+
+inline FastDiv make_fast_div(uint32_t d)
+{
+    FastDiv f{d, 0u, 0u};
+    if (d <= 1) return f;
+    uint32_t l = 0;
+    while ((1ull << l) < d) ++l;                       // l = ceil(log2 d)
+    f.m = (uint32_t)((((1ull << 32) * ((1ull << l) - d)) / d) + 1);
+    f.s = l;
+    return f;
+}
+
+// One radix pass of a Stockham FFT of length n: R-point butterflies over n / R groups; Ns = product of the
+// radices already applied; twiddle exponent stride n / (Ns R).
+// The same stage read as an in-place decimation-in-frequency pass: sub-length L = n / Ns, R groups of
+// m = L / R = tstride elements, twiddle W_L^(j k) = W_n^(j k Ns).
+struct FftStage {
+    int R, Ns, nb, tstride;
+    FastDiv ns_div;   // j -> j / Ns
+    FastDiv nb_div;   // item -> item / nb (row-batched passes)
+    FastDiv m_div;    // item -> item / tstride (in-place passes)
+};
+
+// One FFT axis: length and radix schedule (product of the radices == n).  Powers of two go into as many radix-8
+// passes as possible (a remainder of 2 becomes 4 x 4 or a 4), then the factors 3 and 5.
 struct FftAxis {
     int n;
     int nstages;
-    int radix[kMaxRadixStages];
+    FftStage st[kMaxRadixStages];
 };
 
-// Everything one Poisson iteration needs.  The spectrum holds (nx/2) x ny x nz complex values, kx fastest;
-// column kx = 0 packs the real spectra at kx = 0 (real part) and kx = nx/2 (imaginary part).
+inline FftAxis make_fft_axis(int n)
+{
+    FftAxis a{};
+    a.n = n;
+    int rad[kMaxRadixStages], k = 0;
+    int m = n, twos = 0;
+    while (m % 2 == 0) { m /= 2; ++twos; }
+    int eights = twos / 3;
+    const int rem = twos % 3;
+    if (rem == 1 && eights > 0) { --eights; rad[k++] = 4; rad[k++] = 4; }
+    else if (rem == 1) rad[k++] = 2;
+    else if (rem == 2) rad[k++] = 4;
+    for (int i = 0; i < eights && k < kMaxRadixStages; ++i) rad[k++] = 8;
+    while (m % 3 == 0 && k < kMaxRadixStages) { m /= 3; rad[k++] = 3; }
+    while (m % 5 == 0 && k < kMaxRadixStages) { m /= 5; rad[k++] = 5; }
+    a.nstages = k;
+    int Ns = 1;
+    for (int s = 0; s < k; ++s) {
+        FftStage& S = a.st[s];
+        S.R = rad[s];
+        S.Ns = Ns;
+        S.nb = n / S.R;
+        S.tstride = n / (Ns * S.R);
+        S.ns_div = make_fast_div((uint32_t)Ns);
+        S.nb_div = make_fast_div((uint32_t)S.nb);
+        S.m_div = make_fast_div((uint32_t)S.tstride);
+        Ns *= S.R;
+    }
+    return a;
+}
+
+// Everything one Poisson iteration needs.  Two spectrum layouts, (nx/2) x ny x nz complex values in both:
+//   tile  : [z][y][kx], kx fastest; the y and z passes work on tiles of cols_per_block consecutive kx columns;
+//   plane : [kx][z][y], y fastest; one CTA per kx transforms its whole (y, z) plane in shared memory (y FFT,
+//           z FFT, eigenvalue division, inverse z and y FFTs), used when a plane fits in one CTA.
+// Column kx = 0 packs the real spectra at kx = 0 (real part) and kx = nx/2 (imaginary part).
 template <typename T>
 struct PoissonArgs {
     int nx, ny, nz, M;        // M = nx / 2
-    const T* r;               // right-hand side D u* (or the f of a plain solve)
-    T* p;                     // in: p^k (for the (1 - beta) term), out: p^{k+1}
+    T* f;                     // right-hand side read by the x forward pass (r, plus the Eq. 9 correction)
+    T* p;                     // in: p^k (for the correction), out: p^{k+1}
     const uint8_t* mask;
-    int use_mask;             // 1: f = r + sum_j delta_j((1 - beta) delta_j p^k); 0: f = r
+    const int* near_list;     // ascending cells with a solid axis neighbour (where the correction is nonzero)
+    T* near_r;                // r at those cells, saved by the first correction of a step
+    int n_near;
+    int plane_layout;
     void* spec;               // complex T [M * ny * nz]
     const void* twx;          // complex T [M]:  exp(-2 pi i m / M)
     const void* twy;          // complex T [ny]
@@ -71,17 +139,42 @@ struct PoissonArgs {
     const T* lamx;            // [M]  sin^2(2 pi kx / nx) / hx^2 (kx = 0 and nx/2 share column 0, both 0)
     const T* lamy;            // [ny]
     const T* lamz;            // [nz]
+    const int* krev_y;        // [ny] spectral index held at each position after the in-place forward y FFT
+    const int* krev_z;        // [nz]
     T i2h2[3];                // (1 / (2 h_j))^2
     T invN;                   // 1 / (nx ny nz)
     FftAxis ax, ay, az;
+    FastDiv ny_div;           // i -> i / ny (plane passes)
     int rows_per_block;       // rows of the x passes per CTA
-    int cols_per_block;       // kx columns of the y / z passes per CTA
+    int cols_per_block;       // kx columns of the y / z tile passes per CTA
 };
+
+// Spectral index at each position after the in-place (decimation-in-frequency) forward FFT of an axis: the
+// position p = d_0 n/R_0 + d_1 n/(R_0 R_1) + ... holds frequency k = d_0 + R_0 (d_1 + R_1 (d_2 + ...)).
+inline void digit_reversal(const FftAxis& ax, int* out)
+{
+    for (int p = 0; p < ax.n; ++p) {
+        int rem = p, L = ax.n, k = 0, mult = 1;
+        for (int s = 0; s < ax.nstages; ++s) {
+            const int m = L / ax.st[s].R;
+            const int d = rem / m;
+            rem -= d * m;
+            k += d * mult;
+            mult *= ax.st[s].R;
+            L = m;
+        }
+        out[p] = k;
+    }
+}
+
+// Block size of the plane kernel (one CTA per kx plane, the plane in shared memory, at most 200 KB).
+constexpr int kPlaneThreads = 1024;
 
 // Reduction scratch: per-CTA partial sums and histogram counts, and the output records.
 struct ReduceArgsDev {
     double* partial;          // [nblocks * kRedSlots]
-    int* hist_partial;        // [nblocks * (kHistBins + 2)]
+    unsigned long long* hist_accum;   // [kHistBins + 2], zero between launches
+    unsigned int* done;       // CTAs finished in the current launch, zero between launches
     vf_reduce* out;           // single record (vf_reductions)
     vf_reduce* history;       // ring buffer
     long long* hist_count;    // records written so far
@@ -104,31 +197,40 @@ struct LaunchHook {
 template <typename T>
 struct Kernels {
     static cudaError_t stage(int s, const StageArgs<T>& a, const FlowConsts<T>& k, cudaStream_t st);
-    static cudaError_t divergence(const T* u, const T* v, const T* w, T* r, const FlowConsts<T>& k,
-                                  cudaStream_t st);
-    // u = beta (u* - G p); ticks the device step counter.  c* is copied to out[3] when out[3] != cs.
-    static cudaError_t project(const T* const us[3], const T* cs, const T* p, T* const out[4],
-                               const uint8_t* mask, long long* step_counter, const FlowConsts<T>& k,
-                               cudaStream_t st);
-    static cudaError_t filter(const T* const in[4], T* const out[4], const uint8_t* mask, const FlowConsts<T>& k,
+    static cudaError_t divergence(const void* qstar, T* r, const FlowConsts<T>& k, cudaStream_t st);
+    // u = beta (u* - dt G p), c* passes through; ticks the device step counter
+    static cudaError_t project(const void* qstar, const T* p, void* out, const uint8_t* mask, long long* step_counter,
+                               const FlowConsts<T>& k, cudaStream_t st);
+    static cudaError_t filter(const void* in, void* out, const uint8_t* mask, const FlowConsts<T>& k,
                               cudaStream_t st);
-    static cudaError_t reduce(const T* const q[4], const uint8_t* mask, const FlowConsts<T>& k,
-                              const ReduceArgsDev& r, int to_history, cudaStream_t st);
+    static cudaError_t reduce(const void* q, const uint8_t* mask, const FlowConsts<T>& k, const ReduceArgsDev& r,
+                              int to_history, cudaStream_t st);
     static int reduce_blocks(const FlowConsts<T>& k);
     static cudaError_t poisson_prepare(const PoissonArgs<T>& a);   // shared-memory limits; call outside capture
-    static cudaError_t poisson_iteration(const PoissonArgs<T>& a, cudaStream_t st, const LaunchHook* hook = nullptr);
-    static cudaError_t convert_in(const void* src, int src_fp64, T* dst, size_t n, double scale,
+    // one iteration of Eq. 9; `first` marks the first iteration of a step (saves r at the near-solid cells)
+    static cudaError_t poisson_iteration(const PoissonArgs<T>& a, int first, cudaStream_t st,
+                                         const LaunchHook* hook = nullptr);
+    static bool plane_fits(int ny, int nz);
+    // component comp (0..3) of a 4-vector state array, or a scalar array when comp < 0
+    static cudaError_t convert_in(const void* src, int src_fp64, void* dst, int comp, size_t n, double scale,
                                   const uint8_t* mask, cudaStream_t st);
-    static cudaError_t convert_out(const T* src, void* dst, int dst_fp64, size_t n, double scale,
+    static cudaError_t convert_out(const void* src, int comp, void* dst, int dst_fp64, size_t n, double scale,
                                    cudaStream_t st);
-    static cudaError_t apply_mask(T* f, const uint8_t* mask, size_t n, cudaStream_t st);
+    static cudaError_t apply_mask(void* q4, const uint8_t* mask, size_t n, cudaStream_t st);
     static size_t fft_smem_x(const PoissonArgs<T>& a);
-    static size_t fft_smem_yz(const PoissonArgs<T>& a, int n);
+    static size_t fft_smem_yz(const PoissonArgs<T>& a, int n, int buffers);
+    static size_t fft_smem_plane(const PoissonArgs<T>& a);
 };
 
 // Mask helpers (precision independent).
 cudaError_t mask_merge(uint8_t* mask, const uint8_t* src, uint8_t bit, size_t n, cudaStream_t st);
 cudaError_t mask_fill(uint8_t* mask, uint8_t value, size_t n, cudaStream_t st);
 cudaError_t mask_count_solid(const uint8_t* mask, size_t n, unsigned long long* d_count, cudaStream_t st);
+cudaError_t mask_mark_near_solid(uint8_t* mask, int nx, int ny, int nz, cudaStream_t st);
+// Ordered list of the cells whose near-solid bit is set: per-chunk counts, then (after a host-side exclusive
+// scan into offsets) the cell indices in ascending order.
+constexpr int kListChunk = 1024;
+cudaError_t mask_near_counts(const uint8_t* mask, size_t n, int* chunk_counts, cudaStream_t st);
+cudaError_t mask_near_fill(const uint8_t* mask, size_t n, const int* chunk_offsets, int* list, cudaStream_t st);
 
 }  // namespace vf

@@ -50,12 +50,16 @@ def test_taylor_green_fp64_100_steps(torch):
     g.close()
 
 
+@pytest.mark.parametrize("fft_path", ["plane", "tile"])
 @pytest.mark.parametrize("shape,boxes", [
     ((40, 24, 20), [(12, 16, 6, 10, 2, 8)]),
     ((48, 30, 18), [(20, 26, 12, 20, 2, 9), (30, 34, 4, 8, 2, 5)]),
 ])
-def test_masked_room_fp64_100_steps(torch, shape, boxes):
-    """Walls, inlet/outlet duct, boxes, forcing, filter, 4 pressure iterations: 100 steps vs the oracle."""
+def test_masked_room_fp64_100_steps(torch, monkeypatch, shape, boxes, fft_path):
+    """Walls, inlet/outlet duct, boxes, forcing, filter, 4 pressure iterations: 100 steps vs the oracle, with the
+    y-z transforms done per kx plane in shared memory or as separate tile passes."""
+    if fft_path == "tile":
+        monkeypatch.setenv("VF_TILE_FFT", "1")
     room, prm, geom, st0 = room_case(*shape, boxes=boxes)
     ref, recs = F.run(st0.copy(), geom, prm, 100)
     g = gpu_grid(prm, room.beta, room.S, room.room, "fp64")
@@ -96,10 +100,16 @@ def test_fp32_one_step_from_identical_state(torch, shape):
     g.close()
 
 
+@pytest.mark.parametrize("fft_path", ["plane", "tile"])
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-@pytest.mark.parametrize("shape", [(8, 8, 8), (10, 12, 16), (20, 30, 18), (40, 10, 50), (72, 36, 20), (256, 8, 8)])
-def test_poisson_solve_matches_oracle(torch, precision, shape):
-    """vf_poisson_solve (forward 3D FFT, division by lambda, inverse) against the oracle's numpy.fft solve."""
+@pytest.mark.parametrize("shape", [(8, 8, 8), (10, 12, 16), (20, 30, 18), (40, 10, 50), (72, 36, 20), (256, 8, 8),
+                                   (16, 128, 128)])
+def test_poisson_solve_matches_oracle(torch, monkeypatch, precision, shape, fft_path):
+    """vf_poisson_solve (forward 3D FFT, division by lambda, inverse) against the oracle's numpy.fft solve, with
+    the y-z transforms per kx plane or as tile passes (a 128 x 128 plane exceeds shared memory in FP64, so that
+    case takes the tile path in both settings)."""
+    if fft_path == "tile":
+        monkeypatch.setenv("VF_TILE_FFT", "1")
     nx, ny, nz = shape
     prm = F.Params(nx=nx, ny=ny, nz=nz, lx=nx * 0.1, ly=ny * 0.07, lz=nz * 0.13, nu=0.0, dt=1.0)
     rng = np.random.default_rng(nx * 10007 + ny * 101 + nz)
