@@ -173,6 +173,52 @@ int vf_info(const vf_grid* g, double* t, int64_t* step, int64_t* cells, int64_t*
  * scratch; stream-ordered on the grid's stream, returns without waiting. */
 int vf_poisson_solve(vf_grid* g, const void* f, void* p);
 
+/* ---- batched rooms and continuous batching (many rooms advanced together) --------------------------------- */
+
+/* Device bytes vf_create_grid will allocate for a description (used for admission by memory budget). */
+int64_t vf_grid_bytes(const vf_grid_desc* d);
+
+typedef struct vf_batch vf_batch;
+typedef struct vf_batch_desc {
+    int32_t max_slots;           /* rooms held at once */
+    int64_t hbm_budget_bytes;    /* admission limit: sum of vf_grid_bytes of the rooms held */
+    int32_t reduce_every;        /* record each room's reductions every k batch steps (0 = never) */
+    void* cuda_stream;           /* stream the batch graph runs on; NULL -> a stream the batch creates */
+} vf_batch_desc;
+
+/* Empty batch.  One batch step advances every running room by one time step through a single CUDA graph launch
+ * with one independent branch per room (the rooms' kernels run concurrently); a room's arithmetic is the same as
+ * alone, so its fields are bitwise identical alone and in any mix. */
+int vf_batch_create(const vf_batch_desc* d, vf_batch** out);
+int vf_batch_destroy(vf_batch* b);
+
+/* Admit a room into a free slot: a grid is created from *gd (its cuda_stream is ignored), given the mask beta, the
+ * forcing region S (may be NULL) with set points u_set, c_set, the room region (may be NULL: all fluid cells) and
+ * the initial scalar c0 (may be NULL: zero; nx*ny*nz values, double if c0_is_fp64), all in `mem`; it will run
+ * `steps` steps.  *slot receives the slot.  VF_ENOMEM when no slot is free or its vf_grid_bytes would exceed the
+ * budget (nothing is allocated then). */
+int vf_batch_add(vf_batch* b, const vf_grid_desc* gd, const uint8_t* beta, const uint8_t* S, const uint8_t* room,
+                 const double u_set[3], double c_set, const void* c0, int c0_is_fp64, int64_t steps, int mem,
+                 int32_t* slot);
+
+/* Enqueue up to n batch steps (async).  Every running room advances by min(n, its remaining steps); the steps are
+ * launched in chunks that end when a room reaches its target, which then stops and is reported by vf_batch_poll. */
+int vf_batch_step(vf_batch* b, int64_t n);
+int vf_batch_sync(vf_batch* b);
+
+/* Wait for enqueued steps; write up to max_slots finished slots to done_slots, their total to *n_done. */
+int vf_batch_poll(vf_batch* b, int32_t* done_slots, int32_t max_slots, int32_t* n_done);
+
+/* The grid of a slot (NULL if empty): read its fields and history with the vf_grid calls after vf_batch_poll. */
+vf_grid* vf_batch_grid(vf_batch* b, int32_t slot);
+
+/* Free a slot and its memory (waits for enqueued steps). */
+int vf_batch_remove(vf_batch* b, int32_t slot);
+
+/* Running and finished rooms, bytes held and batch steps taken. */
+int vf_batch_info(const vf_batch* b, int32_t* active, int32_t* done, int64_t* bytes_in_use, int64_t* batch_steps);
+const char* vf_batch_last_error(const vf_batch* b);
+
 /* ---- Poisson solve without device allocation --------------------------------------------------------------- */
 
 /* The paper has no counterpart of this call; it exists for callers that cannot allocate device memory (code that

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(HERE, "libventflow.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CUDA_SOURCES = ["flow_kernels.cu", "fft_kernels.cu", "noalloc.cu"]
-HOST_SOURCES = ["capi.cpp", "metrics.cpp"]
+HOST_SOURCES = ["capi.cpp", "batch.cpp", "metrics.cpp"]
 
 
 def nvcc_path():

@@ -15,77 +15,13 @@
 #include <string>
 #include <vector>
 
-#include "vf_internal.h"
+#include "grid.h"
 
 using vf::FftAxis;
 using vf::FlowConsts;
 using vf::Kernels;
 using vf::PoissonArgs;
 using vf::StageArgs;
-
-struct vf_grid {
-    vf_grid_desc d{};
-    bool fp64 = false;
-    size_t N = 0, esz = 0;
-    cudaStream_t stream = nullptr;
-    bool own_stream = false;
-    cudaStream_t cap_stream = nullptr;
-    vf_allocator alloc{};
-    bool have_alloc = false;
-    std::vector<void*> allocs;
-    size_t bytes = 0;
-    int alloc_count = 0;
-    int fail_alloc_at = 0;       // fault injection: the n-th allocation of this grid fails (0 = off)
-
-    void* q = nullptr;           // state (u, v, w, c) per cell as a 4-vector
-    void* acc = nullptr;         // RK4 accumulator
-    void* qa = nullptr;          // RK4 stage states
-    void* qb = nullptr;
-    void* p = nullptr;
-    void* f = nullptr;           // right-hand side of Eq. 9: D u* / dt, plus the correction next to solids
-    void* spec = nullptr;
-    int* near_list = nullptr;    // cells with a solid axis neighbour, ascending (capacity N)
-    void* near_r = nullptr;      // D u* / dt at those cells (capacity N)
-    int n_near = 0;
-    bool plane_layout = false;
-    void* staging = nullptr;     // N * 8 bytes
-    uint8_t* mask = nullptr;
-    void* twx = nullptr;
-    void* twy = nullptr;
-    void* twz = nullptr;
-    void* twr = nullptr;
-    void* lamx = nullptr;
-    void* lamy = nullptr;
-    void* lamz = nullptr;
-    int* krev_y = nullptr;       // digit-reversal tables of the in-place y and z transforms
-    int* krev_z = nullptr;
-
-    double* red_partial = nullptr;
-    unsigned long long* hist_accum = nullptr;
-    unsigned int* red_done = nullptr;
-    vf_reduce* red_out = nullptr;
-    vf_reduce* history = nullptr;
-    long long* dev_counters = nullptr;   // [0] history count, [1] step counter
-    int* nonfinite = nullptr;
-    unsigned long long* solid_count = nullptr;
-    int nred = 0;
-
-    FftAxis ax{}, ay{}, az{};
-    int rows_per_block = 1, cols_per_block = 16;
-
-    cudaGraphExec_t gexec[2]{nullptr, nullptr};
-    bool graph_ok = false;
-    bool use_graph = true;
-
-    int status = VF_OK;
-    std::string err;
-    bool mask_set = false;
-    bool has_solid = false;
-    double uset[3]{0, 0, 0};
-    double cset = 0;
-    int64_t step = 0;
-    double t0 = 0;
-};
 
 namespace {
 
@@ -405,7 +341,39 @@ cudaError_t mask_fields(vf_grid* g)
 
 }  // namespace
 
+namespace vf_engine {
+
+cudaError_t enqueue_step(vf_grid* g, cudaStream_t st, bool with_reduce)
+{
+    return ::enqueue_step(g, st, with_reduce);
+}
+
+size_t grid_bytes(const vf_grid_desc& d)
+{
+    auto r256 = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    const size_t esz = d.precision == VF_FP64 ? 8 : 4, cpx = 2 * esz;
+    const size_t N = (size_t)d.nx * d.ny * d.nz, M = (size_t)d.nx / 2;
+    FlowConsts<float> k{};
+    k.nx = d.nx; k.ny = d.ny; k.nz = d.nz;
+    const size_t nred = (size_t)Kernels<float>::reduce_blocks(k);
+    size_t b = 4 * r256(4 * N * esz) + 4 * r256(N * esz) + r256(N * 4) + r256(N * 8) + r256(N);
+    b += r256(nred * vf::kRedSlots * 8) + r256((vf::kHistBins + 2) * 8) + r256(4) + r256(sizeof(vf_reduce));
+    b += r256((size_t)d.history_capacity * sizeof(vf_reduce)) + r256(16) + r256(4) + r256(8);
+    b += r256(M * cpx) + r256(d.ny * cpx) + r256(d.nz * cpx) + r256((M + 1) * cpx);
+    b += r256(M * esz) + r256(d.ny * esz) + r256(d.nz * esz) + r256(d.ny * 4) + r256(d.nz * 4);
+    return b;
+}
+
+}  // namespace vf_engine
+
 extern "C" {
+
+int64_t vf_grid_bytes(const vf_grid_desc* d)
+{
+    if (!d) return -1;
+    return (int64_t)vf_engine::grid_bytes(*d);
+}
+
 
 int vf_grid_desc_default(vf_grid_desc* d)
 {

@@ -1,0 +1,85 @@
+// Internal definition of a grid (one room) shared by the C ABI (capi.cpp) and the batch engine (batch.cpp).
+#pragma once
+
+#include <cuda_runtime_api.h>
+
+#include <string>
+#include <vector>
+
+#include "vf_internal.h"
+
+struct vf_grid {
+    vf_grid_desc d{};
+    bool fp64 = false;
+    size_t N = 0, esz = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cudaStream_t cap_stream = nullptr;
+    vf_allocator alloc{};
+    bool have_alloc = false;
+    std::vector<void*> allocs;
+    size_t bytes = 0;
+    int alloc_count = 0;
+    int fail_alloc_at = 0;       // fault injection: the n-th allocation of this grid fails (0 = off)
+
+    void* q = nullptr;           // state (u, v, w, c) per cell as a 4-vector
+    void* acc = nullptr;         // RK4 accumulator
+    void* qa = nullptr;          // RK4 stage states
+    void* qb = nullptr;
+    void* p = nullptr;
+    void* f = nullptr;           // right-hand side of Eq. 9: D u* / dt, plus the correction next to solids
+    void* spec = nullptr;
+    int* near_list = nullptr;    // cells with a solid axis neighbour, ascending (capacity N)
+    void* near_r = nullptr;      // D u* / dt at those cells (capacity N)
+    int n_near = 0;
+    bool plane_layout = false;
+    void* staging = nullptr;     // N * 8 bytes
+    uint8_t* mask = nullptr;
+    void* twx = nullptr;
+    void* twy = nullptr;
+    void* twz = nullptr;
+    void* twr = nullptr;
+    void* lamx = nullptr;
+    void* lamy = nullptr;
+    void* lamz = nullptr;
+    int* krev_y = nullptr;       // digit-reversal tables of the in-place y and z transforms
+    int* krev_z = nullptr;
+
+    double* red_partial = nullptr;
+    unsigned long long* hist_accum = nullptr;
+    unsigned int* red_done = nullptr;
+    vf_reduce* red_out = nullptr;
+    vf_reduce* history = nullptr;
+    long long* dev_counters = nullptr;   // [0] history count, [1] step counter
+    int* nonfinite = nullptr;
+    unsigned long long* solid_count = nullptr;
+    int nred = 0;
+
+    vf::FftAxis ax{}, ay{}, az{};
+    int rows_per_block = 1, cols_per_block = 16;
+
+    cudaGraphExec_t gexec[2]{nullptr, nullptr};
+    bool graph_ok = false;
+    bool use_graph = true;
+
+    int status = VF_OK;
+    std::string err;
+    bool mask_set = false;
+    bool has_solid = false;
+    double uset[3]{0, 0, 0};
+    double cset = 0;
+    int64_t step = 0;
+    double t0 = 0;
+};
+
+
+namespace vf_engine {
+
+// Enqueue one step of grid g on stream st (with the FP64 reductions if with_reduce); the launches a single-room
+// vf_step replays.  Returns the first CUDA error.
+cudaError_t enqueue_step(vf_grid* g, cudaStream_t st, bool with_reduce);
+
+// Device bytes vf_create_grid allocates for a description (each buffer rounded up to 256 bytes).
+size_t grid_bytes(const vf_grid_desc& d);
+
+}  // namespace vf_engine

@@ -41,6 +41,11 @@ class VfGridDesc(C.Structure):
                 ("cuda_stream", C.c_void_p), ("alloc", C.POINTER(VfAllocator))]
 
 
+class VfBatchDesc(C.Structure):
+    _fields_ = [("max_slots", C.c_int32), ("hbm_budget_bytes", C.c_int64), ("reduce_every", C.c_int32),
+                ("cuda_stream", C.c_void_p)]
+
+
 class VfReduce(C.Structure):
     _fields_ = [("t", C.c_double), ("step", C.c_int64), ("ke", C.c_double), ("div_max", C.c_double),
                 ("div_l2", C.c_double), ("u_max", C.c_double), ("c_total", C.c_double), ("c_room", C.c_double),
@@ -83,6 +88,20 @@ _SIGNATURES = {
     "vf_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                           C.POINTER(C.c_int64)]),
     "vf_poisson_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "vf_grid_bytes": (C.c_int64, [C.POINTER(VfGridDesc)]),
+    "vf_batch_create": (C.c_int, [C.POINTER(VfBatchDesc), C.POINTER(C.c_void_p)]),
+    "vf_batch_destroy": (C.c_int, [C.c_void_p]),
+    "vf_batch_add": (C.c_int, [C.c_void_p, C.POINTER(VfGridDesc), C.c_void_p, C.c_void_p, C.c_void_p,
+                               C.POINTER(C.c_double), C.c_double, C.c_void_p, C.c_int, C.c_int64, C.c_int,
+                               C.POINTER(C.c_int32)]),
+    "vf_batch_step": (C.c_int, [C.c_void_p, C.c_int64]),
+    "vf_batch_sync": (C.c_int, [C.c_void_p]),
+    "vf_batch_poll": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.c_int32, C.POINTER(C.c_int32)]),
+    "vf_batch_grid": (C.c_void_p, [C.c_void_p, C.c_int32]),
+    "vf_batch_remove": (C.c_int, [C.c_void_p, C.c_int32]),
+    "vf_batch_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int64),
+                                C.POINTER(C.c_int64)]),
+    "vf_batch_last_error": (C.c_char_p, [C.c_void_p]),
     "vf_poisson_solve_noalloc": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_double, C.c_double, C.c_double,
                                            C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
     "vf_poisson_noalloc_max_cells": (C.c_int64, [C.c_int32]),
@@ -148,40 +167,145 @@ def default_desc():
     return d
 
 
+def make_desc(nx, ny, nz, lx, ly, lz, nu, dt, alpha_c=None, tau_f=0.0, body_force=(0.0, 0.0, 0.0),
+              n_pressure_iters=4, filter=True, precision="fp32", history_capacity=4096, stream=None):
+    d = default_desc()
+    d.nx, d.ny, d.nz = nx, ny, nz
+    d.lx, d.ly, d.lz = lx, ly, lz
+    d.nu = nu
+    d.alpha_c = -1.0 if alpha_c is None else alpha_c
+    d.dt = dt
+    d.tau_f = tau_f
+    for j in range(3):
+        d.body_force[j] = body_force[j]
+    d.n_pressure_iters = n_pressure_iters
+    d.filter = 1 if filter else 0
+    d.precision = PRECISIONS[precision]
+    d.history_capacity = history_capacity
+    d.cuda_stream = C.c_void_p(stream) if stream else None
+    return d
+
+
+def room_desc(room, precision="fp32", filter=True, n_pressure_iters=4, nu=1.6e-5, dt=None, **kw):
+    """Grid description of a ``rooms.Room``."""
+    return make_desc(room.nx, room.ny, room.nz, room.lx, room.ly, room.lz, nu, room.dt if dt is None else dt,
+                     filter=filter, n_pressure_iters=n_pressure_iters, precision=precision, **kw)
+
+
+def grid_bytes(desc):
+    return int(lib().vf_grid_bytes(C.byref(desc)))
+
+
+class Batch:
+    """Rooms of uneven size advanced together (vf_batch_*): one CUDA graph launch per batch step, one branch per
+    room.  Slots are admitted against ``hbm_budget_bytes``."""
+
+    def __init__(self, max_slots, hbm_budget_bytes, reduce_every=1, stream=None):
+        d = VfBatchDesc(max_slots, int(hbm_budget_bytes), reduce_every, C.c_void_p(stream) if stream else None)
+        h = C.c_void_p()
+        rc = lib().vf_batch_create(C.byref(d), C.byref(h))
+        if rc != VF_OK:
+            raise VentflowError(rc, "vf_batch_create")
+        self._h = h
+        self.max_slots = max_slots
+        self._desc = {}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().vf_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc, what):
+        if rc != VF_OK:
+            msg = lib().vf_batch_last_error(self._h)
+            raise VentflowError(rc, f"{what}: {msg.decode() if msg else ''}")
+
+    def add(self, desc, beta, S, u_set, c_set, steps, room=None, c0=None):
+        """Admit a room; returns its slot.  Raises VentflowError(VF_ENOMEM) when it does not fit."""
+        n = desc.nx * desc.ny * desc.nz
+        pb, mem, kb = _pointer(beta, np.uint8, n)
+        ps = _pointer(S, np.uint8, n) if S is not None else (None, mem, None)
+        pr = _pointer(room, np.uint8, n) if room is not None else (None, mem, None)
+        pc = _pointer(c0, np.float64, n) if c0 is not None else (None, mem, None)
+        us = (C.c_double * 3)(*u_set)
+        slot = C.c_int32()
+        rc = lib().vf_batch_add(self._h, C.byref(desc), pb, ps[0], pr[0], us, float(c_set), pc[0], 1, int(steps),
+                                mem, C.byref(slot))
+        self._check(rc, "vf_batch_add")
+        self._desc[slot.value] = desc
+        return slot.value
+
+    def step(self, n):
+        self._check(lib().vf_batch_step(self._h, int(n)), "vf_batch_step")
+
+    def sync(self):
+        self._check(lib().vf_batch_sync(self._h), "vf_batch_sync")
+
+    def poll(self):
+        buf = (C.c_int32 * self.max_slots)()
+        n = C.c_int32()
+        self._check(lib().vf_batch_poll(self._h, buf, self.max_slots, C.byref(n)), "vf_batch_poll")
+        return [buf[i] for i in range(min(n.value, self.max_slots))]
+
+    def grid(self, slot):
+        """Borrowed Grid of a slot (valid until the slot is removed)."""
+        h = lib().vf_batch_grid(self._h, int(slot))
+        if not h:
+            raise VentflowError(VF_EINVAL, f"slot {slot} is empty")
+        return Grid.borrowed(h, self._desc[slot])
+
+    def remove(self, slot):
+        self._check(lib().vf_batch_remove(self._h, int(slot)), "vf_batch_remove")
+        self._desc.pop(slot, None)
+
+    def info(self):
+        a, dn, b, s = C.c_int32(), C.c_int32(), C.c_int64(), C.c_int64()
+        self._check(lib().vf_batch_info(self._h, C.byref(a), C.byref(dn), C.byref(b), C.byref(s)), "vf_batch_info")
+        return dict(active=a.value, done=dn.value, bytes_in_use=b.value, batch_steps=s.value)
+
+
 class Grid:
     """One room grid on the current CUDA device (``vf_create_grid``).  Sizes (nx, ny, nz) must be even, >= 8 and
     2-3-5 smooth.  ``precision`` is 'fp64' or 'fp32' (FP32 fields, FP64 reductions)."""
 
     def __init__(self, nx, ny, nz, lx, ly, lz, nu, dt, alpha_c=None, tau_f=0.0, body_force=(0.0, 0.0, 0.0),
                  n_pressure_iters=4, filter=True, precision="fp32", history_capacity=4096, stream=None):
-        d = default_desc()
-        d.nx, d.ny, d.nz = nx, ny, nz
-        d.lx, d.ly, d.lz = lx, ly, lz
-        d.nu = nu
-        d.alpha_c = -1.0 if alpha_c is None else alpha_c
-        d.dt = dt
-        d.tau_f = tau_f
-        for j in range(3):
-            d.body_force[j] = body_force[j]
-        d.n_pressure_iters = n_pressure_iters
-        d.filter = 1 if filter else 0
-        d.precision = PRECISIONS[precision]
-        d.history_capacity = history_capacity
-        d.cuda_stream = C.c_void_p(stream) if stream else None
+        d = make_desc(nx, ny, nz, lx, ly, lz, nu, dt, alpha_c, tau_f, body_force, n_pressure_iters, filter,
+                      precision, history_capacity, stream)
         h = C.c_void_p()
         rc = lib().vf_create_grid(C.byref(d), C.byref(h))
         if rc != VF_OK:
             raise VentflowError(rc, "vf_create_grid")
+        self._owned = True
         self._h = h
         self.desc = d
         self.shape = (nz, ny, nx)
         self.n = nx * ny * nz
         self.precision = precision
 
+    @classmethod
+    def borrowed(cls, handle, desc):
+        """A view of a grid owned by someone else (a batch slot): never destroyed by this object."""
+        g = cls.__new__(cls)
+        g._owned = False
+        g._h = C.c_void_p(handle)
+        g.desc = desc
+        g.shape = (desc.nz, desc.ny, desc.nx)
+        g.n = desc.nx * desc.ny * desc.nz
+        g.precision = "fp64" if desc.precision == VF_FP64 else "fp32"
+        return g
+
     # -- lifecycle
     def close(self):
         if getattr(self, "_h", None):
-            lib().vf_destroy(self._h)
+            if getattr(self, "_owned", True):
+                lib().vf_destroy(self._h)
             self._h = None
 
     def __del__(self):
