@@ -88,8 +88,9 @@ typedef struct vf_reduce {
     double t;                    /* simulated time of the state [s] */
     int64_t step;                /* steps taken to reach it */
     double ke;                   /* 1/2 sum dV |u|^2 */
-    double div_max;              /* max |D u| */
-    double div_l2;               /* sqrt(sum dV (D u)^2) */
+    double div_max;              /* max |D u|: records taken by vf_step use the velocity right after the
+                                    projection (before the filter), vf_reductions the current velocity */
+    double div_l2;               /* sqrt(sum dV (D u)^2), same velocity as div_max */
     double u_max;                /* max over cells and components of |u_i| */
     double c_total;              /* sum dV c over all cells */
     double c_room;               /* sum dV c over room cells */

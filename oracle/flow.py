@@ -322,11 +322,12 @@ def histogram(c, room):
     return counts, under, over
 
 
-def reductions(state: State, geom: Geometry, prm: Params):
-    """Per-step diagnostics of a state, all in FP64."""
+def reductions(state: State, geom: Geometry, prm: Params, div_velocity=None):
+    """Diagnostics of a state, all in FP64.  The divergence is that of ``div_velocity`` (u, v, w) when given,
+    else of the state's velocity."""
     dV = prm.cell_volume
     u, v, w, c = state.u, state.v, state.w, state.c
-    div = divergence(u, v, w, prm)
+    div = divergence(*(div_velocity if div_velocity is not None else (u, v, w)), prm)
     counts, under, over = histogram(c, geom.room)
     room = geom.room
     return {
@@ -354,13 +355,15 @@ def step(state: State, geom: Geometry, prm: Params, with_budget=False):
     """Advance one time step; returns (new_state, record).
 
     Order: RK4 predictor on (u, v, w, c) -> r = D u* -> n iterations of Eq. 9 warm-started from the previous p ->
-    u = beta (u* - grad p) -> sixth-order filter of u, v, w, c and re-mask (if enabled) -> reductions."""
+    u = beta (u* - grad p) -> sixth-order filter of u, v, w, c and re-mask (if enabled) -> reductions of the new
+    state, whose divergence entries are those of the projected velocity (before the filter)."""
     budget = {} if with_budget else None
     q = [state.u, state.v, state.w, state.c]
     us, vs, ws, cs = rk4_predictor(q, geom, prm, record=budget)
     r = divergence(us, vs, ws, prm)
     p = pressure_iterations(r, state.p, geom, prm)
     u, v, w = project(us, vs, ws, p, geom, prm)
+    projected = (u, v, w)
     c = cs
     if budget is not None:
         budget['c_star_total'] = prm.cell_volume * float(np.sum(cs))
@@ -372,7 +375,8 @@ def step(state: State, geom: Geometry, prm: Params, with_budget=False):
     elif budget is not None:
         budget['mask_loss'] = 0.0
     new = State(u, v, w, c, p, state.t + prm.dt, state.step + 1)
-    rec = reductions(new, geom, prm)
+    # the step's divergence diagnostic measures the projection: D u right after it, before the filter (Sec. 2.2)
+    rec = reductions(new, geom, prm, div_velocity=projected)
     if budget is not None:
         rec.update(budget)
     return new, rec

@@ -210,10 +210,12 @@ cudaError_t enqueue_step_t(vf_grid* g, cudaStream_t st, bool with_reduce, const 
         return e;
     mark(VF_PHASE_PROJECT);
     if (g->d.filter) {
-        if ((e = Kernels<T>::filter(g->acc, g->q, g->mask, k, st)) != cudaSuccess) return e;
+        // with the filter on, the reductions ride along in the filter kernel
+        const vf::ReduceArgsDev ra = reduce_args(g);
+        if ((e = Kernels<T>::filter(g->acc, g->q, g->mask, k, with_reduce ? &ra : nullptr, 1, st)) != cudaSuccess)
+            return e;
         mark(VF_PHASE_FILTER);
-    }
-    if (with_reduce) {
+    } else if (with_reduce) {
         if ((e = Kernels<T>::reduce(g->q, g->mask, k, reduce_args(g), 1, st)) != cudaSuccess) return e;
         mark(VF_PHASE_REDUCE);
     }

@@ -177,6 +177,7 @@ __global__ void __launch_bounds__(TX * TY) k_div(const void* __restrict__ q, T* 
     const int xm = wrap(x - 1, nx), xp = wrap(x + 1, nx);
     T wzm = ld1<T>(q, wrap(z0 - 1, nz) * plane + rowc + x, 2);
     T wz0 = ld1<T>(q, z0 * plane + rowc + x, 2);
+#pragma unroll 4
     for (int z = z0; z < z1; ++z) {
         const int zb = z * plane;
         const T wzp = ld1<T>(q, wrap(z + 1, nz) * plane + rowc + x, 2);
@@ -210,6 +211,7 @@ __global__ void __launch_bounds__(TX * TY) k_project(const void* __restrict__ qs
     const int xm = wrap(x - 1, nx), xp = wrap(x + 1, nx);
     T pzm = __ldg(p + wrap(z0 - 1, nz) * plane + rowc + x);
     T pz0 = __ldg(p + z0 * plane + rowc + x);
+#pragma unroll 4
     for (int z = z0; z < z1; ++z) {
         const int zb = z * plane;
         const int ic = zb + rowc + x;
@@ -227,72 +229,13 @@ __global__ void __launch_bounds__(TX * TY) k_project(const void* __restrict__ qs
 }
 
 // ------------------------------------------------------------------------------------------------------------
-// Sixth-order filter q <- beta (q + pi^-6 sum_j S6_j q), S6 = (1, -6, 15, -20, 15, -6, 1) (a10, Eq. 6)
+// Reductions (a11).  Each thread accumulates the cells it visits (CellStats): compensated (TwoSum) float sums for
+// the scalar inventories, plain per-thread sums of at most ZCHUNK values for energy and squared divergence, an
+// exact room-cell count, and the histogram as runs of equal bins (one shared atomic per run).  The CTA epilogue
+// combines the warps in float-float arithmetic, writes one FP64 partial per quantity, and the last CTA to finish
+// (atomic ticket) adds the partials in CTA order, so the result does not depend on scheduling.  A NaN or Inf in a
+// field propagates into the energy or the scalar total, which the last CTA checks.
 // ------------------------------------------------------------------------------------------------------------
-template <typename T>
-__device__ __forceinline__ T s6(T m3, T m2, T m1, T c, T p1, T p2, T p3)
-{
-    return (m3 + p3) - T(6) * (m2 + p2) + T(15) * (m1 + p1) - T(20) * c;
-}
-
-template <typename T>
-__global__ void __launch_bounds__(TX * TY) k_filter(const void* __restrict__ in, void* __restrict__ out,
-                                                    const uint8_t* __restrict__ mask, FlowConsts<T> k)
-{
-    const int x = blockIdx.x * TX + threadIdx.x;
-    const int y = blockIdx.y * TY + threadIdx.y;
-    if (x >= k.nx || y >= k.ny) return;
-    const int nx = k.nx, ny = k.ny, nz = k.nz;
-    const int plane = nx * ny;
-    const int z0 = blockIdx.z * ZCHUNK, z1 = min(z0 + ZCHUNK, nz);
-    int xo[7], yo[7];
-#pragma unroll
-    for (int m = 0; m < 7; ++m) {
-        xo[m] = wrap(x + m - 3, nx);
-        yo[m] = wrap(y + m - 3, ny) * nx;
-    }
-    // z window of 7 planes of the 4-vector, in registers
-    T zw[7][4];
-#pragma unroll
-    for (int m = 0; m < 6; ++m) ld4(in, wrap(z0 + m - 3, nz) * plane + yo[3] + x, zw[m + 1]);
-    for (int z = z0; z < z1; ++z) {
-        const int zb = z * plane;
-        const int ic = zb + yo[3] + x;
-#pragma unroll
-        for (int m = 0; m < 6; ++m)
-#pragma unroll
-            for (int f = 0; f < 4; ++f) zw[m][f] = zw[m + 1][f];
-        ld4(in, wrap(z + 3, nz) * plane + yo[3] + x, zw[6]);
-        T xn[7][4], yn[7][4];
-#pragma unroll
-        for (int m = 0; m < 7; ++m) {
-            if (m == 3) continue;
-            ld4(in, zb + yo[3] + xo[m], xn[m]);
-            ld4(in, zb + yo[m] + x, yn[m]);
-        }
-        const T beta = beta_of<T>(__ldg(mask + ic));
-        T o[4];
-#pragma unroll
-        for (int f = 0; f < 4; ++f) {
-            const T c = zw[3][f];
-            const T sx = s6(xn[0][f], xn[1][f], xn[2][f], c, xn[4][f], xn[5][f], xn[6][f]);
-            const T sy = s6(yn[0][f], yn[1][f], yn[2][f], c, yn[4][f], yn[5][f], yn[6][f]);
-            const T sz = s6(zw[0][f], zw[1][f], zw[2][f], c, zw[4][f], zw[5][f], zw[6][f]);
-            o[f] = beta * (c + k.filt * (sx + sy + sz));
-        }
-        st4(out, ic, o);
-    }
-}
-
-// ------------------------------------------------------------------------------------------------------------
-// Reductions (a11), one launch.  Each thread sums a z column of ZRED cells; in float it uses compensated
-// (TwoSum) additions and the warp combines the (sum, error) pairs as float-float values, so no FP64 arithmetic
-// runs per cell.  Each CTA writes one FP64 partial per quantity; the last CTA to finish (atomic ticket) adds
-// the partials in CTA order, so the result does not depend on scheduling.  The histogram counts runs of equal
-// bins along each column (one shared atomic per run) and adds its CTA counts to global 64-bit counters.
-// ------------------------------------------------------------------------------------------------------------
-constexpr int ZRED = 16;
-
 template <typename T>
 struct Acc {
     T s, e;   // running sum and its compensation
@@ -304,8 +247,8 @@ struct Acc {
         e += (s - (t - bp)) + (v - bp);
         s = t;
     }
-    // warp-wide sum of the (s, e) pairs, every lane ends with the total
-    __device__ double warp_total()
+    // warp-wide sum of the (s, e) pairs (float-float), every lane ends with the total
+    __device__ void warp_combine()
     {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -315,24 +258,25 @@ struct Acc {
             e = e + e2 + ((s - (t - bp)) + (s2 - bp));
             s = t;
         }
-        return (double)s + (double)e;
     }
+    __device__ double value() const { return (double)s + (double)e; }
 };
 
 template <>
 struct Acc<double> {
-    double s;
-    __device__ void init() { s = 0.0; }
+    double s, unused;
+    __device__ void init() { s = 0.0; unused = 0.0; }
     __device__ void add(double v) { s += v; }
-    __device__ double warp_total()
+    __device__ void warp_combine()
     {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        return s;
     }
+    __device__ double value() const { return s; }
 };
 
-__device__ __forceinline__ double warp_max(double v)
+template <typename T>
+__device__ __forceinline__ T warp_maxT(T v)
 {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
@@ -340,110 +284,113 @@ __device__ __forceinline__ double warp_max(double v)
 }
 
 template <typename T>
-__global__ void __launch_bounds__(TX * TY) k_reduce(const void* __restrict__ q, const uint8_t* __restrict__ mask,
-                                                    FlowConsts<T> k, ReduceArgsDev r, int to_history)
+struct CellStats {
+    Acc<T> ct, cr, c2, ke, d2;
+    T dmax, umax;
+    int vr, run_bin, run_len;
+    __device__ void init()
+    {
+        ct.init(); cr.init(); c2.init(); ke.init(); d2.init();
+        dmax = umax = T(0);
+        vr = 0;
+        run_bin = -1;
+        run_len = 0;
+    }
+    // q: the cell's (u, v, w, c); d: its divergence; m: its mask byte
+    __device__ __forceinline__ void add(const T q[4], T d, uint8_t m, int* hist)
+    {
+        ke.s += q[0] * q[0] + q[1] * q[1] + q[2] * q[2];
+        d2.s += d * d;
+        ct.add(q[3]);
+        dmax = fmax(dmax, fabs(d));
+        umax = fmax(umax, fmax(fabs(q[0]), fmax(fabs(q[1]), fabs(q[2]))));
+        if (m & kBitRoom) {
+            const T cc = q[3];
+            cr.add(cc);
+            c2.add(cc * cc);
+            ++vr;
+            const int bin = cc < T(0) ? kHistBins
+                          : (cc > T(1) ? kHistBins + 1 : min((int)(cc * T(kHistBins)), kHistBins - 1));
+            if (bin == run_bin) {
+                ++run_len;
+            } else {
+                if (run_len) atomicAdd(&hist[run_bin], run_len);
+                run_bin = bin;
+                run_len = 1;
+            }
+        }
+    }
+};
+
+struct RedShared {
+    int hist[kHistBins + 2];
+    long long hist_total[kHistBins + 2];
+    double red[kRedSlots][TX * TY / 32];
+    bool is_last;
+};
+
+__device__ __forceinline__ void red_init(RedShared& sh)
+{
+    const int tid = threadIdx.y * TX + threadIdx.x;
+    for (int i = tid; i < kHistBins + 2; i += TX * TY) sh.hist[i] = 0;
+}
+
+// CTA epilogue: every thread of the CTA calls it once (after red_init and a barrier)
+template <typename T>
+__device__ void red_finish(CellStats<T>& cs, RedShared& sh, const ReduceArgsDev& r, int to_history)
 {
     constexpr int NW = TX * TY / 32;
     static_assert(NW == kRedSlots, "one warp per reduced quantity in the final pass");
-    __shared__ int hist[kHistBins + 2];
-    __shared__ long long hist_total[kHistBins + 2];
-    __shared__ double red[kRedSlots][NW];
-    __shared__ bool is_last;
     const int tid = threadIdx.y * TX + threadIdx.x;
-    for (int i = tid; i < kHistBins + 2; i += TX * TY) hist[i] = 0;
-    __syncthreads();
-
-    const int x = blockIdx.x * TX + threadIdx.x;
-    const int y = blockIdx.y * TY + threadIdx.y;
-    Acc<T> ke, d2, ct, cr, c2, vr;
-    ke.init(); d2.init(); ct.init(); cr.init(); c2.init(); vr.init();
-    T dmax = T(0), umax = T(0);
-    bool bad = false;
-    int run_bin = -1, run_len = 0;
-    if (x < k.nx && y < k.ny) {
-        const int nx = k.nx, ny = k.ny, nz = k.nz;
-        const int plane = nx * ny;
-        const int z0 = blockIdx.z * ZRED, z1 = min(z0 + ZRED, nz);
-        const int rowc = y * nx, rowm = wrap(y - 1, ny) * nx, rowp = wrap(y + 1, ny) * nx;
-        const int xm = wrap(x - 1, nx), xp = wrap(x + 1, nx);
-        T wzm = ld1<T>(q, wrap(z0 - 1, nz) * plane + rowc + x, 2);
-        T c4[4];
-        ld4(q, z0 * plane + rowc + x, c4);
-        for (int z = z0; z < z1; ++z) {
-            const int zb = z * plane;
-            const int ic = zb + rowc + x;
-            T n4[4];
-            ld4(q, wrap(z + 1, nz) * plane + rowc + x, n4);
-            const T uu = c4[0], vv = c4[1], ww = c4[2], cc = c4[3];
-            const T d = k.i2h[0] * (ld1<T>(q, zb + rowc + xp, 0) - ld1<T>(q, zb + rowc + xm, 0)) +
-                        k.i2h[1] * (ld1<T>(q, zb + rowp + x, 1) - ld1<T>(q, zb + rowm + x, 1)) +
-                        k.i2h[2] * (n4[2] - wzm);
-            ke.add(uu * uu + vv * vv + ww * ww);
-            d2.add(d * d);
-            ct.add(cc);
-            dmax = fmax(dmax, fabs(d));
-            umax = fmax(umax, fmax(fabs(uu), fmax(fabs(vv), fabs(ww))));
-            if (!isfinite(uu) || !isfinite(vv) || !isfinite(ww) || !isfinite(cc)) bad = true;
-            if (__ldg(mask + ic) & kBitRoom) {
-                cr.add(cc);
-                c2.add(cc * cc);
-                vr.add(T(1));
-                int bin;
-                if (cc < T(0)) bin = kHistBins;
-                else if (cc > T(1)) bin = kHistBins + 1;
-                else bin = min((int)floor(cc * T(kHistBins)), kHistBins - 1);
-                if (bin == run_bin) {
-                    ++run_len;
-                } else {
-                    if (run_len) atomicAdd(&hist[run_bin], run_len);
-                    run_bin = bin;
-                    run_len = 1;
-                }
-            }
-            wzm = ww;
-#pragma unroll
-            for (int f = 0; f < 4; ++f) c4[f] = n4[f];
-        }
-    }
-    if (run_len) atomicAdd(&hist[run_bin], run_len);
-    if (bad) *r.nonfinite = 1;
-    const double vals[kRedSlots] = {ke.warp_total(), d2.warp_total(), ct.warp_total(), cr.warp_total(),
-                                    c2.warp_total(), vr.warp_total(), warp_max((double)dmax),
-                                    warp_max((double)umax)};
     const int lane = tid & 31, wid = tid >> 5;
-    if (lane == 0)
-#pragma unroll
-        for (int qq = 0; qq < kRedSlots; ++qq) red[qq][wid] = vals[qq];
+    if (cs.run_len) atomicAdd(&sh.hist[cs.run_bin], cs.run_len);
+    Acc<T> vr{};
+    vr.init();
+    vr.s = T(cs.vr);
+    cs.ke.warp_combine(); cs.d2.warp_combine(); cs.ct.warp_combine(); cs.cr.warp_combine(); cs.c2.warp_combine();
+    vr.warp_combine();
+    const T dmax = warp_maxT(cs.dmax), umax = warp_maxT(cs.umax);
+    if (lane == 0) {
+        sh.red[0][wid] = cs.ke.value();
+        sh.red[1][wid] = cs.d2.value();
+        sh.red[2][wid] = cs.ct.value();
+        sh.red[3][wid] = cs.cr.value();
+        sh.red[4][wid] = cs.c2.value();
+        sh.red[5][wid] = vr.value();
+        sh.red[6][wid] = (double)dmax;
+        sh.red[7][wid] = (double)umax;
+    }
     __syncthreads();
     const int nblocks = gridDim.x * gridDim.y * gridDim.z;
     const long long bid = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
     if (tid < kRedSlots) {
-        double s = red[tid][0];
-        for (int i = 1; i < NW; ++i) s = (tid < 6) ? s + red[tid][i] : fmax(s, red[tid][i]);
-        r.partial[bid * kRedSlots + tid] = s;
+        double v = sh.red[tid][0];
+        for (int i = 1; i < NW; ++i) v = (tid < 6) ? v + sh.red[tid][i] : fmax(v, sh.red[tid][i]);
+        r.partial[bid * kRedSlots + tid] = v;
     }
     for (int i = tid; i < kHistBins + 2; i += TX * TY)
-        if (hist[i]) atomicAdd(r.hist_accum + i, (unsigned long long)hist[i]);
+        if (sh.hist[i]) atomicAdd(r.hist_accum + i, (unsigned long long)sh.hist[i]);
     __threadfence();
     __syncthreads();
-    if (tid == 0) is_last = atomicAdd(r.done, 1u) == (unsigned)(nblocks - 1);
+    if (tid == 0) sh.is_last = atomicAdd(r.done, 1u) == (unsigned)(nblocks - 1);
     __syncthreads();
-    if (!is_last) return;
+    if (!sh.is_last) return;
     __threadfence();
-    // final pass: warp qq adds partial qq of every CTA in CTA order (fixed tree); the histogram counters are read
-    // and cleared by one thread each
+    // last CTA: warp qq adds partial qq of every CTA in CTA order (fixed tree); histogram counters read and cleared
     {
         const int qq = wid;
-        double s = 0.0;
+        double v = 0.0;
         for (int b = lane; b < nblocks; b += 32) {
             const double pv = __ldcg(r.partial + (long long)b * kRedSlots + qq);
-            s = (qq < 6) ? s + pv : fmax(s, pv);
+            v = (qq < 6) ? v + pv : fmax(v, pv);
         }
-        Acc<double> acc{s};
-        s = (qq < 6) ? acc.warp_total() : warp_max(s);
-        if (lane == 0) red[qq][0] = s;
+        Acc<double> acc{v, 0.0};
+        if (qq < 6) { acc.warp_combine(); v = acc.value(); }
+        else v = warp_maxT(v);
+        if (lane == 0) sh.red[qq][0] = v;
     }
-    for (int i = tid; i < kHistBins + 2; i += TX * TY) hist_total[i] = (long long)atomicExch(r.hist_accum + i, 0ull);
+    for (int i = tid; i < kHistBins + 2; i += TX * TY)
+        sh.hist_total[i] = (long long)atomicExch(r.hist_accum + i, 0ull);
     __syncthreads();
     // the record is written field by field by several threads (no per-thread copy of the whole struct)
     const long long slot = to_history ? (*r.hist_count % r.history_capacity) : 0;
@@ -452,30 +399,137 @@ __global__ void __launch_bounds__(TX * TY) k_reduce(const void* __restrict__ q, 
         vf_reduce* dst = outs[o];
         if (!dst) continue;
         for (int i = tid; i < kHistBins + 2; i += TX * TY) {
-            if (i < kHistBins) dst->hist[i] = hist_total[i];
-            else if (i == kHistBins) dst->hist_under = hist_total[i];
-            else dst->hist_over = hist_total[i];
+            if (i < kHistBins) dst->hist[i] = sh.hist_total[i];
+            else if (i == kHistBins) dst->hist_under = sh.hist_total[i];
+            else dst->hist_over = sh.hist_total[i];
         }
         if (tid == 0) {
             const long long step = *r.step_counter;
             dst->step = step;
             dst->t = r.t0 + (double)step * r.dt;
-            dst->ke = 0.5 * r.dV * red[0][0];
-            dst->div_l2 = sqrt(r.dV * red[1][0]);
-            dst->c_total = r.dV * red[2][0];
-            dst->c_room = r.dV * red[3][0];
-            dst->c2_room = r.dV * red[4][0];
-            dst->v_room = r.dV * red[5][0];
-            dst->div_max = red[6][0];
-            dst->u_max = red[7][0];
+            dst->ke = 0.5 * r.dV * sh.red[0][0];
+            dst->div_l2 = sqrt(r.dV * sh.red[1][0]);
+            dst->c_total = r.dV * sh.red[2][0];
+            dst->c_room = r.dV * sh.red[3][0];
+            dst->c2_room = r.dV * sh.red[4][0];
+            dst->v_room = r.dV * sh.red[5][0];
+            dst->div_max = sh.red[6][0];
+            dst->u_max = sh.red[7][0];
         }
     }
     __syncthreads();
     if (tid == 0) {
-        if (!isfinite(red[0][0]) || !isfinite(red[2][0])) *r.nonfinite = 1;
+        if (!isfinite(sh.red[0][0]) || !isfinite(sh.red[2][0])) *r.nonfinite = 1;
         if (to_history) *r.hist_count += 1;
         *r.done = 0u;
     }
+}
+
+// Standalone reductions of a state (filter off, or on demand): divergence of the state itself.
+template <typename T>
+__global__ void __launch_bounds__(TX * TY) k_reduce(const void* __restrict__ q, const uint8_t* __restrict__ mask,
+                                                    FlowConsts<T> k, ReduceArgsDev r, int to_history)
+{
+    __shared__ RedShared sh;
+    red_init(sh);
+    __syncthreads();
+    CellStats<T> cs;
+    cs.init();
+    const int x = blockIdx.x * TX + threadIdx.x;
+    const int y = blockIdx.y * TY + threadIdx.y;
+    if (x < k.nx && y < k.ny) {
+        const int nx = k.nx, ny = k.ny, nz = k.nz;
+        const int plane = nx * ny;
+        const int z0 = blockIdx.z * ZCHUNK, z1 = min(z0 + ZCHUNK, nz);
+        const int rowc = y * nx, rowm = wrap(y - 1, ny) * nx, rowp = wrap(y + 1, ny) * nx;
+        const int xm = wrap(x - 1, nx), xp = wrap(x + 1, nx);
+        T wzm = ld1<T>(q, wrap(z0 - 1, nz) * plane + rowc + x, 2);
+        T c4[4], n4[4];
+        ld4(q, z0 * plane + rowc + x, c4);
+        ld4(q, wrap(z0 + 1, nz) * plane + rowc + x, n4);
+        for (int z = z0; z < z1; ++z) {
+            const int zb = z * plane;
+            T nn4[4] = {T(0), T(0), T(0), T(0)};
+            if (z + 1 < z1) ld4(q, wrap(z + 2, nz) * plane + rowc + x, nn4);   // prefetch
+            const T d = k.i2h[0] * (ld1<T>(q, zb + rowc + xp, 0) - ld1<T>(q, zb + rowc + xm, 0)) +
+                        k.i2h[1] * (ld1<T>(q, zb + rowp + x, 1) - ld1<T>(q, zb + rowm + x, 1)) +
+                        k.i2h[2] * (n4[2] - wzm);
+            cs.add(c4, d, __ldg(mask + zb + rowc + x), sh.hist);
+            wzm = c4[2];
+#pragma unroll
+            for (int f = 0; f < 4; ++f) { c4[f] = n4[f]; n4[f] = nn4[f]; }
+        }
+    }
+    red_finish(cs, sh, r, to_history);
+}
+
+// ------------------------------------------------------------------------------------------------------------
+// Sixth-order filter q <- beta (q + pi^-6 sum_j S6_j q), S6 = (1, -6, 15, -20, 15, -6, 1) (a10, Eq. 6).
+// REDUCE: also the reductions (a11) of the filtered state, with the divergence of the projected velocity (the
+// filter's input: after the projection, before the filter), saving a separate pass over the fields.
+// ------------------------------------------------------------------------------------------------------------
+template <typename T, bool REDUCE>
+__global__ void __launch_bounds__(TX * TY, sizeof(T) == 4 ? (REDUCE ? 3 : 4) : 2)
+k_filter(const void* __restrict__ in, void* __restrict__ out, const uint8_t* __restrict__ mask, FlowConsts<T> k,
+         ReduceArgsDev r, int to_history)
+{
+    __shared__ RedShared sh;
+    if (REDUCE) {
+        red_init(sh);
+        __syncthreads();
+    }
+    CellStats<T> cs;
+    cs.init();
+    const int x = blockIdx.x * TX + threadIdx.x;
+    const int y = blockIdx.y * TY + threadIdx.y;
+    if (x < k.nx && y < k.ny) {
+        const int nx = k.nx, ny = k.ny, nz = k.nz;
+        const int plane = nx * ny;
+        const int z0 = blockIdx.z * ZCHUNK, z1 = min(z0 + ZCHUNK, nz);
+        const int yc = y * nx;
+        // z window of 7 planes of the 4-vector, in registers
+        T zw[7][4];
+#pragma unroll
+        for (int m = 0; m < 6; ++m) ld4(in, wrap(z0 + m - 3, nz) * plane + yc + x, zw[m + 1]);
+        for (int z = z0; z < z1; ++z) {
+            const int zb = z * plane;
+            const int ic = zb + yc + x;
+#pragma unroll
+            for (int m = 0; m < 6; ++m)
+#pragma unroll
+                for (int f = 0; f < 4; ++f) zw[m][f] = zw[m + 1][f];
+            ld4(in, wrap(z + 3, nz) * plane + yc + x, zw[6]);
+            // sum of the three sixth differences: sum_m S6[m] (q_x[m] + q_y[m] + q_z[m]); centre weight -20 x 3
+            T acc[4];
+#pragma unroll
+            for (int f = 0; f < 4; ++f)
+                acc[f] = (zw[0][f] + zw[6][f]) - T(6) * (zw[1][f] + zw[5][f]) + T(15) * (zw[2][f] + zw[4][f]) -
+                         T(60) * zw[3][f];
+            const T coef[3] = {T(1), T(-6), T(15)};
+            T div = T(0);
+#pragma unroll
+            for (int d = 3; d >= 1; --d) {
+                const T cf = coef[3 - d];
+                T a[4], b[4], c[4], e[4];
+                ld4(in, zb + yc + wrap(x - d, nx), a);
+                ld4(in, zb + yc + wrap(x + d, nx), b);
+                ld4(in, zb + wrap(y - d, ny) * nx + x, c);
+                ld4(in, zb + wrap(y + d, ny) * nx + x, e);
+#pragma unroll
+                for (int f = 0; f < 4; ++f) acc[f] += cf * ((a[f] + b[f]) + (c[f] + e[f]));
+                if (REDUCE && d == 1)
+                    div = k.i2h[0] * (b[0] - a[0]) + k.i2h[1] * (e[1] - c[1]) + k.i2h[2] * (zw[4][2] - zw[2][2]);
+            }
+            const uint8_t m0 = __ldg(mask + ic);
+            const T beta = beta_of<T>(m0);
+            T o[4];
+#pragma unroll
+            for (int f = 0; f < 4; ++f) o[f] = beta * (zw[3][f] + k.filt * acc[f]);
+            st4(out, ic, o);
+            if (REDUCE) cs.add(o, div, m0, sh.hist);
+        }
+    }
+    if (REDUCE) red_finish(cs, sh, r, to_history);
 }
 
 // ------------------------------------------------------------------------------------------------------------
@@ -600,10 +654,7 @@ inline dim3 flow_grid(int nx, int ny, int nz)
     return dim3((nx + TX - 1) / TX, (ny + TY - 1) / TY, (nz + ZCHUNK - 1) / ZCHUNK);
 }
 
-inline dim3 reduce_grid(int nx, int ny, int nz)
-{
-    return dim3((nx + TX - 1) / TX, (ny + TY - 1) / TY, (nz + ZRED - 1) / ZRED);
-}
+inline dim3 reduce_grid(int nx, int ny, int nz) { return flow_grid(nx, ny, nz); }
 
 inline int elementwise_blocks(size_t n) { return (int)std::min<size_t>((n + 255) / 256, 152 * 16); }
 
@@ -643,9 +694,11 @@ cudaError_t Kernels<T>::project(const void* qstar, const T* p, void* out, const 
 
 template <typename T>
 cudaError_t Kernels<T>::filter(const void* in, void* out, const uint8_t* mask, const FlowConsts<T>& k,
-                               cudaStream_t st)
+                               const ReduceArgsDev* r, int to_history, cudaStream_t st)
 {
-    k_filter<T><<<flow_grid(k.nx, k.ny, k.nz), dim3(TX, TY), 0, st>>>(in, out, mask, k);
+    const dim3 g = flow_grid(k.nx, k.ny, k.nz), b(TX, TY);
+    if (r) k_filter<T, true><<<g, b, 0, st>>>(in, out, mask, k, *r, to_history);
+    else k_filter<T, false><<<g, b, 0, st>>>(in, out, mask, k, ReduceArgsDev{}, 0);
     return cudaGetLastError();
 }
 

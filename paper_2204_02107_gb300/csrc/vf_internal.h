@@ -201,8 +201,9 @@ struct Kernels {
     // u = beta (u* - dt G p), c* passes through; ticks the device step counter
     static cudaError_t project(const void* qstar, const T* p, void* out, const uint8_t* mask, long long* step_counter,
                                const FlowConsts<T>& k, cudaStream_t st);
+    // r != nullptr: also record the reductions of the filtered state (divergence of the projected velocity)
     static cudaError_t filter(const void* in, void* out, const uint8_t* mask, const FlowConsts<T>& k,
-                              cudaStream_t st);
+                              const ReduceArgsDev* r, int to_history, cudaStream_t st);
     static cudaError_t reduce(const void* q, const uint8_t* mask, const FlowConsts<T>& k, const ReduceArgsDev& r,
                               int to_history, cudaStream_t st);
     static int reduce_blocks(const FlowConsts<T>& k);
