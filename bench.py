@@ -214,6 +214,77 @@ def run_reference(args):
     return 0
 
 
+def time_grid_steps(g, steps, stream, reduce_every=1):
+    import torch
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    g.step(steps, reduce_every=reduce_every)
+    end.record(stream)
+    end.synchronize()
+    return start.elapsed_time(end) / 1e3
+
+
+def bench_large_room(stream, steps):
+    """512 x 256 x 256 room (partition wall with doorway, two duct pairs, 20 seeded boxes, U_in = 0.1 m/s), FP32."""
+    from paper_2204_02107_gb300 import native, rooms
+    room = rooms.large_room()
+    g = native.room_grid(room, precision="fp32", stream=stream.cuda_stream, history_capacity=max(16, steps + 3))
+    g.step(3, reduce_every=1)
+    g.sync()
+    sec = time_grid_steps(g, steps, stream)
+    g.close()
+    return {"workload": "large room 512x256x256, FP32 bulk + FP64 reductions every step, n = 4",
+            "value": room.cells * steps / sec / 1e9, "unit": UNIT, "ms_per_step": sec * 1e3 / steps,
+            "steps": steps, "cells": room.cells,
+            "step_roofline_frac": STEP_MODEL_BYTES_PER_CELL_FP32 * room.cells * steps / sec / 1e9 / measured_peaks()[0]}
+
+
+def bench_batch(stream, steps):
+    """64 rooms of uneven size (64^3 .. 192x96x96, 0-10 boxes, U_in in [0.1, 1] m/s) advanced together."""
+    import torch
+    from paper_2204_02107_gb300 import native, rooms
+    rs = rooms.batch_rooms(64)
+    b = native.Batch(max_slots=64, hbm_budget_bytes=120 << 30, reduce_every=1, stream=stream.cuda_stream)
+    total = 0
+    for r in rs:
+        b.add(native.room_desc(r, precision="fp32", history_capacity=max(16, steps + 3)), r.beta, r.S,
+              (r.u_in, 0.0, 0.0), 0.0, steps + 3, room=r.room, c0=r.initial_c())
+        total += r.cells
+    b.step(3)
+    b.sync()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    b.step(steps)
+    end.record(stream)
+    end.synchronize()
+    sec = start.elapsed_time(end) / 1e3
+    info = b.info()
+    b.close()
+    return {"workload": "64 rooms 64^3..192x96x96 in one batch graph per step, FP32 bulk + FP64 reductions",
+            "value": total * steps / sec / 1e9, "unit": UNIT, "ms_per_batch_step": sec * 1e3 / steps,
+            "steps": steps, "rooms": len(rs), "cells": total, "bytes_in_use": info["bytes_in_use"]}
+
+
+def bench_serve(n_requests):
+    """Poisson arrivals (4 per second) of ventilation requests served by continuous batching in FP32, against the
+    same trace served one at a time in FP64; ACH agreement between the two."""
+    from paper_2204_02107_gb300 import rooms, serve
+    sizes = [(nx, n, n) for n in (64, 72, 80, 96) for nx in (64, 96, 128, 160) if nx >= n] + [(256, 128, 128)]
+    reqs = rooms.request_trace(count=n_requests, seed=5, rate_per_s=4.0, sizes=sizes, step_range=(100, 400))
+    srv = serve.Server(hbm_budget_bytes=120 << 30, max_slots=64, chunk_steps=25, precision="fp32")
+    served = srv.run(reqs, realtime=True)
+    srv.close()
+    base = serve.run_one_at_a_time(reqs, precision="fp64", realtime=True)
+    by_id = {r.id: r for r in base}
+    rel = [abs(r.ach_per_hour - by_id[r.id].ach_per_hour) / abs(by_id[r.id].ach_per_hour) for r in served
+           if by_id[r.id].ach_per_hour]
+    return {"workload": f"{n_requests} requests, Poisson arrivals 4/s (seed 5), grids 64^3..256x128x128, "
+                        f"100-400 steps, inflow 0.1 or 1 m/s, 120 GB budget",
+            "continuous_batching_fp32": serve.summarize(served),
+            "one_at_a_time_fp64": serve.summarize(base),
+            "ach_rel_diff_max": max(rel) if rel else None}
+
+
 def e2e_run(room, precision, steps, stream):
     """End to end through the C ABI with pinned host buffers: grid creation, mask / inflow / region / scalar
     upload, ``steps`` steps with a reduction record each, then the records and all five fields read back."""
@@ -263,6 +334,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=100)
+    ap.add_argument("--extra-steps", type=int, default=30, help="timed steps of the large-room and batch legs")
+    ap.add_argument("--serve-requests", type=int, default=24, help="requests of the serving leg (0: skip)")
+    ap.add_argument("--no-extras", action="store_true", help="skip the large-room, batch and serving legs")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -333,6 +407,12 @@ def main():
 
     e2e = e2e_run(room, "fp32", args.steps, stream)
     g.close()
+    extras = {}
+    if not args.no_extras and world == 1:
+        extras["large_room"] = bench_large_room(stream, args.extra_steps)
+        extras["batch"] = bench_batch(stream, args.extra_steps)
+        if args.serve_requests > 0:
+            extras["serve"] = bench_serve(args.serve_requests)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -356,6 +436,7 @@ def main():
         "clocks": clocks.summary(),
         "last_record": {k: hist[-1][k] for k in ("step", "ke", "c_room", "div_max", "u_max")} if hist else None,
     }
+    line.update(extras)
     if world == 1 and rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_oracle(room, "FP64, filter on, 4 pressure iterations")
     if rank == 0:

@@ -539,11 +539,19 @@ __global__ void __launch_bounds__(kPlaneThreads) k_fft_yz_solve(PoissonArgs<T> A
     }
 }
 
+// The dynamic shared-memory limit is a per-kernel, process-wide attribute: it is raised to the device's opt-in
+// maximum (an upper bound only; each launch uses its own size), never lowered, so grids of different sizes can
+// be created in any order.
 template <typename K>
 cudaError_t set_smem(K kernel, size_t bytes)
 {
     if (bytes <= 48 * 1024) return cudaSuccess;
-    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    if (bytes > (size_t)optin) return cudaErrorInvalidValue;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
 }
 
 template <typename T> constexpr int cols_tb() { return sizeof(T) == 8 ? 8 : 16; }

@@ -106,3 +106,18 @@ def test_rooms_added_while_others_run(torch):
         for n in FIELD_NAMES:
             assert np.array_equal(g.read_field(n), ref[n]), (slot, n)
     b.close()
+
+
+def test_grids_created_large_then_small_both_run(torch):
+    """Kernel shared-memory limits are process-wide: a smaller grid created later must not break a larger one."""
+    big = rooms.make_room(64, 64, 64, h=0.05, u_in=1.0)
+    small = rooms.make_room(40, 24, 20, h=0.05, u_in=1.0)
+    g1 = native.room_grid(big, precision="fp64")
+    g2 = native.room_grid(small, precision="fp32")
+    g1.step(2)
+    g2.step(2)
+    g1.sync()
+    g2.sync()
+    assert g1.info()["step"] == 2 and np.isfinite(g1.read_field("u")).all()
+    g1.close()
+    g2.close()
