@@ -36,10 +36,10 @@ UNIT = "Gcell-updates/s"
 # reads it): what each launch must read and write at least once.
 F32 = 4
 PHASE_BYTES_PER_CELL = {
-    "stage1": 12 * F32 + 1,      # read q (4), write acc (4), q2 (4), mask
-    "stage2": 20 * F32 + 1,      # read q_s, q_n, acc; write acc, q_next; mask
-    "stage3": 20 * F32 + 1,
-    "stage4": 12 * F32 + 1,      # read q_s, acc; write q*; mask
+    "stage1": 8 * F32 + 1,       # read q_n (4 values), write q2 (4), mask
+    "stage2": 12 * F32 + 1,      # read q2 (stencil), q_n; write q3; mask
+    "stage3": 12 * F32 + 1,      # read q3 (stencil), q_n; write q4; mask
+    "stage4": 20 * F32 + 1,      # read q4 (stencil), q_n, q2, q3; write q*; mask
     "div": 4 * F32,              # read u*, v*, w*; write r
     "fft_x_fwd": 3 * F32 + 1,    # read r, p, mask; write the half spectrum (N/2 complex = N F bytes)
     "fft_y_fwd": 2 * F32,        # read + write the spectrum

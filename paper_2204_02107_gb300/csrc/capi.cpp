@@ -118,6 +118,7 @@ FlowConsts<T> flow_consts(const vf_grid* g)
     k.dt2 = (T)(d.dt / 2.0);
     k.dt3 = (T)(d.dt / 3.0);
     k.dt6 = (T)(d.dt / 6.0);
+    k.third = (T)(1.0 / 3.0);
     k.cset = (T)g->cset;
     k.filt = (T)(1.0 / std::pow(M_PI, 6));
     return k;
@@ -180,39 +181,39 @@ cudaError_t enqueue_step_t(vf_grid* g, cudaStream_t st, bool with_reduce, const 
     StageArgs<T> a{};
     a.mask = g->mask;
     a.qn = g->q;
-    a.acc = g->acc;
     cudaError_t e;
-    // stage s reads q_s with the stencil: q, qa, qb, qa; writes the next stage state: qa, qb, qa, then q* in qb
+    // stage states: q2 in qa, q3 in qb, q4 in acc; stage 4 writes q* over q2 (each cell reads its own q2 first)
     a.qs = g->q; a.out = g->qa;
     if ((e = Kernels<T>::stage(1, a, k, st)) != cudaSuccess) return e;
     mark(VF_PHASE_STAGE1);
     a.qs = g->qa; a.out = g->qb;
     if ((e = Kernels<T>::stage(2, a, k, st)) != cudaSuccess) return e;
     mark(VF_PHASE_STAGE2);
-    a.qs = g->qb; a.out = g->qa;
+    a.qs = g->qb; a.out = g->acc;
     if ((e = Kernels<T>::stage(3, a, k, st)) != cudaSuccess) return e;
     mark(VF_PHASE_STAGE3);
-    a.qs = g->qa; a.out = g->qb;
+    a.qs = g->acc; a.q2 = g->qa; a.q3 = g->qb; a.out = g->qa;
     if ((e = Kernels<T>::stage(4, a, k, st)) != cudaSuccess) return e;
     mark(VF_PHASE_STAGE4);
+    void* qstar = g->qa;
     const int iters = pressure_iters(g);
     if (iters > 0) {
-        if ((e = Kernels<T>::divergence(g->qb, (T*)g->f, k, st)) != cudaSuccess) return e;
+        if ((e = Kernels<T>::divergence(qstar, (T*)g->f, k, st)) != cudaSuccess) return e;
         mark(VF_PHASE_DIV);
         const PoissonArgs<T> pa = poisson_args<T>(g, (T*)g->f, (T*)g->p, g->has_solid ? 1 : 0);
         for (int it = 0; it < iters; ++it)
             if ((e = Kernels<T>::poisson_iteration(pa, it == 0, st, hook)) != cudaSuccess) return e;
     }
     long long* step_counter = g->dev_counters + 1;
-    // projection into acc (then filtered into q) or straight into q
-    void* proj_out = g->d.filter ? g->acc : g->q;
-    if ((e = Kernels<T>::project(g->qb, (const T*)g->p, proj_out, g->mask, step_counter, k, st)) != cudaSuccess)
+    // projection into qb (then filtered into q) or straight into q
+    void* proj_out = g->d.filter ? g->qb : g->q;
+    if ((e = Kernels<T>::project(qstar, (const T*)g->p, proj_out, g->mask, step_counter, k, st)) != cudaSuccess)
         return e;
     mark(VF_PHASE_PROJECT);
     if (g->d.filter) {
         // with the filter on, the reductions ride along in the filter kernel
         const vf::ReduceArgsDev ra = reduce_args(g);
-        if ((e = Kernels<T>::filter(g->acc, g->q, g->mask, k, with_reduce ? &ra : nullptr, 1, st)) != cudaSuccess)
+        if ((e = Kernels<T>::filter(g->qb, g->q, g->mask, k, with_reduce ? &ra : nullptr, 1, st)) != cudaSuccess)
             return e;
         mark(VF_PHASE_FILTER);
     } else if (with_reduce) {

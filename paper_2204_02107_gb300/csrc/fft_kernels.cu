@@ -12,7 +12,7 @@
 // and kx = nx/2 (imaginary part): both are real for real data and both have sin^2(2 pi kx / nx) = 0, so the
 // y/z transforms and the eigenvalue division treat the packed pair exactly like any other column.
 //
-// The transforms are mixed-radix (2, 3, 4, 5, 8) Stockham FFTs: each radix pass is done by R-point butterflies
+// The transforms are mixed-radix (2, 3, 4, 5, 8, 16) Stockham FFTs: each radix pass is done by R-point butterflies
 // in registers, passes exchange data through shared memory.  In the row and tile passes the first radix pass
 // reads its operands straight from global memory and the last writes straight to its destination; the plane
 // kernel works in place on one shared-memory plane (a barrier between the reads and the writes of each pass).
@@ -120,6 +120,31 @@ __device__ __forceinline__ void dft8(C* v)
     v[3] = cadd(e3, o3); v[7] = csub(e3, o3);
 }
 
+// order 16 as 4 x 4: DFT4 over the stride-4 columns, twiddles W16^(n2 k1), DFT4 over the rows, transpose
+template <typename C, bool INV>
+__device__ __forceinline__ void dft16(C* v)
+{
+    using R = decltype(C::x);
+    const R c1 = R(0.92387953251128675613), s1 = R(0.38268343236508977173), h = R(0.70710678118654752440);
+    const R sg = INV ? R(1) : R(-1);   // sign of the imaginary part of W16^k
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) dft4<C, INV>(v[n2], v[n2 + 4], v[n2 + 8], v[n2 + 12]);
+    const C w1 = mk<C>(c1, sg * s1), w2 = mk<C>(h, sg * h), w3 = mk<C>(s1, sg * c1);
+    const C w6 = mk<C>(-h, sg * h), w9 = mk<C>(-c1, -sg * s1);
+    v[5] = cmul(v[5], w1); v[9] = cmul(v[9], w2); v[13] = cmul(v[13], w3);
+    v[6] = cmul(v[6], w2); v[10] = rot<C, INV>(v[10]); v[14] = cmul(v[14], w6);
+    v[7] = cmul(v[7], w3); v[11] = cmul(v[11], w6); v[15] = cmul(v[15], w9);
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) dft4<C, INV>(v[4 * k1], v[4 * k1 + 1], v[4 * k1 + 2], v[4 * k1 + 3]);
+    C t[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) t[i] = v[i];
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1)
+#pragma unroll
+        for (int k2 = 0; k2 < 4; ++k2) v[k1 + 4 * k2] = t[4 * k1 + k2];
+}
+
 template <typename C, int R, bool INV>
 __device__ __forceinline__ void dft(C* v)
 {
@@ -127,7 +152,8 @@ __device__ __forceinline__ void dft(C* v)
     else if (R == 3) dft3<C, INV>(v[0], v[1], v[2]);
     else if (R == 4) dft4<C, INV>(v[0], v[1], v[2], v[3]);
     else if (R == 5) dft5<C, INV>(v[0], v[1], v[2], v[3], v[4]);
-    else dft8<C, INV>(v);
+    else if (R == 8) dft8<C, INV>(v);
+    else dft16<C, INV>(v);
 }
 
 // One radix-R Stockham pass over nseq sequences.  Work item (j, b) reads element j + r nb of sequence b
@@ -170,7 +196,8 @@ __device__ __forceinline__ void radix_pass_any(const FftStage& S, int nseq, cons
         case 3: radix_pass<C, 3, INV, SEQFAST, TB>(S, nseq, tw, ld, st); break;
         case 4: radix_pass<C, 4, INV, SEQFAST, TB>(S, nseq, tw, ld, st); break;
         case 5: radix_pass<C, 5, INV, SEQFAST, TB>(S, nseq, tw, ld, st); break;
-        default: radix_pass<C, 8, INV, SEQFAST, TB>(S, nseq, tw, ld, st); break;
+        case 8: radix_pass<C, 8, INV, SEQFAST, TB>(S, nseq, tw, ld, st); break;
+        default: radix_pass<C, 16, INV, SEQFAST, TB>(S, nseq, tw, ld, st); break;
     }
 }
 
@@ -397,10 +424,24 @@ __global__ void __launch_bounds__(256) k_fft_x_inv(PoissonArgs<T> A)
     const C* spec = reinterpret_cast<const C*>(A.spec);
     const C* twr = reinterpret_cast<const C*>(A.twr);
     if (A.plane_layout) {
-        // stage the block's rows in shared memory with coalesced reads (consecutive rows of one kx)
-        for (int it = threadIdx.x; it < B * M; it += blockDim.x) {
-            const int k = it / B, b = it - k * B, row = row0 + b;
-            in[b * SS + padded(k)] = (row < rows) ? spec[(long long)k * rows + row] : mk<C>(T(0), T(0));
+        // stage the block's rows in shared memory with coalesced reads (consecutive rows of one kx), 8 loads in
+        // flight per thread
+        for (int it0 = threadIdx.x; it0 < B * M; it0 += 8 * blockDim.x) {
+            C tmp[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int it = it0 + u * blockDim.x;
+                const int k = it / B, b = it - k * B, row = row0 + b;
+                tmp[u] = (it < B * M && row < rows) ? spec[(long long)k * rows + row] : mk<C>(T(0), T(0));
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int it = it0 + u * blockDim.x;
+                if (it < B * M) {
+                    const int k = it / B, b = it - k * B;
+                    in[b * SS + padded(k)] = tmp[u];
+                }
+            }
         }
     }
     auto spec_at = [&](int k, int b) -> C {
@@ -486,7 +527,8 @@ __device__ void inplace_fft(C* buf, const FftAxis& ax, int nseq, const FastDiv& 
             case 3: inplace_pass<C, 3, INV, SEQFAST>(buf, S, nseq, nseq_div, idx, tw); break;
             case 4: inplace_pass<C, 4, INV, SEQFAST>(buf, S, nseq, nseq_div, idx, tw); break;
             case 5: inplace_pass<C, 5, INV, SEQFAST>(buf, S, nseq, nseq_div, idx, tw); break;
-            default: inplace_pass<C, 8, INV, SEQFAST>(buf, S, nseq, nseq_div, idx, tw); break;
+            case 8: inplace_pass<C, 8, INV, SEQFAST>(buf, S, nseq, nseq_div, idx, tw); break;
+            default: inplace_pass<C, 16, INV, SEQFAST>(buf, S, nseq, nseq_div, idx, tw); break;
         }
     }
 }
@@ -507,9 +549,22 @@ __global__ void __launch_bounds__(kPlaneThreads) k_fft_yz_solve(PoissonArgs<T> A
     int* kz_of = ky_of + ny;
     const int kx = blockIdx.x;
     C* g = reinterpret_cast<C*>(A.spec) + (long long)kx * n_el;
-    for (int i = threadIdx.x; i < n_el; i += blockDim.x) {
-        const int z = (int)fdiv((uint32_t)i, A.ny_div), y = i - z * ny;
-        plane[z * SP + padded(y)] = g[i];
+    // load the plane 8 values per thread at a time, so the global loads of a thread overlap
+    for (int i0 = threadIdx.x; i0 < n_el; i0 += 8 * kPlaneThreads) {
+        C tmp[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int i = i0 + u * kPlaneThreads;
+            if (i < n_el) tmp[u] = g[i];
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int i = i0 + u * kPlaneThreads;
+            if (i < n_el) {
+                const int z = (int)fdiv((uint32_t)i, A.ny_div), y = i - z * ny;
+                plane[z * SP + padded(y)] = tmp[u];
+            }
+        }
     }
     stage_table(twy, A.twy, ny);
     stage_table(twz, A.twz, nz);

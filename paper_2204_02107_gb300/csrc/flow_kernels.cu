@@ -107,9 +107,12 @@ __global__ void __launch_bounds__(TX * TY) k_stage(StageArgs<T> a, FlowConsts<T>
         ld4(a.qs, zb + rowp + x, qp[1]);
 #pragma unroll
         for (int f = 0; f < 4; ++f) { qm[2][f] = qzm[f]; qp[2][f] = qzp[f]; }
-        T qn[4], ac[4];
-        if (STAGE == 2 || STAGE == 3) ld4(a.qn, ic, qn);
-        if (STAGE >= 2) ld4(a.acc, ic, ac);   // read by its owner thread before that thread overwrites it
+        T qn[4], q2[4], q3[4];
+        if (STAGE >= 2) ld4(a.qn, ic, qn);
+        if (STAGE == 4) {   // read by their owner thread before it overwrites q2 with q* (in place, own cell only)
+            ld4(a.q2, ic, q2);
+            ld4(a.q3, ic, q3);
+        }
         const uint8_t mxm = __ldg(a.mask + zb + rowc + xm), mxp = __ldg(a.mask + zb + rowc + xp);
         const uint8_t mym = __ldg(a.mask + zb + rowm + x), myp = __ldg(a.mask + zb + rowp + x);
         const T bm[3] = {beta_of<T>(mxm), beta_of<T>(mym), beta_of<T>(mzm)};
@@ -142,17 +145,18 @@ __global__ void __launch_bounds__(TX * TY) k_stage(StageArgs<T> a, FlowConsts<T>
             kq[3] = beta * (-conv + k.alpha * diff + S * (k.cset - c0) * k.inv_tau);
         }
 
-        // RK4 combine (classic tableau: nodes 0, 1/2, 1/2, 1; weights 1/6, 1/3, 1/3, 1/6)
-        T o1[4], o2[4];
+        // RK4 combine, classic tableau (nodes 0, 1/2, 1/2, 1; weights 1/6, 1/3, 1/3, 1/6) with the stage states as
+        // the only registers: q2 = q_n + dt/2 k1, q3 = q_n + dt/2 k2, q4 = q_n + dt k3, so that
+        // q* = q_n + dt/6 (k1 + 2 k2 + 2 k3 + k4) = (q2 + 2 q3 + q4 - q_n) / 3 + dt/6 k4  (q4 is the stencil centre)
+        T o[4];
 #pragma unroll
         for (int f = 0; f < 4; ++f) {
-            if (STAGE == 1) { o1[f] = q0[f] + k.dt6 * kq[f]; o2[f] = q0[f] + k.dt2 * kq[f]; }
-            else if (STAGE == 2) { o1[f] = ac[f] + k.dt3 * kq[f]; o2[f] = qn[f] + k.dt2 * kq[f]; }
-            else if (STAGE == 3) { o1[f] = ac[f] + k.dt3 * kq[f]; o2[f] = qn[f] + k.dt * kq[f]; }
-            else { o1[f] = T(0); o2[f] = ac[f] + k.dt6 * kq[f]; }
+            if (STAGE == 1) o[f] = q0[f] + k.dt2 * kq[f];
+            else if (STAGE == 2) o[f] = qn[f] + k.dt2 * kq[f];
+            else if (STAGE == 3) o[f] = qn[f] + k.dt * kq[f];
+            else o[f] = (q2[f] + T(2) * q3[f] + q0[f] - qn[f]) * k.third + k.dt6 * kq[f];
         }
-        if (STAGE <= 3) st4(a.acc, ic, o1);
-        st4(a.out, ic, o2);
+        st4(a.out, ic, o);
 #pragma unroll
         for (int f = 0; f < 4; ++f) { qzm[f] = q0[f]; q0[f] = qzp[f]; qzp[f] = qn2[f]; }
         mzm = m0;

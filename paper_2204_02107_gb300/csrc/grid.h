@@ -23,8 +23,8 @@ struct vf_grid {
     int fail_alloc_at = 0;       // fault injection: the n-th allocation of this grid fails (0 = off)
 
     void* q = nullptr;           // state (u, v, w, c) per cell as a 4-vector
-    void* acc = nullptr;         // RK4 accumulator
-    void* qa = nullptr;          // RK4 stage states
+    void* acc = nullptr;         // RK4 stage states (q2, q3, q4 and q*; see enqueue_step)
+    void* qa = nullptr;
     void* qb = nullptr;
     void* p = nullptr;
     void* f = nullptr;           // right-hand side of Eq. 9: D u* / dt, plus the correction next to solids

@@ -33,6 +33,7 @@ struct FlowConsts {
     T ih2[3];     // 1 / h_j^2
     T nu, alpha, inv_tau;
     T dt6, dt3, dt2, dt;  // dt/6, dt/3, dt/2, dt
+    T third;              // 1/3
     T bf[3];      // body force
     T uset[3];    // forcing target velocity
     T cset;       // forcing target scalar
@@ -40,12 +41,13 @@ struct FlowConsts {
 };
 
 // Pointers of one RK4 stage.  Every state array holds one 4-vector (u, v, w, c) of T per cell (16 bytes for
-// float, 32 for double): q_s (stencil input), q_n, the accumulator and the output state.
+// float, 32 for double): q_s (stencil input), q_n, the stage states q2, q3 (read by stage 4) and the output.
 template <typename T>
 struct StageArgs {
     const void* qs;
     const void* qn;
-    void* acc;
+    const void* q2;
+    const void* q3;
     void* out;
     const uint8_t* mask;
 };
@@ -77,8 +79,9 @@ struct FftStage {
     FastDiv m_div;    // item -> item / tstride (in-place passes)
 };
 
-// One FFT axis: length and radix schedule (product of the radices == n).  Powers of two go into as many radix-8
-// passes as possible (a remainder of 2 becomes 4 x 4 or a 4), then the factors 3 and 5.
+// One FFT axis: length and radix schedule (product of the radices == n).  The power-of-two part takes as few
+// passes as possible: radix-16 passes where they need fewer passes than radix 8 (e.g. 128 = 16 x 8), otherwise
+// radix-8 passes with a remainder of 2 as 4 x 4 or a 4; then the factors 3 and 5.
 struct FftAxis {
     int n;
     int nstages;
@@ -92,12 +95,24 @@ inline FftAxis make_fft_axis(int n)
     int rad[kMaxRadixStages], k = 0;
     int m = n, twos = 0;
     while (m % 2 == 0) { m /= 2; ++twos; }
-    int eights = twos / 3;
-    const int rem = twos % 3;
-    if (rem == 1 && eights > 0) { --eights; rad[k++] = 4; rad[k++] = 4; }
-    else if (rem == 1) rad[k++] = 2;
-    else if (rem == 2) rad[k++] = 4;
-    for (int i = 0; i < eights && k < kMaxRadixStages; ++i) rad[k++] = 8;
+    const int p16 = (twos + 3) / 4, p8 = (twos + 2) / 3;
+    if (twos >= 4 && p16 < p8) {
+        // p16 passes: radix 16 while at least 4 factors of two remain for it, the rest as 8, 4 or 2
+        int left = twos;
+        for (int i = 0; i < p16 && k < kMaxRadixStages; ++i) {
+            const int passes_left = p16 - i;
+            const int e = (left + passes_left - 1) / passes_left >= 4 ? 4 : (left + passes_left - 1) / passes_left;
+            rad[k++] = 1 << e;
+            left -= e;
+        }
+    } else {
+        int eights = twos / 3;
+        const int rem = twos % 3;
+        if (rem == 1 && eights > 0) { --eights; rad[k++] = 4; rad[k++] = 4; }
+        else if (rem == 1) rad[k++] = 2;
+        else if (rem == 2) rad[k++] = 4;
+        for (int i = 0; i < eights && k < kMaxRadixStages; ++i) rad[k++] = 8;
+    }
     while (m % 3 == 0 && k < kMaxRadixStages) { m /= 3; rad[k++] = 3; }
     while (m % 5 == 0 && k < kMaxRadixStages) { m /= 5; rad[k++] = 5; }
     a.nstages = k;
@@ -168,7 +183,7 @@ inline void digit_reversal(const FftAxis& ax, int* out)
 }
 
 // Block size of the plane kernel (one CTA per kx plane, the plane in shared memory, at most 200 KB).
-constexpr int kPlaneThreads = 1024;
+constexpr int kPlaneThreads = 512;
 
 // Reduction scratch: per-CTA partial sums and histogram counts, and the output records.
 struct ReduceArgsDev {
