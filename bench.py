@@ -234,6 +234,7 @@ def bench_large_room(stream, steps):
     from paper_2204_02107_gb300 import native, rooms
     room = rooms.large_room()
     g = native.room_grid(room, precision="fp32", stream=stream.cuda_stream, history_capacity=max(16, steps + 3))
+    g.autotune(reps=5)
     g.step(3, reduce_every=1)
     g.sync()
     sec = time_grid_steps(g, steps, stream)
@@ -249,7 +250,8 @@ def bench_batch(stream, steps):
     import torch
     from paper_2204_02107_gb300 import native, rooms
     rs = rooms.batch_rooms(64)
-    b = native.Batch(max_slots=64, hbm_budget_bytes=120 << 30, reduce_every=1, stream=stream.cuda_stream)
+    b = native.Batch(max_slots=64, hbm_budget_bytes=120 << 30, reduce_every=1, stream=stream.cuda_stream,
+                     autotune=5)
     total = 0
     for r in rs:
         b.add(native.room_desc(r, precision="fp32", history_capacity=max(16, steps + 3)), r.beta, r.S,
@@ -265,7 +267,8 @@ def bench_batch(stream, steps):
     sec = start.elapsed_time(end) / 1e3
     info = b.info()
     b.close()
-    return {"workload": "64 rooms 64^3..192x96x96 in one batch graph per step, FP32 bulk + FP64 reductions",
+    return {"workload": "64 rooms 64^3..192x96x96 in one batch graph per step, FP32 bulk + FP64 reductions, "
+                        "tiles autotuned per room shape on admission",
             "value": total * steps / sec / 1e9, "unit": UNIT, "ms_per_batch_step": sec * 1e3 / steps,
             "steps": steps, "rooms": len(rs), "cells": total, "bytes_in_use": info["bytes_in_use"]}
 
@@ -342,6 +345,7 @@ def main():
     ap.add_argument("--extra-steps", type=int, default=30, help="timed steps of the large-room and batch legs")
     ap.add_argument("--serve-requests", type=int, default=24, help="requests of the serving leg (0: skip)")
     ap.add_argument("--no-extras", action="store_true", help="skip the large-room, batch and serving legs")
+    ap.add_argument("--no-autotune", action="store_true", help="launch with the default tiles")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -355,6 +359,7 @@ def main():
     room = rooms.single_room(256, 128, 128)
     stream = torch.cuda.Stream()
     g = native.room_grid(room, precision="fp32", stream=stream.cuda_stream)
+    tiles = g.tiles() if args.no_autotune else g.autotune(reps=20)
     cells = room.cells
     launches_per_step = None   # counted from the profiled steps below
 
@@ -410,6 +415,7 @@ def main():
 
     # FP64 form of the same step (parity path)
     g64 = native.room_grid(room, precision="fp64", stream=stream.cuda_stream)
+    tiles64 = g64.tiles() if args.no_autotune else g64.autotune(reps=5)
     g64.step(3, reduce_every=1)
     g64.sync()
     s64, e64 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -437,7 +443,8 @@ def main():
                                "FP32 bulk + FP64 reductions every step, filter on, 4 pressure iterations",
                    "cells": cells, "global_cells": cells * world, "precision": "fp32_mixed",
                    "l2": "state 0.3 GB > 126 MB L2: inputs larger than L2, no flush",
-                   "parallelism": "one independent room per GPU" if world > 1 else "single GPU"},
+                   "parallelism": "one independent room per GPU" if world > 1 else "single GPU",
+                   "tiles": tiles, "tiles_source": "defaults" if args.no_autotune else "autotuned before warm-up"},
         "roofline": {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                      "algorithmic_bytes_per_launch": g_b / g_n, "launches_per_step": g_n / prof_steps,
@@ -446,7 +453,7 @@ def main():
                           "frac": step_gbs / peak, "peak_kind": peak_kind},
         "kernels": per_kernel,
         "fp64": {"value": cells * args.fp64_steps / (fp64_ms / 1e3) / 1e9, "unit": UNIT,
-                 "ms_per_step": fp64_ms / args.fp64_steps, "steps": args.fp64_steps},
+                 "ms_per_step": fp64_ms / args.fp64_steps, "steps": args.fp64_steps, "tiles": tiles64},
         "e2e": e2e,
         "gpu_launches": int(round(sum(n for _, n in phases.values()) / prof_steps)) * args.steps,
         "clocks": clocks.summary(),

@@ -174,6 +174,39 @@ int vf_info(const vf_grid* g, double* t, int64_t* step, int64_t* cells, int64_t*
  * scratch; stream-ordered on the grid's stream, returns without waiting. */
 int vf_poisson_solve(vf_grid* g, const void* f, void* p);
 
+/* ---- launch tiles and the autotuner ---------------------------------------------------------------------- */
+
+/* Planes one CTA of a stencil kernel marches along z, per kernel family (the paper has no counterpart: these are
+ * launch shapes of this implementation).  A tile changes no field value; the FP64 reductions are summed per CTA,
+ * so their last bits follow zc_filter.  Each chunk lies in [VF_ZCHUNK_MIN, VF_ZCHUNK_MAX]. */
+#define VF_ZCHUNK_MIN 4
+#define VF_ZCHUNK_MAX 64
+typedef struct vf_tiles {
+    int32_t zc_stage;    /* the four RK4 stage kernels */
+    int32_t zc_div;      /* divergence */
+    int32_t zc_project;  /* projection */
+    int32_t zc_filter;   /* filter, and the reductions it carries (also the standalone reductions) */
+} vf_tiles;
+
+/* The tiles a grid launches with.  A new grid takes the process-wide tile cache's entry for its (nx, ny, nz,
+ * precision) if there is one, else (8, 8, 8, 16). */
+int vf_get_tiles(const vf_grid* g, vf_tiles* out);
+
+/* Set a grid's tiles (VF_EINVAL if a chunk is out of range; the grid is unchanged then).  Takes effect at the next
+ * vf_step (the step graph is captured again). */
+int vf_set_tiles(vf_grid* g, const vf_tiles* t);
+
+/* Autotuner: time every chunk in {4, 8, 16, 32} for each kernel family on this grid's own arrays (reps launches
+ * each after one warm-up, CUDA events on the grid's stream, the least mean time wins), set the winners on the grid,
+ * store them in the tile cache under the grid's (nx, ny, nz, precision) and copy them to *chosen (may be NULL).
+ * Only scratch arrays are written: the state, the pressure, the history and the step count are unchanged.  Waits;
+ * reps in [1, 1000].  Other work on the GPU at the same time perturbs the timings. */
+int vf_autotune(vf_grid* g, int32_t reps, vf_tiles* chosen);
+
+/* Tile cache: look up (1 found and *out set, 0 not found), or forget every entry. */
+int vf_tile_cache_lookup(int32_t nx, int32_t ny, int32_t nz, int32_t precision, vf_tiles* out);
+int vf_tile_cache_clear(void);
+
 /* ---- batched rooms and continuous batching (many rooms advanced together) --------------------------------- */
 
 /* Device bytes vf_create_grid will allocate for a description (used for admission by memory budget). */
@@ -185,6 +218,9 @@ typedef struct vf_batch_desc {
     int64_t hbm_budget_bytes;    /* admission limit: sum of vf_grid_bytes of the rooms held */
     int32_t reduce_every;        /* record each room's reductions every k batch steps (0 = never) */
     void* cuda_stream;           /* stream the batch graph runs on; NULL -> a stream the batch creates */
+    int32_t autotune;            /* > 0: a room whose (nx, ny, nz, precision) has no tile-cache entry is autotuned
+                                    with this many reps when admitted (the batch stream is drained first, so the
+                                    timings see an idle GPU); 0: rooms take the cached or default tiles */
 } vf_batch_desc;
 
 /* Empty batch.  One batch step advances every running room by one time step through a single CUDA graph launch

@@ -6,6 +6,9 @@
 // advances every room, and the rooms' kernels run concurrently on the GPU.  Each room's arithmetic is exactly the
 // one it would do alone, so a room's fields are bitwise the same alone and in any mix.
 //
+// Launch tiles: with autotune set, the first room of each (nx, ny, nz, precision) is autotuned on admission and
+// the result cached; later rooms of that shape, and grids created alone, take the cached tiles.
+//
 // Admission: a room is accepted only while the bytes its grid allocates (vf_grid_bytes) fit in the batch's budget.
 // Rooms run for their own number of steps; vf_batch_step advances in chunks that end when some room finishes, so
 // no room is stepped past its target.  Finished rooms keep their results until vf_batch_remove.
@@ -99,7 +102,9 @@ extern "C" {
 
 int vf_batch_create(const vf_batch_desc* d, vf_batch** out)
 {
-    if (!d || !out || d->max_slots < 1 || d->hbm_budget_bytes <= 0 || d->reduce_every < 0) return VF_EINVAL;
+    if (!d || !out || d->max_slots < 1 || d->hbm_budget_bytes <= 0 || d->reduce_every < 0 || d->autotune < 0 ||
+        d->autotune > 1000)
+        return VF_EINVAL;
     *out = nullptr;
     vf_batch* b = new vf_batch();
     b->d = *d;
@@ -162,6 +167,12 @@ int vf_batch_add(vf_batch* b, const vf_grid_desc* gd, const uint8_t* beta, const
     if ((rc = vf_set_inflow(g, S, u_set, c_set, mem))) return undo(rc);
     if (room && (rc = vf_set_region(g, room, mem))) return undo(rc);
     if (c0 && (rc = vf_set_field(g, VF_C, c0, c0_is_fp64, mem))) return undo(rc);
+    if (b->d.autotune > 0 && vf_tile_cache_lookup(desc.nx, desc.ny, desc.nz, desc.precision, nullptr) == 0) {
+        // a shape seen for the first time: tune on an idle GPU (the running rooms are drained first)
+        const cudaError_t e = cudaStreamSynchronize(b->stream);
+        if (e != cudaSuccess) { vf_destroy(g); return bfail(b, e, "vf_batch_add: drain before autotune"); }
+        if ((rc = vf_autotune(g, b->d.autotune, nullptr))) return undo(rc);
+    }
     vf_batch_slot& s = b->slots[(size_t)free_slot];
     if (!s.join && cudaEventCreateWithFlags(&s.join, cudaEventDisableTiming) != cudaSuccess) return undo(VF_ECUDA);
     s.g = g;

@@ -12,6 +12,8 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -99,6 +101,7 @@ FlowConsts<T> flow_consts(const vf_grid* g)
     FlowConsts<T> k{};
     const vf_grid_desc& d = g->d;
     k.nx = d.nx; k.ny = d.ny; k.nz = d.nz;
+    for (int i = 0; i < vf::kZcKinds; ++i) k.zc[i] = g->zc[i];
     const double h[3] = {d.lx / d.nx, d.ly / d.ny, d.lz / d.nz};
     for (int j = 0; j < 3; ++j) {
         k.i2h[j] = (T)(1.0 / (2.0 * h[j]));
@@ -457,8 +460,14 @@ int vf_create_grid(const vf_grid_desc* d, vf_grid** out)
     if (!(g->staging = galloc(g, g->N * 8))) return fail(VF_ENOMEM);
     if (!(g->mask = (uint8_t*)galloc(g, g->N))) return fail(VF_ENOMEM);
 
+    {
+        vf_tiles t{};
+        if (vf_tile_cache_lookup(d->nx, d->ny, d->nz, d->precision, &t) == 1) {
+            g->zc[0] = t.zc_stage; g->zc[1] = t.zc_div; g->zc[2] = t.zc_project; g->zc[3] = t.zc_filter;
+        }
+    }
     const FlowConsts<float> kf = flow_consts<float>(g);
-    g->nred = Kernels<float>::reduce_blocks(kf);
+    g->nred = Kernels<float>::reduce_blocks(kf);   // enough partial slots for the smallest filter chunk
     if (!(g->red_partial = (double*)galloc(g, (size_t)g->nred * vf::kRedSlots * sizeof(double)))) return fail(VF_ENOMEM);
     if (!(g->hist_accum = (unsigned long long*)galloc(g, (vf::kHistBins + 2) * sizeof(unsigned long long))))
         return fail(VF_ENOMEM);
@@ -769,6 +778,196 @@ const char* vf_last_error(const vf_grid* g)
 {
     if (!g) return "null grid";
     return g->err.c_str();
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------------------------------------------------
+// Launch tiles and the autotuner
+// ------------------------------------------------------------------------------------------------------------
+namespace {
+
+struct TileKey {
+    int nx, ny, nz, precision;
+    bool operator<(const TileKey& o) const
+    {
+        if (nx != o.nx) return nx < o.nx;
+        if (ny != o.ny) return ny < o.ny;
+        if (nz != o.nz) return nz < o.nz;
+        return precision < o.precision;
+    }
+};
+
+std::mutex& tile_mutex()
+{
+    static std::mutex m;
+    return m;
+}
+
+std::map<TileKey, vf_tiles>& tile_cache()
+{
+    static std::map<TileKey, vf_tiles> c;
+    return c;
+}
+
+bool tiles_valid(const vf_tiles& t)
+{
+    for (int v : {t.zc_stage, t.zc_div, t.zc_project, t.zc_filter})
+        if (v < vf::kZChunkMin || v > vf::kZChunkMax) return false;
+    return true;
+}
+
+// Mean milliseconds of `reps` enqueues of `launch` on the grid's stream, after one warm-up enqueue.
+template <typename F>
+cudaError_t time_launches(cudaStream_t st, int reps, F&& launch, float* ms)
+{
+    cudaEvent_t a = nullptr, b = nullptr;
+    cudaError_t e = cudaEventCreate(&a);
+    if (e == cudaSuccess) e = cudaEventCreate(&b);
+    if (e == cudaSuccess) e = launch();
+    if (e == cudaSuccess) e = cudaEventRecord(a, st);
+    for (int i = 0; i < reps && e == cudaSuccess; ++i) e = launch();
+    if (e == cudaSuccess) e = cudaEventRecord(b, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(b);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(ms, a, b);
+    if (e == cudaSuccess) *ms /= (float)reps;
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    return e;
+}
+
+// Each family is timed on the grid's arrays exactly as a step launches it, except that every output goes to a
+// scratch array: stage states (qa, qb, acc), divergence (f), projection (qb, no step tick), filter (acc, its
+// reduction record and non-finite flag redirected into the staging buffer, no history).
+template <typename T>
+int autotune_t(vf_grid* g, int reps, vf_tiles* best)
+{
+    static const int kCand[] = {4, 8, 16, 32};
+    FlowConsts<T> k = flow_consts<T>(g);
+    const cudaStream_t st = g->stream;
+    vf::ReduceArgsDev ra = reduce_args(g);
+    const bool redirect = g->N * 8 >= sizeof(vf_reduce) + 256;
+    if (redirect) {
+        ra.out = (vf_reduce*)g->staging;
+        ra.nonfinite = (int*)((char*)g->staging + ((sizeof(vf_reduce) + 255) & ~(size_t)255));
+    }
+    int chosen[vf::kZcKinds];
+    for (int fam = 0; fam < vf::kZcKinds; ++fam) {
+        float best_ms = 0.f;
+        chosen[fam] = g->zc[fam];
+        int prev = 0;
+        for (int c : kCand) {
+            // chunks at or beyond nz all launch one CTA per column: time only the first of them
+            const int eff = std::min(c, k.nz);
+            if (eff == prev) continue;
+            prev = eff;
+            k.zc[fam] = c;
+            auto launch = [&]() -> cudaError_t {
+                StageArgs<T> a{};
+                a.mask = g->mask;
+                a.qn = g->q;
+                cudaError_t e = cudaSuccess;
+                switch (fam) {
+                    case vf::kZcStage:
+                        a.qs = g->q; a.out = g->qa;
+                        if ((e = Kernels<T>::stage(1, a, k, st)) != cudaSuccess) return e;
+                        a.qs = g->qa; a.out = g->qb;
+                        if ((e = Kernels<T>::stage(2, a, k, st)) != cudaSuccess) return e;
+                        a.qs = g->qb; a.out = g->acc;
+                        if ((e = Kernels<T>::stage(3, a, k, st)) != cudaSuccess) return e;
+                        a.qs = g->acc; a.q2 = g->qa; a.q3 = g->qb; a.out = g->qa;
+                        return Kernels<T>::stage(4, a, k, st);
+                    case vf::kZcDiv: return Kernels<T>::divergence(g->qa, (T*)g->f, k, st);
+                    case vf::kZcProject:
+                        return Kernels<T>::project(g->qa, (const T*)g->p, g->qb, g->mask, nullptr, k, st);
+                    default:
+                        if (!g->d.filter) return Kernels<T>::reduce(g->qb, g->mask, k, ra, 0, st);
+                        return Kernels<T>::filter(g->qb, g->acc, g->mask, k, redirect ? &ra : nullptr, 0, st);
+                }
+            };
+            float ms = 0.f;
+            const cudaError_t e = time_launches(st, reps, launch, &ms);
+            if (e != cudaSuccess) return fail_cuda(g, e, "vf_autotune");
+            if (best_ms == 0.f || ms < best_ms) {
+                best_ms = ms;
+                chosen[fam] = c;
+            }
+        }
+        k.zc[fam] = chosen[fam];
+    }
+    best->zc_stage = chosen[0];
+    best->zc_div = chosen[1];
+    best->zc_project = chosen[2];
+    best->zc_filter = chosen[3];
+    return VF_OK;
+}
+
+void apply_tiles(vf_grid* g, const vf_tiles& t)
+{
+    g->zc[vf::kZcStage] = t.zc_stage;
+    g->zc[vf::kZcDiv] = t.zc_div;
+    g->zc[vf::kZcProject] = t.zc_project;
+    g->zc[vf::kZcFilter] = t.zc_filter;
+    drop_graphs(g);
+}
+
+}  // namespace
+
+extern "C" {
+
+int vf_get_tiles(const vf_grid* g, vf_tiles* out)
+{
+    if (!g || !out) return VF_EINVAL;
+    out->zc_stage = g->zc[vf::kZcStage];
+    out->zc_div = g->zc[vf::kZcDiv];
+    out->zc_project = g->zc[vf::kZcProject];
+    out->zc_filter = g->zc[vf::kZcFilter];
+    return VF_OK;
+}
+
+int vf_set_tiles(vf_grid* g, const vf_tiles* t)
+{
+    int rc = check(g);
+    if (rc) return rc;
+    if (!t || !tiles_valid(*t)) return set_err(g, VF_EINVAL, "vf_set_tiles: chunk out of range");
+    VF_CK(cudaStreamSynchronize(g->stream));
+    apply_tiles(g, *t);
+    return VF_OK;
+}
+
+int vf_autotune(vf_grid* g, int32_t reps, vf_tiles* chosen)
+{
+    int rc = check(g);
+    if (rc) return rc;
+    if (reps < 1 || reps > 1000) return set_err(g, VF_EINVAL, "vf_autotune: reps outside [1, 1000]");
+    VF_CK(cudaStreamSynchronize(g->stream));
+    vf_tiles t{};
+    rc = g->fp64 ? autotune_t<double>(g, reps, &t) : autotune_t<float>(g, reps, &t);
+    if (rc) return rc;
+    VF_CK(cudaStreamSynchronize(g->stream));
+    apply_tiles(g, t);
+    {
+        std::lock_guard<std::mutex> lock(tile_mutex());
+        tile_cache()[TileKey{g->d.nx, g->d.ny, g->d.nz, g->d.precision}] = t;
+    }
+    if (chosen) *chosen = t;
+    return VF_OK;
+}
+
+int vf_tile_cache_lookup(int32_t nx, int32_t ny, int32_t nz, int32_t precision, vf_tiles* out)
+{
+    std::lock_guard<std::mutex> lock(tile_mutex());
+    auto it = tile_cache().find(TileKey{nx, ny, nz, precision});
+    if (it == tile_cache().end()) return 0;
+    if (out) *out = it->second;
+    return 1;
+}
+
+int vf_tile_cache_clear(void)
+{
+    std::lock_guard<std::mutex> lock(tile_mutex());
+    tile_cache().clear();
+    return VF_OK;
 }
 
 }  // extern "C"

@@ -17,9 +17,10 @@
 namespace vf {
 namespace {
 
+// Tile of a CTA (x by y threads).  Each CTA marches k.zc[kind] planes along z; the z-chunks are run-time
+// parameters per kernel family (FlowConsts::zc), chosen by the autotuner or the defaults.
 constexpr int TX = 32;
 constexpr int TY = 8;
-constexpr int ZCHUNK = 16;   // planes per CTA along z
 
 __device__ __forceinline__ void ld4(const void* base, int i, float q[4])
 {
@@ -64,15 +65,17 @@ __device__ __forceinline__ T beta_of(uint8_t m) { return (m & kBitBeta) ? T(1) :
 //              + S (cset - c^0) inv_tau ],  F^+ = beta^+ (U_j^0 c^0 + U_j^+ c^+) / 2 (face weight beta^0 beta^+,
 //              beta^0 is applied by the outer factor)
 template <typename T, int STAGE>
-__global__ void __launch_bounds__(TX * TY) k_stage(StageArgs<T> a, FlowConsts<T> k)
+__global__ void __launch_bounds__(TX * TY)
+k_stage(StageArgs<T> a, FlowConsts<T> k)
 {
     const int x = blockIdx.x * TX + threadIdx.x;
     const int y = blockIdx.y * TY + threadIdx.y;
     if (x >= k.nx || y >= k.ny) return;
     const int nx = k.nx, ny = k.ny, nz = k.nz;
     const int plane = nx * ny;
-    const int z0 = blockIdx.z * ZCHUNK;
-    const int z1 = min(z0 + ZCHUNK, nz);
+    const int zc = k.zc[kZcStage];
+    const int z0 = blockIdx.z * zc;
+    const int z1 = min(z0 + zc, nz);
     const int xm = wrap(x - 1, nx), xp = wrap(x + 1, nx);
     const int rowc = y * nx, rowm = wrap(y - 1, ny) * nx, rowp = wrap(y + 1, ny) * nx;
 
@@ -176,7 +179,7 @@ __global__ void __launch_bounds__(TX * TY) k_div(const void* __restrict__ q, T* 
     if (x >= k.nx || y >= k.ny) return;
     const int nx = k.nx, ny = k.ny, nz = k.nz;
     const int plane = nx * ny;
-    const int z0 = blockIdx.z * ZCHUNK, z1 = min(z0 + ZCHUNK, nz);
+    const int z0 = blockIdx.z * k.zc[kZcDiv], z1 = min(z0 + k.zc[kZcDiv], nz);
     const int rowc = y * nx, rowm = wrap(y - 1, ny) * nx, rowp = wrap(y + 1, ny) * nx;
     const int xm = wrap(x - 1, nx), xp = wrap(x + 1, nx);
     T wzm = ld1<T>(q, wrap(z0 - 1, nz) * plane + rowc + x, 2);
@@ -210,7 +213,7 @@ __global__ void __launch_bounds__(TX * TY) k_project(const void* __restrict__ qs
     if (x >= k.nx || y >= k.ny) return;
     const int nx = k.nx, ny = k.ny, nz = k.nz;
     const int plane = nx * ny;
-    const int z0 = blockIdx.z * ZCHUNK, z1 = min(z0 + ZCHUNK, nz);
+    const int z0 = blockIdx.z * k.zc[kZcProject], z1 = min(z0 + k.zc[kZcProject], nz);
     const int rowc = y * nx, rowm = wrap(y - 1, ny) * nx, rowp = wrap(y + 1, ny) * nx;
     const int xm = wrap(x - 1, nx), xp = wrap(x + 1, nx);
     T pzm = __ldg(p + wrap(z0 - 1, nz) * plane + rowc + x);
@@ -234,7 +237,7 @@ __global__ void __launch_bounds__(TX * TY) k_project(const void* __restrict__ qs
 
 // ------------------------------------------------------------------------------------------------------------
 // Reductions (a11).  Each thread accumulates the cells it visits (CellStats): compensated (TwoSum) float sums for
-// the scalar inventories, plain per-thread sums of at most ZCHUNK values for energy and squared divergence, an
+// the scalar inventories, plain per-thread sums of at most one z-chunk of values for energy and squared divergence, an
 // exact room-cell count, and the histogram as runs of equal bins (one shared atomic per run).  The CTA epilogue
 // combines the warps in float-float arithmetic, writes one FP64 partial per quantity, and the last CTA to finish
 // (atomic ticket) adds the partials in CTA order, so the result does not depend on scheduling.  A NaN or Inf in a
@@ -444,7 +447,7 @@ __global__ void __launch_bounds__(TX * TY) k_reduce(const void* __restrict__ q, 
     if (x < k.nx && y < k.ny) {
         const int nx = k.nx, ny = k.ny, nz = k.nz;
         const int plane = nx * ny;
-        const int z0 = blockIdx.z * ZCHUNK, z1 = min(z0 + ZCHUNK, nz);
+        const int z0 = blockIdx.z * k.zc[kZcFilter], z1 = min(z0 + k.zc[kZcFilter], nz);
         const int rowc = y * nx, rowm = wrap(y - 1, ny) * nx, rowp = wrap(y + 1, ny) * nx;
         const int xm = wrap(x - 1, nx), xp = wrap(x + 1, nx);
         T wzm = ld1<T>(q, wrap(z0 - 1, nz) * plane + rowc + x, 2);
@@ -489,7 +492,7 @@ k_filter(const void* __restrict__ in, void* __restrict__ out, const uint8_t* __r
     if (x < k.nx && y < k.ny) {
         const int nx = k.nx, ny = k.ny, nz = k.nz;
         const int plane = nx * ny;
-        const int z0 = blockIdx.z * ZCHUNK, z1 = min(z0 + ZCHUNK, nz);
+        const int z0 = blockIdx.z * k.zc[kZcFilter], z1 = min(z0 + k.zc[kZcFilter], nz);
         const int yc = y * nx;
         // z window of 7 planes of the 4-vector, in registers
         T zw[7][4];
@@ -653,12 +656,12 @@ __global__ void k_near_fill(const uint8_t* __restrict__ mask, size_t n, const in
     }
 }
 
-inline dim3 flow_grid(int nx, int ny, int nz)
+template <typename T>
+inline dim3 flow_grid(const FlowConsts<T>& k, int kind)
 {
-    return dim3((nx + TX - 1) / TX, (ny + TY - 1) / TY, (nz + ZCHUNK - 1) / ZCHUNK);
+    const int zc = k.zc[kind];
+    return dim3((k.nx + TX - 1) / TX, (k.ny + TY - 1) / TY, (k.nz + zc - 1) / zc);
 }
-
-inline dim3 reduce_grid(int nx, int ny, int nz) { return flow_grid(nx, ny, nz); }
 
 inline int elementwise_blocks(size_t n) { return (int)std::min<size_t>((n + 255) / 256, 152 * 16); }
 
@@ -670,7 +673,7 @@ inline int elementwise_blocks(size_t n) { return (int)std::min<size_t>((n + 255)
 template <typename T>
 cudaError_t Kernels<T>::stage(int s, const StageArgs<T>& a, const FlowConsts<T>& k, cudaStream_t st)
 {
-    const dim3 g = flow_grid(k.nx, k.ny, k.nz), b(TX, TY);
+    const dim3 g = flow_grid(k, kZcStage), b(TX, TY);
     switch (s) {
         case 1: k_stage<T, 1><<<g, b, 0, st>>>(a, k); break;
         case 2: k_stage<T, 2><<<g, b, 0, st>>>(a, k); break;
@@ -684,7 +687,7 @@ cudaError_t Kernels<T>::stage(int s, const StageArgs<T>& a, const FlowConsts<T>&
 template <typename T>
 cudaError_t Kernels<T>::divergence(const void* qstar, T* r, const FlowConsts<T>& k, cudaStream_t st)
 {
-    k_div<T><<<flow_grid(k.nx, k.ny, k.nz), dim3(TX, TY), 0, st>>>(qstar, r, k);
+    k_div<T><<<flow_grid(k, kZcDiv), dim3(TX, TY), 0, st>>>(qstar, r, k);
     return cudaGetLastError();
 }
 
@@ -692,7 +695,7 @@ template <typename T>
 cudaError_t Kernels<T>::project(const void* qstar, const T* p, void* out, const uint8_t* mask,
                                 long long* step_counter, const FlowConsts<T>& k, cudaStream_t st)
 {
-    k_project<T><<<flow_grid(k.nx, k.ny, k.nz), dim3(TX, TY), 0, st>>>(qstar, p, out, mask, step_counter, k);
+    k_project<T><<<flow_grid(k, kZcProject), dim3(TX, TY), 0, st>>>(qstar, p, out, mask, step_counter, k);
     return cudaGetLastError();
 }
 
@@ -700,7 +703,7 @@ template <typename T>
 cudaError_t Kernels<T>::filter(const void* in, void* out, const uint8_t* mask, const FlowConsts<T>& k,
                                const ReduceArgsDev* r, int to_history, cudaStream_t st)
 {
-    const dim3 g = flow_grid(k.nx, k.ny, k.nz), b(TX, TY);
+    const dim3 g = flow_grid(k, kZcFilter), b(TX, TY);
     if (r) k_filter<T, true><<<g, b, 0, st>>>(in, out, mask, k, *r, to_history);
     else k_filter<T, false><<<g, b, 0, st>>>(in, out, mask, k, ReduceArgsDev{}, 0);
     return cudaGetLastError();
@@ -709,7 +712,10 @@ cudaError_t Kernels<T>::filter(const void* in, void* out, const uint8_t* mask, c
 template <typename T>
 int Kernels<T>::reduce_blocks(const FlowConsts<T>& k)
 {
-    const dim3 g = reduce_grid(k.nx, k.ny, k.nz);
+    // the most CTAs any allowed filter/reduce z-chunk launches: the smallest chunk
+    FlowConsts<T> c = k;
+    c.zc[kZcFilter] = kZChunkMin;
+    const dim3 g = flow_grid(c, kZcFilter);
     return (int)(g.x * g.y * g.z);
 }
 
@@ -717,7 +723,7 @@ template <typename T>
 cudaError_t Kernels<T>::reduce(const void* q, const uint8_t* mask, const FlowConsts<T>& k, const ReduceArgsDev& r,
                                int to_history, cudaStream_t st)
 {
-    k_reduce<T><<<reduce_grid(k.nx, k.ny, k.nz), dim3(TX, TY), 0, st>>>(q, mask, k, r, to_history);
+    k_reduce<T><<<flow_grid(k, kZcFilter), dim3(TX, TY), 0, st>>>(q, mask, k, r, to_history);
     return cudaGetLastError();
 }
 

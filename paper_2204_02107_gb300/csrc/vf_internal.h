@@ -22,9 +22,15 @@ constexpr uint8_t kBitRoom = 4u;
 constexpr uint8_t kBitNearSolid = 8u;
 
 // Constants of the flow kernels, in the compute precision T.
+// Kernel families with their own z-chunk (planes one CTA marches along z); the allowed range of a chunk.
+enum ZcKind { kZcStage = 0, kZcDiv = 1, kZcProject = 2, kZcFilter = 3, kZcKinds = 4 };
+constexpr int kZChunkMin = 4;
+constexpr int kZChunkMax = 64;
+
 template <typename T>
 struct FlowConsts {
     int nx, ny, nz;
+    int zc[kZcKinds]; // z-chunk per kernel family (the filter's also sets the reduction's CTAs)
     T i2h[3];     // 1 / (2 h_j)
     T i2h_div[3]; // 1 / (2 h_j dt): the divergence is stored divided by dt
     T i2h_dt[3];  // dt / (2 h_j): the pressure is stored as p / rho, the projection subtracts dt G p

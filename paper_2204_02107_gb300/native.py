@@ -43,7 +43,15 @@ class VfGridDesc(C.Structure):
 
 class VfBatchDesc(C.Structure):
     _fields_ = [("max_slots", C.c_int32), ("hbm_budget_bytes", C.c_int64), ("reduce_every", C.c_int32),
-                ("cuda_stream", C.c_void_p)]
+                ("cuda_stream", C.c_void_p), ("autotune", C.c_int32)]
+
+
+class VfTiles(C.Structure):
+    _fields_ = [("zc_stage", C.c_int32), ("zc_div", C.c_int32), ("zc_project", C.c_int32),
+                ("zc_filter", C.c_int32)]
+
+    def to_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
 
 
 class VfReduce(C.Structure):
@@ -89,6 +97,11 @@ _SIGNATURES = {
                           C.POINTER(C.c_int64)]),
     "vf_poisson_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "vf_grid_bytes": (C.c_int64, [C.POINTER(VfGridDesc)]),
+    "vf_get_tiles": (C.c_int, [C.c_void_p, C.POINTER(VfTiles)]),
+    "vf_set_tiles": (C.c_int, [C.c_void_p, C.POINTER(VfTiles)]),
+    "vf_autotune": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(VfTiles)]),
+    "vf_tile_cache_lookup": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.POINTER(VfTiles)]),
+    "vf_tile_cache_clear": (C.c_int, []),
     "vf_batch_create": (C.c_int, [C.POINTER(VfBatchDesc), C.POINTER(C.c_void_p)]),
     "vf_batch_destroy": (C.c_int, [C.c_void_p]),
     "vf_batch_add": (C.c_int, [C.c_void_p, C.POINTER(VfGridDesc), C.c_void_p, C.c_void_p, C.c_void_p,
@@ -200,8 +213,9 @@ class Batch:
     """Rooms of uneven size advanced together (vf_batch_*): one CUDA graph launch per batch step, one branch per
     room.  Slots are admitted against ``hbm_budget_bytes``."""
 
-    def __init__(self, max_slots, hbm_budget_bytes, reduce_every=1, stream=None):
-        d = VfBatchDesc(max_slots, int(hbm_budget_bytes), reduce_every, C.c_void_p(stream) if stream else None)
+    def __init__(self, max_slots, hbm_budget_bytes, reduce_every=1, stream=None, autotune=0):
+        d = VfBatchDesc(max_slots, int(hbm_budget_bytes), reduce_every, C.c_void_p(stream) if stream else None,
+                        int(autotune))
         h = C.c_void_p()
         rc = lib().vf_batch_create(C.byref(d), C.byref(h))
         if rc != VF_OK:
@@ -405,10 +419,37 @@ class Grid:
         self._check(lib().vf_profile_steps(self._h, int(n), int(reduce_every), ms, cnt), "vf_profile_steps")
         return {lib().vf_phase_name(i).decode(): (ms[i], cnt[i]) for i in range(N_PHASES) if cnt[i] > 0}
 
+    def tiles(self):
+        """The launch tiles (z-chunks per kernel family) of this grid."""
+        t = VfTiles()
+        self._check(lib().vf_get_tiles(self._h, C.byref(t)), "vf_get_tiles")
+        return t.to_dict()
+
+    def set_tiles(self, zc_stage, zc_div, zc_project, zc_filter):
+        t = VfTiles(zc_stage, zc_div, zc_project, zc_filter)
+        self._check(lib().vf_set_tiles(self._h, C.byref(t)), "vf_set_tiles")
+
+    def autotune(self, reps=5):
+        """Time every z-chunk per kernel family on this grid, keep the fastest and cache it for the shape."""
+        t = VfTiles()
+        self._check(lib().vf_autotune(self._h, int(reps), C.byref(t)), "vf_autotune")
+        return t.to_dict()
+
     def poisson_solve(self, f, p):
         """Solve L p = f on the device (f, p: contiguous CUDA tensors in the grid's precision)."""
         self._check(lib().vf_poisson_solve(self._h, C.c_void_p(f.data_ptr()), C.c_void_p(p.data_ptr())),
                     "vf_poisson_solve")
+
+
+def tile_cache_lookup(nx, ny, nz, precision="fp32"):
+    """The cached tiles of a shape, or None."""
+    t = VfTiles()
+    prec = VF_FP64 if precision == "fp64" else VF_FP32_MIXED
+    return t.to_dict() if lib().vf_tile_cache_lookup(nx, ny, nz, prec, C.byref(t)) == 1 else None
+
+
+def tile_cache_clear():
+    lib().vf_tile_cache_clear()
 
 
 def poisson_solve_noalloc(nx, ny, nz, lx, ly, lz, f, p, stream=None):
