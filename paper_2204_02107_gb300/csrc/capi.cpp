@@ -138,6 +138,9 @@ PoissonArgs<T> poisson_args(const vf_grid* g, T* f, T* p, int use_mask)
     a.near_r = (T*)g->near_r;
     a.n_near = use_mask ? g->n_near : 0;
     a.plane_layout = g->plane_layout ? 1 : 0;
+    a.reg = g->reg;
+    a.gx = g->reg_gx; a.gy = g->reg_gy; a.gz = g->reg_gz;
+    a.reg_sp = g->reg_sp; a.reg_spx = g->reg_spx; a.reg_sb = g->reg_sb;
     a.spec = g->spec;
     a.twx = g->twx; a.twy = g->twy; a.twz = g->twz; a.twr = g->twr;
     a.lamx = (const T*)g->lamx; a.lamy = (const T*)g->lamy; a.lamz = (const T*)g->lamz;
@@ -318,6 +321,13 @@ int build_tables_t(vf_grid* g)
     }
     VF_CK(cudaStreamSynchronize(g->stream));   // host vectors die here
     g->plane_layout = Kernels<T>::plane_fits(d.ny, d.nz) && !std::getenv("VF_TILE_FFT");
+    if (g->plane_layout && !std::getenv("VF_GENERIC_FFT")) {
+        PoissonArgs<T> ra = poisson_args<T>(g, nullptr, nullptr, 0);
+        vf::RegFft<T>::configure(ra);
+        g->reg = ra.reg;
+        g->reg_gx = ra.gx; g->reg_gy = ra.gy; g->reg_gz = ra.gz;
+        g->reg_sp = ra.reg_sp; g->reg_spx = ra.reg_spx; g->reg_sb = ra.reg_sb;
+    }
     const PoissonArgs<T> pa = poisson_args<T>(g, nullptr, nullptr, 0);
     VF_CK(Kernels<T>::poisson_prepare(pa));
     return VF_OK;

@@ -22,139 +22,10 @@
 
 #include <cstdint>
 
-#include "vf_internal.h"
+#include "fft_common.cuh"
 
 namespace vf {
 namespace {
-
-template <typename T> struct CxT;
-template <> struct CxT<float> { using type = float2; };
-template <> struct CxT<double> { using type = double2; };
-
-template <typename C> __device__ __forceinline__ C mk(decltype(C::x) a, decltype(C::x) b) { C r; r.x = a; r.y = b; return r; }
-template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return mk<C>(a.x + b.x, a.y + b.y); }
-template <typename C> __device__ __forceinline__ C csub(C a, C b) { return mk<C>(a.x - b.x, a.y - b.y); }
-template <typename C> __device__ __forceinline__ C cmul(C a, C b) { return mk<C>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
-template <typename C> __device__ __forceinline__ C cscale(C a, decltype(C::x) s) { return mk<C>(a.x * s, a.y * s); }
-// multiply by +i (INV) or -i (forward): the rotation of a forward / inverse DFT of order 4
-template <typename C, bool INV> __device__ __forceinline__ C rot(C a) { return INV ? mk<C>(-a.y, a.x) : mk<C>(a.y, -a.x); }
-
-// Shared-memory row layout of the row passes and the plane: one padding element per 16 complex values inside a
-// row and an odd row stride, so the strided writes of a radix pass and the row-crossing reads of the split steps
-// spread over the banks.
-__host__ __device__ __forceinline__ int padded(int e) { return e + (e >> 4); }
-__host__ __device__ __forceinline__ int padded_stride(int n) { return (padded(n - 1) + 1) | 1; }
-
-__device__ __forceinline__ FastDiv make_fast_div_dev(uint32_t d)
-{
-    FastDiv f{d, 0u, 0u};
-    if (d <= 1) return f;
-    uint32_t l = 32 - __clz(d - 1);   // ceil(log2 d)
-    f.m = (uint32_t)((((1ull << 32) * ((1ull << l) - d)) / d) + 1);
-    f.s = l;
-    return f;
-}
-
-__device__ __forceinline__ uint32_t fdiv(uint32_t n, const FastDiv& f)
-{
-    if (f.d <= 1) return n;
-    const uint32_t t = __umulhi(f.m, n);
-    return (t + ((n - t) >> 1)) >> (f.s - 1);
-}
-
-// ---- small DFTs in registers: X_k = sum_m v_m exp(-+ 2 pi i m k / R) (minus forward, plus inverse) ----------
-template <typename C, bool INV>
-__device__ __forceinline__ void dft2(C& a, C& b) { const C t = a; a = cadd(t, b); b = csub(t, b); }
-
-template <typename C, bool INV>
-__device__ __forceinline__ void dft4(C& v0, C& v1, C& v2, C& v3)
-{
-    const C t0 = cadd(v0, v2), t1 = csub(v0, v2), t2 = cadd(v1, v3), t3 = rot<C, INV>(csub(v1, v3));
-    v0 = cadd(t0, t2); v2 = csub(t0, t2); v1 = cadd(t1, t3); v3 = csub(t1, t3);
-}
-
-template <typename C, bool INV>
-__device__ __forceinline__ void dft3(C& v0, C& v1, C& v2)
-{
-    using R = decltype(C::x);
-    const R s3 = R(0.86602540378443864676);   // sin(2 pi / 3)
-    const C t = cadd(v1, v2);
-    const C m = mk<C>(v0.x - R(0.5) * t.x, v0.y - R(0.5) * t.y);
-    const C d = rot<C, INV>(cscale(csub(v1, v2), s3));
-    v0 = cadd(v0, t); v1 = cadd(m, d); v2 = csub(m, d);
-}
-
-template <typename C, bool INV>
-__device__ __forceinline__ void dft5(C& v0, C& v1, C& v2, C& v3, C& v4)
-{
-    using R = decltype(C::x);
-    const R c1 = R(0.30901699437494742410), c2 = R(-0.80901699437494742410);   // cos(2 pi/5), cos(4 pi/5)
-    const R s1 = R(0.95105651629515357212), s2 = R(0.58778525229247312917);    // sin(2 pi/5), sin(4 pi/5)
-    const C t1 = cadd(v1, v4), t2 = cadd(v2, v3), d1 = csub(v1, v4), d2 = csub(v2, v3);
-    const C a1 = mk<C>(v0.x + c1 * t1.x + c2 * t2.x, v0.y + c1 * t1.y + c2 * t2.y);
-    const C a2 = mk<C>(v0.x + c2 * t1.x + c1 * t2.x, v0.y + c2 * t1.y + c1 * t2.y);
-    const C b1 = rot<C, INV>(mk<C>(s1 * d1.x + s2 * d2.x, s1 * d1.y + s2 * d2.y));
-    const C b2 = rot<C, INV>(mk<C>(s2 * d1.x - s1 * d2.x, s2 * d1.y - s1 * d2.y));
-    v0 = cadd(v0, cadd(t1, t2));
-    v1 = cadd(a1, b1); v4 = csub(a1, b1);
-    v2 = cadd(a2, b2); v3 = csub(a2, b2);
-}
-
-template <typename C, bool INV>
-__device__ __forceinline__ void dft8(C* v)
-{
-    using R = decltype(C::x);
-    const R h = R(0.70710678118654752440);
-    dft4<C, INV>(v[0], v[2], v[4], v[6]);
-    dft4<C, INV>(v[1], v[3], v[5], v[7]);
-    // odd outputs times W8^k, W8 = exp(-+ 2 pi i / 8)
-    const C o1 = INV ? mk<C>(h * (v[3].x - v[3].y), h * (v[3].x + v[3].y))
-                     : mk<C>(h * (v[3].x + v[3].y), h * (v[3].y - v[3].x));
-    const C o2 = rot<C, INV>(v[5]);
-    const C o3 = INV ? mk<C>(-h * (v[7].x + v[7].y), h * (v[7].x - v[7].y))
-                     : mk<C>(h * (v[7].y - v[7].x), -h * (v[7].x + v[7].y));
-    const C e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6], o0 = v[1];
-    v[0] = cadd(e0, o0); v[4] = csub(e0, o0);
-    v[1] = cadd(e1, o1); v[5] = csub(e1, o1);
-    v[2] = cadd(e2, o2); v[6] = csub(e2, o2);
-    v[3] = cadd(e3, o3); v[7] = csub(e3, o3);
-}
-
-// order 16 as 4 x 4: DFT4 over the stride-4 columns, twiddles W16^(n2 k1), DFT4 over the rows, transpose
-template <typename C, bool INV>
-__device__ __forceinline__ void dft16(C* v)
-{
-    using R = decltype(C::x);
-    const R c1 = R(0.92387953251128675613), s1 = R(0.38268343236508977173), h = R(0.70710678118654752440);
-    const R sg = INV ? R(1) : R(-1);   // sign of the imaginary part of W16^k
-#pragma unroll
-    for (int n2 = 0; n2 < 4; ++n2) dft4<C, INV>(v[n2], v[n2 + 4], v[n2 + 8], v[n2 + 12]);
-    const C w1 = mk<C>(c1, sg * s1), w2 = mk<C>(h, sg * h), w3 = mk<C>(s1, sg * c1);
-    const C w6 = mk<C>(-h, sg * h), w9 = mk<C>(-c1, -sg * s1);
-    v[5] = cmul(v[5], w1); v[9] = cmul(v[9], w2); v[13] = cmul(v[13], w3);
-    v[6] = cmul(v[6], w2); v[10] = rot<C, INV>(v[10]); v[14] = cmul(v[14], w6);
-    v[7] = cmul(v[7], w3); v[11] = cmul(v[11], w6); v[15] = cmul(v[15], w9);
-#pragma unroll
-    for (int k1 = 0; k1 < 4; ++k1) dft4<C, INV>(v[4 * k1], v[4 * k1 + 1], v[4 * k1 + 2], v[4 * k1 + 3]);
-    C t[16];
-#pragma unroll
-    for (int i = 0; i < 16; ++i) t[i] = v[i];
-#pragma unroll
-    for (int k1 = 0; k1 < 4; ++k1)
-#pragma unroll
-        for (int k2 = 0; k2 < 4; ++k2) v[k1 + 4 * k2] = t[4 * k1 + k2];
-}
-
-template <typename C, int R, bool INV>
-__device__ __forceinline__ void dft(C* v)
-{
-    if (R == 2) dft2<C, INV>(v[0], v[1]);
-    else if (R == 3) dft3<C, INV>(v[0], v[1], v[2]);
-    else if (R == 4) dft4<C, INV>(v[0], v[1], v[2], v[3]);
-    else if (R == 5) dft5<C, INV>(v[0], v[1], v[2], v[3], v[4]);
-    else if (R == 8) dft8<C, INV>(v);
-    else dft16<C, INV>(v);
-}
 
 // One radix-R Stockham pass over nseq sequences.  Work item (j, b) reads element j + r nb of sequence b
 // (r = 0..R-1), multiplies it by W_n^(r (j mod Ns) tstride), does a DFT of order R and writes element
@@ -229,48 +100,6 @@ __device__ void fft_run(const FftAxis& ax, int nseq, int es, int ss, const C* tw
             dst = (dst == bufA) ? bufB : bufA;
         }
     }
-}
-
-template <typename C>
-__device__ __forceinline__ void stage_table(C* dst, const void* src, int n)
-{
-    const C* s = reinterpret_cast<const C*>(src);
-    for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = __ldg(s + i);
-}
-
-__device__ __forceinline__ int wrapi(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
-
-// Eq. 9 correction at one cell: sum_j (1/(2h_j))^2 [(1 - beta^+)(p^{++} - p^0) - (1 - beta^-)(p^0 - p^{--})]
-// (= sum_j delta_j((1 - beta) delta_j p) with central differences).  Only called for cells with a solid neighbour.
-template <typename T>
-__device__ T poisson_correction(const PoissonArgs<T>& A, long long i, int x, int y, int z)
-{
-    const long long nx = A.nx, plane = (long long)A.nx * A.ny;
-    const long long zb = (long long)z * plane, yb = (long long)y * nx;
-    const T p0 = __ldg(A.p + i);
-    T corr = T(0);
-    {
-        const bool bm = __ldg(A.mask + zb + yb + wrapi(x - 1, A.nx)) & kBitBeta;
-        const bool bp = __ldg(A.mask + zb + yb + wrapi(x + 1, A.nx)) & kBitBeta;
-        const T pp = bp ? T(0) : __ldg(A.p + zb + yb + wrapi(x + 2, A.nx)) - p0;
-        const T pm = bm ? T(0) : p0 - __ldg(A.p + zb + yb + wrapi(x - 2, A.nx));
-        corr += A.i2h2[0] * (pp - pm);
-    }
-    {
-        const bool bm = __ldg(A.mask + zb + wrapi(y - 1, A.ny) * nx + x) & kBitBeta;
-        const bool bp = __ldg(A.mask + zb + wrapi(y + 1, A.ny) * nx + x) & kBitBeta;
-        const T pp = bp ? T(0) : __ldg(A.p + zb + wrapi(y + 2, A.ny) * nx + x) - p0;
-        const T pm = bm ? T(0) : p0 - __ldg(A.p + zb + wrapi(y - 2, A.ny) * nx + x);
-        corr += A.i2h2[1] * (pp - pm);
-    }
-    {
-        const bool bm = __ldg(A.mask + wrapi(z - 1, A.nz) * plane + yb + x) & kBitBeta;
-        const bool bp = __ldg(A.mask + wrapi(z + 1, A.nz) * plane + yb + x) & kBitBeta;
-        const T pp = bp ? T(0) : __ldg(A.p + wrapi(z + 2, A.nz) * plane + yb + x) - p0;
-        const T pm = bm ? T(0) : p0 - __ldg(A.p + wrapi(z - 2, A.nz) * plane + yb + x);
-        corr += A.i2h2[2] * (pp - pm);
-    }
-    return corr;
 }
 
 // f = r + correction at every listed cell; the first iteration of a step also saves r there (f holds r then)
@@ -645,6 +474,7 @@ size_t Kernels<T>::fft_smem_plane(const PoissonArgs<T>& a)
 template <typename T>
 cudaError_t Kernels<T>::poisson_prepare(const PoissonArgs<T>& a)
 {
+    if (a.reg) return RegFft<T>::prepare(a);
     constexpr int TB = cols_tb<T>();
     const size_t sx = fft_smem_x(a), sy = fft_smem_yz(a, a.ny, 2), sz = fft_smem_yz(a, a.nz, 3);
     cudaError_t e;
@@ -660,16 +490,17 @@ template <typename T>
 cudaError_t Kernels<T>::poisson_iteration(const PoissonArgs<T>& a, int first, cudaStream_t st,
                                           const LaunchHook* hook)
 {
-    constexpr int TB = cols_tb<T>();
-    if (a.cols_per_block != TB) return cudaErrorInvalidValue;
-    const size_t sx = fft_smem_x(a);
-    const int rows = a.ny * a.nz;
-    const int gx = (rows + a.rows_per_block - 1) / a.rows_per_block;
     if (a.n_near > 0) {
         const int gb = (a.n_near + 255) / 256;
         k_poisson_correction<T><<<gb < 4096 ? gb : 4096, 256, 0, st>>>(a, first);
         if (hook) (*hook)(VF_PHASE_POISSON_RHS);
     }
+    if (a.reg) return RegFft<T>::iteration(a, st, hook);
+    constexpr int TB = cols_tb<T>();
+    if (a.cols_per_block != TB) return cudaErrorInvalidValue;
+    const size_t sx = fft_smem_x(a);
+    const int rows = a.ny * a.nz;
+    const int gx = (rows + a.rows_per_block - 1) / a.rows_per_block;
     k_fft_x_fwd<T><<<gx, 256, sx, st>>>(a);
     if (hook) (*hook)(VF_PHASE_FFT_X_FWD);
     if (a.plane_layout) {

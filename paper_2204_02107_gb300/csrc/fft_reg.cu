@@ -1,0 +1,615 @@
+// Register-resident passes of the FFT Poisson solve (Sec. 2.2, Eqs. 7-9) for grids whose axis lengths are all
+// 16 G with G in {1, 2, 4, 8, 16} (nx = 32 G_x) and whose (y, z) plane fits in shared memory.
+//
+// A transform of n = 16 G points is done by G threads of one warp.  Thread t holds x[t + G m] (m = 0..15),
+// does a 16-point DFT in registers, multiplies by W_n^(t k1), exchanges through a slice of shared memory that
+// only its group touches (so a __syncwarp orders the exchange, never a CTA barrier), and finishes with 16 / G
+// DFTs of order G.  It then holds X[t Q + q + 16 k2] (Q = 16 / G) in register q G + k2.  The inverse is the
+// mirror image and ends with thread t holding x[t + G m] again, so global loads and stores stay coalesced.
+//
+// One iteration of Eq. 9 is the correction (masked grids) and three kernels:
+//   x forward : real-to-complex FFT along x of f (r plus the Eq. 9 correction, added beforehand at the cells
+//               next to solids by the correction kernel of the generic path), two reals packed per complex
+//               value, split step, then the rows of a CTA are transposed through shared memory into the plane
+//               layout spec[kx][z][y];
+//   (y, z)    : one CTA per kx plane: y FFT of every z row straight from global memory into the shared plane,
+//               z FFT of every column, division by lambda N, inverse z FFT (one register pass per column),
+//               inverse y FFT back to global memory;
+//   x inverse : the rows of a CTA are gathered from the plane layout, joined, inverse FFT, p^{k+1} written.
+// The arithmetic (DFT kernels, twiddle tables, packing, eigenvalues) is the one of the generic passes; only the
+// order of the butterflies and the data movement differ.
+#include <algorithm>
+
+#include "fft_common.cuh"
+
+namespace vf {
+namespace {
+
+template <int G>
+struct RegShape {
+    static constexpr int Q = 16 / G;
+    // exchange slot of the k1-th 16-point output of thread t (skewed so both sides of the exchange spread over
+    // the shared-memory banks)
+    static __device__ __forceinline__ int xpos(int t, int k1) { return k1 * G + ((t + k1 / Q) & (G - 1)); }
+    // slot and frequency of held value (q, k2) of thread t
+    static __device__ __forceinline__ int slot(int t, int q, int k2) { return t + G * q + 16 * k2; }
+    static __device__ __forceinline__ int freq(int t, int q, int k2) { return t * Q + q + 16 * k2; }
+};
+
+// slot of frequency k (the inverse of RegShape::freq followed by RegShape::slot)
+template <int G>
+__device__ __forceinline__ int slot_of_freq(int k)
+{
+    constexpr int Q = 16 / G;
+    const int k1 = k & 15, k2 = k >> 4;
+    return (k1 / Q) + G * (k1 % Q) + 16 * k2;
+}
+
+// frequency held at slot s
+template <int G>
+__device__ __forceinline__ int freq_of_slot(int s)
+{
+    constexpr int Q = 16 / G;
+    const int r = s & 15, k2 = s >> 4;
+    return (r % G) * Q + r / G + 16 * k2;
+}
+
+// forward transform of v (thread t of its group); buf(e) is element e of the group's exchange slice
+template <typename C, int G, typename BUF>
+__device__ __forceinline__ void reg_fwd(C v[16], int t, const C* tw, BUF buf)
+{
+    dft<C, 16, false>(v);
+    if constexpr (G > 1) {
+        constexpr int Q = 16 / G;
+#pragma unroll
+        for (int k1 = 1; k1 < 16; ++k1) v[k1] = cmul(v[k1], tw[t * k1]);
+        __syncwarp();
+#pragma unroll
+        for (int k1 = 0; k1 < 16; ++k1) buf(RegShape<G>::xpos(t, k1)) = v[k1];
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < Q; ++q)
+#pragma unroll
+            for (int s = 0; s < G; ++s) v[q * G + s] = buf(RegShape<G>::xpos(s, t * Q + q));
+#pragma unroll
+        for (int q = 0; q < Q; ++q) dft<C, G, false>(v + q * G);
+    }
+}
+
+// inverse transform (unnormalised) from the held layout back to v[m] = n x[t + G m]
+template <typename C, int G, typename BUF>
+__device__ __forceinline__ void reg_inv(C v[16], int t, const C* tw, BUF buf)
+{
+    if constexpr (G > 1) {
+        constexpr int Q = 16 / G;
+#pragma unroll
+        for (int q = 0; q < Q; ++q) dft<C, G, true>(v + q * G);
+#pragma unroll
+        for (int q = 0; q < Q; ++q)
+#pragma unroll
+            for (int s = 1; s < G; ++s) {
+                C w = tw[s * (t * Q + q)];
+                w.y = -w.y;
+                v[q * G + s] = cmul(v[q * G + s], w);
+            }
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < Q; ++q)
+#pragma unroll
+            for (int s = 0; s < G; ++s) buf(RegShape<G>::xpos(s, t * Q + q)) = v[q * G + s];
+        __syncwarp();
+#pragma unroll
+        for (int k1 = 0; k1 < 16; ++k1) v[k1] = buf(RegShape<G>::xpos(t, k1));
+    }
+    dft<C, 16, true>(v);
+}
+
+template <typename T> __host__ __device__ constexpr int x_threads() { return sizeof(T) == 4 ? 256 : 128; }
+#ifndef VF_REG_YZ_THREADS
+#define VF_REG_YZ_THREADS 1024
+#endif
+template <typename T> __host__ __device__ constexpr int yz_threads() { return sizeof(T) == 4 ? VF_REG_YZ_THREADS : 512; }
+
+// ---- x forward ---------------------------------------------------------------------------------------------
+template <typename T, int GX>
+__global__ void __launch_bounds__(x_threads<T>()) k_reg_x_fwd(PoissonArgs<T> A)
+{
+    using C = typename CxT<T>::type;
+    constexpr int M = 16 * GX, NT = x_threads<T>(), B = NT / GX, P = 32 / GX, Q = 16 / GX;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int SPX = A.reg_spx, SB = A.reg_sb;
+    C* tw = reinterpret_cast<C*>(smem_raw);
+    C* twr = tw + M;
+    C* rowbuf = twr + (M + 1);
+    C* stage = rowbuf + B * SPX;
+    stage_table(tw, A.twx, M);
+    stage_table(twr, A.twr, M + 1);
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int gi = lane % P, t = lane / P;
+    const int b = warp * P + gi;
+    const int rows = A.ny * A.nz, row0 = blockIdx.x * B, row = row0 + b;
+    const bool act = row < rows;
+    C v[16];
+    {
+        const long long base = (long long)(act ? row : 0) * A.nx;
+#pragma unroll
+        for (int m = 0; m < 16; ++m) {
+            const int j = t + GX * m;
+            v[m] = act ? *reinterpret_cast<const C*>(A.f + base + 2 * j) : mk<C>(T(0), T(0));
+        }
+    }
+    C* rb = rowbuf + b * SPX;
+    auto buf = [rb](int e) -> C& { return rb[e]; };
+    reg_fwd<C, GX>(v, t, tw, buf);
+    __syncwarp();
+#pragma unroll
+    for (int q = 0; q < Q; ++q)
+#pragma unroll
+        for (int k2 = 0; k2 < GX; ++k2) rb[RegShape<GX>::slot(t, q, k2)] = v[q * GX + k2];
+    __syncwarp();
+    // split step: X_k = E_k + W^k O_k from Z_k and conj Z_{M-k}; pairs (k, M - k) by one thread
+    for (int k = t; k <= M / 2; k += GX) {
+        const C Zk = rb[slot_of_freq<GX>(k)];
+        if (k == 0) {
+            stage[b] = mk<C>(Zk.x + Zk.y, Zk.x - Zk.y);        // (X_0, X_{nx/2})
+            continue;
+        }
+        const C Zm = rb[slot_of_freq<GX>(M - k)];
+        {
+            const C E = mk<C>(T(0.5) * (Zk.x + Zm.x), T(0.5) * (Zk.y - Zm.y));
+            const C O = mk<C>(T(0.5) * (Zk.y + Zm.y), T(-0.5) * (Zk.x - Zm.x));
+            stage[k * SB + b] = cadd(E, cmul(twr[k], O));
+        }
+        if (2 * k != M) {
+            const C E = mk<C>(T(0.5) * (Zm.x + Zk.x), T(0.5) * (Zm.y - Zk.y));
+            const C O = mk<C>(T(0.5) * (Zm.y + Zk.y), T(-0.5) * (Zm.x - Zk.x));
+            stage[(M - k) * SB + b] = cadd(E, cmul(twr[M - k], O));
+        }
+    }
+    __syncthreads();
+    // plane layout: spec[k][row], B consecutive rows per frequency
+    C* spec = reinterpret_cast<C*>(A.spec);
+    for (int it = threadIdx.x; it < M * B; it += NT) {
+        const int k = it / B, bb = it - k * B;
+        if (row0 + bb < rows) spec[(long long)k * rows + row0 + bb] = stage[k * SB + bb];
+    }
+}
+
+// ---- x inverse ---------------------------------------------------------------------------------------------
+template <typename T, int GX>
+__global__ void __launch_bounds__(x_threads<T>()) k_reg_x_inv(PoissonArgs<T> A)
+{
+    using C = typename CxT<T>::type;
+    constexpr int M = 16 * GX, NT = x_threads<T>(), B = NT / GX, P = 32 / GX, Q = 16 / GX;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int SPX = A.reg_spx, SB = A.reg_sb;
+    C* tw = reinterpret_cast<C*>(smem_raw);
+    C* twr = tw + M;
+    C* rowbuf = twr + (M + 1);
+    C* stage = rowbuf + B * SPX;
+    stage_table(tw, A.twx, M);
+    stage_table(twr, A.twr, M + 1);
+    const int rows = A.ny * A.nz, row0 = blockIdx.x * B;
+    const C* spec = reinterpret_cast<const C*>(A.spec);
+    // M * B is a multiple of 8 NT: eight loads in flight per thread
+    for (int it0 = threadIdx.x; it0 < M * B; it0 += 8 * NT) {
+        C tmp[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int it = it0 + u * NT, k = it / B, bb = it - k * B;
+            tmp[u] = row0 + bb < rows ? spec[(long long)k * rows + row0 + bb] : mk<C>(T(0), T(0));
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int it = it0 + u * NT, k = it / B, bb = it - k * B;
+            stage[k * SB + bb] = tmp[u];
+        }
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int gi = lane % P, t = lane / P;
+    const int b = warp * P + gi;
+    const int row = row0 + b;
+    C* rb = rowbuf + b * SPX;
+    // join: Z'_k = (X_k + conj X_{M-k}) + i W^{-k} (X_k - conj X_{M-k}); pairs (k, M - k) by one thread
+    for (int k = t; k <= M / 2; k += GX) {
+        const C Xk = stage[k * SB + b];
+        if (k == 0) {
+            rb[slot_of_freq<GX>(0)] = mk<C>(Xk.x + Xk.y, Xk.x - Xk.y);
+            continue;
+        }
+        const C Xm = stage[(M - k) * SB + b];
+        {
+            const C s = mk<C>(Xk.x + Xm.x, Xk.y - Xm.y), d = mk<C>(Xk.x - Xm.x, Xk.y + Xm.y);
+            C w = twr[k];
+            w.y = -w.y;
+            const C wd = cmul(w, d);
+            rb[slot_of_freq<GX>(k)] = mk<C>(s.x - wd.y, s.y + wd.x);
+        }
+        if (2 * k != M) {
+            const C s = mk<C>(Xm.x + Xk.x, Xm.y - Xk.y), d = mk<C>(Xm.x - Xk.x, Xm.y + Xk.y);
+            C w = twr[M - k];
+            w.y = -w.y;
+            const C wd = cmul(w, d);
+            rb[slot_of_freq<GX>(M - k)] = mk<C>(s.x - wd.y, s.y + wd.x);
+        }
+    }
+    __syncwarp();
+    C v[16];
+#pragma unroll
+    for (int q = 0; q < Q; ++q)
+#pragma unroll
+        for (int k2 = 0; k2 < GX; ++k2) v[q * GX + k2] = rb[RegShape<GX>::slot(t, q, k2)];
+    auto buf = [rb](int e) -> C& { return rb[e]; };
+    reg_inv<C, GX>(v, t, tw, buf);
+    if (row < rows) {
+        const long long base = (long long)row * A.nx;
+#pragma unroll
+        for (int m = 0; m < 16; ++m) *reinterpret_cast<C*>(A.p + base + 2 * (t + GX * m)) = v[m];
+    }
+}
+
+// ---- (y, z) plane of one kx ----------------------------------------------------------------------------------
+template <typename T, int GY, int GZ>
+__global__ void __launch_bounds__(yz_threads<T>()) k_reg_yz_solve(PoissonArgs<T> A)
+{
+    using C = typename CxT<T>::type;
+    constexpr int NY = 16 * GY, NZ = 16 * GZ, QY = 16 / GY, QZ = 16 / GZ;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int SP = A.reg_sp;
+    C* plane = reinterpret_cast<C*>(smem_raw);     // row z at z * SP, slot s of the y transform at s
+    C* twy = plane + NZ * SP;
+    C* twz = twy + NY;
+    stage_table(twy, A.twy, NY);
+    stage_table(twz, A.twz, NZ);
+    const int kx = blockIdx.x;
+    C* g = reinterpret_cast<C*>(A.spec) + (long long)kx * NY * NZ;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    // y forward: a group per z row, global memory -> registers -> shared plane (slots)
+    {
+        constexpr int P = 32 / GY;
+        const int gi = lane % P, t = lane / P;
+        for (int z0 = warp * P; z0 < NZ; z0 += nwarps * P) {
+            const int z = z0 + gi;
+            const bool act = z < NZ;             // false only for G = 1 with NZ = 16 (no exchange then)
+            C v[16];
+#pragma unroll
+            for (int m = 0; m < 16; ++m) v[m] = act ? g[z * NY + t + GY * m] : mk<C>(T(0), T(0));
+            C* row = plane + (act ? z : 0) * SP;
+            auto buf = [row](int e) -> C& { return row[e]; };
+            reg_fwd<C, GY>(v, t, twy, buf);
+            __syncwarp();
+            if (act) {
+#pragma unroll
+                for (int q = 0; q < QY; ++q)
+#pragma unroll
+                    for (int k2 = 0; k2 < GY; ++k2) row[RegShape<GY>::slot(t, q, k2)] = v[q * GY + k2];
+            }
+        }
+    }
+    __syncthreads();
+    // z: a group per column (y slot c): forward FFT, x 1 / (lambda N), inverse FFT, in place in the column
+    {
+        constexpr int P = 32 / GZ;
+        const int gi = lane % P, t = lane / P;
+        const T lx = __ldg(A.lamx + kx);
+        for (int c0 = warp * P; c0 < NY; c0 += nwarps * P) {
+            const int c = c0 + gi;
+            const bool act = c < NY;
+            const int cc = act ? c : 0;
+            const int ky = freq_of_slot<GY>(cc);
+            const T lxy = lx + __ldg(A.lamy + ky);
+            const bool ky_null = (kx == 0) && (ky == 0 || 2 * ky == NY);
+            C v[16];
+#pragma unroll
+            for (int m = 0; m < 16; ++m) v[m] = plane[(t + GZ * m) * SP + cc];
+            auto buf = [plane, SP, cc](int e) -> C& { return plane[e * SP + cc]; };
+            reg_fwd<C, GZ>(v, t, twz, buf);
+#pragma unroll
+            for (int q = 0; q < QZ; ++q)
+#pragma unroll
+                for (int k2 = 0; k2 < GZ; ++k2) {
+                    const int kz = RegShape<GZ>::freq(t, q, k2);
+                    const bool null = ky_null && (kz == 0 || 2 * kz == NZ);
+                    const T s = null ? T(0) : A.invN / -(lxy + __ldg(A.lamz + kz));
+                    v[q * GZ + k2] = cscale(v[q * GZ + k2], s);
+                }
+            reg_inv<C, GZ>(v, t, twz, buf);
+            __syncwarp();
+            if (act) {
+#pragma unroll
+                for (int m = 0; m < 16; ++m) plane[(t + GZ * m) * SP + cc] = v[m];
+            }
+        }
+    }
+    __syncthreads();
+    // y inverse: a group per z row, shared plane -> registers -> global memory
+    {
+        constexpr int P = 32 / GY;
+        const int gi = lane % P, t = lane / P;
+        for (int z0 = warp * P; z0 < NZ; z0 += nwarps * P) {
+            const int z = z0 + gi;
+            const bool act = z < NZ;
+            C* row = plane + (act ? z : 0) * SP;
+            C v[16];
+#pragma unroll
+            for (int q = 0; q < QY; ++q)
+#pragma unroll
+                for (int k2 = 0; k2 < GY; ++k2) v[q * GY + k2] = row[RegShape<GY>::slot(t, q, k2)];
+            auto buf = [row](int e) -> C& { return row[e]; };
+            reg_inv<C, GY>(v, t, twy, buf);
+            if (act) {
+#pragma unroll
+                for (int m = 0; m < 16; ++m) g[z * NY + t + GY * m] = v[m];
+            }
+        }
+    }
+}
+
+// ---- host side ---------------------------------------------------------------------------------------------
+int g_of(int n)
+{
+    for (int g = 1; g <= 16; g *= 2)
+        if (n == 16 * g) return g;
+    return 0;
+}
+
+// Worst number of distinct 8-byte words one bank serves in a warp access (shared memory: 16 banks of 8 bytes
+// per 128-byte wavefront for 8-byte elements, 32 of 4 bytes = 16 of 8).  addr(lane, step) in elements of esz bytes.
+template <typename F>
+int worst_ways(int esz, F addr)
+{
+    int worst = 1;
+    for (int step = 0; step < 16; ++step) {
+        int ways[32] = {0};
+        long long seen[32][32];
+        int nseen[32] = {0};
+        for (int lane = 0; lane < 32; ++lane) {
+            const long long byte = addr(lane, step) * (long long)esz;
+            for (int w = 0; w < esz / 4; ++w) {
+                const long long word = byte / 4 + w;
+                const int bank = (int)(word % 32);
+                bool dup = false;
+                for (int i = 0; i < nseen[bank]; ++i) dup |= seen[bank][i] == word;
+                if (!dup && nseen[bank] < 32) { seen[bank][nseen[bank]++] = word; ways[bank]++; }
+            }
+        }
+        for (int i = 0; i < 32; ++i) worst = ways[i] > worst ? ways[i] : worst;
+    }
+    return worst;
+}
+
+int xpos_h(int G, int t, int k1) { const int Q = 16 / G; return k1 * G + ((t + k1 / Q) & (G - 1)); }
+
+// conflicts of the row-owned accesses (a group of G threads per row, rows `stride` apart)
+int row_ways(int G, int stride, int esz)
+{
+    const int P = 32 / G, Q = 16 / G;
+    int w = 0;
+    auto mx = [&](int v) { w = v > w ? v : w; };
+    if (G > 1) {
+        mx(worst_ways(esz, [&](int l, int s) { return (long long)(l % P) * stride + xpos_h(G, l / P, s); }));
+        mx(worst_ways(esz, [&](int l, int s) {
+            return (long long)(l % P) * stride + xpos_h(G, s % G, (l / P) * Q + (s / G) % Q); }));
+    }
+    mx(worst_ways(esz, [&](int l, int s) { return (long long)(l % P) * stride + (l / P) + G * (s % Q) + 16 * ((s / Q) % G); }));
+    return w;
+}
+
+// conflicts of the column-owned accesses (element e of column c at e * stride + c)
+int col_ways(int G, int stride, int esz)
+{
+    const int P = 32 / G, Q = 16 / G;
+    int w = 0;
+    auto mx = [&](int v) { w = v > w ? v : w; };
+    mx(worst_ways(esz, [&](int l, int s) { return (long long)((l / P) + G * s) * stride + (l % P); }));
+    if (G > 1) {
+        mx(worst_ways(esz, [&](int l, int s) { return (long long)xpos_h(G, l / P, s) * stride + (l % P); }));
+        mx(worst_ways(esz, [&](int l, int s) {
+            return (long long)xpos_h(G, s % G, (l / P) * Q + (s / G) % Q) * stride + (l % P); }));
+    }
+    return w;
+}
+
+template <typename T>
+size_t x_smem(int M, int spx, int sb)
+{
+    const int B = x_threads<T>() / (M / 16);
+    return ((size_t)M + (M + 1) + (size_t)B * spx + (size_t)M * sb) * sizeof(typename CxT<T>::type);
+}
+
+template <typename T>
+size_t yz_smem(int ny, int nz, int sp)
+{
+    return ((size_t)nz * sp + ny + nz) * sizeof(typename CxT<T>::type);
+}
+
+constexpr size_t kRegSmemLimit = 200 * 1024;
+
+template <typename T, int GX>
+cudaError_t launch_x(const PoissonArgs<T>& a, bool fwd, cudaStream_t st)
+{
+    constexpr int B = x_threads<T>() / GX;
+    const int rows = a.ny * a.nz;
+    const unsigned grid = (unsigned)((rows + B - 1) / B);
+    const size_t sm = x_smem<T>(16 * GX, a.reg_spx, a.reg_sb);
+    if (fwd) k_reg_x_fwd<T, GX><<<grid, x_threads<T>(), sm, st>>>(a);
+    else k_reg_x_inv<T, GX><<<grid, x_threads<T>(), sm, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t dispatch_x(const PoissonArgs<T>& a, bool fwd, cudaStream_t st)
+{
+    switch (a.gx) {
+        case 1: return launch_x<T, 1>(a, fwd, st);
+        case 2: return launch_x<T, 2>(a, fwd, st);
+        case 4: return launch_x<T, 4>(a, fwd, st);
+        case 8: return launch_x<T, 8>(a, fwd, st);
+        case 16: return launch_x<T, 16>(a, fwd, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename T, int GY, int GZ>
+cudaError_t launch_yz(const PoissonArgs<T>& a, cudaStream_t st)
+{
+    const int want = (16 * GY) * (16 * GZ) / 16;
+    const int threads = want < 32 ? 32 : (want > yz_threads<T>() ? yz_threads<T>() : want);
+    k_reg_yz_solve<T, GY, GZ><<<a.M, threads, yz_smem<T>(a.ny, a.nz, a.reg_sp), st>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename T, int GY>
+cudaError_t dispatch_yz_z(const PoissonArgs<T>& a, cudaStream_t st)
+{
+    switch (a.gz) {
+        case 1: return launch_yz<T, GY, 1>(a, st);
+        case 2: return launch_yz<T, GY, 2>(a, st);
+        case 4: return launch_yz<T, GY, 4>(a, st);
+        case 8: return launch_yz<T, GY, 8>(a, st);
+        case 16: return launch_yz<T, GY, 16>(a, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename T>
+cudaError_t dispatch_yz(const PoissonArgs<T>& a, cudaStream_t st)
+{
+    switch (a.gy) {
+        case 1: return dispatch_yz_z<T, 1>(a, st);
+        case 2: return dispatch_yz_z<T, 2>(a, st);
+        case 4: return dispatch_yz_z<T, 4>(a, st);
+        case 8: return dispatch_yz_z<T, 8>(a, st);
+        case 16: return dispatch_yz_z<T, 16>(a, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename K>
+cudaError_t raise_smem(K kernel, size_t bytes)
+{
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    if (bytes > (size_t)optin) return cudaErrorInvalidValue;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+}
+
+template <typename T, int GX>
+cudaError_t prepare_x(const PoissonArgs<T>& a)
+{
+    const size_t sm = x_smem<T>(16 * GX, a.reg_spx, a.reg_sb);
+    cudaError_t e = raise_smem(k_reg_x_fwd<T, GX>, sm);
+    if (e == cudaSuccess) e = raise_smem(k_reg_x_inv<T, GX>, sm);
+    return e;
+}
+
+template <typename T, int GY>
+cudaError_t prepare_yz_z(const PoissonArgs<T>& a)
+{
+    const size_t sm = yz_smem<T>(a.ny, a.nz, a.reg_sp);
+    switch (a.gz) {
+        case 1: return raise_smem(k_reg_yz_solve<T, GY, 1>, sm);
+        case 2: return raise_smem(k_reg_yz_solve<T, GY, 2>, sm);
+        case 4: return raise_smem(k_reg_yz_solve<T, GY, 4>, sm);
+        case 8: return raise_smem(k_reg_yz_solve<T, GY, 8>, sm);
+        case 16: return raise_smem(k_reg_yz_solve<T, GY, 16>, sm);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace
+
+template <typename T>
+bool RegFft<T>::eligible(int nx, int ny, int nz)
+{
+    if (nx % 2) return false;
+    const int gx = g_of(nx / 2), gy = g_of(ny), gz = g_of(nz);
+    if (!gx || !gy || !gz) return false;
+    // the plane with the widest padding, and the x passes, must fit
+    return yz_smem<T>(ny, nz, ny + 15) <= kRegSmemLimit && x_smem<T>(nx / 2, nx / 2 + 15, x_threads<T>() / gx + 15) <=
+                                                              kRegSmemLimit;
+}
+
+template <typename T>
+void RegFft<T>::configure(PoissonArgs<T>& a)
+{
+    a.reg = 0;
+    if (!eligible(a.nx, a.ny, a.nz)) return;
+    a.gx = g_of(a.M);
+    a.gy = g_of(a.ny);
+    a.gz = g_of(a.nz);
+    const int esz = (int)sizeof(typename CxT<T>::type);
+    // plane stride: fewest bank conflicts over the y-row and z-column accesses, then the smallest
+    int best = -1, best_w = 1 << 30;
+    for (int pad = 0; pad < 16; ++pad) {
+        const int sp = a.ny + pad;
+        const int w = std::max(row_ways(a.gy, sp, esz), col_ways(a.gz, sp, esz));
+        if (w < best_w) { best_w = w; best = sp; }
+    }
+    a.reg_sp = best;
+    // x passes: rows of the group accesses, and the transposition buffer (frequency-major, rows contiguous)
+    const int B = x_threads<T>() / a.gx;
+    best = -1; best_w = 1 << 30;
+    for (int pad = 0; pad < 16; ++pad) {
+        const int w = row_ways(a.gx, a.M + pad, esz);
+        if (w < best_w) { best_w = w; best = a.M + pad; }
+    }
+    a.reg_spx = best;
+    best = -1; best_w = 1 << 30;
+    for (int pad = 0; pad < 16; ++pad) {
+        const int sb = B + pad, G = a.gx, P = 32 / G;
+        const int w = worst_ways(esz, [&](int l, int s) { return (long long)((l / P) + G * s) * sb + (l % P); });
+        if (w < best_w) { best_w = w; best = sb; }
+    }
+    a.reg_sb = best;
+    a.reg = 1;
+}
+
+template <typename T>
+cudaError_t RegFft<T>::prepare(const PoissonArgs<T>& a)
+{
+    if (!a.reg) return cudaErrorInvalidValue;
+    cudaError_t e;
+    switch (a.gx) {
+        case 1: e = prepare_x<T, 1>(a); break;
+        case 2: e = prepare_x<T, 2>(a); break;
+        case 4: e = prepare_x<T, 4>(a); break;
+        case 8: e = prepare_x<T, 8>(a); break;
+        case 16: e = prepare_x<T, 16>(a); break;
+        default: return cudaErrorInvalidValue;
+    }
+    if (e != cudaSuccess) return e;
+    switch (a.gy) {
+        case 1: return prepare_yz_z<T, 1>(a);
+        case 2: return prepare_yz_z<T, 2>(a);
+        case 4: return prepare_yz_z<T, 4>(a);
+        case 8: return prepare_yz_z<T, 8>(a);
+        case 16: return prepare_yz_z<T, 16>(a);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename T>
+cudaError_t RegFft<T>::iteration(const PoissonArgs<T>& a, cudaStream_t st, const LaunchHook* hook)
+{
+    if (!a.reg) return cudaErrorInvalidValue;
+    cudaError_t e;
+    if ((e = dispatch_x<T>(a, true, st)) != cudaSuccess) return e;
+    if (hook) (*hook)(VF_PHASE_FFT_X_FWD);
+    if ((e = dispatch_yz<T>(a, st)) != cudaSuccess) return e;
+    if (hook) (*hook)(VF_PHASE_FFT_YZ_SOLVE);
+    if ((e = dispatch_x<T>(a, false, st)) != cudaSuccess) return e;
+    if (hook) (*hook)(VF_PHASE_FFT_X_INV);
+    return cudaSuccess;
+}
+
+template struct RegFft<float>;
+template struct RegFft<double>;
+
+}  // namespace vf

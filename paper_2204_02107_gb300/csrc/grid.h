@@ -33,6 +33,8 @@ struct vf_grid {
     void* near_r = nullptr;      // D u* / dt at those cells (capacity N)
     int n_near = 0;
     bool plane_layout = false;
+    // register path of the Poisson solve (PoissonArgs::reg and its shape), fixed at creation
+    int reg = 0, reg_gx = 0, reg_gy = 0, reg_gz = 0, reg_sp = 0, reg_spx = 0, reg_sb = 0;
     void* staging = nullptr;     // N * 8 bytes
     uint8_t* mask = nullptr;
     void* twx = nullptr;

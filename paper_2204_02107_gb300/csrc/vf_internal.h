@@ -168,7 +168,15 @@ struct PoissonArgs {
     FastDiv ny_div;           // i -> i / ny (plane passes)
     int rows_per_block;       // rows of the x passes per CTA
     int cols_per_block;       // kx columns of the y / z tile passes per CTA
+    // register path (every axis length 16 G with G in 1, 2, 4, 8, 16 and the plane in shared memory): the
+    // transforms are held in registers, G threads per sequence
+    int reg;
+    int gx, gy, gz;           // M / 16, ny / 16, nz / 16
+    int reg_sp;               // complex stride between the z rows of the shared plane
+    int reg_spx;              // complex stride between the rows of the x passes
+    int reg_sb;               // complex stride between the frequencies of the x passes' transposition buffer
 };
+
 
 // Spectral index at each position after the in-place (decimation-in-frequency) forward FFT of an axis: the
 // position p = d_0 n/R_0 + d_1 n/(R_0 R_1) + ... holds frequency k = d_0 + R_0 (d_1 + R_1 (d_2 + ...)).
@@ -213,6 +221,15 @@ struct LaunchHook {
     void (*fn)(void* ctx, int phase);
     void* ctx;
     void operator()(int phase) const { if (fn) fn(ctx, phase); }
+};
+
+// Register path of the Poisson solve: eligibility and launch (fft_reg.cu).
+template <typename T>
+struct RegFft {
+    static bool eligible(int nx, int ny, int nz);              // axis lengths and shared-memory fit
+    static void configure(PoissonArgs<T>& a);                   // sets reg, g*, strides (a.reg = 0 if ineligible)
+    static cudaError_t prepare(const PoissonArgs<T>& a);        // shared-memory limits; call outside capture
+    static cudaError_t iteration(const PoissonArgs<T>& a, cudaStream_t st, const LaunchHook* hook);
 };
 
 template <typename T>

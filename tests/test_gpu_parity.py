@@ -54,6 +54,7 @@ def test_taylor_green_fp64_100_steps(torch):
 @pytest.mark.parametrize("shape,boxes", [
     ((40, 24, 20), [(12, 16, 6, 10, 2, 8)]),
     ((48, 30, 18), [(20, 26, 12, 20, 2, 9), (30, 34, 4, 8, 2, 5)]),
+    ((64, 32, 32), [(20, 26, 8, 14, 2, 12), (40, 46, 18, 26, 2, 9)]),   # register FFT path on the plane layout
 ])
 def test_masked_room_fp64_100_steps(torch, monkeypatch, shape, boxes, fft_path):
     """Walls, inlet/outlet duct, boxes, forcing, filter, 4 pressure iterations: 100 steps vs the oracle, with the
@@ -80,7 +81,7 @@ def test_masked_room_fp64_100_steps(torch, monkeypatch, shape, boxes, fft_path):
     g.close()
 
 
-@pytest.mark.parametrize("shape", [(40, 24, 20), (64, 36, 30)])
+@pytest.mark.parametrize("shape", [(40, 24, 20), (64, 36, 30), (64, 32, 32)])
 def test_fp32_one_step_from_identical_state(torch, shape):
     """FP32 bulk: one step from a state that is exactly representable in float, compared with the oracle."""
     room, prm, geom, st0 = room_case(*shape, boxes=[(10, 14, 6, 12, 2, 8)], seed=17)
