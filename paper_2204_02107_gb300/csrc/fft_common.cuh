@@ -152,32 +152,39 @@ __device__ __forceinline__ int wrapi(int i, int n) { return i < 0 ? i + n : (i >
 
 // Eq. 9 correction at one cell: sum_j (1/(2h_j))^2 [(1 - beta^+)(p^{++} - p^0) - (1 - beta^-)(p^0 - p^{--})]
 // (= sum_j delta_j((1 - beta) delta_j p) with central differences).  Only called for cells with a solid neighbour.
+// All thirteen loads are issued before any is used (one round trip), the mask then selects the terms.
 template <typename T>
 __device__ T poisson_correction(const PoissonArgs<T>& A, long long i, int x, int y, int z)
 {
     const long long nx = A.nx, plane = (long long)A.nx * A.ny;
     const long long zb = (long long)z * plane, yb = (long long)y * nx;
+    const long long ixm = zb + yb + wrapi(x - 1, A.nx), ixp = zb + yb + wrapi(x + 1, A.nx);
+    const long long ixmm = zb + yb + wrapi(x - 2, A.nx), ixpp = zb + yb + wrapi(x + 2, A.nx);
+    const long long iym = zb + wrapi(y - 1, A.ny) * nx + x, iyp = zb + wrapi(y + 1, A.ny) * nx + x;
+    const long long iymm = zb + wrapi(y - 2, A.ny) * nx + x, iypp = zb + wrapi(y + 2, A.ny) * nx + x;
+    const long long izm = wrapi(z - 1, A.nz) * plane + yb + x, izp = wrapi(z + 1, A.nz) * plane + yb + x;
+    const long long izmm = wrapi(z - 2, A.nz) * plane + yb + x, izpp = wrapi(z + 2, A.nz) * plane + yb + x;
     const T p0 = __ldg(A.p + i);
+    const uint8_t mxm = __ldg(A.mask + ixm), mxp = __ldg(A.mask + ixp);
+    const uint8_t mym = __ldg(A.mask + iym), myp = __ldg(A.mask + iyp);
+    const uint8_t mzm = __ldg(A.mask + izm), mzp = __ldg(A.mask + izp);
+    const T pxm = __ldg(A.p + ixmm), pxp = __ldg(A.p + ixpp);
+    const T pym = __ldg(A.p + iymm), pyp = __ldg(A.p + iypp);
+    const T pzm = __ldg(A.p + izmm), pzp = __ldg(A.p + izpp);
     T corr = T(0);
     {
-        const bool bm = __ldg(A.mask + zb + yb + wrapi(x - 1, A.nx)) & kBitBeta;
-        const bool bp = __ldg(A.mask + zb + yb + wrapi(x + 1, A.nx)) & kBitBeta;
-        const T pp = bp ? T(0) : __ldg(A.p + zb + yb + wrapi(x + 2, A.nx)) - p0;
-        const T pm = bm ? T(0) : p0 - __ldg(A.p + zb + yb + wrapi(x - 2, A.nx));
+        const T pp = (mxp & kBitBeta) ? T(0) : pxp - p0;
+        const T pm = (mxm & kBitBeta) ? T(0) : p0 - pxm;
         corr += A.i2h2[0] * (pp - pm);
     }
     {
-        const bool bm = __ldg(A.mask + zb + wrapi(y - 1, A.ny) * nx + x) & kBitBeta;
-        const bool bp = __ldg(A.mask + zb + wrapi(y + 1, A.ny) * nx + x) & kBitBeta;
-        const T pp = bp ? T(0) : __ldg(A.p + zb + wrapi(y + 2, A.ny) * nx + x) - p0;
-        const T pm = bm ? T(0) : p0 - __ldg(A.p + zb + wrapi(y - 2, A.ny) * nx + x);
+        const T pp = (myp & kBitBeta) ? T(0) : pyp - p0;
+        const T pm = (mym & kBitBeta) ? T(0) : p0 - pym;
         corr += A.i2h2[1] * (pp - pm);
     }
     {
-        const bool bm = __ldg(A.mask + wrapi(z - 1, A.nz) * plane + yb + x) & kBitBeta;
-        const bool bp = __ldg(A.mask + wrapi(z + 1, A.nz) * plane + yb + x) & kBitBeta;
-        const T pp = bp ? T(0) : __ldg(A.p + wrapi(z + 2, A.nz) * plane + yb + x) - p0;
-        const T pm = bm ? T(0) : p0 - __ldg(A.p + wrapi(z - 2, A.nz) * plane + yb + x);
+        const T pp = (mzp & kBitBeta) ? T(0) : pzp - p0;
+        const T pm = (mzm & kBitBeta) ? T(0) : p0 - pzm;
         corr += A.i2h2[2] * (pp - pm);
     }
     return corr;

@@ -10,12 +10,12 @@
 // One iteration of Eq. 9 is the correction (masked grids) and three kernels:
 //   x forward : real-to-complex FFT along x of f (r plus the Eq. 9 correction, added beforehand at the cells
 //               next to solids by the correction kernel of the generic path), two reals packed per complex
-//               value, split step, then the rows of a CTA are transposed through shared memory into the plane
-//               layout spec[kx][z][y];
+//               value, split step written straight into the plane layout spec[kx][z][y] (the rows of a warp
+//               are consecutive, so every frequency is one contiguous piece of at least 32 bytes);
 //   (y, z)    : one CTA per kx plane: y FFT of every z row straight from global memory into the shared plane,
 //               z FFT of every column, division by lambda N, inverse z FFT (one register pass per column),
 //               inverse y FFT back to global memory;
-//   x inverse : the rows of a CTA are gathered from the plane layout, joined, inverse FFT, p^{k+1} written.
+//   x inverse : each warp gathers its rows from the plane layout, joins, inverse FFT, writes p^{k+1}.
 // The arithmetic (DFT kernels, twiddle tables, packing, eigenvalues) is the one of the generic passes; only the
 // order of the butterflies and the data movement differ.
 #include <algorithm>
@@ -111,33 +111,32 @@ template <typename T> __host__ __device__ constexpr int x_threads() { return siz
 template <typename T> __host__ __device__ constexpr int yz_threads() { return sizeof(T) == 4 ? VF_REG_YZ_THREADS : 512; }
 
 // ---- x forward ---------------------------------------------------------------------------------------------
+// Each warp works alone on its 32 / GX rows: the split step writes X_k of its rows straight to the plane layout
+// spec[k][row] (the rows of a warp are consecutive, so each frequency is one contiguous 32-byte or longer piece).
 template <typename T, int GX>
 __global__ void __launch_bounds__(x_threads<T>()) k_reg_x_fwd(PoissonArgs<T> A)
 {
     using C = typename CxT<T>::type;
     constexpr int M = 16 * GX, NT = x_threads<T>(), B = NT / GX, P = 32 / GX, Q = 16 / GX;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int SPX = A.reg_spx, SB = A.reg_sb;
+    const int SPX = A.reg_spx;
     C* tw = reinterpret_cast<C*>(smem_raw);
     C* twr = tw + M;
     C* rowbuf = twr + (M + 1);
-    C* stage = rowbuf + B * SPX;
     stage_table(tw, A.twx, M);
     stage_table(twr, A.twr, M + 1);
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int gi = lane % P, t = lane / P;
     const int b = warp * P + gi;
-    const int rows = A.ny * A.nz, row0 = blockIdx.x * B, row = row0 + b;
+    const int rows = A.ny * A.nz, row = blockIdx.x * B + b;
     const bool act = row < rows;
     C v[16];
     {
-        const long long base = (long long)(act ? row : 0) * A.nx;
+        const T* __restrict__ src = A.f + (long long)(act ? row : 0) * A.nx;
 #pragma unroll
-        for (int m = 0; m < 16; ++m) {
-            const int j = t + GX * m;
-            v[m] = act ? *reinterpret_cast<const C*>(A.f + base + 2 * j) : mk<C>(T(0), T(0));
-        }
+        for (int m = 0; m < 16; ++m)
+            v[m] = act ? *reinterpret_cast<const C*>(src + 2 * (t + GX * m)) : mk<C>(T(0), T(0));
     }
     C* rb = rowbuf + b * SPX;
     auto buf = [rb](int e) -> C& { return rb[e]; };
@@ -148,31 +147,30 @@ __global__ void __launch_bounds__(x_threads<T>()) k_reg_x_fwd(PoissonArgs<T> A)
 #pragma unroll
         for (int k2 = 0; k2 < GX; ++k2) rb[RegShape<GX>::slot(t, q, k2)] = v[q * GX + k2];
     __syncwarp();
-    // split step: X_k = E_k + W^k O_k from Z_k and conj Z_{M-k}; pairs (k, M - k) by one thread
-    for (int k = t; k <= M / 2; k += GX) {
+    if (!act) return;
+    C* __restrict__ spec = reinterpret_cast<C*>(A.spec) + row;
+    // split step: X_k = E_k + W^k O_k from Z_k and conj Z_{M-k}; the pair (k, M - k) by one thread,
+    // k = t + GX i for i = 0..8 (k = M / 2 only for t = 0)
+#pragma unroll
+    for (int i = 0; i <= 8; ++i) {
+        const int k = t + GX * i;
+        if (k > M / 2) break;
         const C Zk = rb[slot_of_freq<GX>(k)];
         if (k == 0) {
-            stage[b] = mk<C>(Zk.x + Zk.y, Zk.x - Zk.y);        // (X_0, X_{nx/2})
+            spec[0] = mk<C>(Zk.x + Zk.y, Zk.x - Zk.y);                  // (X_0, X_{nx/2})
             continue;
         }
         const C Zm = rb[slot_of_freq<GX>(M - k)];
         {
             const C E = mk<C>(T(0.5) * (Zk.x + Zm.x), T(0.5) * (Zk.y - Zm.y));
             const C O = mk<C>(T(0.5) * (Zk.y + Zm.y), T(-0.5) * (Zk.x - Zm.x));
-            stage[k * SB + b] = cadd(E, cmul(twr[k], O));
+            spec[(long long)k * rows] = cadd(E, cmul(twr[k], O));
         }
         if (2 * k != M) {
             const C E = mk<C>(T(0.5) * (Zm.x + Zk.x), T(0.5) * (Zm.y - Zk.y));
             const C O = mk<C>(T(0.5) * (Zm.y + Zk.y), T(-0.5) * (Zm.x - Zk.x));
-            stage[(M - k) * SB + b] = cadd(E, cmul(twr[M - k], O));
+            spec[(long long)(M - k) * rows] = cadd(E, cmul(twr[M - k], O));
         }
-    }
-    __syncthreads();
-    // plane layout: spec[k][row], B consecutive rows per frequency
-    C* spec = reinterpret_cast<C*>(A.spec);
-    for (int it = threadIdx.x; it < M * B; it += NT) {
-        const int k = it / B, bb = it - k * B;
-        if (row0 + bb < rows) spec[(long long)k * rows + row0 + bb] = stage[k * SB + bb];
     }
 }
 
@@ -183,43 +181,41 @@ __global__ void __launch_bounds__(x_threads<T>()) k_reg_x_inv(PoissonArgs<T> A)
     using C = typename CxT<T>::type;
     constexpr int M = 16 * GX, NT = x_threads<T>(), B = NT / GX, P = 32 / GX, Q = 16 / GX;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int SPX = A.reg_spx, SB = A.reg_sb;
+    const int SPX = A.reg_spx;
     C* tw = reinterpret_cast<C*>(smem_raw);
     C* twr = tw + M;
     C* rowbuf = twr + (M + 1);
-    C* stage = rowbuf + B * SPX;
     stage_table(tw, A.twx, M);
     stage_table(twr, A.twr, M + 1);
-    const int rows = A.ny * A.nz, row0 = blockIdx.x * B;
-    const C* spec = reinterpret_cast<const C*>(A.spec);
-    // M * B is a multiple of 8 NT: eight loads in flight per thread
-    for (int it0 = threadIdx.x; it0 < M * B; it0 += 8 * NT) {
-        C tmp[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int it = it0 + u * NT, k = it / B, bb = it - k * B;
-            tmp[u] = row0 + bb < rows ? spec[(long long)k * rows + row0 + bb] : mk<C>(T(0), T(0));
-        }
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int it = it0 + u * NT, k = it / B, bb = it - k * B;
-            stage[k * SB + bb] = tmp[u];
-        }
-    }
-    __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int gi = lane % P, t = lane / P;
     const int b = warp * P + gi;
-    const int row = row0 + b;
+    const int rows = A.ny * A.nz, row = blockIdx.x * B + b;
+    const bool act = row < rows;
+    // the pairs (X_k, X_{M-k}) of this thread, k = t + GX i, all loads in flight together
+    C xk[9], xm[9];
+    {
+        const C* __restrict__ spec = reinterpret_cast<const C*>(A.spec) + (act ? row : 0);
+#pragma unroll
+        for (int i = 0; i <= 8; ++i) {
+            const int k = t + GX * i;
+            const bool ok = act && k <= M / 2;
+            xk[i] = ok ? spec[(long long)k * rows] : mk<C>(T(0), T(0));
+            xm[i] = ok && k > 0 ? spec[(long long)(M - k) * rows] : mk<C>(T(0), T(0));
+        }
+    }
+    __syncthreads();   // tables staged
     C* rb = rowbuf + b * SPX;
-    // join: Z'_k = (X_k + conj X_{M-k}) + i W^{-k} (X_k - conj X_{M-k}); pairs (k, M - k) by one thread
-    for (int k = t; k <= M / 2; k += GX) {
-        const C Xk = stage[k * SB + b];
+    // join: Z'_k = (X_k + conj X_{M-k}) + i W^{-k} (X_k - conj X_{M-k})
+#pragma unroll
+    for (int i = 0; i <= 8; ++i) {
+        const int k = t + GX * i;
+        if (k > M / 2) break;
+        const C Xk = xk[i], Xm = xm[i];
         if (k == 0) {
             rb[slot_of_freq<GX>(0)] = mk<C>(Xk.x + Xk.y, Xk.x - Xk.y);
             continue;
         }
-        const C Xm = stage[(M - k) * SB + b];
         {
             const C s = mk<C>(Xk.x + Xm.x, Xk.y - Xm.y), d = mk<C>(Xk.x - Xm.x, Xk.y + Xm.y);
             C w = twr[k];
@@ -243,10 +239,10 @@ __global__ void __launch_bounds__(x_threads<T>()) k_reg_x_inv(PoissonArgs<T> A)
         for (int k2 = 0; k2 < GX; ++k2) v[q * GX + k2] = rb[RegShape<GX>::slot(t, q, k2)];
     auto buf = [rb](int e) -> C& { return rb[e]; };
     reg_inv<C, GX>(v, t, tw, buf);
-    if (row < rows) {
-        const long long base = (long long)row * A.nx;
+    if (act) {
+        T* __restrict__ dst = A.p + (long long)row * A.nx;
 #pragma unroll
-        for (int m = 0; m < 16; ++m) *reinterpret_cast<C*>(A.p + base + 2 * (t + GX * m)) = v[m];
+        for (int m = 0; m < 16; ++m) *reinterpret_cast<C*>(dst + 2 * (t + GX * m)) = v[m];
     }
 }
 
@@ -414,10 +410,10 @@ int col_ways(int G, int stride, int esz)
 }
 
 template <typename T>
-size_t x_smem(int M, int spx, int sb)
+size_t x_smem(int M, int spx)
 {
     const int B = x_threads<T>() / (M / 16);
-    return ((size_t)M + (M + 1) + (size_t)B * spx + (size_t)M * sb) * sizeof(typename CxT<T>::type);
+    return ((size_t)M + (M + 1) + (size_t)B * spx) * sizeof(typename CxT<T>::type);
 }
 
 template <typename T>
@@ -434,7 +430,7 @@ cudaError_t launch_x(const PoissonArgs<T>& a, bool fwd, cudaStream_t st)
     constexpr int B = x_threads<T>() / GX;
     const int rows = a.ny * a.nz;
     const unsigned grid = (unsigned)((rows + B - 1) / B);
-    const size_t sm = x_smem<T>(16 * GX, a.reg_spx, a.reg_sb);
+    const size_t sm = x_smem<T>(16 * GX, a.reg_spx);
     if (fwd) k_reg_x_fwd<T, GX><<<grid, x_threads<T>(), sm, st>>>(a);
     else k_reg_x_inv<T, GX><<<grid, x_threads<T>(), sm, st>>>(a);
     return cudaGetLastError();
@@ -503,7 +499,7 @@ cudaError_t raise_smem(K kernel, size_t bytes)
 template <typename T, int GX>
 cudaError_t prepare_x(const PoissonArgs<T>& a)
 {
-    const size_t sm = x_smem<T>(16 * GX, a.reg_spx, a.reg_sb);
+    const size_t sm = x_smem<T>(16 * GX, a.reg_spx);
     cudaError_t e = raise_smem(k_reg_x_fwd<T, GX>, sm);
     if (e == cudaSuccess) e = raise_smem(k_reg_x_inv<T, GX>, sm);
     return e;
@@ -532,7 +528,7 @@ bool RegFft<T>::eligible(int nx, int ny, int nz)
     const int gx = g_of(nx / 2), gy = g_of(ny), gz = g_of(nz);
     if (!gx || !gy || !gz) return false;
     // the plane with the widest padding, and the x passes, must fit
-    return yz_smem<T>(ny, nz, ny + 15) <= kRegSmemLimit && x_smem<T>(nx / 2, nx / 2 + 15, x_threads<T>() / gx + 15) <=
+    return yz_smem<T>(ny, nz, ny + 15) <= kRegSmemLimit && x_smem<T>(nx / 2, nx / 2 + 15) <=
                                                               kRegSmemLimit;
 }
 
@@ -553,21 +549,14 @@ void RegFft<T>::configure(PoissonArgs<T>& a)
         if (w < best_w) { best_w = w; best = sp; }
     }
     a.reg_sp = best;
-    // x passes: rows of the group accesses, and the transposition buffer (frequency-major, rows contiguous)
-    const int B = x_threads<T>() / a.gx;
+    // x passes: the row slices of the groups
     best = -1; best_w = 1 << 30;
     for (int pad = 0; pad < 16; ++pad) {
         const int w = row_ways(a.gx, a.M + pad, esz);
         if (w < best_w) { best_w = w; best = a.M + pad; }
     }
     a.reg_spx = best;
-    best = -1; best_w = 1 << 30;
-    for (int pad = 0; pad < 16; ++pad) {
-        const int sb = B + pad, G = a.gx, P = 32 / G;
-        const int w = worst_ways(esz, [&](int l, int s) { return (long long)((l / P) + G * s) * sb + (l % P); });
-        if (w < best_w) { best_w = w; best = sb; }
-    }
-    a.reg_sb = best;
+    a.reg_sb = 0;
     a.reg = 1;
 }
 

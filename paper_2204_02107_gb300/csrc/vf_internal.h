@@ -174,7 +174,7 @@ struct PoissonArgs {
     int gx, gy, gz;           // M / 16, ny / 16, nz / 16
     int reg_sp;               // complex stride between the z rows of the shared plane
     int reg_spx;              // complex stride between the rows of the x passes
-    int reg_sb;               // complex stride between the frequencies of the x passes' transposition buffer
+    int reg_sb;               // unused (0)
 };
 
 
