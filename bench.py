@@ -41,7 +41,7 @@ PHASE_BYTES_PER_CELL = {
     "stage3": 12 * F32 + 1,      # read q3 (stencil), q_n; write q4; mask
     "stage4": 20 * F32 + 1,      # read q4 (stencil), q_n, q2, q3; write q*; mask
     "div": 4 * F32,              # read u*, v*, w*; write r
-    "fft_x_fwd": 3 * F32 + 1,    # read r, p, mask; write the half spectrum (N/2 complex = N F bytes)
+    "fft_x_fwd": 2 * F32,        # read f; write the half spectrum (N/2 complex = N F bytes)
     "fft_y_fwd": 2 * F32,        # read + write the spectrum
     "fft_z_solve": 2 * F32,
     "fft_y_inv": 2 * F32,
@@ -150,8 +150,9 @@ def dist_barrier(world):
         dist.barrier()
 
 
-def traffic_record(kernel):
-    """DRAM bytes per launch of ``kernel`` from the committed ncu summary, if taken on the current source."""
+def traffic_record(kernel, tiles):
+    """DRAM bytes per launch of ``kernel`` from the committed ncu summary, if taken on the current source with
+    the same launch tiles."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
@@ -165,6 +166,8 @@ def traffic_record(kernel):
         return None
     digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
     if digest != entry.get("source_sha256"):
+        return None
+    if entry.get("tiles") is not None and entry["tiles"] != tiles:
         return None
     scale = entry.get("scale_to_full", 1.0)
     return entry["dram_bytes_per_launch"] * scale
@@ -346,6 +349,7 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=24, help="requests of the serving leg (0: skip)")
     ap.add_argument("--no-extras", action="store_true", help="skip the large-room, batch and serving legs")
     ap.add_argument("--no-autotune", action="store_true", help="launch with the default tiles")
+    ap.add_argument("--tiles", default=None, help="z-chunks stage,div,project,filter (skips the autotuner)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -359,7 +363,13 @@ def main():
     room = rooms.single_room(256, 128, 128)
     stream = torch.cuda.Stream()
     g = native.room_grid(room, precision="fp32", stream=stream.cuda_stream)
-    tiles = g.tiles() if args.no_autotune else g.autotune(reps=20)
+    if args.tiles:
+        g.set_tiles(*[int(v) for v in args.tiles.split(",")])
+        tiles, tiles_source = g.tiles(), "given"
+    elif args.no_autotune:
+        tiles, tiles_source = g.tiles(), "defaults"
+    else:
+        tiles, tiles_source = g.autotune(reps=20), "autotuned before warm-up"
     cells = room.cells
     launches_per_step = None   # counted from the profiled steps below
 
@@ -409,13 +419,13 @@ def main():
     dominant = max(groups, key=lambda k: groups[k][0])
     g_ms, g_n, g_b = groups[dominant]
     achieved = (g_b / g_n) / (g_ms / g_n / 1e3) / 1e9
-    traffic = traffic_record(dominant)
+    traffic = traffic_record(dominant, tiles)
     step_s = ms_max / 1e3 / args.steps
     step_gbs = STEP_MODEL_BYTES_PER_CELL_FP32 * cells / step_s / 1e9
 
     # FP64 form of the same step (parity path)
     g64 = native.room_grid(room, precision="fp64", stream=stream.cuda_stream)
-    tiles64 = g64.tiles() if args.no_autotune else g64.autotune(reps=5)
+    tiles64 = g64.tiles() if (args.no_autotune or args.tiles) else g64.autotune(reps=5)
     g64.step(3, reduce_every=1)
     g64.sync()
     s64, e64 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -444,7 +454,7 @@ def main():
                    "cells": cells, "global_cells": cells * world, "precision": "fp32_mixed",
                    "l2": "state 0.3 GB > 126 MB L2: inputs larger than L2, no flush",
                    "parallelism": "one independent room per GPU" if world > 1 else "single GPU",
-                   "tiles": tiles, "tiles_source": "defaults" if args.no_autotune else "autotuned before warm-up"},
+                   "tiles": tiles, "tiles_source": tiles_source},
         "roofline": {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                      "algorithmic_bytes_per_launch": g_b / g_n, "launches_per_step": g_n / prof_steps,

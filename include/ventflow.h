@@ -189,7 +189,7 @@ typedef struct vf_tiles {
 } vf_tiles;
 
 /* The tiles a grid launches with.  A new grid takes the process-wide tile cache's entry for its (nx, ny, nz,
- * precision) if there is one, else (8, 8, 8, 16). */
+ * precision) if there is one, else (4, 32, 8, 16), the autotuner's choice for a 256 x 128 x 128 room on GB300. */
 int vf_get_tiles(const vf_grid* g, vf_tiles* out);
 
 /* Set a grid's tiles (VF_EINVAL if a chunk is out of range; the grid is unchanged then).  Takes effect at the next

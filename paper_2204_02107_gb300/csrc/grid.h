@@ -57,7 +57,7 @@ struct vf_grid {
     unsigned long long* solid_count = nullptr;
     int nred = 0;
 
-    int zc[vf::kZcKinds] = {8, 8, 8, 16};   // z-chunks (vf_tiles): stage, divergence, projection, filter
+    int zc[vf::kZcKinds] = {4, 32, 8, 16};  // z-chunks (vf_tiles): stage, divergence, projection, filter
 
     vf::FftAxis ax{}, ay{}, az{};
     int rows_per_block = 1, cols_per_block = 16;

@@ -15,6 +15,7 @@ from gpu_helpers import room_case as oracle_case
 pytestmark = pytest.mark.gpu
 
 ALL = FIELD_NAMES + ("p",)
+DEFAULT = {"zc_stage": 4, "zc_div": 32, "zc_project": 8, "zc_filter": 16}
 # Reductions under another filter chunk are summed in another order.  FP32: the kinetic energy is a plain float sum
 # of at most 64 non-negative terms per thread before the float-float and FP64 stages, so its relative change is
 # below 64 * 2^-24 < 4e-6; the scalar inventories are compensated (float-float) sums, good to ~2^-44 of the sum.
@@ -127,14 +128,14 @@ def test_new_grid_takes_cached_tiles(torch):
     native.tile_cache_clear()
     room = room_case()
     g = native.room_grid(room, precision="fp32")
-    assert g.tiles() == {"zc_stage": 8, "zc_div": 8, "zc_project": 8, "zc_filter": 16}
+    assert g.tiles() == DEFAULT
     chosen = g.autotune(reps=2)
     g.close()
     g2 = native.room_grid(room, precision="fp32")
     assert g2.tiles() == chosen
     g2.close()
     g3 = native.room_grid(room, precision="fp64")        # another precision: not cached
-    assert g3.tiles() == {"zc_stage": 8, "zc_div": 8, "zc_project": 8, "zc_filter": 16}
+    assert g3.tiles() == DEFAULT
     g3.close()
     native.tile_cache_clear()
     assert native.tile_cache_lookup(room.nx, room.ny, room.nz, "fp32") is None
