@@ -391,6 +391,45 @@ def run(state: State, geom: Geometry, prm: Params, n_steps: int, with_budget=Fal
     return state, recs
 
 
+# ----------------------------------------------------------------------------------------------------------------
+# Dynamic time step (Sec. 2.4: the user sets the maximum Courant number and AdjustDt adapts dt as the flow evolves)
+# ----------------------------------------------------------------------------------------------------------------
+
+def courant_rate(state: State, prm: Params):
+    """sigma = max over cells of sum_j |u_j| / h_j, so that the advective Courant number of a step is dt * sigma.
+    The paper names the maximum Courant number as the control but not its form; this is the three-dimensional
+    advective one (the sum over axes, the stricter of the usual choices)."""
+    hx, hy, hz = prm.h
+    return float(np.max(np.abs(state.u) / hx + np.abs(state.v) / hy + np.abs(state.w) / hz))
+
+
+def adjust_dt(state: State, prm: Params, courant_max: float):
+    """The time step for the next step from the current velocity: dt = min(prm.dt, courant_max / sigma); prm.dt
+    is the upper bound (and the step used while the fluid is at rest)."""
+    sigma = courant_rate(state, prm)
+    if sigma == 0.0:
+        return prm.dt
+    return min(prm.dt, courant_max / sigma)
+
+
+def run_adaptive(state: State, geom: Geometry, prm: Params, n_steps: int, courant_max: float):
+    """n_steps steps, each with dt = adjust_dt(current state).  The internal pressure carries a factor dt
+    (u = u* - grad p has none), so the warm start is rescaled by dt_new / dt_old when dt changes: the physical
+    pressure p / dt the next solve starts from is the one the previous step produced.  The incoming state's
+    pressure is taken to be relative to prm.dt.  Returns (final state, records with 'dt', dt of the last step)."""
+    recs = []
+    dt_prev = prm.dt
+    for _ in range(n_steps):
+        dt = adjust_dt(state, prm, courant_max)
+        if dt != dt_prev:
+            state = State(state.u, state.v, state.w, state.c, state.p * (dt / dt_prev), state.t, state.step)
+        state, rec = step(state, geom, prm.with_(dt=dt))
+        rec['dt'] = dt
+        recs.append(rec)
+        dt_prev = dt
+    return state, recs, dt_prev
+
+
 def physical_pressure(state: State, prm: Params):
     """p / rho in physical units: the internal p carries a factor dt because u = u* - grad p has none."""
     return state.p / prm.dt

@@ -150,6 +150,7 @@ PoissonArgs<T> poisson_args(const vf_grid* g, T* f, T* p, int use_mask)
     a.invN = (T)(1.0 / ((double)d.nx * d.ny * d.nz));
     a.ax = g->ax; a.ay = g->ay; a.az = g->az;
     a.ny_div = vf::make_fast_div((uint32_t)d.ny);
+    a.nx_div = vf::make_fast_div((uint32_t)d.nx);
     a.rows_per_block = g->rows_per_block;
     a.cols_per_block = g->cols_per_block;
     return a;

@@ -108,7 +108,8 @@ __global__ void __launch_bounds__(256) k_poisson_correction(PoissonArgs<T> A, in
 {
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < A.n_near; j += gridDim.x * blockDim.x) {
         const int i = __ldg(A.near_list + j);
-        const int x = i % A.nx, t = i / A.nx, y = t % A.ny, z = t / A.ny;
+        const int t = (int)fdiv((uint32_t)i, A.nx_div), x = i - t * A.nx;
+        const int z = (int)fdiv((uint32_t)t, A.ny_div), y = t - z * A.ny;
         T rr;
         if (first) {
             rr = A.f[i];

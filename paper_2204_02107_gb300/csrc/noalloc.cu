@@ -124,6 +124,7 @@ int solve(int nx, int ny, int nz, double lx, double ly, double lz, const void* f
     a.ay = vf::make_fft_axis(ny);
     a.az = vf::make_fft_axis(nz);
     a.ny_div = vf::make_fast_div((uint32_t)ny);
+    a.nx_div = vf::make_fast_div((uint32_t)nx);
     const int per_cta = sizeof(T) == 8 ? 1024 : 2048;   // complex values per CTA in the x passes
     a.rows_per_block = per_cta / M > 0 ? per_cta / M : 1;
     a.cols_per_block = (int)tb;

@@ -166,6 +166,7 @@ struct PoissonArgs {
     T invN;                   // 1 / (nx ny nz)
     FftAxis ax, ay, az;
     FastDiv ny_div;           // i -> i / ny (plane passes)
+    FastDiv nx_div;           // i -> i / nx (cell index -> row, correction kernel)
     int rows_per_block;       // rows of the x passes per CTA
     int cols_per_block;       // kx columns of the y / z tile passes per CTA
     // register path (every axis length 16 G with G in 1, 2, 4, 8, 16 and the plane in shared memory): the
