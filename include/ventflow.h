@@ -80,6 +80,11 @@ typedef struct vf_grid_desc {
     int32_t history_capacity;    /* number of per-step reduction records kept on the device (ring buffer) */
     void* cuda_stream;           /* cudaStream_t the grid works on; NULL -> a stream the grid creates */
     const vf_allocator* alloc;   /* NULL -> cudaMallocAsync */
+    double courant_max;          /* > 0: dynamic time step (Sec. 2.4, AdjustDt: the user sets the maximum Courant
+                                    number).  Before every step dt = min(dt, courant_max / sigma) with
+                                    sigma = max over cells of sum_j |u_j| / h_j of the current state (dt itself
+                                    while the fluid is at rest), chosen on the device; p/rho needs no rescale.
+                                    0: fixed dt.  tau_f <= 0 follows the current dt. */
 } vf_grid_desc;
 
 /* FP64 reductions of one state (Sec. 3.3 diagnostics).  dV = hx*hy*hz.  Room cells are those flagged by
@@ -99,6 +104,7 @@ typedef struct vf_reduce {
     int64_t hist[64];            /* room cells with c in [b/64, (b+1)/64) (c == 1 in bin 63) */
     int64_t hist_under;          /* room cells with c < 0 */
     int64_t hist_over;           /* room cells with c > 1 */
+    double dt;                   /* time step that produced the state (the grid's dt for vf_reductions) */
 } vf_reduce;
 
 typedef struct vf_grid vf_grid;
@@ -165,7 +171,8 @@ int vf_history(vf_grid* g, vf_reduce* out, int64_t max_records, int64_t* count);
 /* Forget the recorded history. */
 int vf_clear_history(vf_grid* g);
 
-/* Simulated time, step count, cell count and bytes of device memory held by the grid. */
+/* Simulated time, step count, cell count and bytes of device memory held by the grid.  With a dynamic time step the
+ * time is read from the device (waits for the enqueued steps). */
 int vf_info(const vf_grid* g, double* t, int64_t* step, int64_t* cells, int64_t* device_bytes);
 
 /* Solve L p = f once with the grid's FFT Poisson solver (Sec. 2.2, one pass of steps a6-a8): forward 3D FFT,
@@ -296,7 +303,8 @@ int64_t vf_poisson_noalloc_max_cells(int32_t precision);
 #define VF_PHASE_REDUCE 12      /* FP64 reductions */
 #define VF_PHASE_POISSON_RHS 13 /* Eq. 9 correction D((1 - beta) G p) at the cells next to solids */
 #define VF_PHASE_FFT_YZ_SOLVE 14 /* per-kx plane: y, z FFTs, division by lambda, inverse z, y FFTs */
-#define VF_N_PHASES 15
+#define VF_PHASE_ADJUST_DT 15   /* dynamic time step: dt from the Courant rate of the current state */
+#define VF_N_PHASES 16
 
 /* Run n steps like vf_step but with direct launches bracketed by CUDA events on the grid's stream; adds the
  * elapsed milliseconds of every phase to phase_ms[VF_N_PHASES] and its launch count to launches[VF_N_PHASES]
@@ -309,6 +317,10 @@ const char* vf_phase_name(int phase);
 /* ---- status ---------------------------------------------------------------------------------------------- */
 
 const char* vf_status_string(int status);
+
+/* Byte sizes of the ABI structs as this library was compiled: out[0] vf_grid_desc, out[1] vf_reduce,
+ * out[2] vf_batch_desc, out[3] vf_tiles (for bindings to check their layouts). */
+int vf_abi_sizes(int64_t out[4]);
 const char* vf_last_error(const vf_grid* g);
 
 /* ---- host-side ventilation metrics (Sec. 3.3.2, 3.4), from a reduction series -------------------------------- */

@@ -200,6 +200,9 @@ int vf_batch_step(vf_batch* b, int64_t n)
             int rc = capture(b);
             if (rc) return rc;
         }
+        // rooms with a dynamic time step whose fields changed: their Courant rate, ahead of the graph
+        for (vf_batch_slot& s : b->slots)
+            if (stepping(s)) VB_CK(vf_engine::refresh_sigma(s.g, b->stream));
         const int re = b->d.reduce_every;
         for (int64_t i = 0; i < chunk; ++i) {
             const int64_t s = b->batch_step + 1;

@@ -124,6 +124,7 @@ FlowConsts<T> flow_consts(const vf_grid* g)
     k.third = (T)(1.0 / 3.0);
     k.cset = (T)g->cset;
     k.filt = (T)(1.0 / std::pow(M_PI, 6));
+    k.dyn = g->dynamic ? g->dtctl : nullptr;
     return k;
 }
 
@@ -171,6 +172,7 @@ vf::ReduceArgsDev reduce_args(const vf_grid* g)
     r.dV = (g->d.lx / g->d.nx) * (g->d.ly / g->d.ny) * (g->d.lz / g->d.nz);
     r.dt = g->d.dt;
     r.t0 = g->t0;
+    r.dyn = g->dynamic ? g->dtctl : nullptr;
     return r;
 }
 
@@ -185,10 +187,16 @@ cudaError_t enqueue_step_t(vf_grid* g, cudaStream_t st, bool with_reduce, const 
 {
     auto mark = [&](int phase) { if (hook) (*hook)(phase); };
     const FlowConsts<T> k = flow_consts<T>(g);
+    cudaError_t e;
+    // dynamic time step: dt of this step from the Courant rate of the state it starts from (device side)
+    unsigned long long* sigma_out = g->dynamic ? &g->dtctl->sigma_bits : nullptr;
+    if (g->dynamic) {
+        if ((e = vf::adjust_dt(g->dtctl, st)) != cudaSuccess) return e;
+        mark(VF_PHASE_ADJUST_DT);
+    }
     StageArgs<T> a{};
     a.mask = g->mask;
     a.qn = g->q;
-    cudaError_t e;
     // stage states: q2 in qa, q3 in qb, q4 in acc; stage 4 writes q* over q2 (each cell reads its own q2 first)
     a.qs = g->q; a.out = g->qa;
     if ((e = Kernels<T>::stage(1, a, k, st)) != cudaSuccess) return e;
@@ -214,13 +222,15 @@ cudaError_t enqueue_step_t(vf_grid* g, cudaStream_t st, bool with_reduce, const 
     long long* step_counter = g->dev_counters + 1;
     // projection into qb (then filtered into q) or straight into q
     void* proj_out = g->d.filter ? g->qb : g->q;
-    if ((e = Kernels<T>::project(qstar, (const T*)g->p, proj_out, g->mask, step_counter, k, st)) != cudaSuccess)
+    if ((e = Kernels<T>::project(qstar, (const T*)g->p, proj_out, g->mask, step_counter, k, st,
+                                 g->d.filter ? nullptr : sigma_out)) != cudaSuccess)
         return e;
     mark(VF_PHASE_PROJECT);
     if (g->d.filter) {
         // with the filter on, the reductions ride along in the filter kernel
         const vf::ReduceArgsDev ra = reduce_args(g);
-        if ((e = Kernels<T>::filter(g->qb, g->q, g->mask, k, with_reduce ? &ra : nullptr, 1, st)) != cudaSuccess)
+        if ((e = Kernels<T>::filter(g->qb, g->q, g->mask, k, with_reduce ? &ra : nullptr, 1, st, sigma_out)) !=
+            cudaSuccess)
             return e;
         mark(VF_PHASE_FILTER);
     } else if (with_reduce) {
@@ -360,6 +370,17 @@ cudaError_t mask_fields(vf_grid* g)
 
 namespace vf_engine {
 
+cudaError_t refresh_sigma(vf_grid* g, cudaStream_t st)
+{
+    if (!g->dynamic || !g->sigma_stale) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(&g->dtctl->sigma_bits, 0, sizeof(unsigned long long), st);
+    if (e == cudaSuccess)
+        e = g->fp64 ? Kernels<double>::courant_rate(g->q, flow_consts<double>(g), g->N, &g->dtctl->sigma_bits, st)
+                    : Kernels<float>::courant_rate(g->q, flow_consts<float>(g), g->N, &g->dtctl->sigma_bits, st);
+    if (e == cudaSuccess) g->sigma_stale = false;
+    return e;
+}
+
 cudaError_t enqueue_step(vf_grid* g, cudaStream_t st, bool with_reduce)
 {
     return ::enqueue_step(g, st, with_reduce);
@@ -376,6 +397,7 @@ size_t grid_bytes(const vf_grid_desc& d)
     size_t b = 4 * r256(4 * N * esz) + 4 * r256(N * esz) + r256(N * 4) + r256(N * 8) + r256(N);
     b += r256(nred * vf::kRedSlots * 8) + r256((vf::kHistBins + 2) * 8) + r256(4) + r256(sizeof(vf_reduce));
     b += r256((size_t)d.history_capacity * sizeof(vf_reduce)) + r256(16) + r256(4) + r256(8);
+    b += r256(sizeof(vf::DtCtl));
     b += r256(M * cpx) + r256(d.ny * cpx) + r256(d.nz * cpx) + r256((M + 1) * cpx);
     b += r256(M * esz) + r256(d.ny * esz) + r256(d.nz * esz) + r256(d.ny * 4) + r256(d.nz * 4);
     return b;
@@ -419,6 +441,7 @@ int vf_create_grid(const vf_grid_desc* d, vf_grid** out)
     if (!(d->lx > 0) || !(d->ly > 0) || !(d->lz > 0) || !(d->dt > 0) || !(d->nu >= 0)) return VF_EINVAL;
     if (d->precision != VF_FP64 && d->precision != VF_FP32_MIXED) return VF_EINVAL;
     if (d->n_pressure_iters < 0 || d->history_capacity < 1) return VF_EINVAL;
+    if (!(d->courant_max >= 0.0)) return VF_EINVAL;
     if ((long long)d->nx * d->ny * d->nz > (1LL << 31)) return VF_ESIZE;
 
     vf_grid* g = new vf_grid();
@@ -488,6 +511,31 @@ int vf_create_grid(const vf_grid_desc* d, vf_grid** out)
     if (!(g->dev_counters = (long long*)galloc(g, 2 * sizeof(long long)))) return fail(VF_ENOMEM);
     if (!(g->nonfinite = (int*)galloc(g, sizeof(int)))) return fail(VF_ENOMEM);
     if (!(g->solid_count = (unsigned long long*)galloc(g, sizeof(unsigned long long)))) return fail(VF_ENOMEM);
+    if (!(g->dtctl = (vf::DtCtl*)galloc(g, sizeof(vf::DtCtl)))) return fail(VF_ENOMEM);
+    {
+        // the control block starts at the given dt (constants with the same formulas as the adjust kernel)
+        g->dynamic = d->courant_max > 0.0;
+        vf::DtCtl c{};
+        c.dt = d->dt;
+        c.t_end = 0.0;
+        c.dt2 = d->dt / 2.0;
+        c.dt3 = d->dt / 3.0;
+        c.dt6 = d->dt / 6.0;
+        c.inv_tau = 1.0 / (d->tau_f > 0.0 ? d->tau_f : d->dt);
+        const double h[3] = {d->lx / d->nx, d->ly / d->ny, d->lz / d->nz};
+        for (int j = 0; j < 3; ++j) {
+            c.h[j] = h[j];
+            c.i2h_div[j] = 1.0 / (2.0 * h[j] * d->dt);
+            c.i2h_dt[j] = d->dt / (2.0 * h[j]);
+        }
+        c.sigma_bits = 0ull;
+        c.courant_max = d->courant_max;
+        c.dt_max = d->dt;
+        c.tau_f = d->tau_f;
+        if (cudaMemcpyAsync(g->dtctl, &c, sizeof(c), cudaMemcpyHostToDevice, g->stream) != cudaSuccess ||
+            cudaStreamSynchronize(g->stream) != cudaSuccess)
+            return fail(VF_ECUDA);
+    }
 
     int rc = g->fp64 ? build_tables_t<double>(g) : build_tables_t<float>(g);
     if (rc != VF_OK) return fail(rc == VF_ECUDA ? VF_ECUDA : rc);
@@ -544,6 +592,7 @@ int vf_set_mask(vf_grid* g, const uint8_t* beta, int mem)
     VF_CK(cudaStreamSynchronize(g->stream));
     g->has_solid = solids > 0;
     g->mask_set = true;
+    g->sigma_stale = true;   // the fields were re-masked
     drop_graphs(g);
     return VF_OK;
 }
@@ -592,6 +641,7 @@ int vf_set_field(vf_grid* g, int field, const void* src, int is_fp64, int mem)
     if (g->fp64) VF_CK(Kernels<double>::convert_in(dsrc, is_fp64, dst, comp, g->N, 1.0, mask, g->stream));
     else VF_CK(Kernels<float>::convert_in(dsrc, is_fp64, dst, comp, g->N, 1.0, mask, g->stream));
     VF_CK(cudaStreamSynchronize(g->stream));
+    if (field <= VF_W) g->sigma_stale = true;
     return VF_OK;
 }
 
@@ -605,6 +655,7 @@ int vf_set_time(vf_grid* g, double t, int64_t step)
     g->t0 = t - (double)step * g->d.dt;
     long long s = step;
     VF_CK(cudaMemcpyAsync(g->dev_counters + 1, &s, sizeof(s), cudaMemcpyHostToDevice, g->stream));
+    VF_CK(cudaMemcpyAsync(&g->dtctl->t_end, &t, sizeof(double), cudaMemcpyHostToDevice, g->stream));
     VF_CK(cudaStreamSynchronize(g->stream));
     drop_graphs(g);   // t0 is baked into the reduction launch
     return VF_OK;
@@ -620,6 +671,7 @@ int vf_step(vf_grid* g, int64_t n, int32_t reduce_every)
         rc = capture_graphs(g);
         if (rc) return rc;
     }
+    if (n > 0) VF_CK(vf_engine::refresh_sigma(g, g->stream));
     for (int64_t i = 0; i < n; ++i) {
         const int64_t s = g->step + 1;
         const bool red = reduce_every > 0 && (s % reduce_every) == 0;
@@ -711,7 +763,18 @@ int vf_clear_history(vf_grid* g)
 int vf_info(const vf_grid* g, double* t, int64_t* step, int64_t* cells, int64_t* device_bytes)
 {
     if (!g) return VF_EINVAL;
-    if (t) *t = g->t0 + (double)g->step * g->d.dt;
+    if (t) {
+        if (g->dynamic) {
+            double te = 0.0;
+            if (cudaMemcpyAsync(&te, &g->dtctl->t_end, sizeof(double), cudaMemcpyDeviceToHost, g->stream) !=
+                    cudaSuccess ||
+                cudaStreamSynchronize(g->stream) != cudaSuccess)
+                return VF_ECUDA;
+            *t = te;
+        } else {
+            *t = g->t0 + (double)g->step * g->d.dt;
+        }
+    }
     if (step) *step = g->step;
     if (cells) *cells = (int64_t)g->N;
     if (device_bytes) *device_bytes = (int64_t)g->bytes;
@@ -739,6 +802,7 @@ int vf_profile_steps(vf_grid* g, int64_t n, int32_t reduce_every, double* phase_
     if (rc) return rc;
     if (n < 0 || reduce_every < 0 || !phase_ms || !launches) return set_err(g, VF_EINVAL, "vf_profile_steps: bad argument");
     if (!g->mask_set) return set_err(g, VF_ESTATE, "vf_profile_steps: call vf_set_mask first");
+    if (n > 0) VF_CK(vf_engine::refresh_sigma(g, g->stream));
     for (int64_t i = 0; i < n; ++i) {
         PhaseRecorder rec;
         rec.stream = g->stream;
@@ -774,9 +838,19 @@ const char* vf_phase_name(int phase)
 {
     static const char* names[VF_N_PHASES] = {"stage1", "stage2", "stage3", "stage4", "div", "fft_x_fwd",
                                              "fft_y_fwd", "fft_z_solve", "fft_y_inv", "fft_x_inv", "project",
-                                             "filter", "reduce", "poisson_rhs", "fft_yz_solve"};
+                                             "filter", "reduce", "poisson_rhs", "fft_yz_solve", "adjust_dt"};
     if (phase < 0 || phase >= VF_N_PHASES) return "unknown";
     return names[phase];
+}
+
+int vf_abi_sizes(int64_t out[4])
+{
+    if (!out) return VF_EINVAL;
+    out[0] = (int64_t)sizeof(vf_grid_desc);
+    out[1] = (int64_t)sizeof(vf_reduce);
+    out[2] = (int64_t)sizeof(vf_batch_desc);
+    out[3] = (int64_t)sizeof(vf_tiles);
+    return VF_OK;
 }
 
 const char* vf_status_string(int status)

@@ -55,6 +55,25 @@ __device__ __forceinline__ int wrap(int i, int n) { return i < 0 ? i + n : (i >=
 template <typename T>
 __device__ __forceinline__ T beta_of(uint8_t m) { return (m & kBitBeta) ? T(1) : T(0); }
 
+// Courant rate of one cell, sum_j |u_j| / h_j (Sec. 2.4 dynamic time step), with fixed rounding (no contraction)
+// so that every kernel that forms it gets the same bits for the same velocity
+__device__ __forceinline__ float sigma_cell(float u, float v, float w, const float ih[3])
+{
+    return __fadd_rn(__fadd_rn(__fmul_rn(fabsf(u), ih[0]), __fmul_rn(fabsf(v), ih[1])), __fmul_rn(fabsf(w), ih[2]));
+}
+__device__ __forceinline__ double sigma_cell(double u, double v, double w, const double ih[3])
+{
+    return __dadd_rn(__dadd_rn(__dmul_rn(fabs(u), ih[0]), __dmul_rn(fabs(v), ih[1])), __dmul_rn(fabs(w), ih[2]));
+}
+
+// warp maximum of s, then one atomic max of its double bits per warp (every lane of the warp calls it)
+__device__ __forceinline__ void sigma_flush(double s, unsigned long long* out)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s = fmax(s, __shfl_xor_sync(0xffffffffu, s, o));
+    if ((threadIdx.x & 31) == 0 && s > 0.0) atomicMax(out, (unsigned long long)__double_as_longlong(s));
+}
+
 // ------------------------------------------------------------------------------------------------------------
 // RK4 stage (a1 + a2 + a3)
 // ------------------------------------------------------------------------------------------------------------
@@ -64,13 +83,21 @@ __device__ __forceinline__ T beta_of(uint8_t m) { return (m & kBitBeta) ? T(1) :
 // k_c = beta [ -sum_j ih_j (F^+ - F^-) + alpha sum_j ih2_j (beta^+ (c^+ - c^0) - beta^- (c^0 - c^-))
 //              + S (cset - c^0) inv_tau ],  F^+ = beta^+ (U_j^0 c^0 + U_j^+ c^+) / 2 (face weight beta^0 beta^+,
 //              beta^0 is applied by the outer factor)
-template <typename T, int STAGE>
+template <typename T, int STAGE, bool DYN>
 __global__ void __launch_bounds__(TX * TY)
 k_stage(StageArgs<T> a, FlowConsts<T> k)
 {
     const int x = blockIdx.x * TX + threadIdx.x;
     const int y = blockIdx.y * TY + threadIdx.y;
     if (x >= k.nx || y >= k.ny) return;
+    // dt-dependent constants: kernel parameters for a fixed dt, the step's control block for a dynamic one
+    T dt2 = k.dt2, dtf = k.dt, dt6 = k.dt6, inv_tau = k.inv_tau;
+    if constexpr (DYN) {
+        dt2 = (T)k.dyn->dt2;
+        dtf = (T)k.dyn->dt;
+        dt6 = (T)k.dyn->dt6;
+        inv_tau = (T)k.dyn->inv_tau;
+    }
     const int nx = k.nx, ny = k.ny, nz = k.nz;
     const int plane = nx * ny;
     const int zc = k.zc[kZcStage];
@@ -132,7 +159,7 @@ k_stage(StageArgs<T> a, FlowConsts<T> k)
                 conv += k.q4h[j] * ((qp[j][j] * qp[j][i] - qm[j][j] * qm[j][i]) + q0[j] * (qp[j][i] - qm[j][i]));
                 diff += k.ih2[j] * (qp[j][i] - T(2) * q0[i] + qm[j][i]);
             }
-            kq[i] = beta * (-conv + k.nu * diff + S * (k.uset[i] - q0[i]) * k.inv_tau + k.bf[i]);
+            kq[i] = beta * (-conv + k.nu * diff + S * (k.uset[i] - q0[i]) * inv_tau + k.bf[i]);
         }
         {
             const T c0 = q0[3];
@@ -145,7 +172,7 @@ k_stage(StageArgs<T> a, FlowConsts<T> k)
                 conv += k.ih[j] * (Fp - Fm);
                 diff += k.ih2[j] * (bp[j] * (qp[j][3] - c0) - bm[j] * (c0 - qm[j][3]));
             }
-            kq[3] = beta * (-conv + k.alpha * diff + S * (k.cset - c0) * k.inv_tau);
+            kq[3] = beta * (-conv + k.alpha * diff + S * (k.cset - c0) * inv_tau);
         }
 
         // RK4 combine, classic tableau (nodes 0, 1/2, 1/2, 1; weights 1/6, 1/3, 1/3, 1/6) with the stage states as
@@ -154,10 +181,10 @@ k_stage(StageArgs<T> a, FlowConsts<T> k)
         T o[4];
 #pragma unroll
         for (int f = 0; f < 4; ++f) {
-            if (STAGE == 1) o[f] = q0[f] + k.dt2 * kq[f];
-            else if (STAGE == 2) o[f] = qn[f] + k.dt2 * kq[f];
-            else if (STAGE == 3) o[f] = qn[f] + k.dt * kq[f];
-            else o[f] = (q2[f] + T(2) * q3[f] + q0[f] - qn[f]) * k.third + k.dt6 * kq[f];
+            if (STAGE == 1) o[f] = q0[f] + dt2 * kq[f];
+            else if (STAGE == 2) o[f] = qn[f] + dt2 * kq[f];
+            else if (STAGE == 3) o[f] = qn[f] + dtf * kq[f];
+            else o[f] = (q2[f] + T(2) * q3[f] + q0[f] - qn[f]) * k.third + dt6 * kq[f];
         }
         st4(a.out, ic, o);
 #pragma unroll
@@ -171,12 +198,17 @@ k_stage(StageArgs<T> a, FlowConsts<T> k)
 // ------------------------------------------------------------------------------------------------------------
 // Divergence r = sum_j delta_j u_j / dt (a4; divided by dt because the solver works on p / rho)
 // ------------------------------------------------------------------------------------------------------------
-template <typename T>
+template <typename T, bool DYN>
 __global__ void __launch_bounds__(TX * TY) k_div(const void* __restrict__ q, T* __restrict__ r, FlowConsts<T> k)
 {
     const int x = blockIdx.x * TX + threadIdx.x;
     const int y = blockIdx.y * TY + threadIdx.y;
     if (x >= k.nx || y >= k.ny) return;
+    T i2h[3] = {k.i2h_div[0], k.i2h_div[1], k.i2h_div[2]};
+    if constexpr (DYN) {
+#pragma unroll
+        for (int j = 0; j < 3; ++j) i2h[j] = (T)k.dyn->i2h_div[j];
+    }
     const int nx = k.nx, ny = k.ny, nz = k.nz;
     const int plane = nx * ny;
     const int z0 = blockIdx.z * k.zc[kZcDiv], z1 = min(z0 + k.zc[kZcDiv], nz);
@@ -188,9 +220,9 @@ __global__ void __launch_bounds__(TX * TY) k_div(const void* __restrict__ q, T* 
     for (int z = z0; z < z1; ++z) {
         const int zb = z * plane;
         const T wzp = ld1<T>(q, wrap(z + 1, nz) * plane + rowc + x, 2);
-        const T d = k.i2h_div[0] * (ld1<T>(q, zb + rowc + xp, 0) - ld1<T>(q, zb + rowc + xm, 0)) +
-                    k.i2h_div[1] * (ld1<T>(q, zb + rowp + x, 1) - ld1<T>(q, zb + rowm + x, 1)) +
-                    k.i2h_div[2] * (wzp - wzm);
+        const T d = i2h[0] * (ld1<T>(q, zb + rowc + xp, 0) - ld1<T>(q, zb + rowc + xm, 0)) +
+                    i2h[1] * (ld1<T>(q, zb + rowp + x, 1) - ld1<T>(q, zb + rowm + x, 1)) +
+                    i2h[2] * (wzp - wzm);
         r[zb + rowc + x] = d;
         wzm = wz0;
         wz0 = wzp;
@@ -200,39 +232,49 @@ __global__ void __launch_bounds__(TX * TY) k_div(const void* __restrict__ q, T* 
 // ------------------------------------------------------------------------------------------------------------
 // Projection u = beta (u* - dt G p) with p = p / rho (a9); c* passes through.  Ticks the device step counter.
 // ------------------------------------------------------------------------------------------------------------
-template <typename T>
+template <typename T, bool DYN>
 __global__ void __launch_bounds__(TX * TY) k_project(const void* __restrict__ qs, const T* __restrict__ p,
                                                      void* __restrict__ out, const uint8_t* __restrict__ mask,
-                                                     long long* step_counter, FlowConsts<T> k)
+                                                     long long* step_counter, FlowConsts<T> k,
+                                                     unsigned long long* sigma_out)
 {
     if (step_counter && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0 &&
         threadIdx.y == 0)
         *step_counter += 1;
+    T i2h[3] = {k.i2h_dt[0], k.i2h_dt[1], k.i2h_dt[2]};
+    if constexpr (DYN) {
+#pragma unroll
+        for (int j = 0; j < 3; ++j) i2h[j] = (T)k.dyn->i2h_dt[j];
+    }
     const int x = blockIdx.x * TX + threadIdx.x;
     const int y = blockIdx.y * TY + threadIdx.y;
-    if (x >= k.nx || y >= k.ny) return;
-    const int nx = k.nx, ny = k.ny, nz = k.nz;
-    const int plane = nx * ny;
-    const int z0 = blockIdx.z * k.zc[kZcProject], z1 = min(z0 + k.zc[kZcProject], nz);
-    const int rowc = y * nx, rowm = wrap(y - 1, ny) * nx, rowp = wrap(y + 1, ny) * nx;
-    const int xm = wrap(x - 1, nx), xp = wrap(x + 1, nx);
-    T pzm = __ldg(p + wrap(z0 - 1, nz) * plane + rowc + x);
-    T pz0 = __ldg(p + z0 * plane + rowc + x);
+    T smax = T(0);   // Courant rate of the written velocity (DYN with the filter off: the step's final state)
+    if (x < k.nx && y < k.ny) {
+        const int nx = k.nx, ny = k.ny, nz = k.nz;
+        const int plane = nx * ny;
+        const int z0 = blockIdx.z * k.zc[kZcProject], z1 = min(z0 + k.zc[kZcProject], nz);
+        const int rowc = y * nx, rowm = wrap(y - 1, ny) * nx, rowp = wrap(y + 1, ny) * nx;
+        const int xm = wrap(x - 1, nx), xp = wrap(x + 1, nx);
+        T pzm = __ldg(p + wrap(z0 - 1, nz) * plane + rowc + x);
+        T pz0 = __ldg(p + z0 * plane + rowc + x);
 #pragma unroll 4
-    for (int z = z0; z < z1; ++z) {
-        const int zb = z * plane;
-        const int ic = zb + rowc + x;
-        const T pzp = __ldg(p + wrap(z + 1, nz) * plane + rowc + x);
-        T q[4];
-        ld4(qs, ic, q);
-        const T beta = beta_of<T>(__ldg(mask + ic));
-        q[0] = beta * (q[0] - k.i2h_dt[0] * (__ldg(p + zb + rowc + xp) - __ldg(p + zb + rowc + xm)));
-        q[1] = beta * (q[1] - k.i2h_dt[1] * (__ldg(p + zb + rowp + x) - __ldg(p + zb + rowm + x)));
-        q[2] = beta * (q[2] - k.i2h_dt[2] * (pzp - pzm));
-        st4(out, ic, q);
-        pzm = pz0;
-        pz0 = pzp;
+        for (int z = z0; z < z1; ++z) {
+            const int zb = z * plane;
+            const int ic = zb + rowc + x;
+            const T pzp = __ldg(p + wrap(z + 1, nz) * plane + rowc + x);
+            T q[4];
+            ld4(qs, ic, q);
+            const T beta = beta_of<T>(__ldg(mask + ic));
+            q[0] = beta * (q[0] - i2h[0] * (__ldg(p + zb + rowc + xp) - __ldg(p + zb + rowc + xm)));
+            q[1] = beta * (q[1] - i2h[1] * (__ldg(p + zb + rowp + x) - __ldg(p + zb + rowm + x)));
+            q[2] = beta * (q[2] - i2h[2] * (pzp - pzm));
+            st4(out, ic, q);
+            if (DYN) smax = fmax(smax, sigma_cell(q[0], q[1], q[2], k.ih));
+            pzm = pz0;
+            pz0 = pzp;
+        }
     }
+    if (DYN && sigma_out) sigma_flush((double)smax, sigma_out);
 }
 
 // ------------------------------------------------------------------------------------------------------------
@@ -413,7 +455,8 @@ __device__ void red_finish(CellStats<T>& cs, RedShared& sh, const ReduceArgsDev&
         if (tid == 0) {
             const long long step = *r.step_counter;
             dst->step = step;
-            dst->t = r.t0 + (double)step * r.dt;
+            dst->t = r.dyn ? r.dyn->t_end : r.t0 + (double)step * r.dt;
+            dst->dt = r.dyn ? r.dyn->dt : r.dt;
             dst->ke = 0.5 * r.dV * sh.red[0][0];
             dst->div_l2 = sqrt(r.dV * sh.red[1][0]);
             dst->c_total = r.dV * sh.red[2][0];
@@ -475,11 +518,12 @@ __global__ void __launch_bounds__(TX * TY) k_reduce(const void* __restrict__ q, 
 // REDUCE: also the reductions (a11) of the filtered state, with the divergence of the projected velocity (the
 // filter's input: after the projection, before the filter), saving a separate pass over the fields.
 // ------------------------------------------------------------------------------------------------------------
-template <typename T, bool REDUCE>
+template <typename T, bool REDUCE, bool SIGMA>
 __global__ void __launch_bounds__(TX * TY, sizeof(T) == 4 ? (REDUCE ? 3 : 4) : 2)
 k_filter(const void* __restrict__ in, void* __restrict__ out, const uint8_t* __restrict__ mask, FlowConsts<T> k,
-         ReduceArgsDev r, int to_history)
+         ReduceArgsDev r, int to_history, unsigned long long* sigma_out)
 {
+    T smax = T(0);   // SIGMA: Courant rate of the filtered velocity (the step's final state)
     __shared__ RedShared sh;
     if (REDUCE) {
         red_init(sh);
@@ -534,9 +578,51 @@ k_filter(const void* __restrict__ in, void* __restrict__ out, const uint8_t* __r
             for (int f = 0; f < 4; ++f) o[f] = beta * (zw[3][f] + k.filt * acc[f]);
             st4(out, ic, o);
             if (REDUCE) cs.add(o, div, m0, sh.hist);
+            if (SIGMA) smax = fmax(smax, sigma_cell(o[0], o[1], o[2], k.ih));
         }
     }
+    if (SIGMA) sigma_flush((double)smax, sigma_out);
     if (REDUCE) red_finish(cs, sh, r, to_history);
+}
+
+// ------------------------------------------------------------------------------------------------------------
+// Dynamic time step (Sec. 2.4): the Courant rate of a state, and the adjust kernel at the start of a step
+// ------------------------------------------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_courant_rate(const void* __restrict__ q, FlowConsts<T> k, size_t n,
+                                                      unsigned long long* sigma)
+{
+    T smax = T(0);
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        T v[4];
+        ld4(q, (int)i, v);
+        smax = fmax(smax, sigma_cell(v[0], v[1], v[2], k.ih));
+    }
+    sigma_flush((double)smax, sigma);
+}
+
+// dt = min(dt_max, courant_max / sigma) (dt_max at rest), then the dt-dependent constants with the formulas the
+// host uses for a fixed dt, the time at the end of the step, and a cleared sigma for the step's last kernel
+__global__ void k_adjust_dt(DtCtl* c)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const double sigma = __longlong_as_double((long long)c->sigma_bits);
+    double dt = c->dt_max;
+    if (sigma > 0.0) {
+        const double lim = c->courant_max / sigma;
+        if (lim < dt) dt = lim;
+    }
+    c->dt = dt;
+    c->t_end = c->t_end + dt;
+    c->dt2 = dt / 2.0;
+    c->dt3 = dt / 3.0;
+    c->dt6 = dt / 6.0;
+    c->inv_tau = 1.0 / (c->tau_f > 0.0 ? c->tau_f : dt);
+    for (int j = 0; j < 3; ++j) {
+        c->i2h_div[j] = 1.0 / (2.0 * c->h[j] * dt);
+        c->i2h_dt[j] = dt / (2.0 * c->h[j]);
+    }
+    c->sigma_bits = 0ull;
 }
 
 // ------------------------------------------------------------------------------------------------------------
@@ -674,11 +760,12 @@ template <typename T>
 cudaError_t Kernels<T>::stage(int s, const StageArgs<T>& a, const FlowConsts<T>& k, cudaStream_t st)
 {
     const dim3 g = flow_grid(k, kZcStage), b(TX, TY);
+    const bool dyn = k.dyn != nullptr;
     switch (s) {
-        case 1: k_stage<T, 1><<<g, b, 0, st>>>(a, k); break;
-        case 2: k_stage<T, 2><<<g, b, 0, st>>>(a, k); break;
-        case 3: k_stage<T, 3><<<g, b, 0, st>>>(a, k); break;
-        case 4: k_stage<T, 4><<<g, b, 0, st>>>(a, k); break;
+        case 1: dyn ? k_stage<T, 1, true><<<g, b, 0, st>>>(a, k) : k_stage<T, 1, false><<<g, b, 0, st>>>(a, k); break;
+        case 2: dyn ? k_stage<T, 2, true><<<g, b, 0, st>>>(a, k) : k_stage<T, 2, false><<<g, b, 0, st>>>(a, k); break;
+        case 3: dyn ? k_stage<T, 3, true><<<g, b, 0, st>>>(a, k) : k_stage<T, 3, false><<<g, b, 0, st>>>(a, k); break;
+        case 4: dyn ? k_stage<T, 4, true><<<g, b, 0, st>>>(a, k) : k_stage<T, 4, false><<<g, b, 0, st>>>(a, k); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -687,25 +774,45 @@ cudaError_t Kernels<T>::stage(int s, const StageArgs<T>& a, const FlowConsts<T>&
 template <typename T>
 cudaError_t Kernels<T>::divergence(const void* qstar, T* r, const FlowConsts<T>& k, cudaStream_t st)
 {
-    k_div<T><<<flow_grid(k, kZcDiv), dim3(TX, TY), 0, st>>>(qstar, r, k);
+    if (k.dyn) k_div<T, true><<<flow_grid(k, kZcDiv), dim3(TX, TY), 0, st>>>(qstar, r, k);
+    else k_div<T, false><<<flow_grid(k, kZcDiv), dim3(TX, TY), 0, st>>>(qstar, r, k);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t Kernels<T>::project(const void* qstar, const T* p, void* out, const uint8_t* mask,
-                                long long* step_counter, const FlowConsts<T>& k, cudaStream_t st)
+                                long long* step_counter, const FlowConsts<T>& k, cudaStream_t st,
+                                unsigned long long* sigma)
 {
-    k_project<T><<<flow_grid(k, kZcProject), dim3(TX, TY), 0, st>>>(qstar, p, out, mask, step_counter, k);
+    const dim3 g = flow_grid(k, kZcProject), b(TX, TY);
+    if (k.dyn) k_project<T, true><<<g, b, 0, st>>>(qstar, p, out, mask, step_counter, k, sigma);
+    else k_project<T, false><<<g, b, 0, st>>>(qstar, p, out, mask, step_counter, k, nullptr);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t Kernels<T>::filter(const void* in, void* out, const uint8_t* mask, const FlowConsts<T>& k,
-                               const ReduceArgsDev* r, int to_history, cudaStream_t st)
+                               const ReduceArgsDev* r, int to_history, cudaStream_t st, unsigned long long* sigma)
 {
     const dim3 g = flow_grid(k, kZcFilter), b(TX, TY);
-    if (r) k_filter<T, true><<<g, b, 0, st>>>(in, out, mask, k, *r, to_history);
-    else k_filter<T, false><<<g, b, 0, st>>>(in, out, mask, k, ReduceArgsDev{}, 0);
+    if (r && sigma) k_filter<T, true, true><<<g, b, 0, st>>>(in, out, mask, k, *r, to_history, sigma);
+    else if (r) k_filter<T, true, false><<<g, b, 0, st>>>(in, out, mask, k, *r, to_history, nullptr);
+    else if (sigma) k_filter<T, false, true><<<g, b, 0, st>>>(in, out, mask, k, ReduceArgsDev{}, 0, sigma);
+    else k_filter<T, false, false><<<g, b, 0, st>>>(in, out, mask, k, ReduceArgsDev{}, 0, nullptr);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Kernels<T>::courant_rate(const void* q, const FlowConsts<T>& k, size_t n, unsigned long long* sigma,
+                                     cudaStream_t st)
+{
+    k_courant_rate<T><<<elementwise_blocks(n), 256, 0, st>>>(q, k, n, sigma);
+    return cudaGetLastError();
+}
+
+cudaError_t adjust_dt(DtCtl* c, cudaStream_t st)
+{
+    k_adjust_dt<<<1, 32, 0, st>>>(c);
     return cudaGetLastError();
 }
 

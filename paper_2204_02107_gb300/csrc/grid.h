@@ -54,6 +54,9 @@ struct vf_grid {
     vf_reduce* history = nullptr;
     long long* dev_counters = nullptr;   // [0] history count, [1] step counter
     int* nonfinite = nullptr;
+    vf::DtCtl* dtctl = nullptr;          // time-step control (read by the kernels only with a dynamic dt)
+    bool dynamic = false;                // courant_max > 0
+    bool sigma_stale = true;             // the Courant rate of the current state must be recomputed
     unsigned long long* solid_count = nullptr;
     int nred = 0;
 
@@ -78,6 +81,10 @@ struct vf_grid {
 
 
 namespace vf_engine {
+
+// Dynamic time step: recompute the Courant rate of the current state on stream st if a field changed since the
+// last step (no-op otherwise).
+cudaError_t refresh_sigma(vf_grid* g, cudaStream_t st);
 
 // Enqueue one step of grid g on stream st (with the FP64 reductions if with_reduce); the launches a single-room
 // vf_step replays.  Returns the first CUDA error.

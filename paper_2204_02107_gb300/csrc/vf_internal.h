@@ -27,6 +27,23 @@ enum ZcKind { kZcStage = 0, kZcDiv = 1, kZcProject = 2, kZcFilter = 3, kZcKinds 
 constexpr int kZChunkMin = 4;
 constexpr int kZChunkMax = 64;
 
+// Device-resident control of a dynamic time step (Sec. 2.4: the user sets the maximum Courant number and AdjustDt
+// adapts dt).  The adjust kernel at the start of every step reads sigma_bits (max over cells of sum_j |u_j| / h_j
+// of the state the step starts from), chooses dt = min(dt_max, courant_max / sigma), writes the dt-dependent
+// constants below with the same formulas the host uses for a fixed dt, advances the time and clears sigma_bits
+// for the kernel that writes the step's final state.  All in double; kernels convert to their precision.
+struct DtCtl {
+    double dt;                    // time step of the current step
+    double t_end;                 // simulated time at the end of the current step
+    double dt2, dt3, dt6;         // dt / 2, dt / 3, dt / 6
+    double inv_tau;               // 1 / tau_f (tau_f <= 0: 1 / dt)
+    double i2h_div[3];            // 1 / (2 h_j dt)
+    double i2h_dt[3];             // dt / (2 h_j)
+    unsigned long long sigma_bits;   // double bits of the Courant rate (non-negative: bit order = value order)
+    double courant_max, dt_max, tau_f;
+    double h[3];
+};
+
 template <typename T>
 struct FlowConsts {
     int nx, ny, nz;
@@ -44,6 +61,7 @@ struct FlowConsts {
     T uset[3];    // forcing target velocity
     T cset;       // forcing target scalar
     T filt;       // pi^-6
+    const DtCtl* dyn;   // dynamic time step: dt-dependent constants come from here (nullptr: the fields above)
 };
 
 // Pointers of one RK4 stage.  Every state array holds one 4-vector (u, v, w, c) of T per cell (16 bytes for
@@ -214,6 +232,7 @@ struct ReduceArgsDev {
     double dV;
     double dt;
     double t0;                // simulated time at step 0
+    const DtCtl* dyn;         // dynamic time step: time and dt of the record from here (nullptr: t0 + step dt)
 };
 constexpr int kRedSlots = 8;   // ke, div2, c_total, c_room, c2_room, v_room, div_max, u_max
 
@@ -223,6 +242,9 @@ struct LaunchHook {
     void* ctx;
     void operator()(int phase) const { if (fn) fn(ctx, phase); }
 };
+
+// The adjust kernel of a dynamic time step (one thread; see DtCtl).
+cudaError_t adjust_dt(DtCtl* c, cudaStream_t st);
 
 // Register path of the Poisson solve: eligibility and launch (fft_reg.cu).
 template <typename T>
@@ -238,11 +260,16 @@ struct Kernels {
     static cudaError_t stage(int s, const StageArgs<T>& a, const FlowConsts<T>& k, cudaStream_t st);
     static cudaError_t divergence(const void* qstar, T* r, const FlowConsts<T>& k, cudaStream_t st);
     // u = beta (u* - dt G p), c* passes through; ticks the device step counter
+    // sigma != nullptr: also the Courant rate of the written velocity into *sigma (atomic max of double bits)
     static cudaError_t project(const void* qstar, const T* p, void* out, const uint8_t* mask, long long* step_counter,
-                               const FlowConsts<T>& k, cudaStream_t st);
+                               const FlowConsts<T>& k, cudaStream_t st, unsigned long long* sigma = nullptr);
     // r != nullptr: also record the reductions of the filtered state (divergence of the projected velocity)
     static cudaError_t filter(const void* in, void* out, const uint8_t* mask, const FlowConsts<T>& k,
-                              const ReduceArgsDev* r, int to_history, cudaStream_t st);
+                              const ReduceArgsDev* r, int to_history, cudaStream_t st,
+                              unsigned long long* sigma = nullptr);
+    // Courant rate of a state into *sigma (atomic max; the caller clears it)
+    static cudaError_t courant_rate(const void* q, const FlowConsts<T>& k, size_t n, unsigned long long* sigma,
+                                    cudaStream_t st);
     static cudaError_t reduce(const void* q, const uint8_t* mask, const FlowConsts<T>& k, const ReduceArgsDev& r,
                               int to_history, cudaStream_t st);
     static int reduce_blocks(const FlowConsts<T>& k);

@@ -20,7 +20,7 @@ VF_OK, VF_EINVAL, VF_ESIZE, VF_ENOMEM, VF_ECUDA, VF_ESTATE, VF_ENONFINITE, VF_ET
 VF_FP64, VF_FP32_MIXED = 0, 1
 VF_HOST, VF_DEVICE = 0, 1
 FIELDS = {"u": 0, "v": 1, "w": 2, "c": 3, "p": 4}
-N_PHASES = 15
+N_PHASES = 16
 PRECISIONS = {"fp64": VF_FP64, "fp32": VF_FP32_MIXED, "fp32_mixed": VF_FP32_MIXED}
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -38,7 +38,7 @@ class VfGridDesc(C.Structure):
                 ("body_force", C.c_double * 3),
                 ("n_pressure_iters", C.c_int32), ("filter", C.c_int32), ("precision", C.c_int32),
                 ("history_capacity", C.c_int32),
-                ("cuda_stream", C.c_void_p), ("alloc", C.POINTER(VfAllocator))]
+                ("cuda_stream", C.c_void_p), ("alloc", C.POINTER(VfAllocator)), ("courant_max", C.c_double)]
 
 
 class VfBatchDesc(C.Structure):
@@ -58,7 +58,7 @@ class VfReduce(C.Structure):
     _fields_ = [("t", C.c_double), ("step", C.c_int64), ("ke", C.c_double), ("div_max", C.c_double),
                 ("div_l2", C.c_double), ("u_max", C.c_double), ("c_total", C.c_double), ("c_room", C.c_double),
                 ("c2_room", C.c_double), ("v_room", C.c_double), ("hist", C.c_int64 * 64),
-                ("hist_under", C.c_int64), ("hist_over", C.c_int64)]
+                ("hist_under", C.c_int64), ("hist_over", C.c_int64), ("dt", C.c_double)]
 
     def to_dict(self):
         d = {name: getattr(self, name) for name, _ in self._fields_ if name != "hist"}
@@ -122,6 +122,7 @@ _SIGNATURES = {
                                    C.POINTER(C.c_int64)]),
     "vf_phase_name": (C.c_char_p, [C.c_int]),
     "vf_status_string": (C.c_char_p, [C.c_int]),
+    "vf_abi_sizes": (C.c_int, [C.POINTER(C.c_int64)]),
     "vf_last_error": (C.c_char_p, [C.c_void_p]),
     "vf_ach_log_slope": (C.c_int, [C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_int64,
                                    C.POINTER(C.c_double)]),
@@ -181,7 +182,8 @@ def default_desc():
 
 
 def make_desc(nx, ny, nz, lx, ly, lz, nu, dt, alpha_c=None, tau_f=0.0, body_force=(0.0, 0.0, 0.0),
-              n_pressure_iters=4, filter=True, precision="fp32", history_capacity=4096, stream=None):
+              n_pressure_iters=4, filter=True, precision="fp32", history_capacity=4096, stream=None,
+              courant_max=0.0):
     d = default_desc()
     d.nx, d.ny, d.nz = nx, ny, nz
     d.lx, d.ly, d.lz = lx, ly, lz
@@ -196,6 +198,7 @@ def make_desc(nx, ny, nz, lx, ly, lz, nu, dt, alpha_c=None, tau_f=0.0, body_forc
     d.precision = PRECISIONS[precision]
     d.history_capacity = history_capacity
     d.cuda_stream = C.c_void_p(stream) if stream else None
+    d.courant_max = courant_max
     return d
 
 
@@ -289,9 +292,10 @@ class Grid:
     2-3-5 smooth.  ``precision`` is 'fp64' or 'fp32' (FP32 fields, FP64 reductions)."""
 
     def __init__(self, nx, ny, nz, lx, ly, lz, nu, dt, alpha_c=None, tau_f=0.0, body_force=(0.0, 0.0, 0.0),
-                 n_pressure_iters=4, filter=True, precision="fp32", history_capacity=4096, stream=None):
+                 n_pressure_iters=4, filter=True, precision="fp32", history_capacity=4096, stream=None,
+                 courant_max=0.0):
         d = make_desc(nx, ny, nz, lx, ly, lz, nu, dt, alpha_c, tau_f, body_force, n_pressure_iters, filter,
-                      precision, history_capacity, stream)
+                      precision, history_capacity, stream, courant_max)
         h = C.c_void_p()
         rc = lib().vf_create_grid(C.byref(d), C.byref(h))
         if rc != VF_OK:

@@ -27,10 +27,10 @@ def params_of(prm_kw):
     return F.Params(**prm_kw)
 
 
-def gpu_grid(prm: F.Params, geom_beta, geom_S, geom_room, precision):
+def gpu_grid(prm: F.Params, geom_beta, geom_S, geom_room, precision, **kw):
     g = native.Grid(prm.nx, prm.ny, prm.nz, prm.lx, prm.ly, prm.lz, nu=prm.nu, dt=prm.dt, alpha_c=prm.alpha_c,
                     tau_f=prm.tau_f, body_force=prm.body_force, n_pressure_iters=prm.n_pressure_iters,
-                    filter=prm.filter, precision=precision)
+                    filter=prm.filter, precision=precision, **kw)
     g.set_mask(np.asarray(geom_beta, dtype=np.uint8))
     g.set_inflow(np.asarray(geom_S, dtype=np.uint8), prm.u_set, prm.c_set)
     g.set_region(np.asarray(geom_room, dtype=np.uint8))

@@ -44,8 +44,12 @@ def test_binding_covers_header(lib):
 
 
 def test_struct_sizes_match_header(lib):
-    # vf_reduce: 10 scalars + 64 + 2 counters, all 8 bytes
-    assert ctypes.sizeof(native.VfReduce) == 8 * (10 + 64 + 2)
+    # vf_reduce: 11 scalars + 64 + 2 counters, all 8 bytes
+    assert ctypes.sizeof(native.VfReduce) == 8 * (11 + 64 + 2)
+    sizes = (ctypes.c_int64 * 4)()
+    assert lib.vf_abi_sizes(sizes) == 0
+    assert list(sizes) == [ctypes.sizeof(native.VfGridDesc), ctypes.sizeof(native.VfReduce),
+                           ctypes.sizeof(native.VfBatchDesc), ctypes.sizeof(native.VfTiles)]
     d = native.default_desc()
     assert (d.nx, d.ny, d.nz) == (64, 64, 64) and d.n_pressure_iters == 4 and d.filter == 1
     assert d.precision == native.VF_FP32_MIXED and d.alpha_c < 0
