@@ -392,6 +392,39 @@ def run(state: State, geom: Geometry, prm: Params, n_steps: int, with_budget=Fal
 
 
 # ----------------------------------------------------------------------------------------------------------------
+# Smooth source mask (Eq. 5): a window of widths W_j centred at c_j with tanh edges of sharpness B_j
+# ----------------------------------------------------------------------------------------------------------------
+
+def tanh_window_factor(d, half_width, sharpness):
+    """One axis of Eq. 5: (1 - tanh(B [d / (W/2) - (W/2) / d])) / 2 for the distance d >= 0 to the centre; at d = 0
+    the bracket tends to minus infinity and the factor to its limit 1."""
+    d = np.asarray(d, dtype=np.float64)
+    out = np.ones_like(d)
+    nz = d > 0.0
+    arg = sharpness * (d[nz] / half_width - half_width / d[nz])
+    out[nz] = 0.5 * (1.0 - np.tanh(arg))
+    return out
+
+
+def tanh_source_mask(prm: Params, center, width, sharpness):
+    """S(x, y, z) of Eq. 5 on the cell centres x_i = i h_x (likewise y, z).  The paper does not say how the
+    distance |x - x_c| meets the periodic boundary; this takes the minimum-image distance, so the mask is
+    continuous across the wrap (the same as the plain distance for a window away from the box faces)."""
+    lengths = (prm.lx, prm.ly, prm.lz)
+    S = np.ones(prm.shape)
+    for j, ax in enumerate(AXES):
+        n = prm.shape[ax]
+        coord = np.arange(n) * prm.h[j]
+        d = np.abs(coord - center[j])
+        d = np.minimum(d, lengths[j] - d)
+        f = tanh_window_factor(d, 0.5 * width[j], sharpness[j])
+        shape = [1, 1, 1]
+        shape[ax] = n
+        S = S * f.reshape(shape)
+    return S
+
+
+# ----------------------------------------------------------------------------------------------------------------
 # Dynamic time step (Sec. 2.4: the user sets the maximum Courant number and AdjustDt adapts dt as the flow evolves)
 # ----------------------------------------------------------------------------------------------------------------
 
