@@ -133,6 +133,19 @@ int vf_set_mask(vf_grid* g, const uint8_t* beta, int mem);
  * keep the current region and only change the set point. */
 int vf_set_inflow(vf_grid* g, const uint8_t* S, const double u_set[3], double c_set, int mem);
 
+/* Smooth forcing region of Eq. 5 (the paper's general inlet model): on every cell centre x_j = i h_j
+ *   S = prod_j (1 - tanh(B_j [d_j / (W_j/2) - (W_j/2) / d_j])) / 2,
+ * d_j the periodic (minimum-image) distance from x_j to center[j], each factor 1 where d_j = 0 (its limit).
+ * center [m], width W [m] (> 0) and sharpness B (> 0) per axis (x, y, z).  Replaces the forcing region and sets
+ * the targets u_set, c_set; S is evaluated in double on the device and stored in the grid's precision. */
+int vf_set_inflow_tanh(vf_grid* g, const double center[3], const double width[3], const double sharpness[3],
+                       const double u_set[3], double c_set);
+
+/* Smooth forcing region from values: S is nx*ny*nz values in [0, 1] (double if is_fp64, else float) in `mem`
+ * (for example a sum of Eq. 5 windows).  Replaces the forcing region and sets u_set, c_set.  vf_set_inflow with a
+ * non-NULL S returns to a binary region. */
+int vf_set_inflow_values(vf_grid* g, const void* S, int is_fp64, const double u_set[3], double c_set, int mem);
+
 /* room: nx*ny*nz bytes, nonzero = counted in c_room, c2_room, v_room and the histogram. */
 int vf_set_region(vf_grid* g, const uint8_t* room, int mem);
 

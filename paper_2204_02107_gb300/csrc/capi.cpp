@@ -196,6 +196,7 @@ cudaError_t enqueue_step_t(vf_grid* g, cudaStream_t st, bool with_reduce, const 
     }
     StageArgs<T> a{};
     a.mask = g->mask;
+    a.sval = g->smooth_s ? (const T*)g->sval : nullptr;
     a.qn = g->q;
     // stage states: q2 in qa, q3 in qb, q4 in acc; stage 4 writes q* over q2 (each cell reads its own q2 first)
     a.qs = g->q; a.out = g->qa;
@@ -394,7 +395,7 @@ size_t grid_bytes(const vf_grid_desc& d)
     FlowConsts<float> k{};
     k.nx = d.nx; k.ny = d.ny; k.nz = d.nz;
     const size_t nred = (size_t)Kernels<float>::reduce_blocks(k);
-    size_t b = 4 * r256(4 * N * esz) + 4 * r256(N * esz) + r256(N * 4) + r256(N * 8) + r256(N);
+    size_t b = 4 * r256(4 * N * esz) + 5 * r256(N * esz) + r256(N * 4) + r256(N * 8) + r256(N);
     b += r256(nred * vf::kRedSlots * 8) + r256((vf::kHistBins + 2) * 8) + r256(4) + r256(sizeof(vf_reduce));
     b += r256((size_t)d.history_capacity * sizeof(vf_reduce)) + r256(16) + r256(4) + r256(8);
     b += r256(sizeof(vf::DtCtl));
@@ -487,7 +488,7 @@ int vf_create_grid(const vf_grid_desc* d, vf_grid** out)
     void** states[] = {&g->q, &g->acc, &g->qa, &g->qb};
     for (void** f : states)
         if (!(*f = galloc(g, 4 * fb))) return fail(VF_ENOMEM);
-    void** scalars[] = {&g->p, &g->f, &g->spec, &g->near_r};
+    void** scalars[] = {&g->p, &g->f, &g->spec, &g->near_r, &g->sval};
     for (void** f : scalars)
         if (!(*f = galloc(g, fb))) return fail(VF_ENOMEM);
     if (!(g->near_list = (int*)galloc(g, g->N * sizeof(int)))) return fail(VF_ENOMEM);
@@ -610,6 +611,59 @@ int vf_set_inflow(vf_grid* g, const uint8_t* S, const double u_set[3], double c_
     }
     for (int j = 0; j < 3; ++j) g->uset[j] = u_set[j];
     g->cset = c_set;
+    if (S) g->smooth_s = false;
+    drop_graphs(g);
+    return VF_OK;
+}
+
+int vf_set_inflow_tanh(vf_grid* g, const double center[3], const double width[3], const double sharpness[3],
+                       const double u_set[3], double c_set)
+{
+    int rc = check(g);
+    if (rc) return rc;
+    if (!center || !width || !sharpness || !u_set) return set_err(g, VF_EINVAL, "vf_set_inflow_tanh: null argument");
+    vf::TanhWindow w{};
+    const double L[3] = {g->d.lx, g->d.ly, g->d.lz};
+    const int n[3] = {g->d.nx, g->d.ny, g->d.nz};
+    for (int j = 0; j < 3; ++j) {
+        if (!(width[j] > 0.0) || !(sharpness[j] > 0.0) || !std::isfinite(center[j]) || !std::isfinite(width[j]) ||
+            !std::isfinite(sharpness[j]))
+            return set_err(g, VF_EINVAL, "vf_set_inflow_tanh: width and sharpness must be positive and finite");
+        w.c[j] = center[j];
+        w.hw[j] = 0.5 * width[j];
+        w.B[j] = sharpness[j];
+        w.h[j] = L[j] / n[j];
+        w.L[j] = L[j];
+    }
+    if (g->fp64) VF_CK(Kernels<double>::tanh_source((double*)g->sval, g->mask, w, n[0], n[1], n[2], g->stream));
+    else VF_CK(Kernels<float>::tanh_source((float*)g->sval, g->mask, w, n[0], n[1], n[2], g->stream));
+    VF_CK(cudaStreamSynchronize(g->stream));
+    for (int j = 0; j < 3; ++j) g->uset[j] = u_set[j];
+    g->cset = c_set;
+    g->smooth_s = true;
+    drop_graphs(g);
+    return VF_OK;
+}
+
+int vf_set_inflow_values(vf_grid* g, const void* S, int is_fp64, const double u_set[3], double c_set, int mem)
+{
+    int rc = check(g);
+    if (rc) return rc;
+    if (!S || !u_set || (mem != VF_HOST && mem != VF_DEVICE))
+        return set_err(g, VF_EINVAL, "vf_set_inflow_values: bad argument");
+    const void* src = stage_input(g, S, g->N * (is_fp64 ? 8 : 4), mem, &rc);
+    if (rc) return rc;
+    if (g->fp64) {
+        VF_CK(Kernels<double>::convert_in(src, is_fp64, g->sval, -1, g->N, 1.0, nullptr, g->stream));
+        VF_CK(Kernels<double>::source_bits(g->mask, (const double*)g->sval, g->N, g->stream));
+    } else {
+        VF_CK(Kernels<float>::convert_in(src, is_fp64, g->sval, -1, g->N, 1.0, nullptr, g->stream));
+        VF_CK(Kernels<float>::source_bits(g->mask, (const float*)g->sval, g->N, g->stream));
+    }
+    VF_CK(cudaStreamSynchronize(g->stream));
+    for (int j = 0; j < 3; ++j) g->uset[j] = u_set[j];
+    g->cset = c_set;
+    g->smooth_s = true;
     drop_graphs(g);
     return VF_OK;
 }

@@ -148,7 +148,7 @@ k_stage(StageArgs<T> a, FlowConsts<T> k)
         const T bm[3] = {beta_of<T>(mxm), beta_of<T>(mym), beta_of<T>(mzm)};
         const T bp[3] = {beta_of<T>(mxp), beta_of<T>(myp), beta_of<T>(mzp)};
         const T beta = beta_of<T>(m0);
-        const T S = (m0 & kBitS) ? T(1) : T(0);
+        const T S = (m0 & kBitS) ? (a.sval ? __ldg(a.sval + ic) : T(1)) : T(0);
 
         T kq[4];
 #pragma unroll
@@ -586,6 +586,39 @@ k_filter(const void* __restrict__ in, void* __restrict__ out, const uint8_t* __r
 }
 
 // ------------------------------------------------------------------------------------------------------------
+// Smooth source mask (Eq. 5): S = prod_j (1 - tanh(B_j [d_j / (W_j/2) - (W_j/2) / d_j])) / 2, d_j the
+// minimum-image distance from the cell centre i h_j to c_j; the factor is its limit 1 where d_j = 0.  Evaluated
+// in double, stored in the grid's precision; the mask's S bit marks S > 0.
+// ------------------------------------------------------------------------------------------------------------
+__device__ __forceinline__ double tanh_factor(int i, int j, const TanhWindow& w)
+{
+    double d = fabs((double)i * w.h[j] - w.c[j]);
+    d = fmin(d, w.L[j] - d);
+    if (!(d > 0.0)) return 1.0;
+    return 0.5 * (1.0 - tanh(w.B[j] * (d / w.hw[j] - w.hw[j] / d)));
+}
+
+template <typename T>
+__global__ void k_tanh_source(T* __restrict__ sval, uint8_t* __restrict__ mask, TanhWindow w, int nx, int ny, int nz)
+{
+    const size_t n = (size_t)nx * ny * nz;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(i % nx), y = (int)((i / nx) % ny), z = (int)(i / ((size_t)nx * ny));
+        const double S = ((1.0 * tanh_factor(x, 0, w)) * tanh_factor(y, 1, w)) * tanh_factor(z, 2, w);
+        const T v = (T)S;
+        sval[i] = v;
+        mask[i] = (uint8_t)((mask[i] & ~kBitS) | (v > T(0) ? kBitS : 0));
+    }
+}
+
+template <typename T>
+__global__ void k_source_bits(uint8_t* __restrict__ mask, const T* __restrict__ sval, size_t n)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        mask[i] = (uint8_t)((mask[i] & ~kBitS) | (sval[i] > T(0) ? kBitS : 0));
+}
+
+// ------------------------------------------------------------------------------------------------------------
 // Dynamic time step (Sec. 2.4): the Courant rate of a state, and the adjust kernel at the start of a step
 // ------------------------------------------------------------------------------------------------------------
 template <typename T>
@@ -799,6 +832,21 @@ cudaError_t Kernels<T>::filter(const void* in, void* out, const uint8_t* mask, c
     else if (r) k_filter<T, true, false><<<g, b, 0, st>>>(in, out, mask, k, *r, to_history, nullptr);
     else if (sigma) k_filter<T, false, true><<<g, b, 0, st>>>(in, out, mask, k, ReduceArgsDev{}, 0, sigma);
     else k_filter<T, false, false><<<g, b, 0, st>>>(in, out, mask, k, ReduceArgsDev{}, 0, nullptr);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Kernels<T>::tanh_source(T* sval, uint8_t* mask, const TanhWindow& w, int nx, int ny, int nz,
+                                    cudaStream_t st)
+{
+    k_tanh_source<T><<<elementwise_blocks((size_t)nx * ny * nz), 256, 0, st>>>(sval, mask, w, nx, ny, nz);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Kernels<T>::source_bits(uint8_t* mask, const T* sval, size_t n, cudaStream_t st)
+{
+    k_source_bits<T><<<elementwise_blocks(n), 256, 0, st>>>(mask, sval, n);
     return cudaGetLastError();
 }
 

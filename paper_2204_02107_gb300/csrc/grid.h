@@ -37,6 +37,8 @@ struct vf_grid {
     int reg = 0, reg_gx = 0, reg_gy = 0, reg_gz = 0, reg_sp = 0, reg_spx = 0, reg_sb = 0;
     void* staging = nullptr;     // N * 8 bytes
     uint8_t* mask = nullptr;
+    void* sval = nullptr;        // smooth forcing region values (Eq. 5 or caller's), N values of the precision
+    bool smooth_s = false;       // the stage kernels take S from sval (else S = 1 on the S bit)
     void* twx = nullptr;
     void* twy = nullptr;
     void* twz = nullptr;

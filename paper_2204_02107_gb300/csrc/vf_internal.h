@@ -74,6 +74,13 @@ struct StageArgs {
     const void* q3;
     void* out;
     const uint8_t* mask;
+    const T* sval;      // smooth forcing region S in [0, 1] at the cells whose S bit is set (nullptr: S = 1 there)
+};
+
+// One smooth source window of Eq. 5 on a grid: centre c_j, half widths W_j / 2, sharpness B_j, cell size h_j and
+// box length L_j per axis (x, y, z).
+struct TanhWindow {
+    double c[3], hw[3], B[3], h[3], L[3];
 };
 
 // Division by a run-time invariant d by multiply and shift (Granlund-Montgomery), exact for n < 2^31.
@@ -267,6 +274,11 @@ struct Kernels {
     static cudaError_t filter(const void* in, void* out, const uint8_t* mask, const FlowConsts<T>& k,
                               const ReduceArgsDev* r, int to_history, cudaStream_t st,
                               unsigned long long* sigma = nullptr);
+    // Eq. 5 window into the smooth forcing values and the mask's S bits (S > 0)
+    static cudaError_t tanh_source(T* sval, uint8_t* mask, const TanhWindow& w, int nx, int ny, int nz,
+                                   cudaStream_t st);
+    // the mask's S bits from smooth forcing values (S > 0)
+    static cudaError_t source_bits(uint8_t* mask, const T* sval, size_t n, cudaStream_t st);
     // Courant rate of a state into *sigma (atomic max; the caller clears it)
     static cudaError_t courant_rate(const void* q, const FlowConsts<T>& k, size_t n, unsigned long long* sigma,
                                     cudaStream_t st);

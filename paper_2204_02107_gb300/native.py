@@ -85,6 +85,10 @@ _SIGNATURES = {
     "vf_set_mask": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     "vf_set_inflow": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_double), C.c_double, C.c_int]),
     "vf_set_region": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
+    "vf_set_inflow_tanh": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                     C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_double]),
+    "vf_set_inflow_values": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.POINTER(C.c_double), C.c_double,
+                                       C.c_int]),
     "vf_set_field": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int]),
     "vf_set_time": (C.c_int, [C.c_void_p, C.c_double, C.c_int64]),
     "vf_step": (C.c_int, [C.c_void_p, C.c_int64, C.c_int32]),
@@ -355,6 +359,25 @@ class Grid:
             return
         ptr, mem, _keep = _pointer(S, np.uint8, self.n)
         self._check(lib().vf_set_inflow(self._h, ptr, us, float(c_set), mem), "vf_set_inflow")
+
+    def set_inflow_tanh(self, center, width, sharpness, u_set, c_set):
+        """Smooth forcing window of Eq. 5 (centre, width [m] and sharpness B per axis x, y, z)."""
+        d3 = lambda v: (C.c_double * 3)(*[float(a) for a in v])
+        self._check(lib().vf_set_inflow_tanh(self._h, d3(center), d3(width), d3(sharpness), d3(u_set),
+                                             float(c_set)), "vf_set_inflow_tanh")
+
+    def set_inflow_values(self, S, u_set, c_set):
+        """Smooth forcing region from values in [0, 1] (float64 numpy array or CUDA tensor of the grid's size)."""
+        is64 = True
+        if _is_tensor(S) and S.is_cuda:
+            import torch
+            is64 = S.dtype == torch.float64
+            ptr, mem, _keep = _pointer(S, None, self.n)
+        else:
+            ptr, mem, _keep = _pointer(S, np.float64, self.n)
+        us = (C.c_double * 3)(*u_set)
+        self._check(lib().vf_set_inflow_values(self._h, ptr, 1 if is64 else 0, us, float(c_set), mem),
+                    "vf_set_inflow_values")
 
     def set_region(self, room):
         ptr, mem, _keep = _pointer(room, np.uint8, self.n)
