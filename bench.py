@@ -52,6 +52,7 @@ PHASE_BYTES_PER_CELL = {
     "filter": 8 * F32 + 1,       # read u, v, w, c, mask; write 4 fields
     "reduce": 4 * F32 + 1,       # read u, v, w, c, mask
     "adjust_dt": None,           # one thread: the dynamic time step's control block
+    "particles": None,           # per particle, not per cell
 }
 # kernel function of each phase (phases of one function are one roofline row)
 PHASE_KERNEL = {"stage1": "k_stage", "stage2": "k_stage", "stage3": "k_stage", "stage4": "k_stage",

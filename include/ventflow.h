@@ -298,6 +298,27 @@ int vf_poisson_solve_noalloc(int32_t nx, int32_t ny, int32_t nz, double lx, doub
 /* Largest nx*ny*nz that vf_poisson_solve_noalloc accepts in the given precision (0 for a bad precision). */
 int64_t vf_poisson_noalloc_max_cells(int32_t precision);
 
+/* ---- Lagrangian particles (Sec. 2.3) --------------------------------------------------------------------- */
+
+/* Replace the grid's particles by n particles (n = 0 removes them), one-way coupled: after every step each
+ * airborne particle moves with du_p/dt = (C_d / tau_p)(u_f - u_p) + g, tau_p = rho_p d^2 / (18 rho_f nu),
+ * C_d = 1 + Re_p^(2/3) / 6, Re_p = |u_f - u_p| d / nu, by implicit Euler with C_d from the relative velocity at the
+ * start of the step (u_p' = (u_p + a u_f + dt g) / (1 + a), a = dt C_d / tau_p; x_p' = x_p + dt u_p'), u_f the
+ * new fluid velocity interpolated trilinearly between cell centres.  Positions wrap periodically; a particle
+ * whose nearest cell becomes solid is deposited (stays put with zero velocity).
+ * pos, vel: n x 3 doubles (x, y, z of each particle) [m], [m/s]; size: n doubles d [m] (the paper's sedimentation
+ * times hold for d the diameter); rho_p, rho_f [kg/m^3]; gravity[3] [m/s^2].  Host arrays, copied.  The
+ * particle arrays (n x 64 bytes) are device memory of the grid beyond vf_grid_bytes. */
+int vf_particles_set(vf_grid* g, int64_t n, const double* pos, const double* vel, const double* size, double rho_p,
+                     double rho_f, const double gravity[3]);
+
+/* Copy the particles to host arrays after the enqueued steps (waits): pos, vel n x 3 doubles, deposited n ints
+ * (1 = deposited); any of them may be NULL. */
+int vf_particles_read(vf_grid* g, double* pos, double* vel, int32_t* deposited);
+
+/* Number of particles of the grid. */
+int vf_particles_count(const vf_grid* g, int64_t* n);
+
 /* ---- measurement ----------------------------------------------------------------------------------------- */
 
 /* Kernel phases of one step, in launch order. */
@@ -317,7 +338,8 @@ int64_t vf_poisson_noalloc_max_cells(int32_t precision);
 #define VF_PHASE_POISSON_RHS 13 /* Eq. 9 correction D((1 - beta) G p) at the cells next to solids */
 #define VF_PHASE_FFT_YZ_SOLVE 14 /* per-kx plane: y, z FFTs, division by lambda, inverse z, y FFTs */
 #define VF_PHASE_ADJUST_DT 15   /* dynamic time step: dt from the Courant rate of the current state */
-#define VF_N_PHASES 16
+#define VF_PHASE_PARTICLES 16   /* Lagrangian particles (Sec. 2.3) in the new velocity */
+#define VF_N_PHASES 17
 
 /* Run n steps like vf_step but with direct launches bracketed by CUDA events on the grid's stream; adds the
  * elapsed milliseconds of every phase to phase_ms[VF_N_PHASES] and its launch count to launches[VF_N_PHASES]

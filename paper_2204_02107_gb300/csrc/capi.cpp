@@ -82,11 +82,24 @@ void* galloc(vf_grid* g, size_t bytes)
     return p;
 }
 
+void free_particles(vf_grid* g)
+{
+    if (g->particle_buf) {
+        if (g->have_alloc) g->alloc.free(g->particle_buf, (void*)g->stream, g->alloc.ctx);
+        else cudaFreeAsync(g->particle_buf, g->stream);
+        g->bytes -= g->particle_bytes;
+    }
+    g->particle_buf = nullptr;
+    g->particle_bytes = 0;
+    g->particles.n = 0;
+}
+
 void release_all(vf_grid* g)
 {
     for (int i = 0; i < 2; ++i)
         if (g->gexec[i]) { cudaGraphExecDestroy(g->gexec[i]); g->gexec[i] = nullptr; }
     g->graph_ok = false;
+    free_particles(g);
     for (void* p : g->allocs) {
         if (g->have_alloc) g->alloc.free(p, (void*)g->stream, g->alloc.ctx);
         else cudaFreeAsync(p, g->stream);
@@ -237,6 +250,12 @@ cudaError_t enqueue_step_t(vf_grid* g, cudaStream_t st, bool with_reduce, const 
     } else if (with_reduce) {
         if ((e = Kernels<T>::reduce(g->q, g->mask, k, reduce_args(g), 1, st)) != cudaSuccess) return e;
         mark(VF_PHASE_REDUCE);
+    }
+    if (g->particles.n > 0) {
+        vf::ParticleArgs P = g->particles;
+        P.dyn = g->dynamic ? g->dtctl : nullptr;
+        if ((e = vf::advance_particles<T>(P, g->q, g->mask, st)) != cudaSuccess) return e;
+        mark(VF_PHASE_PARTICLES);
     }
     return cudaSuccess;
 }
@@ -835,6 +854,95 @@ int vf_info(const vf_grid* g, double* t, int64_t* step, int64_t* cells, int64_t*
     return VF_OK;
 }
 
+int vf_particles_set(vf_grid* g, int64_t n, const double* pos, const double* vel, const double* size, double rho_p,
+                     double rho_f, const double gravity[3])
+{
+    int rc = check(g);
+    if (rc) return rc;
+    if (n < 0 || (n > 0 && (!pos || !vel || !size || !gravity)) || !(rho_p > 0.0) || !(rho_f > 0.0))
+        return set_err(g, VF_EINVAL, "vf_particles_set: bad argument");
+    const double L[3] = {g->d.lx, g->d.ly, g->d.lz};
+    for (int64_t i = 0; i < n; ++i) {
+        if (!(size[i] > 0.0)) return set_err(g, VF_EINVAL, "vf_particles_set: sizes must be positive");
+        for (int k = 0; k < 3; ++k)
+            if (!(pos[3 * i + k] >= 0.0 && pos[3 * i + k] < L[k]) || !std::isfinite(vel[3 * i + k]))
+                return set_err(g, VF_EINVAL, "vf_particles_set: positions must lie in the box");
+    }
+    VF_CK(cudaStreamSynchronize(g->stream));
+    free_particles(g);
+    drop_graphs(g);
+    if (n == 0) return VF_OK;
+    // one buffer: x, y, z, u, v, w, d (n doubles each), then the states (n ints)
+    const size_t bytes = ((size_t)n * 7 * sizeof(double) + (size_t)n * sizeof(int) + 255) & ~(size_t)255;
+    void* buf = nullptr;
+    if (g->have_alloc) buf = g->alloc.alloc(bytes, (void*)g->stream, g->alloc.ctx);
+    else if (cudaMallocAsync(&buf, bytes, g->stream) != cudaSuccess) { cudaGetLastError(); buf = nullptr; }
+    if (!buf) return set_err(g, VF_ENOMEM, "vf_particles_set: allocation failed");
+    g->particle_buf = buf;
+    g->particle_bytes = bytes;
+    g->bytes += bytes;
+    std::vector<double> host((size_t)n * 7);
+    for (int64_t i = 0; i < n; ++i)
+        for (int k = 0; k < 3; ++k) {
+            host[(size_t)k * n + i] = pos[3 * i + k];
+            host[(size_t)(3 + k) * n + i] = vel[3 * i + k];
+        }
+    for (int64_t i = 0; i < n; ++i) host[(size_t)6 * n + i] = size[i];
+    double* dbuf = (double*)buf;
+    VF_CK(cudaMemcpyAsync(dbuf, host.data(), host.size() * sizeof(double), cudaMemcpyHostToDevice, g->stream));
+    int* state = (int*)(dbuf + (size_t)n * 7);
+    VF_CK(cudaMemsetAsync(state, 0, (size_t)n * sizeof(int), g->stream));
+    VF_CK(cudaStreamSynchronize(g->stream));   // host staging dies here
+    vf::ParticleArgs& P = g->particles;
+    P = vf::ParticleArgs{};
+    P.n = n;
+    for (int k = 0; k < 3; ++k) {
+        P.pos[k] = dbuf + (size_t)k * n;
+        P.vel[k] = dbuf + (size_t)(3 + k) * n;
+        P.h[k] = L[k] / (k == 0 ? g->d.nx : k == 1 ? g->d.ny : g->d.nz);
+        P.L[k] = L[k];
+        P.g[k] = gravity[k];
+    }
+    P.size = dbuf + (size_t)6 * n;
+    P.state = state;
+    P.nx = g->d.nx; P.ny = g->d.ny; P.nz = g->d.nz;
+    P.nu = g->d.nu;
+    P.rho_p = rho_p;
+    P.rho_f = rho_f;
+    P.dt = g->d.dt;
+    return VF_OK;
+}
+
+int vf_particles_read(vf_grid* g, double* pos, double* vel, int32_t* deposited)
+{
+    int rc = check(g);
+    if (rc) return rc;
+    const int64_t n = g->particles.n;
+    if (n == 0) return VF_OK;
+    std::vector<double> host((size_t)n * 6);
+    std::vector<int> st((size_t)n);
+    VF_CK(cudaMemcpyAsync(host.data(), g->particles.pos[0], host.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                          g->stream));
+    VF_CK(cudaMemcpyAsync(st.data(), g->particles.state, st.size() * sizeof(int), cudaMemcpyDeviceToHost,
+                          g->stream));
+    VF_CK(cudaStreamSynchronize(g->stream));
+    for (int64_t i = 0; i < n; ++i)
+        for (int k = 0; k < 3; ++k) {
+            if (pos) pos[3 * i + k] = host[(size_t)k * n + i];
+            if (vel) vel[3 * i + k] = host[(size_t)(3 + k) * n + i];
+        }
+    if (deposited)
+        for (int64_t i = 0; i < n; ++i) deposited[i] = st[(size_t)i];
+    return VF_OK;
+}
+
+int vf_particles_count(const vf_grid* g, int64_t* n)
+{
+    if (!g || !n) return VF_EINVAL;
+    *n = g->particles.n;
+    return VF_OK;
+}
+
 int vf_poisson_solve(vf_grid* g, const void* f, void* p)
 {
     int rc = check(g);
@@ -892,7 +1000,8 @@ const char* vf_phase_name(int phase)
 {
     static const char* names[VF_N_PHASES] = {"stage1", "stage2", "stage3", "stage4", "div", "fft_x_fwd",
                                              "fft_y_fwd", "fft_z_solve", "fft_y_inv", "fft_x_inv", "project",
-                                             "filter", "reduce", "poisson_rhs", "fft_yz_solve", "adjust_dt"};
+                                             "filter", "reduce", "poisson_rhs", "fft_yz_solve", "adjust_dt",
+                                             "particles"};
     if (phase < 0 || phase >= VF_N_PHASES) return "unknown";
     return names[phase];
 }

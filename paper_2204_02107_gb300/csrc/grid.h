@@ -57,6 +57,9 @@ struct vf_grid {
     long long* dev_counters = nullptr;   // [0] history count, [1] step counter
     int* nonfinite = nullptr;
     vf::DtCtl* dtctl = nullptr;          // time-step control (read by the kernels only with a dynamic dt)
+    vf::ParticleArgs particles{};        // Lagrangian particles (n = 0: none); arrays in one buffer
+    void* particle_buf = nullptr;
+    size_t particle_bytes = 0;
     bool dynamic = false;                // courant_max > 0
     bool sigma_stale = true;             // the Courant rate of the current state must be recomputed
     unsigned long long* solid_count = nullptr;

@@ -250,6 +250,24 @@ struct LaunchHook {
     void operator()(int phase) const { if (fn) fn(ctx, phase); }
 };
 
+// Lagrangian particles of a grid (Sec. 2.3; particles.cu): structure-of-arrays double state on the device.
+struct ParticleArgs {
+    long long n;
+    double* pos[3];             // x, y, z [m], in [0, L_j)
+    double* vel[3];             // u_p [m/s]
+    const double* size;         // d [m] in tau_p = rho_p d^2 / (18 rho_f nu)
+    int* state;                 // 0 airborne, 1 deposited
+    int nx, ny, nz;
+    double h[3], L[3];
+    double nu, rho_p, rho_f, g[3];
+    double dt;                  // fixed time step (dyn == nullptr)
+    const DtCtl* dyn;           // dynamic time step: dt of the current step from here
+};
+
+// Advance every airborne particle by one step in the velocity of the state q (4-vector array of precision T).
+template <typename T>
+cudaError_t advance_particles(const ParticleArgs& P, const void* q, const uint8_t* mask, cudaStream_t st);
+
 // The adjust kernel of a dynamic time step (one thread; see DtCtl).
 cudaError_t adjust_dt(DtCtl* c, cudaStream_t st);
 

@@ -20,7 +20,7 @@ VF_OK, VF_EINVAL, VF_ESIZE, VF_ENOMEM, VF_ECUDA, VF_ESTATE, VF_ENONFINITE, VF_ET
 VF_FP64, VF_FP32_MIXED = 0, 1
 VF_HOST, VF_DEVICE = 0, 1
 FIELDS = {"u": 0, "v": 1, "w": 2, "c": 3, "p": 4}
-N_PHASES = 16
+N_PHASES = 17
 PRECISIONS = {"fp64": VF_FP64, "fp32": VF_FP32_MIXED, "fp32_mixed": VF_FP32_MIXED}
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -127,6 +127,10 @@ _SIGNATURES = {
     "vf_phase_name": (C.c_char_p, [C.c_int]),
     "vf_status_string": (C.c_char_p, [C.c_int]),
     "vf_abi_sizes": (C.c_int, [C.POINTER(C.c_int64)]),
+    "vf_particles_set": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double,
+                                   C.c_double, C.POINTER(C.c_double)]),
+    "vf_particles_read": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "vf_particles_count": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
     "vf_last_error": (C.c_char_p, [C.c_void_p]),
     "vf_ach_log_slope": (C.c_int, [C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_int64,
                                    C.POINTER(C.c_double)]),
@@ -378,6 +382,31 @@ class Grid:
         us = (C.c_double * 3)(*u_set)
         self._check(lib().vf_set_inflow_values(self._h, ptr, 1 if is64 else 0, us, float(c_set), mem),
                     "vf_set_inflow_values")
+
+    def set_particles(self, pos, vel, size, rho_p=1000.0, rho_f=1.2, gravity=(0.0, 0.0, -9.81)):
+        """Lagrangian particles: pos, vel (n, 3) [m], [m/s]; size (n,) d [m]."""
+        pos = np.ascontiguousarray(pos, dtype=np.float64).reshape(-1, 3)
+        vel = np.ascontiguousarray(vel, dtype=np.float64).reshape(-1, 3)
+        size = np.ascontiguousarray(size, dtype=np.float64).reshape(-1)
+        n = pos.shape[0]
+        if vel.shape[0] != n or size.shape[0] != n:
+            raise ValueError("pos, vel and size must describe the same particles")
+        g3 = (C.c_double * 3)(*gravity)
+        self._check(lib().vf_particles_set(self._h, n, C.c_void_p(pos.ctypes.data), C.c_void_p(vel.ctypes.data),
+                                           C.c_void_p(size.ctypes.data), float(rho_p), float(rho_f), g3),
+                    "vf_particles_set")
+
+    def particles(self):
+        """(pos (n, 3), vel (n, 3), deposited (n,) bool) after the enqueued steps."""
+        n = C.c_int64()
+        self._check(lib().vf_particles_count(self._h, C.byref(n)), "vf_particles_count")
+        pos = np.zeros((n.value, 3))
+        vel = np.zeros((n.value, 3))
+        dep = np.zeros(n.value, dtype=np.int32)
+        if n.value:
+            self._check(lib().vf_particles_read(self._h, C.c_void_p(pos.ctypes.data), C.c_void_p(vel.ctypes.data),
+                                                C.c_void_p(dep.ctypes.data)), "vf_particles_read")
+        return pos, vel, dep.astype(bool)
 
     def set_region(self, room):
         ptr, mem, _keep = _pointer(room, np.uint8, self.n)
