@@ -278,6 +278,65 @@ def bench_batch(stream, steps):
             "steps": steps, "rooms": len(rs), "cells": total, "bytes_in_use": info["bytes_in_use"]}
 
 
+def bench_next_rows(stream, steps):
+    """The single room with the paper's other modes: a dynamic time step (maximum Courant number 0.2, started
+    from a developed jet), the inlet as a tanh window of Eq. 5, and one million Lagrangian particles."""
+    import torch
+    from paper_2204_02107_gb300 import native, rooms
+    room = rooms.single_room(256, 128, 128)
+    cells = room.cells
+    out = {}
+
+    def timed(g, n):
+        g.step(3, reduce_every=1)
+        g.sync()
+        sec = time_grid_steps(g, n, stream)
+        return sec
+
+    # dynamic time step: develop the jet first so the Courant limit binds
+    g = native.room_grid(room, precision="fp32", stream=stream.cuda_stream, courant_max=0.2,
+                         history_capacity=max(16, steps + 400))
+    g.step(300, reduce_every=0)
+    sec = timed(g, steps)
+    hist = g.history(steps)
+    ph = g.profile_steps(5, reduce_every=1)
+    g.close()
+    out["dynamic_dt"] = {"value": cells * steps / sec / 1e9, "unit": UNIT, "ms_per_step": sec * 1e3 / steps,
+                         "courant_max": 0.2, "dt_mean_s": float(np.mean([h["dt"] for h in hist])),
+                         "dt_fixed_s": room.dt, "adjust_us": ph["adjust_dt"][0] / ph["adjust_dt"][1] * 1e3}
+    # tanh inlet window over the duct
+    g = native.room_grid(room, precision="fp32", stream=stream.cuda_stream)
+    h = (room.lx / room.nx, room.ly / room.ny, room.lz / room.nz)
+    ys, zs = np.nonzero(room.S.any(axis=2).T)
+    center = (0.5 * h[0], 0.5 * (ys.min() + ys.max()) * h[1], 0.5 * (zs.min() + zs.max()) * h[2])
+    g.set_inflow_tanh(center, (3 * h[0], 5 * h[1], 5 * h[2]), (2.0, 3.0, 3.0), (room.u_in, 0.0, 0.0), 0.0)
+    sec = timed(g, steps)
+    g.close()
+    out["tanh_inlet"] = {"value": cells * steps / sec / 1e9, "unit": UNIT, "ms_per_step": sec * 1e3 / steps}
+    # particles: one million, sizes 1-100 um, uniformly in the fluid
+    n = 1 << 20
+    rng = np.random.default_rng(12)
+    fluid = np.argwhere(room.beta.astype(bool))
+    cellsel = fluid[rng.integers(0, len(fluid), n)]
+    pos = (cellsel[:, ::-1] + rng.uniform(-0.45, 0.45, (n, 3))) * np.array(h)
+    pos = np.mod(pos, np.array([room.lx, room.ly, room.lz]))
+    g = native.room_grid(room, precision="fp32", stream=stream.cuda_stream)
+    g.set_particles(pos, np.zeros((n, 3)), rng.uniform(1e-6, 100e-6, n))
+    sec = timed(g, steps)
+    ph = g.profile_steps(5, reduce_every=1)
+    g.close()
+    p_us = ph["particles"][0] / ph["particles"][1] * 1e3
+    # per particle: read x, y, z, u, v, w, d and the state (60 B), write x, y, z, u, v, w (48 B); the eight
+    # sampled 4-vectors come from the field, mostly through L2
+    p_bytes = 108.0
+    out["particles"] = {"value": cells * steps / sec / 1e9, "unit": UNIT, "ms_per_step": sec * 1e3 / steps,
+                        "particles": n, "particle_kernel_us": p_us,
+                        "particle_updates_per_s": n / (p_us * 1e-6),
+                        "particle_kernel_gb_s": n * p_bytes / (p_us * 1e-6) / 1e9,
+                        "bytes_per_particle": p_bytes}
+    return out
+
+
 def bench_serve(n_requests):
     """Poisson arrivals (4 per second) of ventilation requests served by continuous batching in FP32, against the
     same trace served one at a time in FP64; ACH agreement between the two."""
@@ -444,6 +503,7 @@ def main():
     if not args.no_extras and world == 1:
         extras["large_room"] = bench_large_room(stream, args.extra_steps)
         extras["batch"] = bench_batch(stream, args.extra_steps)
+        extras["next_rows"] = bench_next_rows(stream, max(args.extra_steps, 100))
         if args.serve_requests > 0:
             extras["serve"] = bench_serve(args.serve_requests)
 

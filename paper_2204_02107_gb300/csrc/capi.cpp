@@ -900,6 +900,7 @@ int vf_particles_set(vf_grid* g, int64_t n, const double* pos, const double* vel
         P.pos[k] = dbuf + (size_t)k * n;
         P.vel[k] = dbuf + (size_t)(3 + k) * n;
         P.h[k] = L[k] / (k == 0 ? g->d.nx : k == 1 ? g->d.ny : g->d.nz);
+        P.ih[k] = 1.0 / P.h[k];
         P.L[k] = L[k];
         P.g[k] = gravity[k];
     }

@@ -66,12 +66,22 @@ __device__ __forceinline__ double sigma_cell(double u, double v, double w, const
     return __dadd_rn(__dadd_rn(__dmul_rn(fabs(u), ih[0]), __dmul_rn(fabs(v), ih[1])), __dmul_rn(fabs(w), ih[2]));
 }
 
-// warp maximum of s, then one atomic max of its double bits per warp (every lane of the warp calls it)
+// CTA maximum of s, then one atomic max of its double bits per CTA (every thread of the CTA calls it; at most
+// 32 warps)
 __device__ __forceinline__ void sigma_flush(double s, unsigned long long* out)
 {
+    __shared__ double warp_max[32];
+    const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+    const int nw = (blockDim.x * blockDim.y + 31) >> 5;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s = fmax(s, __shfl_xor_sync(0xffffffffu, s, o));
-    if ((threadIdx.x & 31) == 0 && s > 0.0) atomicMax(out, (unsigned long long)__double_as_longlong(s));
+    if ((tid & 31) == 0) warp_max[tid >> 5] = s;
+    __syncthreads();
+    if (tid == 0) {
+        double m = warp_max[0];
+        for (int w = 1; w < nw; ++w) m = fmax(m, warp_max[w]);
+        if (m > 0.0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
+    }
 }
 
 // ------------------------------------------------------------------------------------------------------------
@@ -638,24 +648,28 @@ __global__ void __launch_bounds__(256) k_courant_rate(const void* __restrict__ q
 // host uses for a fixed dt, the time at the end of the step, and a cleared sigma for the step's last kernel
 __global__ void k_adjust_dt(DtCtl* c)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    const double sigma = __longlong_as_double((long long)c->sigma_bits);
-    double dt = c->dt_max;
-    if (sigma > 0.0) {
-        const double lim = c->courant_max / sigma;
-        if (lim < dt) dt = lim;
+    // lane 0 chooses dt; the lanes then form one dt-dependent constant each (the divisions run side by side)
+    const int lane = threadIdx.x;
+    double dt = 0.0;
+    if (lane == 0) {
+        const double sigma = __longlong_as_double((long long)c->sigma_bits);
+        dt = c->dt_max;
+        if (sigma > 0.0) {
+            const double lim = c->courant_max / sigma;
+            if (lim < dt) dt = lim;
+        }
     }
-    c->dt = dt;
-    c->t_end = c->t_end + dt;
-    c->dt2 = dt / 2.0;
-    c->dt3 = dt / 3.0;
-    c->dt6 = dt / 6.0;
-    c->inv_tau = 1.0 / (c->tau_f > 0.0 ? c->tau_f : dt);
-    for (int j = 0; j < 3; ++j) {
-        c->i2h_div[j] = 1.0 / (2.0 * c->h[j] * dt);
-        c->i2h_dt[j] = dt / (2.0 * c->h[j]);
+    dt = __shfl_sync(0xffffffffu, dt, 0);
+    switch (lane) {
+        case 0: c->dt = dt; c->t_end = c->t_end + dt; c->sigma_bits = 0ull; break;
+        case 1: c->dt2 = dt / 2.0; break;
+        case 2: c->dt3 = dt / 3.0; break;
+        case 3: c->dt6 = dt / 6.0; break;
+        case 4: c->inv_tau = 1.0 / (c->tau_f > 0.0 ? c->tau_f : dt); break;
+        case 5: case 6: case 7: c->i2h_div[lane - 5] = 1.0 / (2.0 * c->h[lane - 5] * dt); break;
+        case 8: case 9: case 10: c->i2h_dt[lane - 8] = dt / (2.0 * c->h[lane - 8]); break;
+        default: break;
     }
-    c->sigma_bits = 0ull;
 }
 
 // ------------------------------------------------------------------------------------------------------------
@@ -860,7 +874,7 @@ cudaError_t Kernels<T>::courant_rate(const void* q, const FlowConsts<T>& k, size
 
 cudaError_t adjust_dt(DtCtl* c, cudaStream_t st)
 {
-    k_adjust_dt<<<1, 32, 0, st>>>(c);
+    k_adjust_dt<<<1, 32, 0, st>>>(c);   // one warp
     return cudaGetLastError();
 }
 

@@ -258,7 +258,7 @@ struct ParticleArgs {
     const double* size;         // d [m] in tau_p = rho_p d^2 / (18 rho_f nu)
     int* state;                 // 0 airborne, 1 deposited
     int nx, ny, nz;
-    double h[3], L[3];
+    double h[3], ih[3], L[3];
     double nu, rho_p, rho_f, g[3];
     double dt;                  // fixed time step (dyn == nullptr)
     const DtCtl* dyn;           // dynamic time step: dt of the current step from here

@@ -112,8 +112,10 @@ def test_particles_fp32_flow(torch):
     g.step(1)
     pos, vel, _ = g.particles()
     g.close()
-    assert np.max(np.abs(vel - ref_vel)) < 1e-5 * max(1.0, np.max(np.abs(ref_vel)))
-    assert np.max(np.abs(pos - ref_pos)) < 1e-9
+    # the drag runs in float: velocities to FP32 rounding, positions to dt times that
+    vbar = 1e-5 * max(1.0, np.max(np.abs(ref_vel)))
+    assert np.max(np.abs(vel - ref_vel)) < vbar
+    assert np.max(np.abs(pos - ref_pos)) < prm.dt * vbar
 
 
 def test_particles_with_dynamic_dt(torch):
