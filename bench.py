@@ -337,6 +337,49 @@ def bench_next_rows(stream, steps):
     return out
 
 
+def bench_cube_wake(stream, cells_per_h=30, warm=24000, meas=12000, every=5, fevery=50):
+    """Cube-in-channel validation (Sec. 3.1.2, Tab. 2): Strouhal number of the vortex street from the transverse
+    velocity at a wake probe (upward zero crossings), mean drag coefficient from the immersed-boundary force on the
+    obstacle, FP32, 30 cells per obstacle side; throughput over the development steps."""
+    import torch
+    from paper_2204_02107_gb300 import native, rooms
+    cc = rooms.cube_channel(cells_per_h)
+    g = native.Grid(cc.nx, cc.ny, cc.nz, cc.lx, cc.ly, cc.lz, nu=cc.nu, dt=cc.dt, precision="fp32",
+                    history_capacity=16, stream=stream.cuda_stream)
+    g.set_mask(cc.beta)
+    g.set_inflow_field(cc.S, cc.targets)
+    g.set_force_region(cc.cube)
+    rng = np.random.default_rng(1)
+    g.set_field("u", cc.u_init)
+    g.set_field("v", 0.01 * rng.standard_normal(cc.shape) * (cc.beta > 0))
+    sec = time_grid_steps(g, warm, stream, reduce_every=0)
+    dst = torch.empty(cc.cells, dtype=torch.float32, device="cuda")
+    pz, py, px = cc.probe
+    pidx = px + cc.nx * (py + cc.ny * pz)
+    probe = torch.empty(meas // every, dtype=torch.float32, device="cuda")
+    forces = []
+    with torch.cuda.stream(stream):
+        for k in range(meas // every):
+            g.step(every, reduce_every=0)
+            native.lib().vf_read_field(g._h, native.FIELDS["v"], native.C.c_void_p(dst.data_ptr()), 0,
+                                       native.VF_DEVICE)
+            probe[k] = dst[pidx]
+            if (k * every) % fevery == 0:
+                forces.append(g.region_force())
+    g.sync()
+    g.close()
+    sig = probe.double().cpu().numpy()
+    t = (np.arange(len(sig)) + 1) * every * cc.dt
+    s = sig - sig.mean()
+    zc = [t[i] - s[i] * (t[i + 1] - t[i]) / (s[i + 1] - s[i]) for i in range(len(s) - 1) if s[i] < 0 <= s[i + 1]]
+    st = cc.h_obstacle / (float(np.mean(np.diff(zc))) * cc.u_bulk) if len(zc) > 2 else None
+    cd = 2.0 * float(np.mean([f[0] for f in forces])) / (cc.u_bulk ** 2 * cc.h_obstacle * cc.lz)
+    return {"workload": f"cube in channel {cc.nx}x{cc.ny}x{cc.nz} (2D flow, periodic z), {cells_per_h} cells per "
+                        f"obstacle side, Re_ob = 84, FP32", "value": cc.cells * warm / sec / 1e9, "unit": UNIT,
+            "strouhal": st, "drag_coefficient": cd, "periods_measured": len(zc) - 1,
+            "paper_table2_30_cells": {"strouhal": 0.2097, "drag_coefficient": 3.12}}
+
+
 def bench_serve(n_requests):
     """Poisson arrivals (4 per second) of ventilation requests served by continuous batching in FP32, against the
     same trace served one at a time in FP64; ACH agreement between the two."""
@@ -504,6 +547,7 @@ def main():
         extras["large_room"] = bench_large_room(stream, args.extra_steps)
         extras["batch"] = bench_batch(stream, args.extra_steps)
         extras["next_rows"] = bench_next_rows(stream, max(args.extra_steps, 100))
+        extras["cube_wake"] = bench_cube_wake(stream)
         if args.serve_requests > 0:
             extras["serve"] = bench_serve(args.serve_requests)
 

@@ -146,6 +146,13 @@ int vf_set_inflow_tanh(vf_grid* g, const double center[3], const double width[3]
  * non-NULL S returns to a binary region. */
 int vf_set_inflow_values(vf_grid* g, const void* S, int is_fp64, const double u_set[3], double c_set, int mem);
 
+/* Forcing with per-cell targets (Eqs. 2-3 with u_set and c_set varying in space, e.g. the parabolic inflow profile
+ * of the cube-in-channel case, Sec. 3.1.2): S is nx*ny*nz values in [0, 1]; targets is 4 arrays of nx*ny*nz
+ * values one after the other (u_set, v_set, w_set, c_set); double if is_fp64, else float; in `mem`.  The targets
+ * take 4 values per cell of device memory, allocated on the first call (beyond vf_grid_bytes).  vf_set_inflow,
+ * vf_set_inflow_tanh and vf_set_inflow_values return to constant targets. */
+int vf_set_inflow_field(vf_grid* g, const void* S, const void* targets, int is_fp64, int mem);
+
 /* room: nx*ny*nz bytes, nonzero = counted in c_room, c2_room, v_room and the histogram. */
 int vf_set_region(vf_grid* g, const uint8_t* room, int mem);
 
@@ -183,6 +190,15 @@ int vf_history(vf_grid* g, vf_reduce* out, int64_t max_records, int64_t* count);
 
 /* Forget the recorded history. */
 int vf_clear_history(vf_grid* g);
+
+/* Immersed-boundary force on a solid region (the drag of the cube-in-channel case, Sec. 3.1.2).  region: nx*ny*nz
+ * bytes in `mem`, nonzero = part of the region (kept until the next call). */
+int vf_set_force_region(vf_grid* g, const uint8_t* region, int mem);
+
+/* force[3] = dV sum over the region of the unmasked right-hand side of Eq. 2 of the current state,
+ * -convection + nu diffusion + S (u_set - u) / tau_f + b - grad(p/rho), in FP64 [m^4/s^2, i.e. N per kg/m^3 of
+ * density]: the rate at which the mask removes momentum there, the force the fluid exerts on the body.  Waits. */
+int vf_region_force(vf_grid* g, double force[3]);
 
 /* Simulated time, step count, cell count and bytes of device memory held by the grid.  With a dynamic time step the
  * time is read from the device (waits for the enqueued steps). */

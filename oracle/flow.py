@@ -392,6 +392,34 @@ def run(state: State, geom: Geometry, prm: Params, n_steps: int, with_budget=Fal
 
 
 # ----------------------------------------------------------------------------------------------------------------
+# Force of the immersed boundary on a solid region (the cube-in-channel drag of Sec. 3.1.2)
+# ----------------------------------------------------------------------------------------------------------------
+
+def region_force(state: State, geom: Geometry, prm: Params, region):
+    """Rate at which the mask removes momentum from the cells of `region` (per unit density): the unmasked
+    right-hand side of Eq. 2 there, -convection + nu diffusion + forcing + body force - grad(p/rho), summed
+    over the region times the cell volume.  The fluid pushes the body with this force (the drag along the flow
+    when the region is an obstacle).  The pressure is the physical p/rho = p/dt of the internal one."""
+    vel = (state.u, state.v, state.w)
+    h = prm.h
+    p_phys = state.p / prm.dt
+    region = np.asarray(region, dtype=bool)
+    out = []
+    for i in range(3):
+        ui = vel[i]
+        conv = np.zeros_like(ui)
+        diff = np.zeros_like(ui)
+        for j in range(3):
+            uj = vel[j]
+            conv += 0.5 * (delta(uj * ui, AXES[j], h[j]) + uj * delta(ui, AXES[j], h[j]))
+            diff += delta2(ui, AXES[j], h[j])
+        rhs = (-conv + prm.nu * diff + geom.S * (prm.u_set[i] - ui) / prm.tau + prm.body_force[i]
+               - delta(p_phys, AXES[i], h[i]))
+        out.append(prm.cell_volume * float(np.sum(rhs[region])))
+    return out
+
+
+# ----------------------------------------------------------------------------------------------------------------
 # Smooth source mask (Eq. 5): a window of widths W_j centred at c_j with tanh edges of sharpness B_j
 # ----------------------------------------------------------------------------------------------------------------
 

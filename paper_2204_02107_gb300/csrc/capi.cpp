@@ -124,7 +124,7 @@ FlowConsts<T> flow_consts(const vf_grid* g)
         k.ih[j] = (T)(1.0 / h[j]);
         k.ih2[j] = (T)(1.0 / (h[j] * h[j]));
         k.bf[j] = (T)d.body_force[j];
-        k.uset[j] = (T)g->uset[j];
+        k.uset[j] = g->has_target ? T(0) : (T)g->uset[j];
     }
     const double tau = d.tau_f > 0 ? d.tau_f : d.dt;
     k.nu = (T)d.nu;
@@ -135,7 +135,7 @@ FlowConsts<T> flow_consts(const vf_grid* g)
     k.dt3 = (T)(d.dt / 3.0);
     k.dt6 = (T)(d.dt / 6.0);
     k.third = (T)(1.0 / 3.0);
-    k.cset = (T)g->cset;
+    k.cset = g->has_target ? T(0) : (T)g->cset;
     k.filt = (T)(1.0 / std::pow(M_PI, 6));
     k.dyn = g->dynamic ? g->dtctl : nullptr;
     return k;
@@ -210,6 +210,7 @@ cudaError_t enqueue_step_t(vf_grid* g, cudaStream_t st, bool with_reduce, const 
     StageArgs<T> a{};
     a.mask = g->mask;
     a.sval = g->smooth_s ? (const T*)g->sval : nullptr;
+    a.target = g->has_target ? g->target : nullptr;
     a.qn = g->q;
     // stage states: q2 in qa, q3 in qb, q4 in acc; stage 4 writes q* over q2 (each cell reads its own q2 first)
     a.qs = g->q; a.out = g->qa;
@@ -417,7 +418,7 @@ size_t grid_bytes(const vf_grid_desc& d)
     size_t b = 4 * r256(4 * N * esz) + 5 * r256(N * esz) + r256(N * 4) + r256(N * 8) + r256(N);
     b += r256(nred * vf::kRedSlots * 8) + r256((vf::kHistBins + 2) * 8) + r256(4) + r256(sizeof(vf_reduce));
     b += r256((size_t)d.history_capacity * sizeof(vf_reduce)) + r256(16) + r256(4) + r256(8);
-    b += r256(sizeof(vf::DtCtl));
+    b += r256(sizeof(vf::DtCtl)) + r256(3 * sizeof(double));
     b += r256(M * cpx) + r256(d.ny * cpx) + r256(d.nz * cpx) + r256((M + 1) * cpx);
     b += r256(M * esz) + r256(d.ny * esz) + r256(d.nz * esz) + r256(d.ny * 4) + r256(d.nz * 4);
     return b;
@@ -532,6 +533,7 @@ int vf_create_grid(const vf_grid_desc* d, vf_grid** out)
     if (!(g->nonfinite = (int*)galloc(g, sizeof(int)))) return fail(VF_ENOMEM);
     if (!(g->solid_count = (unsigned long long*)galloc(g, sizeof(unsigned long long)))) return fail(VF_ENOMEM);
     if (!(g->dtctl = (vf::DtCtl*)galloc(g, sizeof(vf::DtCtl)))) return fail(VF_ENOMEM);
+    if (!(g->force_acc = (double*)galloc(g, 3 * sizeof(double)))) return fail(VF_ENOMEM);
     {
         // the control block starts at the given dt (constants with the same formulas as the adjust kernel)
         g->dynamic = d->courant_max > 0.0;
@@ -631,6 +633,7 @@ int vf_set_inflow(vf_grid* g, const uint8_t* S, const double u_set[3], double c_
     for (int j = 0; j < 3; ++j) g->uset[j] = u_set[j];
     g->cset = c_set;
     if (S) g->smooth_s = false;
+    g->has_target = false;
     drop_graphs(g);
     return VF_OK;
 }
@@ -660,6 +663,7 @@ int vf_set_inflow_tanh(vf_grid* g, const double center[3], const double width[3]
     for (int j = 0; j < 3; ++j) g->uset[j] = u_set[j];
     g->cset = c_set;
     g->smooth_s = true;
+    g->has_target = false;
     drop_graphs(g);
     return VF_OK;
 }
@@ -683,7 +687,73 @@ int vf_set_inflow_values(vf_grid* g, const void* S, int is_fp64, const double u_
     for (int j = 0; j < 3; ++j) g->uset[j] = u_set[j];
     g->cset = c_set;
     g->smooth_s = true;
+    g->has_target = false;
     drop_graphs(g);
+    return VF_OK;
+}
+
+int vf_set_inflow_field(vf_grid* g, const void* S, const void* targets, int is_fp64, int mem)
+{
+    int rc = check(g);
+    if (rc) return rc;
+    if (!S || !targets || (mem != VF_HOST && mem != VF_DEVICE))
+        return set_err(g, VF_EINVAL, "vf_set_inflow_field: bad argument");
+    if (!g->target && !(g->target = galloc(g, 4 * g->N * g->esz)))
+        return set_err(g, VF_ENOMEM, "vf_set_inflow_field: allocation failed");
+    const size_t esz_in = is_fp64 ? 8 : 4, bytes = g->N * esz_in;
+    const void* src = stage_input(g, S, bytes, mem, &rc);
+    if (rc) return rc;
+    if (g->fp64) {
+        VF_CK(Kernels<double>::convert_in(src, is_fp64, g->sval, -1, g->N, 1.0, nullptr, g->stream));
+        VF_CK(Kernels<double>::source_bits(g->mask, (const double*)g->sval, g->N, g->stream));
+    } else {
+        VF_CK(Kernels<float>::convert_in(src, is_fp64, g->sval, -1, g->N, 1.0, nullptr, g->stream));
+        VF_CK(Kernels<float>::source_bits(g->mask, (const float*)g->sval, g->N, g->stream));
+    }
+    for (int comp = 0; comp < 4; ++comp) {
+        // one component at a time through the staging buffer (N values)
+        VF_CK(cudaStreamSynchronize(g->stream));
+        const void* tsrc = stage_input(g, (const char*)targets + comp * bytes, bytes, mem, &rc);
+        if (rc) return rc;
+        if (g->fp64) VF_CK(Kernels<double>::convert_in(tsrc, is_fp64, g->target, comp, g->N, 1.0, nullptr, g->stream));
+        else VF_CK(Kernels<float>::convert_in(tsrc, is_fp64, g->target, comp, g->N, 1.0, nullptr, g->stream));
+    }
+    VF_CK(cudaStreamSynchronize(g->stream));
+    g->smooth_s = true;
+    g->has_target = true;
+    drop_graphs(g);
+    return VF_OK;
+}
+
+int vf_set_force_region(vf_grid* g, const uint8_t* region, int mem)
+{
+    int rc = check(g);
+    if (rc) return rc;
+    if (!region || (mem != VF_HOST && mem != VF_DEVICE)) return set_err(g, VF_EINVAL, "vf_set_force_region: bad argument");
+    const void* src = stage_input(g, region, g->N, mem, &rc);
+    if (rc) return rc;
+    VF_CK(vf::mask_merge(g->mask, (const uint8_t*)src, vf::kBitForce, g->N, g->stream));
+    VF_CK(cudaStreamSynchronize(g->stream));
+    return VF_OK;
+}
+
+int vf_region_force(vf_grid* g, double force[3])
+{
+    int rc = check(g);
+    if (rc) return rc;
+    if (!force) return set_err(g, VF_EINVAL, "vf_region_force: null output");
+    const double dV = (g->d.lx / g->d.nx) * (g->d.ly / g->d.ny) * (g->d.lz / g->d.nz);
+    VF_CK(cudaMemsetAsync(g->force_acc, 0, 3 * sizeof(double), g->stream));
+    if (g->fp64)
+        VF_CK(vf::region_force<double>(g->q, (const double*)g->p, g->mask, g->smooth_s ? (const double*)g->sval : nullptr,
+                                       g->has_target ? g->target : nullptr, flow_consts<double>(g), dV, g->force_acc,
+                                       g->stream));
+    else
+        VF_CK(vf::region_force<float>(g->q, (const float*)g->p, g->mask, g->smooth_s ? (const float*)g->sval : nullptr,
+                                      g->has_target ? g->target : nullptr, flow_consts<float>(g), dV, g->force_acc,
+                                      g->stream));
+    VF_CK(cudaMemcpyAsync(force, g->force_acc, 3 * sizeof(double), cudaMemcpyDeviceToHost, g->stream));
+    VF_CK(cudaStreamSynchronize(g->stream));
     return VF_OK;
 }
 

@@ -185,6 +185,15 @@ k_stage(StageArgs<T> a, FlowConsts<T> k)
             kq[3] = beta * (-conv + k.alpha * diff + S * (k.cset - c0) * inv_tau);
         }
 
+        if (a.target && (m0 & kBitS)) {
+            // per-cell targets: the forcing above used targets of 0, add S beta target / tau_f
+            T t4[4];
+            ld4(a.target, ic, t4);
+            const T sb = beta * S * inv_tau;
+#pragma unroll
+            for (int f = 0; f < 4; ++f) kq[f] += sb * t4[f];
+        }
+
         // RK4 combine, classic tableau (nodes 0, 1/2, 1/2, 1; weights 1/6, 1/3, 1/3, 1/6) with the stage states as
         // the only registers: q2 = q_n + dt/2 k1, q3 = q_n + dt/2 k2, q4 = q_n + dt k3, so that
         // q* = q_n + dt/6 (k1 + 2 k2 + 2 k3 + k4) = (q2 + 2 q3 + q4 - q_n) / 3 + dt/6 k4  (q4 is the stencil centre)
@@ -629,6 +638,72 @@ __global__ void k_source_bits(uint8_t* __restrict__ mask, const T* __restrict__ 
 }
 
 // ------------------------------------------------------------------------------------------------------------
+// Immersed-boundary force on a region: F_i = dV sum_region [-conv_i + nu diff_i + S (target_i - u_i) / tau_f + b_i
+// - delta_i p], the unmasked right-hand side of Eq. 2 in FP64 (the rate at which the mask removes momentum there)
+// ------------------------------------------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_region_force(const void* __restrict__ q, const T* __restrict__ p,
+                                                      const uint8_t* __restrict__ mask, const T* __restrict__ sval,
+                                                      const void* __restrict__ target, FlowConsts<T> k, double dV,
+                                                      double* acc)
+{
+    const size_t n = (size_t)k.nx * k.ny * k.nz;
+    const double inv_tau = k.dyn ? k.dyn->inv_tau : (double)k.inv_tau;
+    double F[3] = {0.0, 0.0, 0.0};
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const uint8_t m = mask[i];
+        if (!(m & kBitForce)) continue;
+        const int x = (int)(i % k.nx), y = (int)((i / k.nx) % k.ny), z = (int)(i / ((size_t)k.nx * k.ny));
+        const int plane = k.nx * k.ny;
+        const int im[3] = {z * plane + y * k.nx + wrap(x - 1, k.nx), z * plane + wrap(y - 1, k.ny) * k.nx + x,
+                           wrap(z - 1, k.nz) * plane + y * k.nx + x};
+        const int ip[3] = {z * plane + y * k.nx + wrap(x + 1, k.nx), z * plane + wrap(y + 1, k.ny) * k.nx + x,
+                           wrap(z + 1, k.nz) * plane + y * k.nx + x};
+        T tc[4], tm[3][4], tp[3][4];
+        ld4(q, (int)i, tc);
+        for (int j = 0; j < 3; ++j) { ld4(q, im[j], tm[j]); ld4(q, ip[j], tp[j]); }
+        double c[3], qm[3][3], qp[3][3];
+        for (int a = 0; a < 3; ++a) {
+            c[a] = tc[a];
+            for (int j = 0; j < 3; ++j) { qm[j][a] = tm[j][a]; qp[j][a] = tp[j][a]; }
+        }
+        double S = 0.0, tgt[3] = {(double)k.uset[0], (double)k.uset[1], (double)k.uset[2]};
+        if (m & kBitS) {
+            S = sval ? (double)sval[i] : 1.0;
+            if (target) {
+                T t4[4];
+                ld4(target, (int)i, t4);
+                for (int a = 0; a < 3; ++a) tgt[a] = t4[a];
+            }
+        }
+        for (int a = 0; a < 3; ++a) {
+            double conv = 0.0, diff = 0.0;
+            for (int j = 0; j < 3; ++j) {
+                const double i2h = (double)k.i2h[j];
+                conv += 0.5 * ((qp[j][j] * qp[j][a] - qm[j][j] * qm[j][a]) * i2h + c[j] * (qp[j][a] - qm[j][a]) * i2h);
+                diff += (qp[j][a] - 2.0 * c[a] + qm[j][a]) * (double)k.ih2[j];
+            }
+            const double grad_p = ((double)p[ip[a]] - (double)p[im[a]]) * (double)k.i2h[a];
+            const double rhs = -conv + (double)k.nu * diff + S * (tgt[a] - c[a]) * inv_tau + (double)k.bf[a] - grad_p;
+            F[a] += rhs * dV;
+        }
+    }
+    __shared__ double part[3][8];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    for (int a = 0; a < 3; ++a) {
+        double v = F[a];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) part[a][wid] = v;
+    }
+    __syncthreads();
+    if (tid < 3) {
+        double v = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += part[tid][w];
+        if (v != 0.0) atomicAdd(acc + tid, v);
+    }
+}
+
+// ------------------------------------------------------------------------------------------------------------
 // Dynamic time step (Sec. 2.4): the Courant rate of a state, and the adjust kernel at the start of a step
 // ------------------------------------------------------------------------------------------------------------
 template <typename T>
@@ -871,6 +946,19 @@ cudaError_t Kernels<T>::courant_rate(const void* q, const FlowConsts<T>& k, size
     k_courant_rate<T><<<elementwise_blocks(n), 256, 0, st>>>(q, k, n, sigma);
     return cudaGetLastError();
 }
+
+template <typename T>
+cudaError_t region_force(const void* q, const T* p, const uint8_t* mask, const T* sval, const void* target,
+                         const FlowConsts<T>& k, double dV, double* acc, cudaStream_t st)
+{
+    const size_t n = (size_t)k.nx * k.ny * k.nz;
+    k_region_force<T><<<elementwise_blocks(n), 256, 0, st>>>(q, p, mask, sval, target, k, dV, acc);
+    return cudaGetLastError();
+}
+template cudaError_t region_force<float>(const void*, const float*, const uint8_t*, const float*, const void*,
+                                         const FlowConsts<float>&, double, double*, cudaStream_t);
+template cudaError_t region_force<double>(const void*, const double*, const uint8_t*, const double*, const void*,
+                                          const FlowConsts<double>&, double, double*, cudaStream_t);
 
 cudaError_t adjust_dt(DtCtl* c, cudaStream_t st)
 {

@@ -39,6 +39,9 @@ struct vf_grid {
     uint8_t* mask = nullptr;
     void* sval = nullptr;        // smooth forcing region values (Eq. 5 or caller's), N values of the precision
     bool smooth_s = false;       // the stage kernels take S from sval (else S = 1 on the S bit)
+    void* target = nullptr;      // per-cell forcing targets (u, v, w, c) as a 4-vector array, allocated on first use
+    bool has_target = false;     // the stage kernels take the targets from `target` (the constants are then 0)
+    double* force_acc = nullptr; // vf_region_force accumulators [3]
     void* twx = nullptr;
     void* twy = nullptr;
     void* twz = nullptr;

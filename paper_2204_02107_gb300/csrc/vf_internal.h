@@ -20,6 +20,7 @@ constexpr uint8_t kBitBeta = 1u;
 constexpr uint8_t kBitS = 2u;
 constexpr uint8_t kBitRoom = 4u;
 constexpr uint8_t kBitNearSolid = 8u;
+constexpr uint8_t kBitForce = 16u;   // cells whose immersed-boundary force vf_region_force sums
 
 // Constants of the flow kernels, in the compute precision T.
 // Kernel families with their own z-chunk (planes one CTA marches along z); the allowed range of a chunk.
@@ -75,6 +76,8 @@ struct StageArgs {
     void* out;
     const uint8_t* mask;
     const T* sval;      // smooth forcing region S in [0, 1] at the cells whose S bit is set (nullptr: S = 1 there)
+    const void* target; // per-cell forcing targets (u, v, w, c)_set as a 4-vector array (nullptr: the constants;
+                        // when given, the constants are 0 and S beta target / tau_f is added at the S cells)
 };
 
 // One smooth source window of Eq. 5 on a grid: centre c_j, half widths W_j / 2, sharpness B_j, cell size h_j and
@@ -249,6 +252,12 @@ struct LaunchHook {
     void* ctx;
     void operator()(int phase) const { if (fn) fn(ctx, phase); }
 };
+
+// Immersed-boundary force on the cells with the kBitForce bit (flow_kernels.cu): sum over them of the unmasked
+// momentum right-hand side (-convection + nu diffusion + forcing + body force - grad p) times dV, into acc[3].
+template <typename T>
+cudaError_t region_force(const void* q, const T* p, const uint8_t* mask, const T* sval, const void* target,
+                         const FlowConsts<T>& k, double dV, double* acc, cudaStream_t st);
 
 // Lagrangian particles of a grid (Sec. 2.3; particles.cu): structure-of-arrays double state on the device.
 struct ParticleArgs {

@@ -127,6 +127,9 @@ _SIGNATURES = {
     "vf_phase_name": (C.c_char_p, [C.c_int]),
     "vf_status_string": (C.c_char_p, [C.c_int]),
     "vf_abi_sizes": (C.c_int, [C.POINTER(C.c_int64)]),
+    "vf_set_inflow_field": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int]),
+    "vf_set_force_region": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
+    "vf_region_force": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
     "vf_particles_set": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double,
                                    C.c_double, C.POINTER(C.c_double)]),
     "vf_particles_read": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -407,6 +410,24 @@ class Grid:
             self._check(lib().vf_particles_read(self._h, C.c_void_p(pos.ctypes.data), C.c_void_p(vel.ctypes.data),
                                                 C.c_void_p(dep.ctypes.data)), "vf_particles_read")
         return pos, vel, dep.astype(bool)
+
+    def set_inflow_field(self, S, targets):
+        """Forcing with per-cell targets: S (grid-sized) and targets (4 grid-sized arrays u, v, w, c), float64."""
+        Sa = np.ascontiguousarray(S, dtype=np.float64).reshape(-1)
+        Ta = np.ascontiguousarray(np.stack([np.asarray(t, dtype=np.float64).reshape(-1) for t in targets]))
+        if Sa.size != self.n or Ta.shape != (4, self.n):
+            raise ValueError("S must have one value per cell and targets four arrays of the grid's size")
+        self._check(lib().vf_set_inflow_field(self._h, C.c_void_p(Sa.ctypes.data), C.c_void_p(Ta.ctypes.data), 1,
+                                              VF_HOST), "vf_set_inflow_field")
+
+    def set_force_region(self, region):
+        ptr, mem, _keep = _pointer(region, np.uint8, self.n)
+        self._check(lib().vf_set_force_region(self._h, ptr, mem), "vf_set_force_region")
+
+    def region_force(self):
+        f = (C.c_double * 3)()
+        self._check(lib().vf_region_force(self._h, f), "vf_region_force")
+        return tuple(f)
 
     def set_region(self, room):
         ptr, mem, _keep = _pointer(room, np.uint8, self.n)

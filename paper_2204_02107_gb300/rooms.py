@@ -239,3 +239,78 @@ def random_mask(shape, seed, solid_fraction=0.2, n_boxes=4):
         beta[np.ix_(zs, ys, xs)] = 0
     beta[rng.random(shape) < solid_fraction * 0.1] = 0
     return beta
+
+
+@dataclass
+class CubeChannel:
+    """The cube-in-channel case of Sec. 3.1.2 (Tab. 1, right column), made periodic in z with nz cells so that the
+    3D solver computes the 2D flow: a channel of width D = 2 pi between solid walls, a square obstacle of side
+    h = D/6 centred at (1.2 D, D/2), a forcing strip at the left end imposing the parabolic profile
+    U(y) = U_max 4 eta (1 - eta) (eta = distance from the lower wall / D), obstacle Reynolds number
+    Re_ob = U_b h / nu with U_b = 2/3 U_max.  Cell sizes are h / cells_per_h in x and y; nx and ny are the
+    nearest 2-3-5 smooth sizes to the paper's 8.8 D x 1.1 D (walls at least 0.05 D thick)."""
+
+    nx: int
+    ny: int
+    nz: int
+    lx: float
+    ly: float
+    lz: float
+    beta: np.ndarray
+    S: np.ndarray
+    targets: tuple          # (u_set, v_set, w_set, c_set) per cell
+    cube: np.ndarray        # uint8 mask of the obstacle's cells
+    u_init: np.ndarray      # the parabolic profile in the channel, 0 in solids
+    nu: float
+    dt: float
+    h_obstacle: float
+    u_bulk: float
+    probe: tuple            # (z, y, x) of the wake probe, 2 h behind the obstacle on the centre line
+    wall: int
+    cells_per_h: int
+
+    @property
+    def cells(self):
+        return self.nx * self.ny * self.nz
+
+    @property
+    def shape(self):
+        return (self.nz, self.ny, self.nx)
+
+
+def cube_channel(cells_per_h=30, nz=8, u_max=1.0, re_ob=84.0, courant=0.2, force_width_h=0.5):
+    D = 2.0 * math.pi
+    c = int(cells_per_h)
+    dx = D / 6.0 / c
+    width = 6 * c                                   # channel cells
+    wall = int(math.ceil(0.05 * width))
+    while not smooth235(width + 2 * wall):
+        wall += 1
+    ny = width + 2 * wall
+    nx = int(math.ceil(8.8 * width))
+    while not smooth235(nx):
+        nx += 1
+    shape = (nz, ny, nx)
+    beta = np.ones(shape, dtype=np.uint8)
+    beta[:, :wall, :] = 0
+    beta[:, wall + width:, :] = 0
+    cube = np.zeros(shape, dtype=np.uint8)
+    x0 = int(round(1.2 * width - c / 2))
+    y0 = wall + (width - c) // 2
+    cube[:, y0:y0 + c, x0:x0 + c] = 1
+    beta[cube == 1] = 0
+    # parabolic profile across the channel, the walls' surfaces half a cell outside the first fluid centres
+    eta = (np.arange(ny) - (wall - 0.5)) / width
+    prof = np.where((eta > 0.0) & (eta < 1.0), u_max * 4.0 * eta * (1.0 - eta), 0.0)
+    u_prof = np.broadcast_to(prof[None, :, None], shape).astype(np.float64) * (beta > 0)
+    S = np.zeros(shape, dtype=np.float64)
+    nf = max(2, int(round(force_width_h * c)))
+    S[:, wall:wall + width, :nf] = 1.0
+    zero = np.zeros(shape)
+    targets = (u_prof * (S > 0), zero, zero, zero)
+    u_b = 2.0 / 3.0 * u_max
+    h = D / 6.0
+    nu = u_b * h / re_ob
+    probe = (nz // 2, wall + width // 2, x0 + 3 * c)
+    return CubeChannel(nx, ny, nz, nx * dx, ny * dx, nz * dx, beta, S, targets, cube, u_prof, nu,
+                       courant * dx / u_max, h, u_b, probe, wall, c)

@@ -1,0 +1,98 @@
+"""Cube-in-channel validation (Sec. 3.1.2, Tab. 2): forcing with per-cell targets (the parabolic inflow profile),
+the immersed-boundary force on the obstacle, and the Strouhal number and drag coefficient of the vortex street
+against the paper's 30 x 30 cells-per-obstacle values."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import flow as F
+from paper_2204_02107_gb300 import native, rooms
+from gpu_helpers import FIELD_NAMES, field_errors, read_state, require_gpu
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")))
+
+
+@pytest.fixture(scope="module")
+def torch():
+    return require_gpu()
+
+
+def grid_for(cc, precision):
+    g = native.Grid(cc.nx, cc.ny, cc.nz, cc.lx, cc.ly, cc.lz, nu=cc.nu, dt=cc.dt, precision=precision,
+                    history_capacity=16)
+    g.set_mask(cc.beta)
+    g.set_inflow_field(cc.S, cc.targets)
+    g.set_force_region(cc.cube)
+    return g
+
+
+def initial_state(cc, seed=1):
+    rng = np.random.default_rng(seed)
+    v0 = 0.01 * rng.standard_normal(cc.shape) * (cc.beta > 0)
+    z = np.zeros(cc.shape)
+    return F.State(cc.u_init.copy(), v0, z.copy(), z.copy(), z.copy())
+
+
+def test_targets_and_region_force_vs_oracle(torch):
+    cc = rooms.cube_channel(6)
+    prm = F.Params(nx=cc.nx, ny=cc.ny, nz=cc.nz, lx=cc.lx, ly=cc.ly, lz=cc.lz, nu=cc.nu, dt=cc.dt,
+                   u_set=cc.targets[:3], c_set=cc.targets[3])
+    geom = F.Geometry(cc.beta, cc.S)
+    st0 = initial_state(cc)
+    ref, _ = F.run(st0.copy(), geom, prm, 20)
+    g = grid_for(cc, "fp64")
+    for n in FIELD_NAMES:
+        g.set_field(n, getattr(st0, n))
+    g.step(20)
+    out = read_state(g, prm)
+    errs = field_errors(out, ref)
+    assert max(errs.values()) < 1e-11, errs
+    fx, fy, fz = g.region_force()
+    rx, ry, rz = F.region_force(ref, geom, prm, cc.cube.astype(bool))
+    assert fx == pytest.approx(rx, rel=1e-9) and abs(fx) > 0
+    assert abs(fy - ry) <= 1e-9 * abs(fx) and abs(fz - rz) <= 1e-9 * abs(fx)
+    g.close()
+
+
+def strouhal_and_drag(cc, warm, meas, every=5, fevery=50):
+    import torch
+    g = grid_for(cc, "fp32")
+    st0 = initial_state(cc)
+    for n in ("u", "v"):
+        g.set_field(n, getattr(st0, n))
+    g.step(warm, reduce_every=0)
+    dst = torch.empty(cc.cells, dtype=torch.float32, device="cuda")
+    pz, py, px = cc.probe
+    pidx = px + cc.nx * (py + cc.ny * pz)
+    probe = torch.empty(meas // every, dtype=torch.float32, device="cuda")
+    forces = []
+    for k in range(meas // every):
+        g.step(every, reduce_every=0)
+        native.lib().vf_read_field(g._h, native.FIELDS["v"], native.C.c_void_p(dst.data_ptr()), 0,
+                                   native.VF_DEVICE)
+        probe[k] = dst[pidx]
+        if (k * every) % fevery == 0:
+            forces.append(g.region_force())
+    g.close()
+    sig = probe.double().cpu().numpy()
+    t = (np.arange(len(sig)) + 1) * every * cc.dt
+    s = sig - sig.mean()
+    # upward zero crossings of the probe's transverse velocity, linearly interpolated: one per shedding period
+    zc = [t[i] - s[i] * (t[i + 1] - t[i]) / (s[i + 1] - s[i]) for i in range(len(s) - 1) if s[i] < 0 <= s[i + 1]]
+    st = cc.h_obstacle / (np.mean(np.diff(zc)) * cc.u_bulk)
+    cd = 2.0 * np.mean([f[0] for f in forces]) / (cc.u_bulk ** 2 * cc.h_obstacle * cc.lz)
+    return st, cd, len(zc) - 1
+
+
+def test_strouhal_and_drag_against_table2(torch):
+    """30 cells per obstacle side, Re_ob = 84: about 22 shedding periods of development, 11 measured."""
+    cc = rooms.cube_channel(30)
+    st, cd, periods = strouhal_and_drag(cc, 24000, 12000)
+    tab = GOLDEN["cube_in_channel"]
+    assert periods >= 8
+    assert abs(st - tab["strouhal_30"]) / tab["strouhal_30"] < 0.10, st
+    assert abs(cd - tab["drag_30"]) / tab["drag_30"] < 0.10, cd

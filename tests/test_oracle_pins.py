@@ -422,3 +422,25 @@ def test_histogram_brute_force():
         else:
             ref[min(int(val * 64), 63)] += 1
     assert list(counts) == ref and under == ru and over == ro
+
+
+def test_region_force_closed_forms():
+    """Force on a region from the unmasked right-hand side: a uniform pressure gradient G over a fluid at rest
+    pushes a region of V cells with -G V dV; a Couette-like shear profile u = a y^2 (diffusion only) gives
+    2 nu a per cell.  Checks the sign, the cell volume and the pressure scaling p = dt p_phys."""
+    prm = F.Params(nx=8, ny=10, nz=6, lx=0.8, ly=1.0, lz=0.6, nu=0.01, dt=0.05)
+    geom = F.open_geometry(prm)
+    st = F.zero_state(prm)
+    region = np.zeros(prm.shape, dtype=bool)
+    region[2:4, 3:6, 2:5] = True                       # 2 x 3 x 3 = 18 cells away from the periodic seams
+    x = np.arange(prm.nx) * prm.h[0]
+    st.p = prm.dt * np.broadcast_to(0.7 * x[None, None, :], prm.shape).copy()   # p_phys = 0.7 x in the middle
+    f = F.region_force(st, geom, prm, region)
+    assert f[0] == pytest.approx(-0.7 * 18 * prm.cell_volume, rel=1e-12)
+    assert abs(f[1]) < 1e-14 and abs(f[2]) < 1e-14
+    st = F.zero_state(prm)
+    y = np.arange(prm.ny) * prm.h[1]
+    st.u = np.broadcast_to(3.0 * (y ** 2)[None, :, None], prm.shape).copy()
+    f = F.region_force(st, geom, prm, region)
+    # convection of u(y) alone vanishes (v = w = 0, d/dx u = 0); diffusion: nu * 2 * 3.0 per cell
+    assert f[0] == pytest.approx(prm.nu * 6.0 * 18 * prm.cell_volume, rel=1e-10)
