@@ -155,6 +155,7 @@ PoissonArgs<T> poisson_args(const vf_grid* g, T* f, T* p, int use_mask)
     a.reg = g->reg;
     a.gx = g->reg_gx; a.gy = g->reg_gy; a.gz = g->reg_gz;
     a.reg_sp = g->reg_sp; a.reg_spx = g->reg_spx; a.reg_sb = g->reg_sb;
+    a.reg_tile = g->reg_tile; a.reg_sy = g->reg_sy; a.reg_tb = g->reg_tb; a.reg_st = g->reg_st;
     a.spec = g->spec;
     a.twx = g->twx; a.twy = g->twy; a.twz = g->twz; a.twr = g->twr;
     a.lamx = (const T*)g->lamx; a.lamy = (const T*)g->lamy; a.lamz = (const T*)g->lamz;
@@ -352,13 +353,19 @@ int build_tables_t(vf_grid* g)
         VF_CK(cudaMemcpyAsync(*u.dst, u.src, u.bytes, cudaMemcpyHostToDevice, g->stream));
     }
     VF_CK(cudaStreamSynchronize(g->stream));   // host vectors die here
-    g->plane_layout = Kernels<T>::plane_fits(d.ny, d.nz) && !std::getenv("VF_TILE_FFT");
-    if (g->plane_layout && !std::getenv("VF_GENERIC_FFT")) {
+    // the register path keeps the spectrum plane by plane ([kx][z][y]) whether or not a plane fits in shared memory;
+    // the generic path uses that layout only with its whole-plane kernel (VF_TILE_FFT / VF_GENERIC_FFT: generic)
+    const bool generic = std::getenv("VF_TILE_FFT") || std::getenv("VF_GENERIC_FFT");
+    if (!generic && vf::RegFft<T>::eligible(d.nx, d.ny, d.nz)) {
+        g->plane_layout = true;
         PoissonArgs<T> ra = poisson_args<T>(g, nullptr, nullptr, 0);
         vf::RegFft<T>::configure(ra);
         g->reg = ra.reg;
         g->reg_gx = ra.gx; g->reg_gy = ra.gy; g->reg_gz = ra.gz;
         g->reg_sp = ra.reg_sp; g->reg_spx = ra.reg_spx; g->reg_sb = ra.reg_sb;
+        g->reg_tile = ra.reg_tile; g->reg_sy = ra.reg_sy; g->reg_tb = ra.reg_tb; g->reg_st = ra.reg_st;
+    } else {
+        g->plane_layout = Kernels<T>::plane_fits(d.ny, d.nz) && !std::getenv("VF_TILE_FFT");
     }
     const PoissonArgs<T> pa = poisson_args<T>(g, nullptr, nullptr, 0);
     VF_CK(Kernels<T>::poisson_prepare(pa));

@@ -7,7 +7,8 @@
 // DFTs of order G.  It then holds X[t Q + q + 16 k2] (Q = 16 / G) in register q G + k2.  The inverse is the
 // mirror image and ends with thread t holding x[t + G m] again, so global loads and stores stay coalesced.
 //
-// One iteration of Eq. 9 is the correction (masked grids) and three kernels:
+// One iteration of Eq. 9 is the correction (masked grids) and three kernels (five when the plane of one kx does not
+// fit in shared memory: the (y, z) kernel becomes a y pass, a z pass over tiles of y slots, and an inverse y pass):
 //   x forward : real-to-complex FFT along x of f (r plus the Eq. 9 correction, added beforehand at the cells
 //               next to solids by the correction kernel of the generic path), two reals packed per complex
 //               value, split step written straight into the plane layout spec[kx][z][y] (the rows of a warp
@@ -19,6 +20,7 @@
 // The arithmetic (DFT kernels, twiddle tables, packing, eigenvalues) is the one of the generic passes; only the
 // order of the butterflies and the data movement differ.
 #include <algorithm>
+#include <cstdlib>
 
 #include "fft_common.cuh"
 
@@ -344,6 +346,145 @@ __global__ void __launch_bounds__(yz_threads<T>()) k_reg_yz_solve(PoissonArgs<T>
     }
 }
 
+// ---- tile mode: the (y, z) plane of one kx does not fit in shared memory ----------------------------------------
+// ky held at y slot s after the forward y pass (run-time G)
+__device__ __forceinline__ int freq_of_slot_rt(int s, int g)
+{
+    const int r = s & 15, k2 = s >> 4;
+    return (r % g) * (16 / g) + r / g + 16 * k2;
+}
+
+// y pass: a group per spectrum row (kx, z), straight from and to global memory.  The forward pass leaves the y
+// spectrum of a row in slot order (ky of slot s is freq_of_slot), which the z pass reads and the inverse pass
+// takes back to natural order.
+template <typename T, int GY, bool INV>
+__global__ void __launch_bounds__(256) k_reg_y(PoissonArgs<T> A)
+{
+    using C = typename CxT<T>::type;
+    constexpr int NY = 16 * GY, B = 256 / GY, P = 32 / GY, Q = 16 / GY;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int SY = A.reg_sy;
+    C* tw = reinterpret_cast<C*>(smem_raw);
+    C* rowbuf = tw + NY;
+    stage_table(tw, A.twy, NY);
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int gi = lane % P, t = lane / P;
+    const int b = warp * P + gi;
+    const long long rows = (long long)A.M * A.nz;
+    const long long row = (long long)blockIdx.x * B + b;
+    const bool act = row < rows;
+    C* g = reinterpret_cast<C*>(A.spec) + (act ? row : 0) * NY;
+    C* rb = rowbuf + b * SY;
+    auto buf = [rb](int e) -> C& { return rb[e]; };
+    C v[16];
+    if (!INV) {
+#pragma unroll
+        for (int m = 0; m < 16; ++m) v[m] = act ? g[t + GY * m] : mk<C>(T(0), T(0));
+        reg_fwd<C, GY>(v, t, tw, buf);
+        if (act) {
+#pragma unroll
+            for (int q = 0; q < Q; ++q)
+#pragma unroll
+                for (int k2 = 0; k2 < GY; ++k2) g[RegShape<GY>::slot(t, q, k2)] = v[q * GY + k2];
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < Q; ++q)
+#pragma unroll
+            for (int k2 = 0; k2 < GY; ++k2)
+                v[q * GY + k2] = act ? g[RegShape<GY>::slot(t, q, k2)] : mk<C>(T(0), T(0));
+        reg_inv<C, GY>(v, t, tw, buf);
+        if (act) {
+#pragma unroll
+            for (int m = 0; m < 16; ++m) g[t + GY * m] = v[m];
+        }
+    }
+}
+
+// z pass: a CTA takes TB consecutive y slots of one kx plane and all z, staged as a shared tile [z][slot] with
+// coalesced loads; a group per column does the forward z FFT, the division by lambda N and the inverse z FFT in
+// registers, then the tile goes back.
+template <typename T, int GZ>
+__global__ void __launch_bounds__(256) k_reg_z_tile(PoissonArgs<T> A)
+{
+    using C = typename CxT<T>::type;
+    constexpr int NZ = 16 * GZ, P = 32 / GZ, QZ = 16 / GZ;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int ST = A.reg_st, TB = A.reg_tb, ny = A.ny;
+    C* tile = reinterpret_cast<C*>(smem_raw);     // element (z, c) at z * ST + c
+    C* twz = tile + (size_t)NZ * ST;
+    const int tiles = ny / TB;
+    const int kx = blockIdx.x / tiles, c0 = (blockIdx.x - kx * tiles) * TB;
+    C* g = reinterpret_cast<C*>(A.spec) + (long long)kx * ny * NZ;
+    const int n_el = NZ * TB, nt = blockDim.x;
+    for (int i0 = threadIdx.x; i0 < n_el; i0 += 8 * nt) {
+        C tmp[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int i = i0 + u * nt;
+            if (i < n_el) {
+                const int z = i / TB, c = i - z * TB;
+                tmp[u] = g[(long long)z * ny + c0 + c];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int i = i0 + u * nt;
+            if (i < n_el) {
+                const int z = i / TB, c = i - z * TB;
+                tile[z * ST + c] = tmp[u];
+            }
+        }
+    }
+    stage_table(twz, A.twz, NZ);
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int gi = lane % P, t = lane / P;
+    const int c = warp * P + gi;                  // blockDim = TB * GZ: every group has a column
+    const int ky = freq_of_slot_rt(c0 + c, A.gy);
+    const T lxy = __ldg(A.lamx + kx) + __ldg(A.lamy + ky);
+    const bool ky_null = (kx == 0) && (ky == 0 || 2 * ky == ny);
+    C v[16];
+#pragma unroll
+    for (int m = 0; m < 16; ++m) v[m] = tile[(t + GZ * m) * ST + c];
+    auto buf = [tile, ST, c](int e) -> C& { return tile[e * ST + c]; };
+    reg_fwd<C, GZ>(v, t, twz, buf);
+#pragma unroll
+    for (int q = 0; q < QZ; ++q)
+#pragma unroll
+        for (int k2 = 0; k2 < GZ; ++k2) {
+            const int kz = RegShape<GZ>::freq(t, q, k2);
+            const bool null = ky_null && (kz == 0 || 2 * kz == NZ);
+            const T s = null ? T(0) : A.invN / -(lxy + __ldg(A.lamz + kz));
+            v[q * GZ + k2] = cscale(v[q * GZ + k2], s);
+        }
+    reg_inv<C, GZ>(v, t, twz, buf);
+    __syncwarp();
+#pragma unroll
+    for (int m = 0; m < 16; ++m) tile[(t + GZ * m) * ST + c] = v[m];
+    __syncthreads();
+    for (int i0 = threadIdx.x; i0 < n_el; i0 += 8 * nt) {
+        C tmp[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int i = i0 + u * nt;
+            if (i < n_el) {
+                const int z = i / TB, cc = i - z * TB;
+                tmp[u] = tile[z * ST + cc];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int i = i0 + u * nt;
+            if (i < n_el) {
+                const int z = i / TB, cc = i - z * TB;
+                g[(long long)z * ny + c0 + cc] = tmp[u];
+            }
+        }
+    }
+}
+
 // ---- host side ---------------------------------------------------------------------------------------------
 int g_of(int n)
 {
@@ -422,7 +563,66 @@ size_t yz_smem(int ny, int nz, int sp)
     return ((size_t)nz * sp + ny + nz) * sizeof(typename CxT<T>::type);
 }
 
+template <typename T>
+size_t y_smem(int ny, int sy)
+{
+    const int B = 256 / (ny / 16);
+    return ((size_t)ny + (size_t)B * sy) * sizeof(typename CxT<T>::type);
+}
+
+template <typename T>
+size_t ztile_smem(int nz, int st)
+{
+    return ((size_t)nz * st + nz) * sizeof(typename CxT<T>::type);
+}
+
 constexpr size_t kRegSmemLimit = 200 * 1024;
+
+template <typename T, int GY>
+cudaError_t launch_y(const PoissonArgs<T>& a, bool inv, cudaStream_t st)
+{
+    constexpr int B = 256 / GY;
+    const long long rows = (long long)a.M * a.nz;
+    const unsigned grid = (unsigned)((rows + B - 1) / B);
+    const size_t sm = y_smem<T>(16 * GY, a.reg_sy);
+    if (inv) k_reg_y<T, GY, true><<<grid, 256, sm, st>>>(a);
+    else k_reg_y<T, GY, false><<<grid, 256, sm, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t dispatch_y(const PoissonArgs<T>& a, bool inv, cudaStream_t st)
+{
+    switch (a.gy) {
+        case 1: return launch_y<T, 1>(a, inv, st);
+        case 2: return launch_y<T, 2>(a, inv, st);
+        case 4: return launch_y<T, 4>(a, inv, st);
+        case 8: return launch_y<T, 8>(a, inv, st);
+        case 16: return launch_y<T, 16>(a, inv, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename T, int GZ>
+cudaError_t launch_ztile(const PoissonArgs<T>& a, cudaStream_t st)
+{
+    const unsigned grid = (unsigned)(a.M * (a.ny / a.reg_tb));
+    k_reg_z_tile<T, GZ><<<grid, a.reg_tb * GZ, ztile_smem<T>(16 * GZ, a.reg_st), st>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t dispatch_ztile(const PoissonArgs<T>& a, cudaStream_t st)
+{
+    switch (a.gz) {
+        case 1: return launch_ztile<T, 1>(a, st);
+        case 2: return launch_ztile<T, 2>(a, st);
+        case 4: return launch_ztile<T, 4>(a, st);
+        case 8: return launch_ztile<T, 8>(a, st);
+        case 16: return launch_ztile<T, 16>(a, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
 
 template <typename T, int GX>
 cudaError_t launch_x(const PoissonArgs<T>& a, bool fwd, cudaStream_t st)
@@ -505,6 +705,20 @@ cudaError_t prepare_x(const PoissonArgs<T>& a)
     return e;
 }
 
+template <typename T, int G>
+cudaError_t prepare_tile(const PoissonArgs<T>& a)
+{
+    // y passes of length 16 G and the z tile of length 16 G (each used when its axis has this G)
+    cudaError_t e = cudaSuccess;
+    if (a.gy == G) {
+        const size_t sm = y_smem<T>(16 * G, a.reg_sy);
+        e = raise_smem(k_reg_y<T, G, false>, sm);
+        if (e == cudaSuccess) e = raise_smem(k_reg_y<T, G, true>, sm);
+    }
+    if (e == cudaSuccess && a.gz == G) e = raise_smem(k_reg_z_tile<T, G>, ztile_smem<T>(16 * G, a.reg_st));
+    return e;
+}
+
 template <typename T, int GY>
 cudaError_t prepare_yz_z(const PoissonArgs<T>& a)
 {
@@ -527,9 +741,8 @@ bool RegFft<T>::eligible(int nx, int ny, int nz)
     if (nx % 2) return false;
     const int gx = g_of(nx / 2), gy = g_of(ny), gz = g_of(nz);
     if (!gx || !gy || !gz) return false;
-    // the plane with the widest padding, and the x passes, must fit
-    return yz_smem<T>(ny, nz, ny + 15) <= kRegSmemLimit && x_smem<T>(nx / 2, nx / 2 + 15) <=
-                                                              kRegSmemLimit;
+    // the x passes must fit; the (y, z) plane goes through shared memory whole when it fits, else in tiles
+    return x_smem<T>(nx / 2, nx / 2 + 15) <= kRegSmemLimit && y_smem<T>(ny, ny + 15) <= kRegSmemLimit;
 }
 
 template <typename T>
@@ -549,6 +762,23 @@ void RegFft<T>::configure(PoissonArgs<T>& a)
         if (w < best_w) { best_w = w; best = sp; }
     }
     a.reg_sp = best;
+    a.reg_tile = (yz_smem<T>(a.ny, a.nz, a.reg_sp) > kRegSmemLimit || std::getenv("VF_REG_TILE")) ? 1 : 0;
+    if (a.reg_tile) {
+        // y passes: the row slices of the groups; z tile: TB slots of one plane, columns as for the plane
+        best = -1; best_w = 1 << 30;
+        for (int pad = 0; pad < 16; ++pad) {
+            const int w = row_ways(a.gy, a.ny + pad, esz);
+            if (w < best_w) { best_w = w; best = a.ny + pad; }
+        }
+        a.reg_sy = best;
+        a.reg_tb = std::min(a.ny, 256 / a.gz);
+        best = -1; best_w = 1 << 30;
+        for (int pad = 0; pad < 16; ++pad) {
+            const int w = col_ways(a.gz, a.reg_tb + pad, esz);
+            if (w < best_w) { best_w = w; best = a.reg_tb + pad; }
+        }
+        a.reg_st = best;
+    }
     // x passes: the row slices of the groups
     best = -1; best_w = 1 << 30;
     for (int pad = 0; pad < 16; ++pad) {
@@ -574,6 +804,13 @@ cudaError_t RegFft<T>::prepare(const PoissonArgs<T>& a)
         default: return cudaErrorInvalidValue;
     }
     if (e != cudaSuccess) return e;
+    if (a.reg_tile) {
+        if ((e = prepare_tile<T, 1>(a)) != cudaSuccess) return e;
+        if ((e = prepare_tile<T, 2>(a)) != cudaSuccess) return e;
+        if ((e = prepare_tile<T, 4>(a)) != cudaSuccess) return e;
+        if ((e = prepare_tile<T, 8>(a)) != cudaSuccess) return e;
+        return prepare_tile<T, 16>(a);
+    }
     switch (a.gy) {
         case 1: return prepare_yz_z<T, 1>(a);
         case 2: return prepare_yz_z<T, 2>(a);
@@ -591,8 +828,17 @@ cudaError_t RegFft<T>::iteration(const PoissonArgs<T>& a, cudaStream_t st, const
     cudaError_t e;
     if ((e = dispatch_x<T>(a, true, st)) != cudaSuccess) return e;
     if (hook) (*hook)(VF_PHASE_FFT_X_FWD);
-    if ((e = dispatch_yz<T>(a, st)) != cudaSuccess) return e;
-    if (hook) (*hook)(VF_PHASE_FFT_YZ_SOLVE);
+    if (a.reg_tile) {
+        if ((e = dispatch_y<T>(a, false, st)) != cudaSuccess) return e;
+        if (hook) (*hook)(VF_PHASE_FFT_Y_FWD);
+        if ((e = dispatch_ztile<T>(a, st)) != cudaSuccess) return e;
+        if (hook) (*hook)(VF_PHASE_FFT_Z_SOLVE);
+        if ((e = dispatch_y<T>(a, true, st)) != cudaSuccess) return e;
+        if (hook) (*hook)(VF_PHASE_FFT_Y_INV);
+    } else {
+        if ((e = dispatch_yz<T>(a, st)) != cudaSuccess) return e;
+        if (hook) (*hook)(VF_PHASE_FFT_YZ_SOLVE);
+    }
     if ((e = dispatch_x<T>(a, false, st)) != cudaSuccess) return e;
     if (hook) (*hook)(VF_PHASE_FFT_X_INV);
     return cudaSuccess;

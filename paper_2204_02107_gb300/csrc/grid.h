@@ -35,6 +35,7 @@ struct vf_grid {
     bool plane_layout = false;
     // register path of the Poisson solve (PoissonArgs::reg and its shape), fixed at creation
     int reg = 0, reg_gx = 0, reg_gy = 0, reg_gz = 0, reg_sp = 0, reg_spx = 0, reg_sb = 0;
+    int reg_tile = 0, reg_sy = 0, reg_tb = 0, reg_st = 0;
     void* staging = nullptr;     // N * 8 bytes
     uint8_t* mask = nullptr;
     void* sval = nullptr;        // smooth forcing region values (Eq. 5 or caller's), N values of the precision

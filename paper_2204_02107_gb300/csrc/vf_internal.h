@@ -204,6 +204,10 @@ struct PoissonArgs {
     int reg_sp;               // complex stride between the z rows of the shared plane
     int reg_spx;              // complex stride between the rows of the x passes
     int reg_sb;               // unused (0)
+    int reg_tile;             // 1: y pass, z tile pass, y pass instead of the whole-plane kernel
+    int reg_sy;               // complex stride between the rows of the y passes (tile mode)
+    int reg_tb;               // y slots per z tile (tile mode)
+    int reg_st;               // complex stride between the z rows of a z tile (tile mode)
 };
 
 

@@ -27,17 +27,14 @@ def torch():
     return require_gpu()
 
 
-def eligible(shape, precision):
-    nx, ny, nz = shape
-    esz = 16 if precision == "fp64" else 8
-    return (nz * (ny + 15) + ny + nz) * esz <= 200 * 1024
-
-
+@pytest.mark.parametrize("mode", ["plane", "tile"])
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 @pytest.mark.parametrize("shape", SHAPES)
-def test_poisson_solve_all_g(torch, precision, shape):
-    if not eligible(shape, precision):
-        pytest.skip("plane exceeds shared memory in this precision (generic tile path)")
+def test_poisson_solve_all_g(torch, monkeypatch, precision, shape, mode):
+    """mode "plane": the whole (y, z) plane of a kx in shared memory where it fits (else tiles anyway);
+    "tile": y passes and z tiles forced."""
+    if mode == "tile":
+        monkeypatch.setenv("VF_REG_TILE", "1")
     nx, ny, nz = shape
     prm = F.Params(nx=nx, ny=ny, nz=nz, lx=nx * 0.1, ly=ny * 0.07, lz=nz * 0.13, nu=0.0, dt=1.0)
     rng = np.random.default_rng(nx * 7919 + ny * 31 + nz)
@@ -59,10 +56,14 @@ def test_poisson_solve_all_g(torch, precision, shape):
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_register_path_matches_generic_passes(torch, monkeypatch, precision):
-    """20 steps of a masked 128 x 64 x 32 room through both FFT implementations."""
+    """20 steps of a masked 128 x 64 x 32 room through the register passes (plane and tile mode) and the generic
+    ones."""
     room, prm, geom, st0 = room_case(128, 64, 32, boxes=[(30, 40, 10, 20, 2, 12), (70, 90, 30, 44, 2, 8)], seed=7)
     out = {}
-    for path in ("register", "generic"):
+    for path in ("register", "register_tile", "generic"):
+        monkeypatch.delenv("VF_REG_TILE", raising=False)
+        if path == "register_tile":
+            monkeypatch.setenv("VF_REG_TILE", "1")
         if path == "generic":
             monkeypatch.setenv("VF_GENERIC_FFT", "1")
         g = gpu_grid(prm, room.beta, room.S, room.room, precision)
@@ -72,5 +73,19 @@ def test_register_path_matches_generic_passes(torch, monkeypatch, precision):
         g.close()
     bar = 1e-12 if precision == "fp64" else 2e-5
     for n in FIELD_NAMES + ("p",):
-        a, b = out["register"][n], out["generic"][n]
-        assert rel_l2(a, b) < bar, n
+        for path in ("register", "register_tile"):
+            assert rel_l2(out[path][n], out["generic"][n]) < bar, (path, n)
+
+
+def test_masked_room_fp64_100_steps_tile_mode(torch, monkeypatch):
+    """The register path with y passes and z tiles (forced) against the oracle over 100 FP64 steps."""
+    from gpu_helpers import field_errors, read_state
+    monkeypatch.setenv("VF_REG_TILE", "1")
+    room, prm, geom, st0 = room_case(64, 32, 32, boxes=[(20, 26, 8, 14, 2, 12), (40, 46, 18, 26, 2, 9)])
+    ref, _ = F.run(st0.copy(), geom, prm, 100)
+    g = gpu_grid(prm, room.beta, room.S, room.room, "fp64")
+    load_state(g, st0, prm)
+    g.step(100)
+    errs = field_errors(read_state(g, prm), ref)
+    g.close()
+    assert max(errs.values()) < 1e-11, errs
