@@ -149,8 +149,17 @@ __global__ void __launch_bounds__(x_threads<T>()) k_reg_x_fwd(PoissonArgs<T> A)
 #pragma unroll
         for (int k2 = 0; k2 < GX; ++k2) rb[RegShape<GX>::slot(t, q, k2)] = v[q * GX + k2];
     __syncwarp();
-    if (!act) return;
-    C* __restrict__ spec = reinterpret_cast<C*>(A.spec) + row;
+    // the split results go straight to the plane layout (rows of a warp are consecutive), or, for rows of 256
+    // frequencies (two rows per warp, 16-byte pieces), through a frequency-major stage so that each frequency of
+    // the CTA's B rows leaves as one contiguous piece
+    constexpr bool STAGED = GX == 16;
+    constexpr int SB = B + 1;
+    C* stage = rowbuf + B * SPX;
+    C* __restrict__ spec = reinterpret_cast<C*>(A.spec) + (act ? row : 0);
+    auto put = [&](int k, C val) {
+        if (STAGED) stage[k * SB + b] = val;
+        else if (act) spec[(long long)k * rows] = val;
+    };
     // split step: X_k = E_k + W^k O_k from Z_k and conj Z_{M-k}; the pair (k, M - k) by one thread,
     // k = t + GX i for i = 0..8 (k = M / 2 only for t = 0)
 #pragma unroll
@@ -159,19 +168,28 @@ __global__ void __launch_bounds__(x_threads<T>()) k_reg_x_fwd(PoissonArgs<T> A)
         if (k > M / 2) break;
         const C Zk = rb[slot_of_freq<GX>(k)];
         if (k == 0) {
-            spec[0] = mk<C>(Zk.x + Zk.y, Zk.x - Zk.y);                  // (X_0, X_{nx/2})
+            put(0, mk<C>(Zk.x + Zk.y, Zk.x - Zk.y));                  // (X_0, X_{nx/2})
             continue;
         }
         const C Zm = rb[slot_of_freq<GX>(M - k)];
         {
             const C E = mk<C>(T(0.5) * (Zk.x + Zm.x), T(0.5) * (Zk.y - Zm.y));
             const C O = mk<C>(T(0.5) * (Zk.y + Zm.y), T(-0.5) * (Zk.x - Zm.x));
-            spec[(long long)k * rows] = cadd(E, cmul(twr[k], O));
+            put(k, cadd(E, cmul(twr[k], O)));
         }
         if (2 * k != M) {
             const C E = mk<C>(T(0.5) * (Zm.x + Zk.x), T(0.5) * (Zm.y - Zk.y));
             const C O = mk<C>(T(0.5) * (Zm.y + Zk.y), T(-0.5) * (Zm.x - Zk.x));
-            spec[(long long)(M - k) * rows] = cadd(E, cmul(twr[M - k], O));
+            put(M - k, cadd(E, cmul(twr[M - k], O)));
+        }
+    }
+    if (STAGED) {
+        __syncthreads();
+        C* out = reinterpret_cast<C*>(A.spec);
+        const int row0 = blockIdx.x * B;
+        for (int it = threadIdx.x; it < M * B; it += NT) {
+            const int k = it / B, bb = it - k * B;
+            if (row0 + bb < rows) out[(long long)k * rows + row0 + bb] = stage[k * SB + bb];
         }
     }
 }
@@ -194,9 +212,37 @@ __global__ void __launch_bounds__(x_threads<T>()) k_reg_x_inv(PoissonArgs<T> A)
     const int b = warp * P + gi;
     const int rows = A.ny * A.nz, row = blockIdx.x * B + b;
     const bool act = row < rows;
-    // the pairs (X_k, X_{M-k}) of this thread, k = t + GX i, all loads in flight together
+    // the pairs (X_k, X_{M-k}) of this thread, k = t + GX i: straight from the plane layout with all loads in
+    // flight together, or (rows of 256 frequencies) gathered first for the CTA's B rows into a frequency-major stage
+    constexpr bool STAGED = GX == 16;
+    constexpr int SB = B + 1;
+    C* stage = rowbuf + B * SPX;
     C xk[9], xm[9];
-    {
+    if (STAGED) {
+        const C* __restrict__ in = reinterpret_cast<const C*>(A.spec);
+        const int row0 = blockIdx.x * B;
+        for (int it0 = threadIdx.x; it0 < M * B; it0 += 8 * NT) {
+            C tmp[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int it = it0 + u * NT, k = it / B, bb = it - k * B;
+                tmp[u] = (it < M * B && row0 + bb < rows) ? in[(long long)k * rows + row0 + bb] : mk<C>(T(0), T(0));
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int it = it0 + u * NT, k = it / B, bb = it - k * B;
+                if (it < M * B) stage[k * SB + bb] = tmp[u];
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i <= 8; ++i) {
+            const int k = t + GX * i;
+            const bool ok = k <= M / 2;
+            xk[i] = ok ? stage[k * SB + b] : mk<C>(T(0), T(0));
+            xm[i] = ok && k > 0 ? stage[(M - k) * SB + b] : mk<C>(T(0), T(0));
+        }
+    } else {
         const C* __restrict__ spec = reinterpret_cast<const C*>(A.spec) + (act ? row : 0);
 #pragma unroll
         for (int i = 0; i <= 8; ++i) {
@@ -205,8 +251,8 @@ __global__ void __launch_bounds__(x_threads<T>()) k_reg_x_inv(PoissonArgs<T> A)
             xk[i] = ok ? spec[(long long)k * rows] : mk<C>(T(0), T(0));
             xm[i] = ok && k > 0 ? spec[(long long)(M - k) * rows] : mk<C>(T(0), T(0));
         }
+        __syncthreads();   // tables staged
     }
-    __syncthreads();   // tables staged
     C* rb = rowbuf + b * SPX;
     // join: Z'_k = (X_k + conj X_{M-k}) + i W^{-k} (X_k - conj X_{M-k})
 #pragma unroll
@@ -405,8 +451,11 @@ __global__ void __launch_bounds__(256) k_reg_y(PoissonArgs<T> A)
 // z pass: a CTA takes TB consecutive y slots of one kx plane and all z, staged as a shared tile [z][slot] with
 // coalesced loads; a group per column does the forward z FFT, the division by lambda N and the inverse z FFT in
 // registers, then the tile goes back.
+#ifndef VF_ZTILE_MIN_CTAS
+#define VF_ZTILE_MIN_CTAS 4
+#endif
 template <typename T, int GZ>
-__global__ void __launch_bounds__(256) k_reg_z_tile(PoissonArgs<T> A)
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? VF_ZTILE_MIN_CTAS : 2) k_reg_z_tile(PoissonArgs<T> A)
 {
     using C = typename CxT<T>::type;
     constexpr int NZ = 16 * GZ, P = 32 / GZ, QZ = 16 / GZ;
@@ -415,6 +464,7 @@ __global__ void __launch_bounds__(256) k_reg_z_tile(PoissonArgs<T> A)
     C* tile = reinterpret_cast<C*>(smem_raw);     // element (z, c) at z * ST + c
     C* twz = tile + (size_t)NZ * ST;
     const int tiles = ny / TB;
+    const int tb_shift = __ffs(TB) - 1;          // TB is a power of two
     const int kx = blockIdx.x / tiles, c0 = (blockIdx.x - kx * tiles) * TB;
     C* g = reinterpret_cast<C*>(A.spec) + (long long)kx * ny * NZ;
     const int n_el = NZ * TB, nt = blockDim.x;
@@ -424,7 +474,7 @@ __global__ void __launch_bounds__(256) k_reg_z_tile(PoissonArgs<T> A)
         for (int u = 0; u < 8; ++u) {
             const int i = i0 + u * nt;
             if (i < n_el) {
-                const int z = i / TB, c = i - z * TB;
+                const int z = i >> tb_shift, c = i & (TB - 1);
                 tmp[u] = g[(long long)z * ny + c0 + c];
             }
         }
@@ -432,7 +482,7 @@ __global__ void __launch_bounds__(256) k_reg_z_tile(PoissonArgs<T> A)
         for (int u = 0; u < 8; ++u) {
             const int i = i0 + u * nt;
             if (i < n_el) {
-                const int z = i / TB, c = i - z * TB;
+                const int z = i >> tb_shift, c = i & (TB - 1);
                 tile[z * ST + c] = tmp[u];
             }
         }
@@ -470,7 +520,7 @@ __global__ void __launch_bounds__(256) k_reg_z_tile(PoissonArgs<T> A)
         for (int u = 0; u < 8; ++u) {
             const int i = i0 + u * nt;
             if (i < n_el) {
-                const int z = i / TB, cc = i - z * TB;
+                const int z = i >> tb_shift, cc = i & (TB - 1);
                 tmp[u] = tile[z * ST + cc];
             }
         }
@@ -478,7 +528,7 @@ __global__ void __launch_bounds__(256) k_reg_z_tile(PoissonArgs<T> A)
         for (int u = 0; u < 8; ++u) {
             const int i = i0 + u * nt;
             if (i < n_el) {
-                const int z = i / TB, cc = i - z * TB;
+                const int z = i >> tb_shift, cc = i & (TB - 1);
                 g[(long long)z * ny + c0 + cc] = tmp[u];
             }
         }
@@ -554,7 +604,8 @@ template <typename T>
 size_t x_smem(int M, int spx)
 {
     const int B = x_threads<T>() / (M / 16);
-    return ((size_t)M + (M + 1) + (size_t)B * spx) * sizeof(typename CxT<T>::type);
+    const size_t stage = M == 256 ? (size_t)M * (B + 1) : 0;     // the frequency-major stage of 256-point rows
+    return ((size_t)M + (M + 1) + (size_t)B * spx + stage) * sizeof(typename CxT<T>::type);
 }
 
 template <typename T>
