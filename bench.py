@@ -169,10 +169,26 @@ def traffic_record(kernel, tiles):
     digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
     if digest != entry.get("source_sha256"):
         return None
-    if entry.get("tiles") is not None and entry["tiles"] != tiles:
-        return None
+    for key, value in (entry.get("tiles") or {}).items():
+        if tiles.get(key) != value:
+            return None
     scale = entry.get("scale_to_full", 1.0)
     return entry["dram_bytes_per_launch"] * scale
+
+
+def fp64_flop_record():
+    """FP64 floating-point operations per cell and step of the FP64 step (DADD + DMUL + 2 DFMA thread
+    instructions counted by ncu over one step of the 256x128x128 room), if counted on the current sources."""
+    path = os.path.join(ROOT, "profiles", "fp64_flops.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        rec = json.load(f)
+    for src, digest in rec.get("sources", {}).items():
+        full = os.path.join(ROOT, src)
+        if not os.path.exists(full) or hashlib.sha256(open(full, "rb").read()).hexdigest() != digest:
+            return None
+    return rec.get("flops_per_cell_step")
 
 
 def cpu_baseline_oracle(room, precision_note, steps=1):
@@ -538,7 +554,15 @@ def main():
     e64.record(stream)
     e64.synchronize()
     fp64_ms = s64.elapsed_time(e64)
+    # one more step inside an NVTX range: the range ncu's FP64 instruction count is taken over
+    torch.cuda.nvtx.range_push("fp64_step")
+    g64.step(1, reduce_every=1)
+    g64.sync()
+    torch.cuda.nvtx.range_pop()
     g64.close()
+    fp64_peak = native.measure_fp64_rate()
+    fp64_flops = fp64_flop_record()
+    fp64_achieved = None if fp64_flops is None else fp64_flops * cells / (fp64_ms / args.fp64_steps / 1e3) / 1e9
 
     e2e = e2e_run(room, "fp32", args.steps, stream)
     g.close()
@@ -569,7 +593,11 @@ def main():
                           "frac": step_gbs / peak, "peak_kind": peak_kind},
         "kernels": per_kernel,
         "fp64": {"value": cells * args.fp64_steps / (fp64_ms / 1e3) / 1e9, "unit": UNIT,
-                 "ms_per_step": fp64_ms / args.fp64_steps, "steps": args.fp64_steps, "tiles": tiles64},
+                 "ms_per_step": fp64_ms / args.fp64_steps, "steps": args.fp64_steps, "tiles": tiles64,
+                 "roofline": {"bound": "fp64_alu", "unit": "GFLOP/s", "achieved": fp64_achieved,
+                              "peak": fp64_peak, "peak_kind": "measured FP64 FMA rate of this device",
+                              "frac": None if fp64_achieved is None else fp64_achieved / fp64_peak,
+                              "flops_per_cell_step": fp64_flops}},
         "e2e": e2e,
         "gpu_launches": int(round(sum(n for _, n in phases.values()) / prof_steps)) * args.steps,
         "clocks": clocks.summary(),

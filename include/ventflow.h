@@ -362,6 +362,11 @@ int vf_particles_count(const vf_grid* g, int64_t* n);
  * (both caller-owned, not cleared).  Waits for completion. */
 int vf_profile_steps(vf_grid* g, int64_t n, int32_t reduce_every, double* phase_ms, int64_t* launches);
 
+/* Measurement helper (no counterpart in the paper): the device's FP64 fused multiply-add rate in GFLOP/s (2 flops
+ * per FMA), from eight independent FMA chains per thread on every SM, timed with CUDA events.  The FP64 form of the
+ * step is bound by this rate on GB300. */
+int vf_measure_fp64_rate(double* gflops);
+
 /* Name of a phase id ("stage1", "fft_z_solve", ...), or "unknown". */
 const char* vf_phase_name(int phase);
 

@@ -18,7 +18,7 @@ BUILD_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(HERE, "libventflow.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CUDA_SOURCES = ["flow_kernels.cu", "fft_kernels.cu", "fft_reg.cu", "particles.cu", "noalloc.cu"]
+CUDA_SOURCES = ["flow_kernels.cu", "fft_kernels.cu", "fft_reg.cu", "particles.cu", "noalloc.cu", "probe.cu"]
 HOST_SOURCES = ["capi.cpp", "batch.cpp", "metrics.cpp"]
 
 

@@ -127,6 +127,7 @@ _SIGNATURES = {
     "vf_phase_name": (C.c_char_p, [C.c_int]),
     "vf_status_string": (C.c_char_p, [C.c_int]),
     "vf_abi_sizes": (C.c_int, [C.POINTER(C.c_int64)]),
+    "vf_measure_fp64_rate": (C.c_int, [C.POINTER(C.c_double)]),
     "vf_set_inflow_field": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int]),
     "vf_set_force_region": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     "vf_region_force": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
@@ -516,6 +517,15 @@ class Grid:
         """Solve L p = f on the device (f, p: contiguous CUDA tensors in the grid's precision)."""
         self._check(lib().vf_poisson_solve(self._h, C.c_void_p(f.data_ptr()), C.c_void_p(p.data_ptr())),
                     "vf_poisson_solve")
+
+
+def measure_fp64_rate():
+    """FP64 FMA rate of the current device [GFLOP/s]."""
+    v = C.c_double()
+    rc = lib().vf_measure_fp64_rate(C.byref(v))
+    if rc != VF_OK:
+        raise VentflowError(rc, "vf_measure_fp64_rate")
+    return v.value
 
 
 def tile_cache_lookup(nx, ny, nz, precision="fp32"):
