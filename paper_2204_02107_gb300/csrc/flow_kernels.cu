@@ -93,6 +93,71 @@ __device__ __forceinline__ void sigma_flush(double s, unsigned long long* out)
 // k_c = beta [ -sum_j ih_j (F^+ - F^-) + alpha sum_j ih2_j (beta^+ (c^+ - c^0) - beta^- (c^0 - c^-))
 //              + S (cset - c^0) inv_tau ],  F^+ = beta^+ (U_j^0 c^0 + U_j^+ c^+) / 2 (face weight beta^0 beta^+,
 //              beta^0 is applied by the outer factor)
+// One cell of RK4 stage STAGE (the right-hand sides of Eqs. 2-3 above and the RK4 combine): from the centre q0, the
+// axis neighbours qm[j], qp[j] (j = x, y, z), the centre mask m0 and the neighbours' masks mm[j], mp[j]; reads the
+// cell's own q_n (and q2, q3 in stage 4) at index ic and leaves the stage output in o.
+template <typename T, int STAGE>
+__device__ __forceinline__ void stage_cell(const StageArgs<T>& a, const FlowConsts<T>& k, int ic, const T q0[4],
+                                           const T qm[3][4], const T qp[3][4], uint8_t m0, const uint8_t mm[3],
+                                           const uint8_t mp[3], T dt2, T dtf, T dt6, T inv_tau, T o[4])
+{
+    T qn[4], q2[4], q3[4];
+    if (STAGE >= 2) ld4(a.qn, ic, qn);
+    if (STAGE == 4) {   // read by their owner thread before it overwrites q2 with q* (in place, own cell only)
+        ld4(a.q2, ic, q2);
+        ld4(a.q3, ic, q3);
+    }
+    const T bm[3] = {beta_of<T>(mm[0]), beta_of<T>(mm[1]), beta_of<T>(mm[2])};
+    const T bp[3] = {beta_of<T>(mp[0]), beta_of<T>(mp[1]), beta_of<T>(mp[2])};
+    const T beta = beta_of<T>(m0);
+    const T S = (m0 & kBitS) ? (a.sval ? __ldg(a.sval + ic) : T(1)) : T(0);
+
+    T kq[4];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        T conv = T(0), diff = T(0);
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            conv += k.q4h[j] * ((qp[j][j] * qp[j][i] - qm[j][j] * qm[j][i]) + q0[j] * (qp[j][i] - qm[j][i]));
+            diff += k.ih2[j] * (qp[j][i] - T(2) * q0[i] + qm[j][i]);
+        }
+        kq[i] = beta * (-conv + k.nu * diff + S * (k.uset[i] - q0[i]) * inv_tau + k.bf[i]);
+    }
+    {
+        const T c0 = q0[3];
+        T conv = T(0), diff = T(0);
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const T uc0 = q0[j] * c0;
+            const T Fp = bp[j] * T(0.5) * (uc0 + qp[j][j] * qp[j][3]);
+            const T Fm = bm[j] * T(0.5) * (qm[j][j] * qm[j][3] + uc0);
+            conv += k.ih[j] * (Fp - Fm);
+            diff += k.ih2[j] * (bp[j] * (qp[j][3] - c0) - bm[j] * (c0 - qm[j][3]));
+        }
+        kq[3] = beta * (-conv + k.alpha * diff + S * (k.cset - c0) * inv_tau);
+    }
+
+    if (a.target && (m0 & kBitS)) {
+        // per-cell targets: the forcing above used targets of 0, add S beta target / tau_f
+        T t4[4];
+        ld4(a.target, ic, t4);
+        const T sb = beta * S * inv_tau;
+#pragma unroll
+        for (int f = 0; f < 4; ++f) kq[f] += sb * t4[f];
+    }
+
+    // RK4 combine, classic tableau (nodes 0, 1/2, 1/2, 1; weights 1/6, 1/3, 1/3, 1/6) with the stage states as
+    // the only registers: q2 = q_n + dt/2 k1, q3 = q_n + dt/2 k2, q4 = q_n + dt k3, so that
+    // q* = q_n + dt/6 (k1 + 2 k2 + 2 k3 + k4) = (q2 + 2 q3 + q4 - q_n) / 3 + dt/6 k4  (q4 is the stencil centre)
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+        if (STAGE == 1) o[f] = q0[f] + dt2 * kq[f];
+        else if (STAGE == 2) o[f] = qn[f] + dt2 * kq[f];
+        else if (STAGE == 3) o[f] = qn[f] + dtf * kq[f];
+        else o[f] = (q2[f] + T(2) * q3[f] + q0[f] - qn[f]) * k.third + dt6 * kq[f];
+    }
+}
+
 template <typename T, int STAGE, bool DYN>
 __global__ void __launch_bounds__(TX * TY)
 k_stage(StageArgs<T> a, FlowConsts<T> k)
@@ -147,64 +212,10 @@ k_stage(StageArgs<T> a, FlowConsts<T> k)
         ld4(a.qs, zb + rowp + x, qp[1]);
 #pragma unroll
         for (int f = 0; f < 4; ++f) { qm[2][f] = qzm[f]; qp[2][f] = qzp[f]; }
-        T qn[4], q2[4], q3[4];
-        if (STAGE >= 2) ld4(a.qn, ic, qn);
-        if (STAGE == 4) {   // read by their owner thread before it overwrites q2 with q* (in place, own cell only)
-            ld4(a.q2, ic, q2);
-            ld4(a.q3, ic, q3);
-        }
-        const uint8_t mxm = __ldg(a.mask + zb + rowc + xm), mxp = __ldg(a.mask + zb + rowc + xp);
-        const uint8_t mym = __ldg(a.mask + zb + rowm + x), myp = __ldg(a.mask + zb + rowp + x);
-        const T bm[3] = {beta_of<T>(mxm), beta_of<T>(mym), beta_of<T>(mzm)};
-        const T bp[3] = {beta_of<T>(mxp), beta_of<T>(myp), beta_of<T>(mzp)};
-        const T beta = beta_of<T>(m0);
-        const T S = (m0 & kBitS) ? (a.sval ? __ldg(a.sval + ic) : T(1)) : T(0);
-
-        T kq[4];
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            T conv = T(0), diff = T(0);
-#pragma unroll
-            for (int j = 0; j < 3; ++j) {
-                conv += k.q4h[j] * ((qp[j][j] * qp[j][i] - qm[j][j] * qm[j][i]) + q0[j] * (qp[j][i] - qm[j][i]));
-                diff += k.ih2[j] * (qp[j][i] - T(2) * q0[i] + qm[j][i]);
-            }
-            kq[i] = beta * (-conv + k.nu * diff + S * (k.uset[i] - q0[i]) * inv_tau + k.bf[i]);
-        }
-        {
-            const T c0 = q0[3];
-            T conv = T(0), diff = T(0);
-#pragma unroll
-            for (int j = 0; j < 3; ++j) {
-                const T uc0 = q0[j] * c0;
-                const T Fp = bp[j] * T(0.5) * (uc0 + qp[j][j] * qp[j][3]);
-                const T Fm = bm[j] * T(0.5) * (qm[j][j] * qm[j][3] + uc0);
-                conv += k.ih[j] * (Fp - Fm);
-                diff += k.ih2[j] * (bp[j] * (qp[j][3] - c0) - bm[j] * (c0 - qm[j][3]));
-            }
-            kq[3] = beta * (-conv + k.alpha * diff + S * (k.cset - c0) * inv_tau);
-        }
-
-        if (a.target && (m0 & kBitS)) {
-            // per-cell targets: the forcing above used targets of 0, add S beta target / tau_f
-            T t4[4];
-            ld4(a.target, ic, t4);
-            const T sb = beta * S * inv_tau;
-#pragma unroll
-            for (int f = 0; f < 4; ++f) kq[f] += sb * t4[f];
-        }
-
-        // RK4 combine, classic tableau (nodes 0, 1/2, 1/2, 1; weights 1/6, 1/3, 1/3, 1/6) with the stage states as
-        // the only registers: q2 = q_n + dt/2 k1, q3 = q_n + dt/2 k2, q4 = q_n + dt k3, so that
-        // q* = q_n + dt/6 (k1 + 2 k2 + 2 k3 + k4) = (q2 + 2 q3 + q4 - q_n) / 3 + dt/6 k4  (q4 is the stencil centre)
+        const uint8_t mm[3] = {__ldg(a.mask + zb + rowc + xm), __ldg(a.mask + zb + rowm + x), mzm};
+        const uint8_t mp[3] = {__ldg(a.mask + zb + rowc + xp), __ldg(a.mask + zb + rowp + x), mzp};
         T o[4];
-#pragma unroll
-        for (int f = 0; f < 4; ++f) {
-            if (STAGE == 1) o[f] = q0[f] + dt2 * kq[f];
-            else if (STAGE == 2) o[f] = qn[f] + dt2 * kq[f];
-            else if (STAGE == 3) o[f] = qn[f] + dtf * kq[f];
-            else o[f] = (q2[f] + T(2) * q3[f] + q0[f] - qn[f]) * k.third + dt6 * kq[f];
-        }
+        stage_cell<T, STAGE>(a, k, ic, q0, qm, qp, m0, mm, mp, dt2, dtf, dt6, inv_tau, o);
         st4(a.out, ic, o);
 #pragma unroll
         for (int f = 0; f < 4; ++f) { qzm[f] = q0[f]; q0[f] = qzp[f]; qzp[f] = qn2[f]; }
@@ -883,6 +894,15 @@ cudaError_t Kernels<T>::stage(int s, const StageArgs<T>& a, const FlowConsts<T>&
 {
     const dim3 g = flow_grid(k, kZcStage), b(TX, TY);
     const bool dyn = k.dyn != nullptr;
+    switch (s) {
+            case 1: dyn ? k_stage_ring<1, true><<<g, b, 0, st>>>(af, kf) : k_stage_ring<1, false><<<g, b, 0, st>>>(af, kf); break;
+            case 2: dyn ? k_stage_ring<2, true><<<g, b, 0, st>>>(af, kf) : k_stage_ring<2, false><<<g, b, 0, st>>>(af, kf); break;
+            case 3: dyn ? k_stage_ring<3, true><<<g, b, 0, st>>>(af, kf) : k_stage_ring<3, false><<<g, b, 0, st>>>(af, kf); break;
+            case 4: dyn ? k_stage_ring<4, true><<<g, b, 0, st>>>(af, kf) : k_stage_ring<4, false><<<g, b, 0, st>>>(af, kf); break;
+            default: return cudaErrorInvalidValue;
+        }
+        return cudaGetLastError();
+    }
     switch (s) {
         case 1: dyn ? k_stage<T, 1, true><<<g, b, 0, st>>>(a, k) : k_stage<T, 1, false><<<g, b, 0, st>>>(a, k); break;
         case 2: dyn ? k_stage<T, 2, true><<<g, b, 0, st>>>(a, k) : k_stage<T, 2, false><<<g, b, 0, st>>>(a, k); break;
