@@ -895,15 +895,6 @@ cudaError_t Kernels<T>::stage(int s, const StageArgs<T>& a, const FlowConsts<T>&
     const dim3 g = flow_grid(k, kZcStage), b(TX, TY);
     const bool dyn = k.dyn != nullptr;
     switch (s) {
-            case 1: dyn ? k_stage_ring<1, true><<<g, b, 0, st>>>(af, kf) : k_stage_ring<1, false><<<g, b, 0, st>>>(af, kf); break;
-            case 2: dyn ? k_stage_ring<2, true><<<g, b, 0, st>>>(af, kf) : k_stage_ring<2, false><<<g, b, 0, st>>>(af, kf); break;
-            case 3: dyn ? k_stage_ring<3, true><<<g, b, 0, st>>>(af, kf) : k_stage_ring<3, false><<<g, b, 0, st>>>(af, kf); break;
-            case 4: dyn ? k_stage_ring<4, true><<<g, b, 0, st>>>(af, kf) : k_stage_ring<4, false><<<g, b, 0, st>>>(af, kf); break;
-            default: return cudaErrorInvalidValue;
-        }
-        return cudaGetLastError();
-    }
-    switch (s) {
         case 1: dyn ? k_stage<T, 1, true><<<g, b, 0, st>>>(a, k) : k_stage<T, 1, false><<<g, b, 0, st>>>(a, k); break;
         case 2: dyn ? k_stage<T, 2, true><<<g, b, 0, st>>>(a, k) : k_stage<T, 2, false><<<g, b, 0, st>>>(a, k); break;
         case 3: dyn ? k_stage<T, 3, true><<<g, b, 0, st>>>(a, k) : k_stage<T, 3, false><<<g, b, 0, st>>>(a, k); break;
