@@ -210,6 +210,7 @@ cudaError_t enqueue_step_t(vf_grid* g, cudaStream_t st, bool with_reduce, const 
     }
     StageArgs<T> a{};
     a.mask = g->mask;
+    a.smask = g->smask;
     a.sval = g->smooth_s ? (const T*)g->sval : nullptr;
     a.target = g->has_target ? g->target : nullptr;
     a.qn = g->q;
@@ -422,7 +423,7 @@ size_t grid_bytes(const vf_grid_desc& d)
     FlowConsts<float> k{};
     k.nx = d.nx; k.ny = d.ny; k.nz = d.nz;
     const size_t nred = (size_t)Kernels<float>::reduce_blocks(k);
-    size_t b = 4 * r256(4 * N * esz) + 5 * r256(N * esz) + r256(N * 4) + r256(N * 8) + r256(N);
+    size_t b = 4 * r256(4 * N * esz) + 5 * r256(N * esz) + r256(N * 4) + r256(N * 8) + 2 * r256(N);
     b += r256(nred * vf::kRedSlots * 8) + r256((vf::kHistBins + 2) * 8) + r256(4) + r256(sizeof(vf_reduce));
     b += r256((size_t)d.history_capacity * sizeof(vf_reduce)) + r256(16) + r256(4) + r256(8);
     b += r256(sizeof(vf::DtCtl)) + r256(3 * sizeof(double));
@@ -521,6 +522,7 @@ int vf_create_grid(const vf_grid_desc* d, vf_grid** out)
     if (!(g->near_list = (int*)galloc(g, g->N * sizeof(int)))) return fail(VF_ENOMEM);
     if (!(g->staging = galloc(g, g->N * 8))) return fail(VF_ENOMEM);
     if (!(g->mask = (uint8_t*)galloc(g, g->N))) return fail(VF_ENOMEM);
+    if (!(g->smask = (uint8_t*)galloc(g, g->N))) return fail(VF_ENOMEM);
 
     {
         vf_tiles t{};
@@ -570,6 +572,7 @@ int vf_create_grid(const vf_grid_desc* d, vf_grid** out)
     if (rc != VF_OK) return fail(rc == VF_ECUDA ? VF_ECUDA : rc);
     // all-fluid mask, every cell in the room region
     if (vf::mask_fill(g->mask, vf::kBitBeta | vf::kBitRoom, g->N, g->stream) != cudaSuccess) return fail(VF_ECUDA);
+    if (vf::build_stencil_mask(g->mask, g->smask, d->nx, d->ny, d->nz, g->stream) != cudaSuccess) return fail(VF_ECUDA);
     if (cudaStreamSynchronize(g->stream) != cudaSuccess) return fail(VF_ECUDA);
     *out = g;
     return VF_OK;
@@ -620,6 +623,8 @@ int vf_set_mask(vf_grid* g, const uint8_t* beta, int mem)
     VF_CK(cudaMemcpyAsync(&solids, g->solid_count, sizeof(solids), cudaMemcpyDeviceToHost, g->stream));
     VF_CK(cudaStreamSynchronize(g->stream));
     g->has_solid = solids > 0;
+    VF_CK(vf::build_stencil_mask(g->mask, g->smask, g->d.nx, g->d.ny, g->d.nz, g->stream));
+    VF_CK(cudaStreamSynchronize(g->stream));
     g->mask_set = true;
     g->sigma_stale = true;   // the fields were re-masked
     drop_graphs(g);
@@ -635,6 +640,7 @@ int vf_set_inflow(vf_grid* g, const uint8_t* S, const double u_set[3], double c_
         const void* src = stage_input(g, S, g->N, mem, &rc);
         if (rc) return rc;
         VF_CK(vf::mask_merge(g->mask, (const uint8_t*)src, vf::kBitS, g->N, g->stream));
+        VF_CK(vf::build_stencil_mask(g->mask, g->smask, g->d.nx, g->d.ny, g->d.nz, g->stream));
         VF_CK(cudaStreamSynchronize(g->stream));
     }
     for (int j = 0; j < 3; ++j) g->uset[j] = u_set[j];
@@ -666,6 +672,7 @@ int vf_set_inflow_tanh(vf_grid* g, const double center[3], const double width[3]
     }
     if (g->fp64) VF_CK(Kernels<double>::tanh_source((double*)g->sval, g->mask, w, n[0], n[1], n[2], g->stream));
     else VF_CK(Kernels<float>::tanh_source((float*)g->sval, g->mask, w, n[0], n[1], n[2], g->stream));
+    VF_CK(vf::build_stencil_mask(g->mask, g->smask, n[0], n[1], n[2], g->stream));
     VF_CK(cudaStreamSynchronize(g->stream));
     for (int j = 0; j < 3; ++j) g->uset[j] = u_set[j];
     g->cset = c_set;
@@ -690,6 +697,7 @@ int vf_set_inflow_values(vf_grid* g, const void* S, int is_fp64, const double u_
         VF_CK(Kernels<float>::convert_in(src, is_fp64, g->sval, -1, g->N, 1.0, nullptr, g->stream));
         VF_CK(Kernels<float>::source_bits(g->mask, (const float*)g->sval, g->N, g->stream));
     }
+    VF_CK(vf::build_stencil_mask(g->mask, g->smask, g->d.nx, g->d.ny, g->d.nz, g->stream));
     VF_CK(cudaStreamSynchronize(g->stream));
     for (int j = 0; j < 3; ++j) g->uset[j] = u_set[j];
     g->cset = c_set;
@@ -717,6 +725,7 @@ int vf_set_inflow_field(vf_grid* g, const void* S, const void* targets, int is_f
         VF_CK(Kernels<float>::convert_in(src, is_fp64, g->sval, -1, g->N, 1.0, nullptr, g->stream));
         VF_CK(Kernels<float>::source_bits(g->mask, (const float*)g->sval, g->N, g->stream));
     }
+    VF_CK(vf::build_stencil_mask(g->mask, g->smask, g->d.nx, g->d.ny, g->d.nz, g->stream));
     for (int comp = 0; comp < 4; ++comp) {
         // one component at a time through the staging buffer (N values)
         VF_CK(cudaStreamSynchronize(g->stream));
@@ -1191,6 +1200,7 @@ int autotune_t(vf_grid* g, int reps, vf_tiles* best)
             auto launch = [&]() -> cudaError_t {
                 StageArgs<T> a{};
                 a.mask = g->mask;
+                a.smask = g->smask;
                 a.qn = g->q;
                 cudaError_t e = cudaSuccess;
                 switch (fam) {

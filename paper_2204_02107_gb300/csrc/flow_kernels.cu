@@ -94,12 +94,12 @@ __device__ __forceinline__ void sigma_flush(double s, unsigned long long* out)
 //              + S (cset - c^0) inv_tau ],  F^+ = beta^+ (U_j^0 c^0 + U_j^+ c^+) / 2 (face weight beta^0 beta^+,
 //              beta^0 is applied by the outer factor)
 // One cell of RK4 stage STAGE (the right-hand sides of Eqs. 2-3 above and the RK4 combine): from the centre q0, the
-// axis neighbours qm[j], qp[j] (j = x, y, z), the centre mask m0 and the neighbours' masks mm[j], mp[j]; reads the
-// cell's own q_n (and q2, q3 in stage 4) at index ic and leaves the stage output in o.
+// axis neighbours qm[j], qp[j] (j = x, y, z) and the cell's stencil mask sm (its beta and S, the neighbours' beta);
+// reads the cell's own q_n (and q2, q3 in stage 4) at index ic and leaves the stage output in o.
 template <typename T, int STAGE>
 __device__ __forceinline__ void stage_cell(const StageArgs<T>& a, const FlowConsts<T>& k, int ic, const T q0[4],
-                                           const T qm[3][4], const T qp[3][4], uint8_t m0, const uint8_t mm[3],
-                                           const uint8_t mp[3], T dt2, T dtf, T dt6, T inv_tau, T o[4])
+                                           const T qm[3][4], const T qp[3][4], uint8_t sm, T dt2, T dtf, T dt6,
+                                           T inv_tau, T o[4])
 {
     T qn[4], q2[4], q3[4];
     if (STAGE >= 2) ld4(a.qn, ic, qn);
@@ -107,10 +107,10 @@ __device__ __forceinline__ void stage_cell(const StageArgs<T>& a, const FlowCons
         ld4(a.q2, ic, q2);
         ld4(a.q3, ic, q3);
     }
-    const T bm[3] = {beta_of<T>(mm[0]), beta_of<T>(mm[1]), beta_of<T>(mm[2])};
-    const T bp[3] = {beta_of<T>(mp[0]), beta_of<T>(mp[1]), beta_of<T>(mp[2])};
-    const T beta = beta_of<T>(m0);
-    const T S = (m0 & kBitS) ? (a.sval ? __ldg(a.sval + ic) : T(1)) : T(0);
+    const T bm[3] = {(sm & kSmXm) ? T(1) : T(0), (sm & kSmYm) ? T(1) : T(0), (sm & kSmZm) ? T(1) : T(0)};
+    const T bp[3] = {(sm & kSmXp) ? T(1) : T(0), (sm & kSmYp) ? T(1) : T(0), (sm & kSmZp) ? T(1) : T(0)};
+    const T beta = (sm & kSmSelf) ? T(1) : T(0);
+    const T S = (sm & kSmS) ? (a.sval ? __ldg(a.sval + ic) : T(1)) : T(0);
 
     T kq[4];
 #pragma unroll
@@ -137,7 +137,7 @@ __device__ __forceinline__ void stage_cell(const StageArgs<T>& a, const FlowCons
         kq[3] = beta * (-conv + k.alpha * diff + S * (k.cset - c0) * inv_tau);
     }
 
-    if (a.target && (m0 & kBitS)) {
+    if (a.target && (sm & kSmS)) {
         // per-cell targets: the forcing above used targets of 0, add S beta target / tau_f
         T t4[4];
         ld4(a.target, ic, t4);
@@ -181,9 +181,9 @@ k_stage(StageArgs<T> a, FlowConsts<T> k)
     const int xm = wrap(x - 1, nx), xp = wrap(x + 1, nx);
     const int rowc = y * nx, rowm = wrap(y - 1, ny) * nx, rowp = wrap(y + 1, ny) * nx;
 
-    // z registers: the 4-vector and mask at z-1, z, z+1, and the prefetched plane z+2
+    // z registers: the 4-vector at z-1, z, z+1 and the prefetched plane z+2; the stencil mask at z and z+1
     T qzm[4], q0[4], qzp[4], qn2[4];
-    uint8_t mzm, m0, mzp, mn2 = 0;
+    uint8_t m0, mzp;
     {
         const int im = wrap(z0 - 1, nz) * plane + rowc + x;
         const int ic = z0 * plane + rowc + x;
@@ -191,19 +191,19 @@ k_stage(StageArgs<T> a, FlowConsts<T> k)
         ld4(a.qs, im, qzm);
         ld4(a.qs, ic, q0);
         ld4(a.qs, ip, qzp);
-        mzm = __ldg(a.mask + im);
-        m0 = __ldg(a.mask + ic);
-        mzp = __ldg(a.mask + ip);
+        m0 = __ldg(a.smask + ic);
+        mzp = __ldg(a.smask + ip);
     }
 #pragma unroll
     for (int f = 0; f < 4; ++f) qn2[f] = T(0);
     for (int z = z0; z < z1; ++z) {
         const int zb = z * plane;
         const int ic = zb + rowc + x;
+        uint8_t mn2 = 0;
         if (z + 1 < z1) {   // prefetch plane z+2 for the next iteration
             const int i2 = wrap(z + 2, nz) * plane + rowc + x;
             ld4(a.qs, i2, qn2);
-            mn2 = __ldg(a.mask + i2);
+            mn2 = __ldg(a.smask + i2);
         }
         T qm[3][4], qp[3][4];
         ld4(a.qs, zb + rowc + xm, qm[0]);
@@ -212,14 +212,11 @@ k_stage(StageArgs<T> a, FlowConsts<T> k)
         ld4(a.qs, zb + rowp + x, qp[1]);
 #pragma unroll
         for (int f = 0; f < 4; ++f) { qm[2][f] = qzm[f]; qp[2][f] = qzp[f]; }
-        const uint8_t mm[3] = {__ldg(a.mask + zb + rowc + xm), __ldg(a.mask + zb + rowm + x), mzm};
-        const uint8_t mp[3] = {__ldg(a.mask + zb + rowc + xp), __ldg(a.mask + zb + rowp + x), mzp};
         T o[4];
-        stage_cell<T, STAGE>(a, k, ic, q0, qm, qp, m0, mm, mp, dt2, dtf, dt6, inv_tau, o);
+        stage_cell<T, STAGE>(a, k, ic, q0, qm, qp, m0, dt2, dtf, dt6, inv_tau, o);
         st4(a.out, ic, o);
 #pragma unroll
         for (int f = 0; f < 4; ++f) { qzm[f] = q0[f]; q0[f] = qzp[f]; qzp[f] = qn2[f]; }
-        mzm = m0;
         m0 = mzp;
         mzp = mn2;
     }
@@ -811,6 +808,23 @@ __global__ void k_count_solid(const uint8_t* __restrict__ mask, size_t n, unsign
     if ((threadIdx.x & 31) == 0 && local) atomicAdd(count, local);
 }
 
+// stencil mask: own beta and S, and the beta of the six axis neighbours
+__global__ void k_build_smask(const uint8_t* __restrict__ mask, uint8_t* __restrict__ smask, int nx, int ny, int nz)
+{
+    const size_t n = (size_t)nx * ny * nz;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(i % nx), y = (int)((i / nx) % ny), z = (int)(i / ((size_t)nx * ny));
+        const size_t plane = (size_t)nx * ny, row = (size_t)y * nx, zb = (size_t)z * plane;
+        const uint8_t m = mask[i];
+        auto fl = [&](size_t j, uint8_t bit) { return (mask[j] & kBitBeta) ? bit : (uint8_t)0; };
+        uint8_t b = (uint8_t)(((m & kBitBeta) ? kSmSelf : 0) | ((m & kBitS) ? kSmS : 0));
+        b |= fl(zb + row + wrap(x - 1, nx), kSmXm) | fl(zb + row + wrap(x + 1, nx), kSmXp);
+        b |= fl(zb + (size_t)wrap(y - 1, ny) * nx + x, kSmYm) | fl(zb + (size_t)wrap(y + 1, ny) * nx + x, kSmYp);
+        b |= fl((size_t)wrap(z - 1, nz) * plane + row + x, kSmZm) | fl((size_t)wrap(z + 1, nz) * plane + row + x, kSmZp);
+        smask[i] = b;
+    }
+}
+
 // bit 3 of every cell: set when one of its six axis neighbours is solid (beta = 0)
 __global__ void k_mark_near_solid(uint8_t* mask, int nx, int ny, int nz)
 {
@@ -1023,6 +1037,12 @@ template <typename T>
 cudaError_t Kernels<T>::apply_mask(void* q4, const uint8_t* mask, size_t n, cudaStream_t st)
 {
     k_apply_mask4<T><<<elementwise_blocks(n), 256, 0, st>>>((T*)q4, mask, n);
+    return cudaGetLastError();
+}
+
+cudaError_t build_stencil_mask(const uint8_t* mask, uint8_t* smask, int nx, int ny, int nz, cudaStream_t st)
+{
+    k_build_smask<<<elementwise_blocks((size_t)nx * ny * nz), 256, 0, st>>>(mask, smask, nx, ny, nz);
     return cudaGetLastError();
 }
 

@@ -38,6 +38,7 @@ struct vf_grid {
     int reg_tile = 0, reg_sy = 0, reg_tb = 0, reg_st = 0;
     void* staging = nullptr;     // N * 8 bytes
     uint8_t* mask = nullptr;
+    uint8_t* smask = nullptr;    // stencil mask of the stage kernels (rebuilt whenever beta or S change)
     void* sval = nullptr;        // smooth forcing region values (Eq. 5 or caller's), N values of the precision
     bool smooth_s = false;       // the stage kernels take S from sval (else S = 1 on the S bit)
     void* target = nullptr;      // per-cell forcing targets (u, v, w, c) as a 4-vector array, allocated on first use

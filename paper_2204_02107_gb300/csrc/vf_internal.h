@@ -22,6 +22,11 @@ constexpr uint8_t kBitRoom = 4u;
 constexpr uint8_t kBitNearSolid = 8u;
 constexpr uint8_t kBitForce = 16u;   // cells whose immersed-boundary force vf_region_force sums
 
+// Stencil mask of the stage kernels: one byte per cell with its own beta and S bits and the beta of its six axis
+// neighbours, so a cell's stencil reads one byte instead of five.
+constexpr uint8_t kSmSelf = 1u, kSmS = 2u, kSmXm = 4u, kSmXp = 8u, kSmYm = 16u, kSmYp = 32u, kSmZm = 64u,
+                  kSmZp = 128u;
+
 // Constants of the flow kernels, in the compute precision T.
 // Kernel families with their own z-chunk (planes one CTA marches along z); the allowed range of a chunk.
 enum ZcKind { kZcStage = 0, kZcDiv = 1, kZcProject = 2, kZcFilter = 3, kZcKinds = 4 };
@@ -75,6 +80,7 @@ struct StageArgs {
     const void* q3;
     void* out;
     const uint8_t* mask;
+    const uint8_t* smask;   // stencil mask (kSm* bits)
     const T* sval;      // smooth forcing region S in [0, 1] at the cells whose S bit is set (nullptr: S = 1 there)
     const void* target; // per-cell forcing targets (u, v, w, c)_set as a 4-vector array (nullptr: the constants;
                         // when given, the constants are 0 and S beta target / tau_f is added at the S cells)
@@ -256,6 +262,9 @@ struct LaunchHook {
     void* ctx;
     void operator()(int phase) const { if (fn) fn(ctx, phase); }
 };
+
+// Stencil mask from the cell mask (beta and S bits of each cell and beta of its axis neighbours).
+cudaError_t build_stencil_mask(const uint8_t* mask, uint8_t* smask, int nx, int ny, int nz, cudaStream_t st);
 
 // Immersed-boundary force on the cells with the kBitForce bit (flow_kernels.cu): sum over them of the unmasked
 // momentum right-hand side (-convection + nu diffusion + forcing + body force - grad p) times dV, into acc[3].
