@@ -58,7 +58,7 @@ PHASE_BYTES_PER_CELL = {
 PHASE_KERNEL = {"stage1": "k_stage", "stage2": "k_stage", "stage3": "k_stage", "stage4": "k_stage",
                 "div": "k_div", "fft_x_fwd": "k_fft_x_fwd", "fft_x_inv": "k_fft_x_inv", "fft_y_fwd": "k_fft_y",
                 "fft_y_inv": "k_fft_y", "fft_z_solve": "k_fft_z_solve", "fft_yz_solve": "k_fft_yz_solve",
-                "project": "k_project", "filter": "k_filter", "reduce": "k_reduce"}
+                "project": "k_project", "filter": "k_filter", "reduce": "k_reduce_state"}
 # Model of one step with the kernels fused as far as the method allows (RK4 121F+9 with n = 4): the survey's
 # algorithmic minimum, used for the step-level roofline fraction.
 STEP_MODEL_BYTES_PER_CELL_FP32 = 121 * F32 + 9

@@ -175,6 +175,7 @@ vf::ReduceArgsDev reduce_args(const vf_grid* g)
 {
     vf::ReduceArgsDev r{};
     r.partial = g->red_partial;
+    r.div_partial = g->div_partial;
     r.hist_accum = g->hist_accum;
     r.done = g->red_done;
     r.out = g->red_out;
@@ -244,12 +245,17 @@ cudaError_t enqueue_step_t(vf_grid* g, cudaStream_t st, bool with_reduce, const 
         return e;
     mark(VF_PHASE_PROJECT);
     if (g->d.filter) {
-        // with the filter on, the reductions ride along in the filter kernel
+        // with the filter on, the filter records the divergence of its input (the projected velocity) and the
+        // flat reduction of the filtered state follows
         const vf::ReduceArgsDev ra = reduce_args(g);
-        if ((e = Kernels<T>::filter(g->qb, g->q, g->mask, k, with_reduce ? &ra : nullptr, 1, st, sigma_out)) !=
+        if ((e = Kernels<T>::filter(g->qb, g->q, g->mask, k, with_reduce ? &ra : nullptr, st, sigma_out)) !=
             cudaSuccess)
             return e;
         mark(VF_PHASE_FILTER);
+        if (with_reduce) {
+            if ((e = Kernels<T>::reduce_state(g->q, g->mask, k, ra, 1, g->nred, st)) != cudaSuccess) return e;
+            mark(VF_PHASE_REDUCE);
+        }
     } else if (with_reduce) {
         if ((e = Kernels<T>::reduce(g->q, g->mask, k, reduce_args(g), 1, st)) != cudaSuccess) return e;
         mark(VF_PHASE_REDUCE);
@@ -423,8 +429,11 @@ size_t grid_bytes(const vf_grid_desc& d)
     FlowConsts<float> k{};
     k.nx = d.nx; k.ny = d.ny; k.nz = d.nz;
     const size_t nred = (size_t)Kernels<float>::reduce_blocks(k);
+    k.zc[vf::kZcFilter] = vf::kZChunkMin;
+    const size_t ndiv = (size_t)Kernels<float>::filter_warps(k);
     size_t b = 4 * r256(4 * N * esz) + 5 * r256(N * esz) + r256(N * 4) + r256(N * 8) + 2 * r256(N);
-    b += r256(nred * vf::kRedSlots * 8) + r256((vf::kHistBins + 2) * 8) + r256(4) + r256(sizeof(vf_reduce));
+    b += r256(nred * vf::kRedSlots * 8) + r256(ndiv * 2 * 8) + r256((vf::kHistBins + 2) * 8) + r256(4) +
+         r256(sizeof(vf_reduce));
     b += r256((size_t)d.history_capacity * sizeof(vf_reduce)) + r256(16) + r256(4) + r256(8);
     b += r256(sizeof(vf::DtCtl)) + r256(3 * sizeof(double));
     b += r256(M * cpx) + r256(d.ny * cpx) + r256(d.nz * cpx) + r256((M + 1) * cpx);
@@ -533,6 +542,12 @@ int vf_create_grid(const vf_grid_desc* d, vf_grid** out)
     const FlowConsts<float> kf = flow_consts<float>(g);
     g->nred = Kernels<float>::reduce_blocks(kf);   // enough partial slots for the smallest filter chunk
     if (!(g->red_partial = (double*)galloc(g, (size_t)g->nred * vf::kRedSlots * sizeof(double)))) return fail(VF_ENOMEM);
+    {
+        FlowConsts<float> kmin = kf;   // the filter's divergence records under its smallest chunk
+        kmin.zc[vf::kZcFilter] = vf::kZChunkMin;
+        g->ndiv = Kernels<float>::filter_warps(kmin);
+    }
+    if (!(g->div_partial = (double*)galloc(g, (size_t)g->ndiv * 2 * sizeof(double)))) return fail(VF_ENOMEM);
     if (!(g->hist_accum = (unsigned long long*)galloc(g, (vf::kHistBins + 2) * sizeof(unsigned long long))))
         return fail(VF_ENOMEM);
     if (!(g->red_done = (unsigned int*)galloc(g, sizeof(unsigned int)))) return fail(VF_ENOMEM);
@@ -1172,8 +1187,9 @@ cudaError_t time_launches(cudaStream_t st, int reps, F&& launch, float* ms)
 }
 
 // Each family is timed on the grid's arrays exactly as a step launches it, except that every output goes to a
-// scratch array: stage states (qa, qb, acc), divergence (f), projection (qb, no step tick), filter (acc, its
-// reduction record and non-finite flag redirected into the staging buffer, no history).
+// scratch array: stage states (qa, qb, acc), divergence (f), projection (qb, no step tick), filter (acc, with its
+// divergence records, read only by a reduction launched after it); with the filter off the standalone reduction,
+// its record and non-finite flag redirected into the staging buffer, no history.
 template <typename T>
 int autotune_t(vf_grid* g, int reps, vf_tiles* best)
 {
@@ -1218,7 +1234,7 @@ int autotune_t(vf_grid* g, int reps, vf_tiles* best)
                         return Kernels<T>::project(g->qa, (const T*)g->p, g->qb, g->mask, nullptr, k, st);
                     default:
                         if (!g->d.filter) return Kernels<T>::reduce(g->qb, g->mask, k, ra, 0, st);
-                        return Kernels<T>::filter(g->qb, g->acc, g->mask, k, redirect ? &ra : nullptr, 0, st);
+                        return Kernels<T>::filter(g->qb, g->acc, g->mask, k, &ra, st);   // scratch records only
                 }
             };
             float ms = 0.f;

@@ -305,51 +305,79 @@ __global__ void __launch_bounds__(TX * TY) k_project(const void* __restrict__ qs
 }
 
 // ------------------------------------------------------------------------------------------------------------
-// Reductions (a11).  Each thread accumulates the cells it visits (CellStats): compensated (TwoSum) float sums for
-// the scalar inventories, plain per-thread sums of at most one z-chunk of values for energy and squared divergence, an
-// exact room-cell count, and the histogram as runs of equal bins (one shared atomic per run).  The CTA epilogue
-// combines the warps in float-float arithmetic, writes one FP64 partial per quantity, and the last CTA to finish
-// (atomic ticket) adds the partials in CTA order, so the result does not depend on scheduling.  A NaN or Inf in a
-// field propagates into the energy or the scalar total, which the last CTA checks.
+// Reductions (a11).  Each thread accumulates the cells it visits: compensated (TwoSum) sums for the scalar
+// inventories, plain per-thread sums of at most 64 terms for energy and squared divergence, an exact room-cell
+// count, and the histogram as runs of equal bins (shared atomics only when a run ends).  The CTA epilogue
+// combines the warps and writes one partial per quantity; the last CTA to finish (atomic ticket) adds the partials
+// in CTA order, so the result does not depend on scheduling.  A NaN or Inf in a field propagates into the energy
+// or the scalar total, which the last CTA checks.
+//
+// Partial sums are float-float pairs on an FP32 grid and doubles on an FP64 grid (Part): GB300 runs FP64 at 1/64
+// of the FP32 rate, so the FP32 path stays in float-float arithmetic (about 2^-44 of the sum, exact for counts)
+// up to the final values, which the last CTA converts to double once.
+//
+// With the filter on, the work is split in two launches: the filter records the divergence of its input (the
+// projected velocity) per warp (sum of d^2, max |d|), and k_reduce_state reads the filtered state once, flat and
+// coalesced, for everything else, folding the filter's divergence records in a fixed order.
 // ------------------------------------------------------------------------------------------------------------
 template <typename T>
-struct Acc {
-    T s, e;   // running sum and its compensation
-    __device__ void init() { s = T(0); e = T(0); }
-    __device__ void add(T v)
+struct Part {
+    T s, e;   // running sum and its compensation (a maximum sits in s with e = 0)
+    __device__ static Part of(T v) { return {v, T(0)}; }
+    __device__ void add(T v)   // one term, TwoSum
     {
         const T t = s + v;
         const T bp = t - s;
         e += (s - (t - bp)) + (v - bp);
         s = t;
     }
-    // warp-wide sum of the (s, e) pairs (float-float), every lane ends with the total
-    __device__ void warp_combine()
+    __device__ Part plus(Part b) const   // float-float sum of two pairs
     {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const T s2 = __shfl_xor_sync(0xffffffffu, s, o), e2 = __shfl_xor_sync(0xffffffffu, e, o);
-            const T t = s + s2;
-            const T bp = t - s;
-            e = e + e2 + ((s - (t - bp)) + (s2 - bp));
-            s = t;
-        }
+        const T t = s + b.s;
+        const T bp = t - s;
+        return {t, (e + b.e) + ((s - (t - bp)) + (b.s - bp))};
     }
+    __device__ Part maxw(Part b) const { return {fmax(s, b.s), T(0)}; }
     __device__ double value() const { return (double)s + (double)e; }
 };
 
 template <>
-struct Acc<double> {
-    double s, unused;
-    __device__ void init() { s = 0.0; unused = 0.0; }
+struct Part<double> {
+    double s;
+    __device__ static Part of(double v) { return {v}; }
     __device__ void add(double v) { s += v; }
-    __device__ void warp_combine()
-    {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    }
+    __device__ Part plus(Part b) const { return {s + b.s}; }
+    __device__ Part maxw(Part b) const { return {fmax(s, b.s)}; }
     __device__ double value() const { return s; }
 };
+static_assert(sizeof(Part<float>) == 8 && sizeof(Part<double>) == 8, "a partial fills one 8-byte slot");
+
+__device__ __forceinline__ Part<float> shfl_part(Part<float> p, int o)
+{
+    return {__shfl_xor_sync(0xffffffffu, p.s, o), __shfl_xor_sync(0xffffffffu, p.e, o)};
+}
+__device__ __forceinline__ Part<double> shfl_part(Part<double> p, int o)
+{
+    return {__shfl_xor_sync(0xffffffffu, p.s, o)};
+}
+__device__ __forceinline__ Part<float> ld_part(const Part<float>* p)
+{
+    const float2 v = __ldcg(reinterpret_cast<const float2*>(p));
+    return {v.x, v.y};
+}
+__device__ __forceinline__ Part<double> ld_part(const Part<double>* p)
+{
+    return {__ldcg(reinterpret_cast<const double*>(p))};
+}
+
+// warp-wide sum (fixed butterfly), every lane ends with the total
+template <typename T>
+__device__ __forceinline__ Part<T> warp_sum(Part<T> p)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) p = p.plus(shfl_part(p, o));
+    return p;
+}
 
 template <typename T>
 __device__ __forceinline__ T warp_maxT(T v)
@@ -359,24 +387,61 @@ __device__ __forceinline__ T warp_maxT(T v)
     return v;
 }
 
+// histogram bin of a room cell's scalar: kHistBins equal bins on [0, 1], then the counts below 0 and above 1
+template <typename T>
+__device__ __forceinline__ int hist_bin(T cc)
+{
+    return cc < T(0) ? kHistBins : (cc > T(1) ? kHistBins + 1 : min((int)(cc * T(kHistBins)), kHistBins - 1));
+}
+
+// One thread's counts of its two most recent histogram bins: a shared atomic only when a third bin displaces the
+// older one, so a scalar that alternates between two neighbouring bins (noise at a bin edge, or around 1 between
+// the top bin and the overflow count) costs no atomics, and the lanes of a warp, which usually share their bins,
+// do not serialise on the same counters cell after cell.
+struct HistRun {
+    int bin0, len0;   // most recent bin
+    int bin1, len1;
+    __device__ void init() { bin0 = bin1 = -1; len0 = len1 = 0; }
+    __device__ __forceinline__ void add(int b, int* hist)
+    {
+        if (b == bin0) {
+            ++len0;
+        } else if (b == bin1) {
+            const int l = len1 + 1;
+            bin1 = bin0; len1 = len0;
+            bin0 = b; len0 = l;
+        } else {
+            if (len1) atomicAdd(&hist[bin1], len1);
+            bin1 = bin0; len1 = len0;
+            bin0 = b; len0 = 1;
+        }
+    }
+    __device__ void flush(int* hist)
+    {
+        if (len0) atomicAdd(&hist[bin0], len0);
+        if (len1) atomicAdd(&hist[bin1], len1);
+    }
+};
+
+// Statistics of cells with their divergence (the standalone reductions, filter off)
 template <typename T>
 struct CellStats {
-    Acc<T> ct, cr, c2, ke, d2;
-    T dmax, umax;
-    int vr, run_bin, run_len;
+    Part<T> ct, cr, c2;
+    T ke, d2, dmax, umax;
+    int vr;
+    HistRun run;
     __device__ void init()
     {
-        ct.init(); cr.init(); c2.init(); ke.init(); d2.init();
-        dmax = umax = T(0);
+        ct = cr = c2 = Part<T>::of(T(0));
+        ke = d2 = dmax = umax = T(0);
         vr = 0;
-        run_bin = -1;
-        run_len = 0;
+        run.init();
     }
     // q: the cell's (u, v, w, c); d: its divergence; m: its mask byte
     __device__ __forceinline__ void add(const T q[4], T d, uint8_t m, int* hist)
     {
-        ke.s += q[0] * q[0] + q[1] * q[1] + q[2] * q[2];
-        d2.s += d * d;
+        ke += q[0] * q[0] + q[1] * q[1] + q[2] * q[2];
+        d2 += d * d;
         ct.add(q[3]);
         dmax = fmax(dmax, fabs(d));
         umax = fmax(umax, fmax(fabs(q[0]), fmax(fabs(q[1]), fabs(q[2]))));
@@ -385,64 +450,79 @@ struct CellStats {
             cr.add(cc);
             c2.add(cc * cc);
             ++vr;
-            const int bin = cc < T(0) ? kHistBins
-                          : (cc > T(1) ? kHistBins + 1 : min((int)(cc * T(kHistBins)), kHistBins - 1));
-            if (bin == run_bin) {
-                ++run_len;
-            } else {
-                if (run_len) atomicAdd(&hist[run_bin], run_len);
-                run_bin = bin;
-                run_len = 1;
-            }
+            run.add(hist_bin(cc), hist);
         }
     }
 };
 
+// Statistics of cells without their divergence (k_reduce_state): the scalar is summed over the room cells and the
+// other cells separately (one compensated sum per cell); the total is their sum.
+template <typename T>
+struct StateStats {
+    Part<T> cr, cn, c2;
+    T ke, umax;
+    int vr;
+    HistRun run;
+    __device__ void init()
+    {
+        cr = cn = c2 = Part<T>::of(T(0));
+        ke = umax = T(0);
+        vr = 0;
+        run.init();
+    }
+    __device__ __forceinline__ void add(const T q[4], uint8_t m, int* hist)
+    {
+        ke += q[0] * q[0] + q[1] * q[1] + q[2] * q[2];
+        umax = fmax(umax, fmax(fabs(q[0]), fmax(fabs(q[1]), fabs(q[2]))));
+        const T cc = q[3];
+        if (m & kBitRoom) {
+            cr.add(cc);
+            c2.add(cc * cc);
+            ++vr;
+            run.add(hist_bin(cc), hist);
+        } else {
+            cn.add(cc);
+        }
+    }
+};
+
+template <typename T>
 struct RedShared {
     int hist[kHistBins + 2];
     long long hist_total[kHistBins + 2];
-    double red[kRedSlots][TX * TY / 32];
+    Part<T> red[kRedSlots][TX * TY / 32];   // [quantity][warp]
+    double fin[kRedSlots];                  // final values (last CTA)
+    long long slot;                         // history slot of the record
     bool is_last;
 };
 
-__device__ __forceinline__ void red_init(RedShared& sh)
+template <typename T>
+__device__ __forceinline__ void red_init(RedShared<T>& sh)
 {
-    const int tid = threadIdx.y * TX + threadIdx.x;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     for (int i = tid; i < kHistBins + 2; i += TX * TY) sh.hist[i] = 0;
 }
 
-// CTA epilogue: every thread of the CTA calls it once (after red_init and a barrier)
-template <typename T>
-__device__ void red_finish(CellStats<T>& cs, RedShared& sh, const ReduceArgsDev& r, int to_history)
+// CTA epilogue after the warps have stored their values in sh.red[quantity][warp] and their histogram runs: the
+// CTA partials (quantity-major, partial[q * nblocks + cta]), the histogram counters, the ticket, and in the last
+// CTA the final sums and the record.  Quantities 0-5 are sums, 6-7 maxima.  SPLIT_C: slot 2 holds the scalar over
+// the non-room cells (total = slot 2 + slot 3).  Every thread of a CTA of TX * TY threads calls it once.
+template <typename T, bool SPLIT_C>
+__device__ void red_tail(RedShared<T>& sh, const ReduceArgsDev& r, int to_history)
 {
     constexpr int NW = TX * TY / 32;
     static_assert(NW == kRedSlots, "one warp per reduced quantity in the final pass");
-    const int tid = threadIdx.y * TX + threadIdx.x;
+    static_assert(TX * TY >= kHistBins + 2, "one thread per histogram counter in the final pass");
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     const int lane = tid & 31, wid = tid >> 5;
-    if (cs.run_len) atomicAdd(&sh.hist[cs.run_bin], cs.run_len);
-    Acc<T> vr{};
-    vr.init();
-    vr.s = T(cs.vr);
-    cs.ke.warp_combine(); cs.d2.warp_combine(); cs.ct.warp_combine(); cs.cr.warp_combine(); cs.c2.warp_combine();
-    vr.warp_combine();
-    const T dmax = warp_maxT(cs.dmax), umax = warp_maxT(cs.umax);
-    if (lane == 0) {
-        sh.red[0][wid] = cs.ke.value();
-        sh.red[1][wid] = cs.d2.value();
-        sh.red[2][wid] = cs.ct.value();
-        sh.red[3][wid] = cs.cr.value();
-        sh.red[4][wid] = cs.c2.value();
-        sh.red[5][wid] = vr.value();
-        sh.red[6][wid] = (double)dmax;
-        sh.red[7][wid] = (double)umax;
-    }
+    Part<T>* part = reinterpret_cast<Part<T>*>(r.partial);
     __syncthreads();
     const int nblocks = gridDim.x * gridDim.y * gridDim.z;
     const long long bid = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
     if (tid < kRedSlots) {
-        double v = sh.red[tid][0];
-        for (int i = 1; i < NW; ++i) v = (tid < 6) ? v + sh.red[tid][i] : fmax(v, sh.red[tid][i]);
-        r.partial[bid * kRedSlots + tid] = v;
+        Part<T> v = sh.red[tid][0];
+        for (int i = 1; i < NW; ++i) v = (tid < 6) ? v.plus(sh.red[tid][i]) : v.maxw(sh.red[tid][i]);
+        part[(long long)tid * nblocks + bid] = v;
     }
     for (int i = tid; i < kHistBins + 2; i += TX * TY)
         if (sh.hist[i]) atomicAdd(r.hist_accum + i, (unsigned long long)sh.hist[i]);
@@ -452,25 +532,40 @@ __device__ void red_finish(CellStats<T>& cs, RedShared& sh, const ReduceArgsDev&
     __syncthreads();
     if (!sh.is_last) return;
     __threadfence();
-    // last CTA: warp qq adds partial qq of every CTA in CTA order (fixed tree); histogram counters read and cleared
-    {
-        const int qq = wid;
-        double v = 0.0;
-        for (int b = lane; b < nblocks; b += 32) {
-            const double pv = __ldcg(r.partial + (long long)b * kRedSlots + qq);
-            v = (qq < 6) ? v + pv : fmax(v, pv);
-        }
-        Acc<double> acc{v, 0.0};
-        if (qq < 6) { acc.warp_combine(); v = acc.value(); }
-        else v = warp_maxT(v);
-        if (lane == 0) sh.red[qq][0] = v;
+    // last CTA: every load of the final pass is issued before the first sum.  Warp qq adds partial qq of every CTA
+    // in CTA order (lane l: CTAs l, l + 32, ...; then a fixed tree); the histogram counters are read and cleared.
+    long long step = 0, count = 0;
+    double t_end = 0.0, dt_dyn = 0.0;
+    if (tid == 0) {
+        step = *r.step_counter;
+        if (to_history) count = *r.hist_count;
+        if (r.dyn) { t_end = r.dyn->t_end; dt_dyn = r.dyn->dt; }
     }
-    for (int i = tid; i < kHistBins + 2; i += TX * TY)
-        sh.hist_total[i] = (long long)atomicExch(r.hist_accum + i, 0ull);
+    if (tid < kHistBins + 2) sh.hist_total[tid] = (long long)atomicExch(r.hist_accum + tid, 0ull);
+    {
+        constexpr int kInFlight = 16;
+        const int qq = wid;
+        const Part<T>* src = part + (long long)qq * nblocks;
+        Part<T> v = Part<T>::of(T(0));   // a sum starts from 0, and so does a maximum (of non-negative values)
+        for (int c0 = 0; c0 < nblocks; c0 += 32 * kInFlight) {
+            Part<T> pv[kInFlight];
+#pragma unroll
+            for (int u = 0; u < kInFlight; ++u) {
+                const int b = c0 + lane + 32 * u;
+                pv[u] = b < nblocks ? ld_part(src + b) : Part<T>::of(T(0));
+            }
+#pragma unroll
+            for (int u = 0; u < kInFlight; ++u) v = (qq < 6) ? v.plus(pv[u]) : v.maxw(pv[u]);
+        }
+        v = (qq < 6) ? warp_sum(v) : Part<T>::of(warp_maxT(v.s));
+        if (lane == 0) sh.fin[qq] = v.value();
+    }
     __syncthreads();
+    const double c_total = SPLIT_C ? sh.fin[2] + sh.fin[3] : sh.fin[2];
     // the record is written field by field by several threads (no per-thread copy of the whole struct)
-    const long long slot = to_history ? (*r.hist_count % r.history_capacity) : 0;
-    vf_reduce* outs[2] = {r.out, to_history ? r.history + slot : nullptr};
+    if (tid == 0) sh.slot = to_history ? count % r.history_capacity : 0;
+    __syncthreads();
+    vf_reduce* outs[2] = {r.out, to_history ? r.history + sh.slot : nullptr};
     for (int o = 0; o < 2; ++o) {
         vf_reduce* dst = outs[o];
         if (!dst) continue;
@@ -480,26 +575,49 @@ __device__ void red_finish(CellStats<T>& cs, RedShared& sh, const ReduceArgsDev&
             else dst->hist_over = sh.hist_total[i];
         }
         if (tid == 0) {
-            const long long step = *r.step_counter;
             dst->step = step;
-            dst->t = r.dyn ? r.dyn->t_end : r.t0 + (double)step * r.dt;
-            dst->dt = r.dyn ? r.dyn->dt : r.dt;
-            dst->ke = 0.5 * r.dV * sh.red[0][0];
-            dst->div_l2 = sqrt(r.dV * sh.red[1][0]);
-            dst->c_total = r.dV * sh.red[2][0];
-            dst->c_room = r.dV * sh.red[3][0];
-            dst->c2_room = r.dV * sh.red[4][0];
-            dst->v_room = r.dV * sh.red[5][0];
-            dst->div_max = sh.red[6][0];
-            dst->u_max = sh.red[7][0];
+            dst->t = r.dyn ? t_end : r.t0 + (double)step * r.dt;
+            dst->dt = r.dyn ? dt_dyn : r.dt;
+            dst->ke = 0.5 * r.dV * sh.fin[0];
+            dst->div_l2 = sqrt(r.dV * sh.fin[1]);
+            dst->c_total = r.dV * c_total;
+            dst->c_room = r.dV * sh.fin[3];
+            dst->c2_room = r.dV * sh.fin[4];
+            dst->v_room = r.dV * sh.fin[5];
+            dst->div_max = sh.fin[6];
+            dst->u_max = sh.fin[7];
         }
     }
     __syncthreads();
     if (tid == 0) {
-        if (!isfinite(sh.red[0][0]) || !isfinite(sh.red[2][0])) *r.nonfinite = 1;
-        if (to_history) *r.hist_count += 1;
+        if (!isfinite(sh.fin[0]) || !isfinite(c_total)) *r.nonfinite = 1;
+        if (to_history) *r.hist_count = count + 1;
         *r.done = 0u;
     }
+}
+
+// CTA epilogue of the standalone reductions: warp values of CellStats, then the common tail
+template <typename T>
+__device__ void red_finish(CellStats<T>& cs, RedShared<T>& sh, const ReduceArgsDev& r, int to_history)
+{
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    const int lane = tid & 31, wid = tid >> 5;
+    cs.run.flush(sh.hist);
+    const Part<T> ke = warp_sum(Part<T>::of(cs.ke)), d2 = warp_sum(Part<T>::of(cs.d2));
+    const Part<T> ct = warp_sum(cs.ct), cr = warp_sum(cs.cr), c2 = warp_sum(cs.c2);
+    const int vr = __reduce_add_sync(0xffffffffu, cs.vr);
+    const T dmax = warp_maxT(cs.dmax), umax = warp_maxT(cs.umax);
+    if (lane == 0) {
+        sh.red[0][wid] = ke;
+        sh.red[1][wid] = d2;
+        sh.red[2][wid] = ct;
+        sh.red[3][wid] = cr;
+        sh.red[4][wid] = c2;
+        sh.red[5][wid] = Part<T>::of((T)vr);   // at most 32 x 64 cells: exact
+        sh.red[6][wid] = Part<T>::of(dmax);
+        sh.red[7][wid] = Part<T>::of(umax);
+    }
+    red_tail<T, false>(sh, r, to_history);
 }
 
 // Standalone reductions of a state (filter off, or on demand): divergence of the state itself.
@@ -507,7 +625,7 @@ template <typename T>
 __global__ void __launch_bounds__(TX * TY) k_reduce(const void* __restrict__ q, const uint8_t* __restrict__ mask,
                                                     FlowConsts<T> k, ReduceArgsDev r, int to_history)
 {
-    __shared__ RedShared sh;
+    __shared__ RedShared<T> sh;
     red_init(sh);
     __syncthreads();
     CellStats<T> cs;
@@ -540,24 +658,97 @@ __global__ void __launch_bounds__(TX * TY) k_reduce(const void* __restrict__ q, 
     red_finish(cs, sh, r, to_history);
 }
 
+// Reductions of the filtered state (filter on): each CTA takes one contiguous chunk of cpt * kRedThreads cells
+// (cpt <= kRedMaxCellsPerThread cells per thread, consecutive threads on consecutive cells), the grid one full
+// wave of CTAs where that bound allows; plus the filter's per-warp divergence records (r.div_count of them, each
+// {sum d^2, max |d|}), folded by the threads in a fixed order.
+constexpr int kRedMaxCellsPerThread = 64;
+constexpr int kRedBatch = 4;
+constexpr int kRedThreads = TX * TY;
+
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads, sizeof(T) == 4 ? 4 : 2)
+k_reduce_state(const void* __restrict__ q, const uint8_t* __restrict__ mask, int n, int cpt, ReduceArgsDev r,
+               int to_history)
+{
+    __shared__ RedShared<T> sh;
+    red_init(sh);
+    __syncthreads();
+    StateStats<T> cs;
+    cs.init();
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, wid = tid >> 5;
+    const int base = blockIdx.x * (kRedThreads * cpt) + tid;
+    // batches of kRedBatch cells, software-pipelined: the loads of the next batch are issued before the current
+    // batch is accumulated (its histogram atomics would otherwise hold the loads back); a cell past the chunk or the
+    // grid reads as zeros outside the room, which adds nothing
+    auto load_batch = [&](int j0, T (&c4)[kRedBatch][4], uint8_t (&m)[kRedBatch]) {
+#pragma unroll
+        for (int u = 0; u < kRedBatch; ++u) {
+            const int i = base + (j0 + u) * kRedThreads;
+            if (j0 + u < cpt && i < n) {
+                ld4(q, i, c4[u]);
+                m[u] = __ldg(mask + i);
+            } else {
+                c4[u][0] = c4[u][1] = c4[u][2] = c4[u][3] = T(0);
+                m[u] = 0;
+            }
+        }
+    };
+    T cur[kRedBatch][4], nxt[kRedBatch][4];
+    uint8_t mcur[kRedBatch], mnxt[kRedBatch];
+    load_batch(0, cur, mcur);
+    for (int j0 = 0; j0 < cpt; j0 += kRedBatch) {
+        load_batch(j0 + kRedBatch, nxt, mnxt);
+#pragma unroll
+        for (int u = 0; u < kRedBatch; ++u) cs.add(cur[u], mcur[u], sh.hist);
+#pragma unroll
+        for (int u = 0; u < kRedBatch; ++u) {
+            mcur[u] = mnxt[u];
+#pragma unroll
+            for (int f = 0; f < 4; ++f) cur[u][f] = nxt[u][f];
+        }
+    }
+    // the filter's divergence records, folded in record order per thread
+    Part<T> d2 = Part<T>::of(T(0));
+    T dmax = T(0);
+    const Part<T>* rec = reinterpret_cast<const Part<T>*>(r.div_partial);
+    for (int j = blockIdx.x * kRedThreads + tid; j < r.div_count; j += gridDim.x * kRedThreads) {
+        d2 = d2.plus(ld_part(rec + 2 * (long long)j));
+        dmax = fmax(dmax, ld_part(rec + 2 * (long long)j + 1).s);
+    }
+    cs.run.flush(sh.hist);
+    const Part<T> ke = warp_sum(Part<T>::of(cs.ke));
+    const Part<T> cn = warp_sum(cs.cn), cr = warp_sum(cs.cr), c2 = warp_sum(cs.c2);
+    d2 = warp_sum(d2);
+    const int vr = __reduce_add_sync(0xffffffffu, cs.vr);
+    const T umax = warp_maxT(cs.umax);
+    dmax = warp_maxT(dmax);
+    if (lane == 0) {
+        sh.red[0][wid] = ke;
+        sh.red[1][wid] = d2;
+        sh.red[2][wid] = cn;
+        sh.red[3][wid] = cr;
+        sh.red[4][wid] = c2;
+        sh.red[5][wid] = Part<T>::of((T)vr);   // at most 32 x 64 cells: exact
+        sh.red[6][wid] = Part<T>::of(dmax);
+        sh.red[7][wid] = Part<T>::of(umax);
+    }
+    red_tail<T, true>(sh, r, to_history);
+}
+
 // ------------------------------------------------------------------------------------------------------------
 // Sixth-order filter q <- beta (q + pi^-6 sum_j S6_j q), S6 = (1, -6, 15, -20, 15, -6, 1) (a10, Eq. 6).
-// REDUCE: also the reductions (a11) of the filtered state, with the divergence of the projected velocity (the
-// filter's input: after the projection, before the filter), saving a separate pass over the fields.
+// DIVSTAT: also the divergence of the filter's input (the projected velocity, after the projection and before the
+// filter) for the reductions (a11): per warp the sum of d^2 and max |d| into r.div_partial, no CTA barrier.
 // ------------------------------------------------------------------------------------------------------------
-template <typename T, bool REDUCE, bool SIGMA>
-__global__ void __launch_bounds__(TX * TY, sizeof(T) == 4 ? (REDUCE ? 3 : 4) : 2)
+template <typename T, bool DIVSTAT, bool SIGMA>
+__global__ void __launch_bounds__(TX * TY, sizeof(T) == 4 ? 4 : 2)
 k_filter(const void* __restrict__ in, void* __restrict__ out, const uint8_t* __restrict__ mask, FlowConsts<T> k,
-         ReduceArgsDev r, int to_history, unsigned long long* sigma_out)
+         ReduceArgsDev r, unsigned long long* sigma_out)
 {
     T smax = T(0);   // SIGMA: Courant rate of the filtered velocity (the step's final state)
-    __shared__ RedShared sh;
-    if (REDUCE) {
-        red_init(sh);
-        __syncthreads();
-    }
-    CellStats<T> cs;
-    cs.init();
+    T d2 = T(0), dmax = T(0);
     const int x = blockIdx.x * TX + threadIdx.x;
     const int y = blockIdx.y * TY + threadIdx.y;
     if (x < k.nx && y < k.ny) {
@@ -595,7 +786,7 @@ k_filter(const void* __restrict__ in, void* __restrict__ out, const uint8_t* __r
                 ld4(in, zb + wrap(y + d, ny) * nx + x, e);
 #pragma unroll
                 for (int f = 0; f < 4; ++f) acc[f] += cf * ((a[f] + b[f]) + (c[f] + e[f]));
-                if (REDUCE && d == 1)
+                if (DIVSTAT && d == 1)
                     div = k.i2h[0] * (b[0] - a[0]) + k.i2h[1] * (e[1] - c[1]) + k.i2h[2] * (zw[4][2] - zw[2][2]);
             }
             const uint8_t m0 = __ldg(mask + ic);
@@ -604,12 +795,26 @@ k_filter(const void* __restrict__ in, void* __restrict__ out, const uint8_t* __r
 #pragma unroll
             for (int f = 0; f < 4; ++f) o[f] = beta * (zw[3][f] + k.filt * acc[f]);
             st4(out, ic, o);
-            if (REDUCE) cs.add(o, div, m0, sh.hist);
+            if (DIVSTAT) {
+                d2 += div * div;
+                dmax = fmax(dmax, fabs(div));
+            }
             if (SIGMA) smax = fmax(smax, sigma_cell(o[0], o[1], o[2], k.ih));
         }
     }
     if (SIGMA) sigma_flush((double)smax, sigma_out);
-    if (REDUCE) red_finish(cs, sh, r, to_history);
+    if (DIVSTAT) {
+        const Part<T> s = warp_sum(Part<T>::of(d2));
+        const T m = warp_maxT(dmax);
+        const int tid = threadIdx.y * TX + threadIdx.x;
+        if ((tid & 31) == 0) {
+            const long long bid = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
+            const long long w = bid * (TX * TY / 32) + (tid >> 5);
+            Part<T>* rec = reinterpret_cast<Part<T>*>(r.div_partial);
+            rec[2 * w] = s;
+            rec[2 * w + 1] = Part<T>::of(m);
+        }
+    }
 }
 
 // ------------------------------------------------------------------------------------------------------------
@@ -939,13 +1144,52 @@ cudaError_t Kernels<T>::project(const void* qstar, const T* p, void* out, const 
 
 template <typename T>
 cudaError_t Kernels<T>::filter(const void* in, void* out, const uint8_t* mask, const FlowConsts<T>& k,
-                               const ReduceArgsDev* r, int to_history, cudaStream_t st, unsigned long long* sigma)
+                               const ReduceArgsDev* r, cudaStream_t st, unsigned long long* sigma)
 {
     const dim3 g = flow_grid(k, kZcFilter), b(TX, TY);
-    if (r && sigma) k_filter<T, true, true><<<g, b, 0, st>>>(in, out, mask, k, *r, to_history, sigma);
-    else if (r) k_filter<T, true, false><<<g, b, 0, st>>>(in, out, mask, k, *r, to_history, nullptr);
-    else if (sigma) k_filter<T, false, true><<<g, b, 0, st>>>(in, out, mask, k, ReduceArgsDev{}, 0, sigma);
-    else k_filter<T, false, false><<<g, b, 0, st>>>(in, out, mask, k, ReduceArgsDev{}, 0, nullptr);
+    if (r && sigma) k_filter<T, true, true><<<g, b, 0, st>>>(in, out, mask, k, *r, sigma);
+    else if (r) k_filter<T, true, false><<<g, b, 0, st>>>(in, out, mask, k, *r, nullptr);
+    else if (sigma) k_filter<T, false, true><<<g, b, 0, st>>>(in, out, mask, k, ReduceArgsDev{}, sigma);
+    else k_filter<T, false, false><<<g, b, 0, st>>>(in, out, mask, k, ReduceArgsDev{}, nullptr);
+    return cudaGetLastError();
+}
+
+template <typename T>
+int Kernels<T>::filter_warps(const FlowConsts<T>& k)
+{
+    const dim3 g = flow_grid(k, kZcFilter);
+    return (int)(g.x * g.y * g.z) * (TX * TY / 32);
+}
+
+template <typename T>
+cudaError_t Kernels<T>::reduce_state(const void* q, const uint8_t* mask, const FlowConsts<T>& k, ReduceArgsDev r,
+                                     int to_history, int max_blocks, cudaStream_t st)
+{
+    // one full wave: SMs x resident CTAs (queried once per device), more waves only where a wave would give a
+    // thread more than kRedMaxCellsPerThread cells; never more CTAs than partial slots
+    static int wave[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!wave[dev]) {
+        int sms = 0, per_sm = 0;
+        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_reduce_state<T>, kRedThreads, 0)) !=
+            cudaSuccess)
+            return e;
+        wave[dev] = std::max(1, sms * std::max(1, per_sm));
+    }
+    const long long n = (long long)k.nx * k.ny * k.nz;
+    const long long rows = (n + kRedThreads - 1) / kRedThreads;   // cells per thread if there were one CTA
+    long long nb = wave[dev];
+    while (nb * kRedMaxCellsPerThread < rows) nb += wave[dev];
+    nb = std::min(nb, std::min(rows, (long long)max_blocks));
+    const int cpt = (int)((rows + nb - 1) / nb);
+    if (cpt > kRedMaxCellsPerThread) return cudaErrorInvalidValue;   // too few partial slots for this grid
+    nb = (rows + cpt - 1) / cpt;
+    r.div_count = filter_warps(k);
+    k_reduce_state<T><<<(unsigned)nb, kRedThreads, 0, st>>>(q, mask, (int)n, cpt, r, to_history);
     return cudaGetLastError();
 }
 
@@ -994,7 +1238,7 @@ cudaError_t adjust_dt(DtCtl* c, cudaStream_t st)
 template <typename T>
 int Kernels<T>::reduce_blocks(const FlowConsts<T>& k)
 {
-    // the most CTAs any allowed filter/reduce z-chunk launches: the smallest chunk
+    // the most CTAs any allowed filter/reduce z-chunk launches: the smallest chunk (k_reduce_state launches fewer)
     FlowConsts<T> c = k;
     c.zc[kZcFilter] = kZChunkMin;
     const dim3 g = flow_grid(c, kZcFilter);

@@ -55,6 +55,7 @@ struct vf_grid {
     int* krev_z = nullptr;
 
     double* red_partial = nullptr;
+    double* div_partial = nullptr;       // the filter's per-warp divergence records
     unsigned long long* hist_accum = nullptr;
     unsigned int* red_done = nullptr;
     vf_reduce* red_out = nullptr;
@@ -69,6 +70,7 @@ struct vf_grid {
     bool sigma_stale = true;             // the Courant rate of the current state must be recomputed
     unsigned long long* solid_count = nullptr;
     int nred = 0;
+    int ndiv = 0;
 
     int zc[vf::kZcKinds] = {4, 32, 8, 16};  // z-chunks (vf_tiles): stage, divergence, projection, filter
 

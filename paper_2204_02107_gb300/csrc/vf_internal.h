@@ -240,7 +240,9 @@ constexpr int kPlaneThreads = 512;
 
 // Reduction scratch: per-CTA partial sums and histogram counts, and the output records.
 struct ReduceArgsDev {
-    double* partial;          // [nblocks * kRedSlots]
+    double* partial;          // [kRedSlots * nblocks], quantity-major
+    double* div_partial;      // the filter's divergence records, {sum d^2, max |d|} per warp
+    int div_count;            // records k_reduce_state folds (set by its launcher)
     unsigned long long* hist_accum;   // [kHistBins + 2], zero between launches
     unsigned int* done;       // CTAs finished in the current launch, zero between launches
     vf_reduce* out;           // single record (vf_reductions)
@@ -310,10 +312,14 @@ struct Kernels {
     // sigma != nullptr: also the Courant rate of the written velocity into *sigma (atomic max of double bits)
     static cudaError_t project(const void* qstar, const T* p, void* out, const uint8_t* mask, long long* step_counter,
                                const FlowConsts<T>& k, cudaStream_t st, unsigned long long* sigma = nullptr);
-    // r != nullptr: also record the reductions of the filtered state (divergence of the projected velocity)
+    // r != nullptr: also the divergence records of the projected velocity (r->div_partial) for reduce_state
     static cudaError_t filter(const void* in, void* out, const uint8_t* mask, const FlowConsts<T>& k,
-                              const ReduceArgsDev* r, int to_history, cudaStream_t st,
-                              unsigned long long* sigma = nullptr);
+                              const ReduceArgsDev* r, cudaStream_t st, unsigned long long* sigma = nullptr);
+    static int filter_warps(const FlowConsts<T>& k);   // divergence records one filter launch writes
+    // reductions of the filtered state q with the divergence records of the filter launched before it with the same
+    // k; max_blocks: the partial slots of r (reduce_blocks)
+    static cudaError_t reduce_state(const void* q, const uint8_t* mask, const FlowConsts<T>& k, ReduceArgsDev r,
+                                    int to_history, int max_blocks, cudaStream_t st);
     // Eq. 5 window into the smooth forcing values and the mask's S bits (S > 0)
     static cudaError_t tanh_source(T* sval, uint8_t* mask, const TanhWindow& w, int nx, int ny, int nz,
                                    cudaStream_t st);
