@@ -7,6 +7,7 @@
 
 #include <cstdint>
 
+#include "launch.cuh"
 #include "vf_internal.h"
 
 namespace vf {

@@ -106,6 +106,7 @@ __device__ void fft_run(const FftAxis& ax, int nseq, int es, int ss, const C* tw
 template <typename T>
 __global__ void __launch_bounds__(256) k_poisson_correction(PoissonArgs<T> A, int first)
 {
+    pdl_enter();
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < A.n_near; j += gridDim.x * blockDim.x) {
         const int i = __ldg(A.near_list + j);
         const int t = (int)fdiv((uint32_t)i, A.nx_div), x = i - t * A.nx;
@@ -125,6 +126,7 @@ __global__ void __launch_bounds__(256) k_poisson_correction(PoissonArgs<T> A, in
 template <typename T>
 __global__ void __launch_bounds__(256) k_fft_x_fwd(PoissonArgs<T> A)
 {
+    pdl_enter();
     using C = typename CxT<T>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int M = A.M, B = A.rows_per_block;
@@ -174,6 +176,7 @@ __global__ void __launch_bounds__(256) k_fft_x_fwd(PoissonArgs<T> A)
 template <typename T, bool INV, int TB>
 __global__ void __launch_bounds__(256) k_fft_y(PoissonArgs<T> A)
 {
+    pdl_enter();
     using C = typename CxT<T>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int n = A.ny, M = A.M;
@@ -198,6 +201,7 @@ __global__ void __launch_bounds__(256) k_fft_y(PoissonArgs<T> A)
 template <typename T, int TB>
 __global__ void __launch_bounds__(256) k_fft_z_solve(PoissonArgs<T> A)
 {
+    pdl_enter();
     using C = typename CxT<T>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int n = A.nz, M = A.M, ny = A.ny;
@@ -240,6 +244,7 @@ __global__ void __launch_bounds__(256) k_fft_z_solve(PoissonArgs<T> A)
 template <typename T>
 __global__ void __launch_bounds__(256) k_fft_x_inv(PoissonArgs<T> A)
 {
+    pdl_enter();
     using C = typename CxT<T>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int M = A.M, B = A.rows_per_block;
@@ -368,6 +373,7 @@ __device__ void inplace_fft(C* buf, const FftAxis& ax, int nseq, const FastDiv& 
 template <typename T>
 __global__ void __launch_bounds__(kPlaneThreads) k_fft_yz_solve(PoissonArgs<T> A)
 {
+    pdl_enter();
     using C = typename CxT<T>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int ny = A.ny, nz = A.nz, n_el = ny * nz;
@@ -493,7 +499,9 @@ cudaError_t Kernels<T>::poisson_iteration(const PoissonArgs<T>& a, int first, cu
 {
     if (a.n_near > 0) {
         const int gb = (a.n_near + 255) / 256;
-        k_poisson_correction<T><<<gb < 4096 ? gb : 4096, 256, 0, st>>>(a, first);
+        const cudaError_t e = launch_pdl(k_poisson_correction<T>, dim3(gb < 4096 ? gb : 4096), dim3(256), 0, st, a,
+                                         first);
+        if (e != cudaSuccess) return e;
         if (hook) (*hook)(VF_PHASE_POISSON_RHS);
     }
     if (a.reg) return RegFft<T>::iteration(a, st, hook);
@@ -502,24 +510,27 @@ cudaError_t Kernels<T>::poisson_iteration(const PoissonArgs<T>& a, int first, cu
     const size_t sx = fft_smem_x(a);
     const int rows = a.ny * a.nz;
     const int gx = (rows + a.rows_per_block - 1) / a.rows_per_block;
-    k_fft_x_fwd<T><<<gx, 256, sx, st>>>(a);
+    cudaError_t e;
+    if ((e = launch_pdl(k_fft_x_fwd<T>, dim3(gx), dim3(256), sx, st, a)) != cudaSuccess) return e;
     if (hook) (*hook)(VF_PHASE_FFT_X_FWD);
     if (a.plane_layout) {
-        k_fft_yz_solve<T><<<a.M, kPlaneThreads, fft_smem_plane(a), st>>>(a);
+        if ((e = launch_pdl(k_fft_yz_solve<T>, dim3(a.M), dim3(kPlaneThreads), fft_smem_plane(a), st, a)) !=
+            cudaSuccess)
+            return e;
         if (hook) (*hook)(VF_PHASE_FFT_YZ_SOLVE);
     } else {
         const size_t sy = fft_smem_yz(a, a.ny, 2), sz = fft_smem_yz(a, a.nz, 3);
         const int gc = (a.M + TB - 1) / TB;
-        k_fft_y<T, false, TB><<<dim3(gc, a.nz), 256, sy, st>>>(a);
+        if ((e = launch_pdl(k_fft_y<T, false, TB>, dim3(gc, a.nz), dim3(256), sy, st, a)) != cudaSuccess) return e;
         if (hook) (*hook)(VF_PHASE_FFT_Y_FWD);
-        k_fft_z_solve<T, TB><<<dim3(gc, a.ny), 256, sz, st>>>(a);
+        if ((e = launch_pdl(k_fft_z_solve<T, TB>, dim3(gc, a.ny), dim3(256), sz, st, a)) != cudaSuccess) return e;
         if (hook) (*hook)(VF_PHASE_FFT_Z_SOLVE);
-        k_fft_y<T, true, TB><<<dim3(gc, a.nz), 256, sy, st>>>(a);
+        if ((e = launch_pdl(k_fft_y<T, true, TB>, dim3(gc, a.nz), dim3(256), sy, st, a)) != cudaSuccess) return e;
         if (hook) (*hook)(VF_PHASE_FFT_Y_INV);
     }
-    k_fft_x_inv<T><<<gx, 256, sx, st>>>(a);
+    if ((e = launch_pdl(k_fft_x_inv<T>, dim3(gx), dim3(256), sx, st, a)) != cudaSuccess) return e;
     if (hook) (*hook)(VF_PHASE_FFT_X_INV);
-    return cudaGetLastError();
+    return cudaSuccess;
 }
 
 template cudaError_t Kernels<float>::poisson_prepare(const PoissonArgs<float>&);

@@ -118,6 +118,7 @@ template <typename T> __host__ __device__ constexpr int yz_threads() { return si
 template <typename T, int GX>
 __global__ void __launch_bounds__(x_threads<T>()) k_reg_x_fwd(PoissonArgs<T> A)
 {
+    pdl_enter();
     using C = typename CxT<T>::type;
     constexpr int M = 16 * GX, NT = x_threads<T>(), B = NT / GX, P = 32 / GX, Q = 16 / GX;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -198,6 +199,7 @@ __global__ void __launch_bounds__(x_threads<T>()) k_reg_x_fwd(PoissonArgs<T> A)
 template <typename T, int GX>
 __global__ void __launch_bounds__(x_threads<T>()) k_reg_x_inv(PoissonArgs<T> A)
 {
+    pdl_enter();
     using C = typename CxT<T>::type;
     constexpr int M = 16 * GX, NT = x_threads<T>(), B = NT / GX, P = 32 / GX, Q = 16 / GX;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -298,6 +300,7 @@ __global__ void __launch_bounds__(x_threads<T>()) k_reg_x_inv(PoissonArgs<T> A)
 template <typename T, int GY, int GZ>
 __global__ void __launch_bounds__(yz_threads<T>()) k_reg_yz_solve(PoissonArgs<T> A)
 {
+    pdl_enter();
     using C = typename CxT<T>::type;
     constexpr int NY = 16 * GY, NZ = 16 * GZ, QY = 16 / GY, QZ = 16 / GZ;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -406,6 +409,7 @@ __device__ __forceinline__ int freq_of_slot_rt(int s, int g)
 template <typename T, int GY, bool INV>
 __global__ void __launch_bounds__(256) k_reg_y(PoissonArgs<T> A)
 {
+    pdl_enter();
     using C = typename CxT<T>::type;
     constexpr int NY = 16 * GY, B = 256 / GY, P = 32 / GY, Q = 16 / GY;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -457,6 +461,7 @@ __global__ void __launch_bounds__(256) k_reg_y(PoissonArgs<T> A)
 template <typename T, int GZ>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? VF_ZTILE_MIN_CTAS : 2) k_reg_z_tile(PoissonArgs<T> A)
 {
+    pdl_enter();
     using C = typename CxT<T>::type;
     constexpr int NZ = 16 * GZ, P = 32 / GZ, QZ = 16 / GZ;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -636,9 +641,7 @@ cudaError_t launch_y(const PoissonArgs<T>& a, bool inv, cudaStream_t st)
     const long long rows = (long long)a.M * a.nz;
     const unsigned grid = (unsigned)((rows + B - 1) / B);
     const size_t sm = y_smem<T>(16 * GY, a.reg_sy);
-    if (inv) k_reg_y<T, GY, true><<<grid, 256, sm, st>>>(a);
-    else k_reg_y<T, GY, false><<<grid, 256, sm, st>>>(a);
-    return cudaGetLastError();
+    return launch_pdl(inv ? k_reg_y<T, GY, true> : k_reg_y<T, GY, false>, dim3(grid), dim3(256), sm, st, a);
 }
 
 template <typename T>
@@ -658,8 +661,7 @@ template <typename T, int GZ>
 cudaError_t launch_ztile(const PoissonArgs<T>& a, cudaStream_t st)
 {
     const unsigned grid = (unsigned)(a.M * (a.ny / a.reg_tb));
-    k_reg_z_tile<T, GZ><<<grid, a.reg_tb * GZ, ztile_smem<T>(16 * GZ, a.reg_st), st>>>(a);
-    return cudaGetLastError();
+    return launch_pdl(k_reg_z_tile<T, GZ>, dim3(grid), dim3(a.reg_tb * GZ), ztile_smem<T>(16 * GZ, a.reg_st), st, a);
 }
 
 template <typename T>
@@ -682,9 +684,7 @@ cudaError_t launch_x(const PoissonArgs<T>& a, bool fwd, cudaStream_t st)
     const int rows = a.ny * a.nz;
     const unsigned grid = (unsigned)((rows + B - 1) / B);
     const size_t sm = x_smem<T>(16 * GX, a.reg_spx);
-    if (fwd) k_reg_x_fwd<T, GX><<<grid, x_threads<T>(), sm, st>>>(a);
-    else k_reg_x_inv<T, GX><<<grid, x_threads<T>(), sm, st>>>(a);
-    return cudaGetLastError();
+    return launch_pdl(fwd ? k_reg_x_fwd<T, GX> : k_reg_x_inv<T, GX>, dim3(grid), dim3(x_threads<T>()), sm, st, a);
 }
 
 template <typename T>
@@ -705,8 +705,7 @@ cudaError_t launch_yz(const PoissonArgs<T>& a, cudaStream_t st)
 {
     const int want = (16 * GY) * (16 * GZ) / 16;
     const int threads = want < 32 ? 32 : (want > yz_threads<T>() ? yz_threads<T>() : want);
-    k_reg_yz_solve<T, GY, GZ><<<a.M, threads, yz_smem<T>(a.ny, a.nz, a.reg_sp), st>>>(a);
-    return cudaGetLastError();
+    return launch_pdl(k_reg_yz_solve<T, GY, GZ>, dim3(a.M), dim3(threads), yz_smem<T>(a.ny, a.nz, a.reg_sp), st, a);
 }
 
 template <typename T, int GY>

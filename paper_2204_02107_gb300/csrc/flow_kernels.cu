@@ -11,7 +11,9 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <cstdlib>
 
+#include "launch.cuh"
 #include "vf_internal.h"
 
 namespace vf {
@@ -162,6 +164,7 @@ template <typename T, int STAGE, bool DYN>
 __global__ void __launch_bounds__(TX * TY)
 k_stage(StageArgs<T> a, FlowConsts<T> k)
 {
+    pdl_enter();
     const int x = blockIdx.x * TX + threadIdx.x;
     const int y = blockIdx.y * TY + threadIdx.y;
     if (x >= k.nx || y >= k.ny) return;
@@ -228,6 +231,7 @@ k_stage(StageArgs<T> a, FlowConsts<T> k)
 template <typename T, bool DYN>
 __global__ void __launch_bounds__(TX * TY) k_div(const void* __restrict__ q, T* __restrict__ r, FlowConsts<T> k)
 {
+    pdl_enter();
     const int x = blockIdx.x * TX + threadIdx.x;
     const int y = blockIdx.y * TY + threadIdx.y;
     if (x >= k.nx || y >= k.ny) return;
@@ -265,6 +269,7 @@ __global__ void __launch_bounds__(TX * TY) k_project(const void* __restrict__ qs
                                                      long long* step_counter, FlowConsts<T> k,
                                                      unsigned long long* sigma_out)
 {
+    pdl_enter();
     if (step_counter && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0 &&
         threadIdx.y == 0)
         *step_counter += 1;
@@ -625,6 +630,7 @@ template <typename T>
 __global__ void __launch_bounds__(TX * TY) k_reduce(const void* __restrict__ q, const uint8_t* __restrict__ mask,
                                                     FlowConsts<T> k, ReduceArgsDev r, int to_history)
 {
+    pdl_enter();
     __shared__ RedShared<T> sh;
     red_init(sh);
     __syncthreads();
@@ -671,6 +677,7 @@ __global__ void __launch_bounds__(kRedThreads, sizeof(T) == 4 ? 4 : 2)
 k_reduce_state(const void* __restrict__ q, const uint8_t* __restrict__ mask, int n, int cpt, ReduceArgsDev r,
                int to_history)
 {
+    pdl_enter();
     __shared__ RedShared<T> sh;
     red_init(sh);
     __syncthreads();
@@ -747,6 +754,7 @@ __global__ void __launch_bounds__(TX * TY, sizeof(T) == 4 ? 4 : 2)
 k_filter(const void* __restrict__ in, void* __restrict__ out, const uint8_t* __restrict__ mask, FlowConsts<T> k,
          ReduceArgsDev r, unsigned long long* sigma_out)
 {
+    pdl_enter();
     T smax = T(0);   // SIGMA: Courant rate of the filtered velocity (the step's final state)
     T d2 = T(0), dmax = T(0);
     const int x = blockIdx.x * TX + threadIdx.x;
@@ -923,6 +931,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_courant_rate(const void* __restrict__ q, FlowConsts<T> k, size_t n,
                                                       unsigned long long* sigma)
 {
+    pdl_enter();
     T smax = T(0);
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
         T v[4];
@@ -936,6 +945,7 @@ __global__ void __launch_bounds__(256) k_courant_rate(const void* __restrict__ q
 // host uses for a fixed dt, the time at the end of the step, and a cleared sigma for the step's last kernel
 __global__ void k_adjust_dt(DtCtl* c)
 {
+    pdl_enter();
     // lane 0 chooses dt; the lanes then form one dt-dependent constant each (the divisions run side by side)
     const int lane = threadIdx.x;
     double dt = 0.0;
@@ -1105,6 +1115,15 @@ inline int elementwise_blocks(size_t n) { return (int)std::min<size_t>((n + 255)
 
 }  // namespace
 
+bool pdl_on()
+{
+    static const bool on = [] {
+        const char* v = std::getenv("VF_PDL");
+        return v && *v && *v != '0';
+    }();
+    return on;
+}
+
 // ------------------------------------------------------------------------------------------------------------
 // launchers
 // ------------------------------------------------------------------------------------------------------------
@@ -1114,21 +1133,19 @@ cudaError_t Kernels<T>::stage(int s, const StageArgs<T>& a, const FlowConsts<T>&
     const dim3 g = flow_grid(k, kZcStage), b(TX, TY);
     const bool dyn = k.dyn != nullptr;
     switch (s) {
-        case 1: dyn ? k_stage<T, 1, true><<<g, b, 0, st>>>(a, k) : k_stage<T, 1, false><<<g, b, 0, st>>>(a, k); break;
-        case 2: dyn ? k_stage<T, 2, true><<<g, b, 0, st>>>(a, k) : k_stage<T, 2, false><<<g, b, 0, st>>>(a, k); break;
-        case 3: dyn ? k_stage<T, 3, true><<<g, b, 0, st>>>(a, k) : k_stage<T, 3, false><<<g, b, 0, st>>>(a, k); break;
-        case 4: dyn ? k_stage<T, 4, true><<<g, b, 0, st>>>(a, k) : k_stage<T, 4, false><<<g, b, 0, st>>>(a, k); break;
+        case 1: return launch_pdl(dyn ? k_stage<T, 1, true> : k_stage<T, 1, false>, g, b, 0, st, a, k);
+        case 2: return launch_pdl(dyn ? k_stage<T, 2, true> : k_stage<T, 2, false>, g, b, 0, st, a, k);
+        case 3: return launch_pdl(dyn ? k_stage<T, 3, true> : k_stage<T, 3, false>, g, b, 0, st, a, k);
+        case 4: return launch_pdl(dyn ? k_stage<T, 4, true> : k_stage<T, 4, false>, g, b, 0, st, a, k);
         default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t Kernels<T>::divergence(const void* qstar, T* r, const FlowConsts<T>& k, cudaStream_t st)
 {
-    if (k.dyn) k_div<T, true><<<flow_grid(k, kZcDiv), dim3(TX, TY), 0, st>>>(qstar, r, k);
-    else k_div<T, false><<<flow_grid(k, kZcDiv), dim3(TX, TY), 0, st>>>(qstar, r, k);
-    return cudaGetLastError();
+    return launch_pdl(k.dyn ? k_div<T, true> : k_div<T, false>, flow_grid(k, kZcDiv), dim3(TX, TY), 0, st, qstar, r,
+                      k);
 }
 
 template <typename T>
@@ -1137,9 +1154,9 @@ cudaError_t Kernels<T>::project(const void* qstar, const T* p, void* out, const 
                                 unsigned long long* sigma)
 {
     const dim3 g = flow_grid(k, kZcProject), b(TX, TY);
-    if (k.dyn) k_project<T, true><<<g, b, 0, st>>>(qstar, p, out, mask, step_counter, k, sigma);
-    else k_project<T, false><<<g, b, 0, st>>>(qstar, p, out, mask, step_counter, k, nullptr);
-    return cudaGetLastError();
+    if (k.dyn) return launch_pdl(k_project<T, true>, g, b, 0, st, qstar, p, out, mask, step_counter, k, sigma);
+    return launch_pdl(k_project<T, false>, g, b, 0, st, qstar, p, out, mask, step_counter, k,
+                      (unsigned long long*)nullptr);
 }
 
 template <typename T>
@@ -1147,11 +1164,10 @@ cudaError_t Kernels<T>::filter(const void* in, void* out, const uint8_t* mask, c
                                const ReduceArgsDev* r, cudaStream_t st, unsigned long long* sigma)
 {
     const dim3 g = flow_grid(k, kZcFilter), b(TX, TY);
-    if (r && sigma) k_filter<T, true, true><<<g, b, 0, st>>>(in, out, mask, k, *r, sigma);
-    else if (r) k_filter<T, true, false><<<g, b, 0, st>>>(in, out, mask, k, *r, nullptr);
-    else if (sigma) k_filter<T, false, true><<<g, b, 0, st>>>(in, out, mask, k, ReduceArgsDev{}, sigma);
-    else k_filter<T, false, false><<<g, b, 0, st>>>(in, out, mask, k, ReduceArgsDev{}, nullptr);
-    return cudaGetLastError();
+    const ReduceArgsDev ra = r ? *r : ReduceArgsDev{};
+    auto kern = r ? (sigma ? k_filter<T, true, true> : k_filter<T, true, false>)
+                  : (sigma ? k_filter<T, false, true> : k_filter<T, false, false>);
+    return launch_pdl(kern, g, b, 0, st, in, out, mask, k, ra, sigma);
 }
 
 template <typename T>
@@ -1189,8 +1205,8 @@ cudaError_t Kernels<T>::reduce_state(const void* q, const uint8_t* mask, const F
     if (cpt > kRedMaxCellsPerThread) return cudaErrorInvalidValue;   // too few partial slots for this grid
     nb = (rows + cpt - 1) / cpt;
     r.div_count = filter_warps(k);
-    k_reduce_state<T><<<(unsigned)nb, kRedThreads, 0, st>>>(q, mask, (int)n, cpt, r, to_history);
-    return cudaGetLastError();
+    return launch_pdl(k_reduce_state<T>, dim3((unsigned)nb), dim3(kRedThreads), 0, st, q, mask, (int)n, cpt, r,
+                      to_history);
 }
 
 template <typename T>
@@ -1231,8 +1247,7 @@ template cudaError_t region_force<double>(const void*, const double*, const uint
 
 cudaError_t adjust_dt(DtCtl* c, cudaStream_t st)
 {
-    k_adjust_dt<<<1, 32, 0, st>>>(c);   // one warp
-    return cudaGetLastError();
+    return launch_pdl(k_adjust_dt, dim3(1), dim3(32), 0, st, c);   // one warp
 }
 
 template <typename T>
@@ -1249,8 +1264,7 @@ template <typename T>
 cudaError_t Kernels<T>::reduce(const void* q, const uint8_t* mask, const FlowConsts<T>& k, const ReduceArgsDev& r,
                                int to_history, cudaStream_t st)
 {
-    k_reduce<T><<<flow_grid(k, kZcFilter), dim3(TX, TY), 0, st>>>(q, mask, k, r, to_history);
-    return cudaGetLastError();
+    return launch_pdl(k_reduce<T>, flow_grid(k, kZcFilter), dim3(TX, TY), 0, st, q, mask, k, r, to_history);
 }
 
 template <typename T>

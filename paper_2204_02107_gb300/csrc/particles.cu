@@ -12,6 +12,7 @@
 // the drag run in the grid's precision (FP64 is a small fraction of FP32 throughput on this GPU).
 #include <cuda_runtime.h>
 
+#include "launch.cuh"
 #include "vf_internal.h"
 
 namespace vf {
@@ -88,6 +89,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_particles(ParticleArgs P, const void* __restrict__ q,
                                                    const uint8_t* __restrict__ mask)
 {
+    pdl_enter();
     const double dt = P.dyn ? P.dyn->dt : P.dt;
     const T dtt = (T)dt;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < P.n;
@@ -147,8 +149,7 @@ cudaError_t advance_particles(const ParticleArgs& P, const void* q, const uint8_
     if (P.n <= 0) return cudaSuccess;
     long long blocks = (P.n + 255) / 256;
     if (blocks > 152 * 16) blocks = 152 * 16;
-    k_particles<T><<<(unsigned)blocks, 256, 0, st>>>(P, q, mask);
-    return cudaGetLastError();
+    return launch_pdl(k_particles<T>, dim3((unsigned)blocks), dim3(256), 0, st, P, q, mask);
 }
 
 template cudaError_t advance_particles<float>(const ParticleArgs&, const void*, const uint8_t*, cudaStream_t);
