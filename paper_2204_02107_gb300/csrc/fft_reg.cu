@@ -126,21 +126,21 @@ __global__ void __launch_bounds__(x_threads<T>()) k_reg_x_fwd(PoissonArgs<T> A)
     C* tw = reinterpret_cast<C*>(smem_raw);
     C* twr = tw + M;
     C* rowbuf = twr + (M + 1);
-    stage_table(tw, A.twx, M);
-    stage_table(twr, A.twr, M + 1);
-    __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int gi = lane % P, t = lane / P;
     const int b = warp * P + gi;
     const int rows = A.ny * A.nz, row = blockIdx.x * B + b;
     const bool act = row < rows;
     C v[16];
-    {
+    {   // the row's loads are issued before the tables are staged
         const T* __restrict__ src = A.f + (long long)(act ? row : 0) * A.nx;
 #pragma unroll
         for (int m = 0; m < 16; ++m)
             v[m] = act ? *reinterpret_cast<const C*>(src + 2 * (t + GX * m)) : mk<C>(T(0), T(0));
     }
+    stage_table(tw, A.twx, M);
+    stage_table(twr, A.twr, M + 1);
+    __syncthreads();
     C* rb = rowbuf + b * SPX;
     auto buf = [rb](int e) -> C& { return rb[e]; };
     reg_fwd<C, GX>(v, t, tw, buf);
