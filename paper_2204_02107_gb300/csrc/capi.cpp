@@ -147,7 +147,7 @@ PoissonArgs<T> poisson_args(const vf_grid* g, T* f, T* p, int use_mask)
     PoissonArgs<T> a{};
     const vf_grid_desc& d = g->d;
     a.nx = d.nx; a.ny = d.ny; a.nz = d.nz; a.M = d.nx / 2;
-    a.f = f; a.p = p; a.mask = g->mask;
+    a.f = f; a.p = p; a.smask = g->smask;
     a.near_list = g->near_list;
     a.near_r = (T*)g->near_r;
     a.n_near = use_mask ? g->n_near : 0;

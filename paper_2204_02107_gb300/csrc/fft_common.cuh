@@ -161,39 +161,37 @@ __device__ __forceinline__ int wrapi(int i, int n) { return i < 0 ? i + n : (i >
 
 // Eq. 9 correction at one cell: sum_j (1/(2h_j))^2 [(1 - beta^+)(p^{++} - p^0) - (1 - beta^-)(p^0 - p^{--})]
 // (= sum_j delta_j((1 - beta) delta_j p) with central differences).  Only called for cells with a solid neighbour.
-// All thirteen loads are issued before any is used (one round trip), the mask then selects the terms.
+// The betas of the six axis neighbours come from the cell's packed stencil-mask byte; p two cells away is loaded
+// only along the directions whose neighbour is solid (the other terms are zero), all loads issued before any use.
 template <typename T>
-__device__ T poisson_correction(const PoissonArgs<T>& A, long long i, int x, int y, int z)
+__device__ T poisson_correction(const PoissonArgs<T>& A, int i, int x, int y, int z)
 {
-    const long long nx = A.nx, plane = (long long)A.nx * A.ny;
-    const long long zb = (long long)z * plane, yb = (long long)y * nx;
-    const long long ixm = zb + yb + wrapi(x - 1, A.nx), ixp = zb + yb + wrapi(x + 1, A.nx);
-    const long long ixmm = zb + yb + wrapi(x - 2, A.nx), ixpp = zb + yb + wrapi(x + 2, A.nx);
-    const long long iym = zb + wrapi(y - 1, A.ny) * nx + x, iyp = zb + wrapi(y + 1, A.ny) * nx + x;
-    const long long iymm = zb + wrapi(y - 2, A.ny) * nx + x, iypp = zb + wrapi(y + 2, A.ny) * nx + x;
-    const long long izm = wrapi(z - 1, A.nz) * plane + yb + x, izp = wrapi(z + 1, A.nz) * plane + yb + x;
-    const long long izmm = wrapi(z - 2, A.nz) * plane + yb + x, izpp = wrapi(z + 2, A.nz) * plane + yb + x;
+    const int nx = A.nx, plane = A.nx * A.ny;
+    const uint8_t sm = __ldg(A.smask + i);
+    const bool sxm = !(sm & kSmXm), sxp = !(sm & kSmXp), sym = !(sm & kSmYm), syp = !(sm & kSmYp);
+    const bool szm = !(sm & kSmZm), szp = !(sm & kSmZp);   // neighbour solid
     const T p0 = __ldg(A.p + i);
-    const uint8_t mxm = __ldg(A.mask + ixm), mxp = __ldg(A.mask + ixp);
-    const uint8_t mym = __ldg(A.mask + iym), myp = __ldg(A.mask + iyp);
-    const uint8_t mzm = __ldg(A.mask + izm), mzp = __ldg(A.mask + izp);
-    const T pxm = __ldg(A.p + ixmm), pxp = __ldg(A.p + ixpp);
-    const T pym = __ldg(A.p + iymm), pyp = __ldg(A.p + iypp);
-    const T pzm = __ldg(A.p + izmm), pzp = __ldg(A.p + izpp);
+    T pxm = T(0), pxp = T(0), pym = T(0), pyp = T(0), pzm = T(0), pzp = T(0);
+    if (sxm) pxm = __ldg(A.p + i - x + wrapi(x - 2, A.nx));
+    if (sxp) pxp = __ldg(A.p + i - x + wrapi(x + 2, A.nx));
+    if (sym) pym = __ldg(A.p + i + (wrapi(y - 2, A.ny) - y) * nx);
+    if (syp) pyp = __ldg(A.p + i + (wrapi(y + 2, A.ny) - y) * nx);
+    if (szm) pzm = __ldg(A.p + i + (wrapi(z - 2, A.nz) - z) * plane);
+    if (szp) pzp = __ldg(A.p + i + (wrapi(z + 2, A.nz) - z) * plane);
     T corr = T(0);
     {
-        const T pp = (mxp & kBitBeta) ? T(0) : pxp - p0;
-        const T pm = (mxm & kBitBeta) ? T(0) : p0 - pxm;
+        const T pp = sxp ? pxp - p0 : T(0);
+        const T pm = sxm ? p0 - pxm : T(0);
         corr += A.i2h2[0] * (pp - pm);
     }
     {
-        const T pp = (myp & kBitBeta) ? T(0) : pyp - p0;
-        const T pm = (mym & kBitBeta) ? T(0) : p0 - pym;
+        const T pp = syp ? pyp - p0 : T(0);
+        const T pm = sym ? p0 - pym : T(0);
         corr += A.i2h2[1] * (pp - pm);
     }
     {
-        const T pp = (mzp & kBitBeta) ? T(0) : pzp - p0;
-        const T pm = (mzm & kBitBeta) ? T(0) : p0 - pzm;
+        const T pp = szp ? pzp - p0 : T(0);
+        const T pm = szm ? p0 - pzm : T(0);
         corr += A.i2h2[2] * (pp - pm);
     }
     return corr;

@@ -107,7 +107,7 @@ int solve(int nx, int ny, int nz, double lx, double ly, double lz, const void* f
     a.nx = nx; a.ny = ny; a.nz = nz; a.M = M;
     a.f = const_cast<T*>(static_cast<const T*>(f));   // only read: no correction runs without a mask
     a.p = static_cast<T*>(p);
-    a.mask = nullptr;
+    a.smask = nullptr;
     a.n_near = 0;
     a.plane_layout = 0;
     a.spec = spectrum;

@@ -181,7 +181,7 @@ struct PoissonArgs {
     int nx, ny, nz, M;        // M = nx / 2
     T* f;                     // right-hand side read by the x forward pass (r, plus the Eq. 9 correction)
     T* p;                     // in: p^k (for the correction), out: p^{k+1}
-    const uint8_t* mask;
+    const uint8_t* smask;     // packed stencil mask: the betas of each cell's six axis neighbours (kSm* bits)
     const int* near_list;     // ascending cells with a solid axis neighbour (where the correction is nonzero)
     T* near_r;                // r at those cells, saved by the first correction of a step
     int n_near;
