@@ -228,6 +228,8 @@ k_stage(StageArgs<T> a, FlowConsts<T> k)
 // ------------------------------------------------------------------------------------------------------------
 // Divergence r = sum_j delta_j u_j / dt (a4; divided by dt because the solver works on p / rho)
 // ------------------------------------------------------------------------------------------------------------
+constexpr int kDivGroup = 4;
+
 template <typename T, bool DYN>
 __global__ void __launch_bounds__(TX * TY) k_div(const void* __restrict__ q, T* __restrict__ r, FlowConsts<T> k)
 {
@@ -245,18 +247,41 @@ __global__ void __launch_bounds__(TX * TY) k_div(const void* __restrict__ q, T* 
     const int z0 = blockIdx.z * k.zc[kZcDiv], z1 = min(z0 + k.zc[kZcDiv], nz);
     const int rowc = y * nx, rowm = wrap(y - 1, ny) * nx, rowp = wrap(y + 1, ny) * nx;
     const int xm = wrap(x - 1, nx), xp = wrap(x + 1, nx);
+    // groups of kDivGroup planes, software-pipelined: the loads of the next group (its u and v neighbours and the w
+    // of the planes above it) are issued before the current group is differenced, so two groups are in flight
+    constexpr int U = kDivGroup;
+    struct Group { T um[U], up[U], vm[U], vp[U], wz[U]; };   // wz[u]: w at plane z + u + 1
+    auto load = [&](int zg, Group& g) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int z = zg + u;
+            const bool ok = z < z1;
+            const int zb = (ok ? z : z0) * plane;
+            g.um[u] = ok ? ld1<T>(q, zb + rowc + xm, 0) : T(0);
+            g.up[u] = ok ? ld1<T>(q, zb + rowc + xp, 0) : T(0);
+            g.vm[u] = ok ? ld1<T>(q, zb + rowm + x, 1) : T(0);
+            g.vp[u] = ok ? ld1<T>(q, zb + rowp + x, 1) : T(0);
+            g.wz[u] = ok ? ld1<T>(q, wrap(z + 1, nz) * plane + rowc + x, 2) : T(0);
+        }
+    };
     T wzm = ld1<T>(q, wrap(z0 - 1, nz) * plane + rowc + x, 2);
     T wz0 = ld1<T>(q, z0 * plane + rowc + x, 2);
-#pragma unroll 4
-    for (int z = z0; z < z1; ++z) {
-        const int zb = z * plane;
-        const T wzp = ld1<T>(q, wrap(z + 1, nz) * plane + rowc + x, 2);
-        const T d = i2h[0] * (ld1<T>(q, zb + rowc + xp, 0) - ld1<T>(q, zb + rowc + xm, 0)) +
-                    i2h[1] * (ld1<T>(q, zb + rowp + x, 1) - ld1<T>(q, zb + rowm + x, 1)) +
-                    i2h[2] * (wzp - wzm);
-        r[zb + rowc + x] = d;
-        wzm = wz0;
-        wz0 = wzp;
+    Group cur, nxt;
+    load(z0, cur);
+    for (int zg = z0; zg < z1; zg += U) {
+        if (zg + U < z1) load(zg + U, nxt);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int z = zg + u;
+            if (z < z1) {
+                const T wzp = cur.wz[u];
+                const T d = i2h[0] * (cur.up[u] - cur.um[u]) + i2h[1] * (cur.vp[u] - cur.vm[u]) + i2h[2] * (wzp - wzm);
+                r[z * plane + rowc + x] = d;
+                wzm = wz0;
+                wz0 = wzp;
+            }
+        }
+        cur = nxt;
     }
 }
 
