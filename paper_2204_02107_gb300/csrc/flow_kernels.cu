@@ -288,6 +288,8 @@ __global__ void __launch_bounds__(TX * TY) k_div(const void* __restrict__ q, T* 
 // ------------------------------------------------------------------------------------------------------------
 // Projection u = beta (u* - dt G p) with p = p / rho (a9); c* passes through.  Ticks the device step counter.
 // ------------------------------------------------------------------------------------------------------------
+constexpr int kProjectGroup = 2;
+
 template <typename T, bool DYN>
 __global__ void __launch_bounds__(TX * TY) k_project(const void* __restrict__ qs, const T* __restrict__ p,
                                                      void* __restrict__ out, const uint8_t* __restrict__ mask,
@@ -312,23 +314,53 @@ __global__ void __launch_bounds__(TX * TY) k_project(const void* __restrict__ qs
         const int z0 = blockIdx.z * k.zc[kZcProject], z1 = min(z0 + k.zc[kZcProject], nz);
         const int rowc = y * nx, rowm = wrap(y - 1, ny) * nx, rowp = wrap(y + 1, ny) * nx;
         const int xm = wrap(x - 1, nx), xp = wrap(x + 1, nx);
+        // groups of kProjectGroup planes, software-pipelined like the divergence: the next group's loads are in
+        // flight while the current group is projected
+        constexpr int U = kProjectGroup;
+        struct Group { T q[U][4], pxm[U], pxp[U], pym[U], pyp[U], pz[U]; uint8_t m[U]; };   // pz[u]: p at z + u + 1
+        auto load = [&](int zg, Group& g) {
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int z = zg + u;
+                const bool ok = z < z1;
+                const int zb = (ok ? z : z0) * plane;
+                if (ok) {
+                    ld4(qs, zb + rowc + x, g.q[u]);
+                } else {
+                    g.q[u][0] = g.q[u][1] = g.q[u][2] = g.q[u][3] = T(0);
+                }
+                g.m[u] = ok ? __ldg(mask + zb + rowc + x) : 0;
+                g.pxm[u] = ok ? __ldg(p + zb + rowc + xm) : T(0);
+                g.pxp[u] = ok ? __ldg(p + zb + rowc + xp) : T(0);
+                g.pym[u] = ok ? __ldg(p + zb + rowm + x) : T(0);
+                g.pyp[u] = ok ? __ldg(p + zb + rowp + x) : T(0);
+                g.pz[u] = ok ? __ldg(p + wrap(z + 1, nz) * plane + rowc + x) : T(0);
+            }
+        };
         T pzm = __ldg(p + wrap(z0 - 1, nz) * plane + rowc + x);
         T pz0 = __ldg(p + z0 * plane + rowc + x);
-#pragma unroll 4
-        for (int z = z0; z < z1; ++z) {
-            const int zb = z * plane;
-            const int ic = zb + rowc + x;
-            const T pzp = __ldg(p + wrap(z + 1, nz) * plane + rowc + x);
-            T q[4];
-            ld4(qs, ic, q);
-            const T beta = beta_of<T>(__ldg(mask + ic));
-            q[0] = beta * (q[0] - i2h[0] * (__ldg(p + zb + rowc + xp) - __ldg(p + zb + rowc + xm)));
-            q[1] = beta * (q[1] - i2h[1] * (__ldg(p + zb + rowp + x) - __ldg(p + zb + rowm + x)));
-            q[2] = beta * (q[2] - i2h[2] * (pzp - pzm));
-            st4(out, ic, q);
-            if (DYN) smax = fmax(smax, sigma_cell(q[0], q[1], q[2], k.ih));
-            pzm = pz0;
-            pz0 = pzp;
+        Group cur, nxt;
+        load(z0, cur);
+        for (int zg = z0; zg < z1; zg += U) {
+            if (zg + U < z1) load(zg + U, nxt);
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int z = zg + u;
+                if (z < z1) {
+                    const int ic = z * plane + rowc + x;
+                    const T pzp = cur.pz[u];
+                    T q[4] = {cur.q[u][0], cur.q[u][1], cur.q[u][2], cur.q[u][3]};
+                    const T beta = beta_of<T>(cur.m[u]);
+                    q[0] = beta * (q[0] - i2h[0] * (cur.pxp[u] - cur.pxm[u]));
+                    q[1] = beta * (q[1] - i2h[1] * (cur.pyp[u] - cur.pym[u]));
+                    q[2] = beta * (q[2] - i2h[2] * (pzp - pzm));
+                    st4(out, ic, q);
+                    if (DYN) smax = fmax(smax, sigma_cell(q[0], q[1], q[2], k.ih));
+                    pzm = pz0;
+                    pz0 = pzp;
+                }
+            }
+            cur = nxt;
         }
     }
     if (DYN && sigma_out) sigma_flush((double)smax, sigma_out);
