@@ -152,9 +152,24 @@ def dist_barrier(world):
         dist.barrier()
 
 
+def source_digest(path, end_marker=None):
+    """SHA-256 of a source file, or of its text up to the first line that starts with ``end_marker`` (the part a
+    kernel and the helpers above it are compiled from); None when the file or the marker is missing."""
+    full = os.path.join(ROOT, path)
+    if not os.path.exists(full):
+        return None
+    data = open(full, "rb").read()
+    if end_marker:
+        cut = data.find(b"\n" + end_marker.encode())
+        if cut < 0:
+            return None
+        data = data[:cut + 1]
+    return hashlib.sha256(data).hexdigest()
+
+
 def traffic_record(kernel, tiles):
-    """DRAM bytes per launch of ``kernel`` from the committed ncu summary, if taken on the current source with
-    the same launch tiles."""
+    """DRAM bytes per launch of ``kernel`` from the committed ncu summary, if taken on the current source of the
+    kernel (and of everything above it in its file, and the shared headers) with the same launch tiles."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
@@ -163,12 +178,12 @@ def traffic_record(kernel, tiles):
     entry = rec.get("kernels", {}).get(kernel)
     if not entry:
         return None
-    src = os.path.join(ROOT, entry["source"])
-    if not os.path.exists(src):
+    digest = source_digest(entry["source"], entry.get("source_end_marker"))
+    if digest is None or digest != entry.get("source_sha256"):
         return None
-    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
-    if digest != entry.get("source_sha256"):
-        return None
+    for hdr, hdr_digest in (entry.get("headers") or {}).items():
+        if source_digest(hdr) != hdr_digest:
+            return None
     for key, value in (entry.get("tiles") or {}).items():
         if tiles.get(key) != value:
             return None
