@@ -96,19 +96,13 @@ __device__ __forceinline__ void sigma_flush(double s, unsigned long long* out)
 //              + S (cset - c^0) inv_tau ],  F^+ = beta^+ (U_j^0 c^0 + U_j^+ c^+) / 2 (face weight beta^0 beta^+,
 //              beta^0 is applied by the outer factor)
 // One cell of RK4 stage STAGE (the right-hand sides of Eqs. 2-3 above and the RK4 combine): from the centre q0, the
-// axis neighbours qm[j], qp[j] (j = x, y, z) and the cell's stencil mask sm (its beta and S, the neighbours' beta);
-// reads the cell's own q_n (and q2, q3 in stage 4) at index ic and leaves the stage output in o.
+// axis neighbours qm[j], qp[j] (j = x, y, z), the cell's stencil mask sm (its beta and S, the neighbours' beta)
+// and the cell's own q_n (stages 2-4) and q2, q3 (stage 4); leaves the stage output in o.
 template <typename T, int STAGE>
 __device__ __forceinline__ void stage_cell(const StageArgs<T>& a, const FlowConsts<T>& k, int ic, const T q0[4],
-                                           const T qm[3][4], const T qp[3][4], uint8_t sm, T dt2, T dtf, T dt6,
-                                           T inv_tau, T o[4])
+                                           const T qm[3][4], const T qp[3][4], uint8_t sm, const T qn[4],
+                                           const T q2[4], const T q3[4], T dt2, T dtf, T dt6, T inv_tau, T o[4])
 {
-    T qn[4], q2[4], q3[4];
-    if (STAGE >= 2) ld4(a.qn, ic, qn);
-    if (STAGE == 4) {   // read by their owner thread before it overwrites q2 with q* (in place, own cell only)
-        ld4(a.q2, ic, q2);
-        ld4(a.q3, ic, q3);
-    }
     const T bm[3] = {(sm & kSmXm) ? T(1) : T(0), (sm & kSmYm) ? T(1) : T(0), (sm & kSmZm) ? T(1) : T(0)};
     const T bp[3] = {(sm & kSmXp) ? T(1) : T(0), (sm & kSmYp) ? T(1) : T(0), (sm & kSmZp) ? T(1) : T(0)};
     const T beta = (sm & kSmSelf) ? T(1) : T(0);
@@ -160,6 +154,12 @@ __device__ __forceinline__ void stage_cell(const StageArgs<T>& a, const FlowCons
     }
 }
 
+// Stage 4 reads three own states (q_n, q2, q3): prefetching them too takes 80 registers (3 CTAs per SM).
+#ifndef VF_STAGE_PREFETCH_OWN4
+#define VF_STAGE_PREFETCH_OWN4 0
+#endif
+constexpr bool kStagePrefetchOwn4 = VF_STAGE_PREFETCH_OWN4 != 0;
+
 template <typename T, int STAGE, bool DYN>
 __global__ void __launch_bounds__(TX * TY)
 k_stage(StageArgs<T> a, FlowConsts<T> k)
@@ -184,8 +184,14 @@ k_stage(StageArgs<T> a, FlowConsts<T> k)
     const int xm = wrap(x - 1, nx), xp = wrap(x + 1, nx);
     const int rowc = y * nx, rowm = wrap(y - 1, ny) * nx, rowp = wrap(y + 1, ny) * nx;
 
-    // z registers: the 4-vector at z-1, z, z+1 and the prefetched plane z+2; the stencil mask at z and z+1
+    // z registers: the 4-vector at z-1, z, z+1 and the prefetched plane z+2; the stencil mask at z and z+1; the
+    // cell's own q_n (and q2, q3 in stage 4) at z and, prefetched, at z+1 (stage 4 overwrites q2 with q* in place:
+    // the cell at z+1 is read before its owner thread writes it)
     T qzm[4], q0[4], qzp[4], qn2[4];
+    T own[3][4] = {}, own_next[3][4] = {};   // q_n, q2, q3 of the cell
+    constexpr int NOWN = STAGE == 1 ? 0 : (STAGE == 4 ? 3 : 1);
+    constexpr bool PF = STAGE != 4 || kStagePrefetchOwn4;   // prefetched one plane ahead, else read in place
+    const void* own_src[3] = {a.qn, a.q2, a.q3};
     uint8_t m0, mzp;
     {
         const int im = wrap(z0 - 1, nz) * plane + rowc + x;
@@ -196,6 +202,10 @@ k_stage(StageArgs<T> a, FlowConsts<T> k)
         ld4(a.qs, ip, qzp);
         m0 = __ldg(a.smask + ic);
         mzp = __ldg(a.smask + ip);
+        if (PF) {
+#pragma unroll
+            for (int o = 0; o < NOWN; ++o) ld4(own_src[o], ic, own[o]);
+        }
     }
 #pragma unroll
     for (int f = 0; f < 4; ++f) qn2[f] = T(0);
@@ -203,10 +213,18 @@ k_stage(StageArgs<T> a, FlowConsts<T> k)
         const int zb = z * plane;
         const int ic = zb + rowc + x;
         uint8_t mn2 = 0;
-        if (z + 1 < z1) {   // prefetch plane z+2 for the next iteration
+        if (z + 1 < z1) {   // prefetch plane z+2 of the stencil state and the cell's own states at z+1
             const int i2 = wrap(z + 2, nz) * plane + rowc + x;
             ld4(a.qs, i2, qn2);
             mn2 = __ldg(a.smask + i2);
+            if (PF) {
+#pragma unroll
+                for (int o = 0; o < NOWN; ++o) ld4(own_src[o], ic + plane, own_next[o]);
+            }
+        }
+        if (!PF) {
+#pragma unroll
+            for (int o = 0; o < NOWN; ++o) ld4(own_src[o], ic, own[o]);
         }
         T qm[3][4], qp[3][4];
         ld4(a.qs, zb + rowc + xm, qm[0]);
@@ -216,10 +234,16 @@ k_stage(StageArgs<T> a, FlowConsts<T> k)
 #pragma unroll
         for (int f = 0; f < 4; ++f) { qm[2][f] = qzm[f]; qp[2][f] = qzp[f]; }
         T o[4];
-        stage_cell<T, STAGE>(a, k, ic, q0, qm, qp, m0, dt2, dtf, dt6, inv_tau, o);
+        stage_cell<T, STAGE>(a, k, ic, q0, qm, qp, m0, own[0], own[1], own[2], dt2, dtf, dt6, inv_tau, o);
         st4(a.out, ic, o);
 #pragma unroll
         for (int f = 0; f < 4; ++f) { qzm[f] = q0[f]; q0[f] = qzp[f]; qzp[f] = qn2[f]; }
+        if (PF) {
+#pragma unroll
+            for (int o = 0; o < NOWN; ++o)
+#pragma unroll
+                for (int f = 0; f < 4; ++f) own[o][f] = own_next[o][f];
+        }
         m0 = mzp;
         mzp = mn2;
     }
