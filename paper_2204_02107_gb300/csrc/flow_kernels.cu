@@ -109,25 +109,37 @@ __device__ __forceinline__ void stage_cell(const StageArgs<T>& a, const FlowCons
     const T S = (sm & kSmS) ? (a.sval ? __ldg(a.sval + ic) : T(1)) : T(0);
 
     T kq[4];
+    // velocity: the skew-symmetric term (U_j^+ Q_i^+ - U_j^- Q_i^-) + U_j^0 (Q_i^+ - Q_i^-) is grouped as
+    // Q_i^+ (U_j^+ + U_j^0) - Q_i^- (U_j^- + U_j^0), the two sums shared by the three components, and the
+    // Laplacian as sum_j ih2_j (Q_i^+ + Q_i^-) - (2 sum_j ih2_j) Q_i^0: the same sums in another rounding order
+    T up[3], um[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        up[j] = qp[j][j] + q0[j];
+        um[j] = qm[j][j] + q0[j];
+    }
+    const T ih2_2 = T(2) * (k.ih2[0] + k.ih2[1] + k.ih2[2]);
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
         T conv = T(0), diff = T(0);
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
-            conv += k.q4h[j] * ((qp[j][j] * qp[j][i] - qm[j][j] * qm[j][i]) + q0[j] * (qp[j][i] - qm[j][i]));
-            diff += k.ih2[j] * (qp[j][i] - T(2) * q0[i] + qm[j][i]);
+            conv += k.q4h[j] * (qp[j][i] * up[j] - qm[j][i] * um[j]);
+            diff += k.ih2[j] * (qp[j][i] + qm[j][i]);
         }
+        diff -= ih2_2 * q0[i];
         kq[i] = beta * (-conv + k.nu * diff + S * (k.uset[i] - q0[i]) * inv_tau + k.bf[i]);
     }
     {
+        // the face fluxes' factor 1/2 is moved onto ih_j (a power-of-two scaling: the same bits)
         const T c0 = q0[3];
         T conv = T(0), diff = T(0);
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
             const T uc0 = q0[j] * c0;
-            const T Fp = bp[j] * T(0.5) * (uc0 + qp[j][j] * qp[j][3]);
-            const T Fm = bm[j] * T(0.5) * (qm[j][j] * qm[j][3] + uc0);
-            conv += k.ih[j] * (Fp - Fm);
+            const T Fp2 = bp[j] * (uc0 + qp[j][j] * qp[j][3]);
+            const T Fm2 = bm[j] * (qm[j][j] * qm[j][3] + uc0);
+            conv += (T(0.5) * k.ih[j]) * (Fp2 - Fm2);
             diff += k.ih2[j] * (bp[j] * (qp[j][3] - c0) - bm[j] * (c0 - qm[j][3]));
         }
         kq[3] = beta * (-conv + k.alpha * diff + S * (k.cset - c0) * inv_tau);
@@ -161,7 +173,7 @@ __device__ __forceinline__ void stage_cell(const StageArgs<T>& a, const FlowCons
 constexpr bool kStagePrefetchOwn4 = VF_STAGE_PREFETCH_OWN4 != 0;
 
 template <typename T, int STAGE, bool DYN>
-__global__ void __launch_bounds__(TX * TY)
+__global__ void __launch_bounds__(TX * TY, sizeof(T) == 4 ? 4 : 1)
 k_stage(StageArgs<T> a, FlowConsts<T> k)
 {
     pdl_enter();
