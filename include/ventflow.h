@@ -20,7 +20,8 @@
  *
  * Memory layout: every field is one array of nx*ny*nz values, x fastest: index = x + nx*(y + ny*z).
  * Precision: VF_FP64 computes everything in double; VF_FP32_MIXED keeps fields, stencils and FFTs in float and
- * accumulates every reduction in double (per-thread compensated float sums, double across threads).
+ * accumulates every reduction to double precision or better (per-thread compensated float sums, float-float
+ * pairs across threads and CTAs, converted to double once at the end; FP64 grids sum in double throughout).
  *
  * Errors: every call returns VF_OK (0) or a negative VF_E* code.  A failing call on a grid records a message
  * (vf_last_error) and, for CUDA failures, a sticky status that later calls on that grid return.  Calls never
@@ -213,15 +214,16 @@ int vf_poisson_solve(vf_grid* g, const void* f, void* p);
 /* ---- launch tiles and the autotuner ---------------------------------------------------------------------- */
 
 /* Planes one CTA of a stencil kernel marches along z, per kernel family (the paper has no counterpart: these are
- * launch shapes of this implementation).  A tile changes no field value; the FP64 reductions are summed per CTA,
- * so their last bits follow zc_filter.  Each chunk lies in [VF_ZCHUNK_MIN, VF_ZCHUNK_MAX]. */
+ * launch shapes of this implementation).  A tile changes no field value; with the filter on, the divergence norm
+ * is summed per filter warp, so its last bits follow zc_filter (with the filter off, every reduction follows it).
+ * Each chunk lies in [VF_ZCHUNK_MIN, VF_ZCHUNK_MAX]. */
 #define VF_ZCHUNK_MIN 4
 #define VF_ZCHUNK_MAX 64
 typedef struct vf_tiles {
     int32_t zc_stage;    /* the four RK4 stage kernels */
     int32_t zc_div;      /* divergence */
     int32_t zc_project;  /* projection */
-    int32_t zc_filter;   /* filter, and the reductions it carries (also the standalone reductions) */
+    int32_t zc_filter;   /* filter and its divergence records (also the standalone reductions) */
 } vf_tiles;
 
 /* The tiles a grid launches with.  A new grid takes the process-wide tile cache's entry for its (nx, ny, nz,
@@ -349,8 +351,8 @@ int vf_particles_count(const vf_grid* g, int64_t* n);
 #define VF_PHASE_FFT_Y_INV 8    /* inverse FFT along y */
 #define VF_PHASE_FFT_X_INV 9    /* complex-to-real inverse FFT along x -> p */
 #define VF_PHASE_PROJECT 10     /* u = beta (u* - dt G p) */
-#define VF_PHASE_FILTER 11      /* Eq. 6 filter */
-#define VF_PHASE_REDUCE 12      /* FP64 reductions */
+#define VF_PHASE_FILTER 11      /* Eq. 6 filter (with the reductions: also the divergence of its input) */
+#define VF_PHASE_REDUCE 12      /* FP64 reductions of the step's final state */
 #define VF_PHASE_POISSON_RHS 13 /* Eq. 9 correction D((1 - beta) G p) at the cells next to solids */
 #define VF_PHASE_FFT_YZ_SOLVE 14 /* per-kx plane: y, z FFTs, division by lambda, inverse z, y FFTs */
 #define VF_PHASE_ADJUST_DT 15   /* dynamic time step: dt from the Courant rate of the current state */
