@@ -1,8 +1,8 @@
 """Register-resident FFT passes of the Poisson solve (every axis 16 G long, G in 1, 2, 4, 8, 16).
 
 The solve is checked against the oracle's numpy.fft solve for every G on every axis, and whole masked-room steps
-(where the x pass forms the Eq. 9 correction from the mask and p on the fly) against the generic mixed-radix
-passes (VF_GENERIC_FFT).  The masked-room parity tests against the oracle include register-path shapes."""
+(the Eq. 9 correction kernel followed by the register passes) against the generic mixed-radix passes
+(VF_GENERIC_FFT).  The masked-room parity tests against the oracle include register-path shapes."""
 import numpy as np
 import pytest
 
