@@ -59,8 +59,9 @@ PHASE_KERNEL = {"stage1": "k_stage", "stage2": "k_stage", "stage3": "k_stage", "
                 "div": "k_div", "fft_x_fwd": "k_fft_x_fwd", "fft_x_inv": "k_fft_x_inv", "fft_y_fwd": "k_fft_y",
                 "fft_y_inv": "k_fft_y", "fft_z_solve": "k_fft_z_solve", "fft_yz_solve": "k_fft_yz_solve",
                 "project": "k_project", "filter": "k_filter", "reduce": "k_reduce_state"}
-# Model of one step with the kernels fused as far as the method allows (RK4 121F+9 with n = 4): the survey's
-# algorithmic minimum, used for the step-level roofline fraction.
+# Byte model of one step with the kernels fused as far as the method allows (121F+9 per cell with n = 4 Poisson
+# iterations: RK4 with an accumulator, divergence, four Poisson iterations, projection fused with the filter),
+# used for the step-level roofline fraction.
 STEP_MODEL_BYTES_PER_CELL_FP32 = 121 * F32 + 9
 
 
@@ -431,6 +432,59 @@ def bench_serve(n_requests):
             "ach_rel_diff_max": max(rel) if rel else None}
 
 
+def bench_fft_vs_cufft(stream, nx=256, ny=128, nz=128, lengths=(10.0, 5.0, 5.0), reps=50):
+    """One FFT Poisson solve of the room's grid (Sec. 2.2: forward 3D FFT, division by lambda with the null modes
+    set to 0, inverse 3D FFT), FP32: the library's own kernels (vf_poisson_solve) against cuFFT doing the same
+    solve through torch.fft (R2C, a multiply by 1/lambda, C2R).  A timed comparison only: the step never calls
+    cuFFT."""
+    import torch
+    from paper_2204_02107_gb300 import native
+    lx, ly, lz = lengths
+    g = native.Grid(nx, ny, nz, lx, ly, lz, nu=1.6e-5, dt=1e-2, precision="fp32", stream=stream.cuda_stream)
+    gen = torch.Generator(device="cuda").manual_seed(11)
+    f = torch.randn((nz, ny, nx), generator=gen, device="cuda", dtype=torch.float32)
+    p = torch.empty_like(f)
+    # eigenvalues of D o G on the R2C half spectrum, shape (nz, ny, nx/2 + 1); the eight null modes -> 0
+    h = (lx / nx, ly / ny, lz / nz)
+    kz = torch.arange(nz, device="cuda", dtype=torch.float64).view(nz, 1, 1)
+    ky = torch.arange(ny, device="cuda", dtype=torch.float64).view(1, ny, 1)
+    kx = torch.arange(nx // 2 + 1, device="cuda", dtype=torch.float64).view(1, 1, nx // 2 + 1)
+    lam = -(torch.sin(2 * math.pi * kx / nx) ** 2 / h[0] ** 2 + torch.sin(2 * math.pi * ky / ny) ** 2 / h[1] ** 2
+            + torch.sin(2 * math.pi * kz / nz) ** 2 / h[2] ** 2)
+    inv_lam = torch.where(lam.abs() > 1e-9 * lam.abs().max(), 1.0 / lam, torch.zeros_like(lam)).float()
+
+    def ours():
+        g.poisson_solve(f, p)
+
+    def cufft():
+        fh = torch.fft.rfftn(f)
+        fh.mul_(inv_lam)
+        return torch.fft.irfftn(fh, s=(nz, ny, nx))
+
+    def timed(fn):
+        for _ in range(5):
+            fn()
+        start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        start.record(stream)
+        for _ in range(reps):
+            fn()
+        end.record(stream)
+        end.synchronize()
+        return start.elapsed_time(end) / reps * 1e3
+
+    with torch.cuda.stream(stream):
+        t_ours = timed(ours)
+        t_cufft = timed(cufft)
+        ref = cufft()
+        ours()
+        torch.cuda.current_stream().synchronize()
+        diff = float((p - ref).norm() / ref.norm())
+    g.close()
+    return {"workload": f"one FFT Poisson solve, {nx}x{ny}x{nz}, FP32 (forward FFT, 1/lambda, inverse FFT)",
+            "ours_us": t_ours, "cufft_us": t_cufft, "cufft_over_ours": t_cufft / t_ours, "rel_l2_diff": diff,
+            "cufft_path": "torch.fft.rfftn, multiply by 1/lambda, torch.fft.irfftn on the same stream"}
+
+
 def e2e_run(room, precision, steps, stream):
     """End to end through the C ABI with pinned host buffers: grid creation, mask / inflow / region / scalar
     upload, ``steps`` steps with a reduction record each, then the records and all five fields read back."""
@@ -581,7 +635,7 @@ def main():
 
     e2e = e2e_run(room, "fp32", args.steps, stream)
     g.close()
-    extras = {}
+    extras = {"fft_vs_cufft": bench_fft_vs_cufft(stream)}
     if not args.no_extras and world == 1:
         extras["large_room"] = bench_large_room(stream, args.extra_steps)
         extras["batch"] = bench_batch(stream, args.extra_steps)
