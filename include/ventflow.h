@@ -213,10 +213,15 @@ int vf_poisson_solve(vf_grid* g, const void* f, void* p);
 
 /* ---- launch tiles and the autotuner ---------------------------------------------------------------------- */
 
-/* Planes one CTA of a stencil kernel marches along z, per kernel family (the paper has no counterpart: these are
- * launch shapes of this implementation).  A tile changes no field value; with the filter on, the divergence norm
- * is summed per filter warp, so its last bits follow zc_filter (with the filter off, every reduction follows it).
- * Each chunk lies in [VF_ZCHUNK_MIN, VF_ZCHUNK_MAX]. */
+/* Launch shapes of this implementation (the paper has no counterpart).
+ * zc_*: planes one CTA of a stencil kernel marches along z, per kernel family.  A chunk changes no field value;
+ * with the filter on, the divergence norm is summed per filter warp, so its last bits follow zc_filter (with the
+ * filter off, every reduction follows it).  Each chunk lies in [VF_ZCHUNK_MIN, VF_ZCHUNK_MAX].
+ * fft_*: radix schedule of the generic mixed-radix FFT passes (Sec. 2.2's FFTs) along the x half length nx/2, y
+ * and z: an index into vf_fft_schedules' candidates for that length, 0 = the default.  Every schedule computes the
+ * same transforms in another rounding order, so fields agree to rounding (not bitwise) across schedules.  Grids
+ * whose FFT takes the register path (nx/2, ny and nz each 16, 32, 64, 128 or 256) keep the indices but do not use
+ * them. */
 #define VF_ZCHUNK_MIN 4
 #define VF_ZCHUNK_MAX 64
 typedef struct vf_tiles {
@@ -224,21 +229,37 @@ typedef struct vf_tiles {
     int32_t zc_div;      /* divergence */
     int32_t zc_project;  /* projection */
     int32_t zc_filter;   /* filter and its divergence records (also the standalone reductions) */
+    int32_t fft_x;       /* radix schedule of the nx/2-point x transforms */
+    int32_t fft_y;       /* of the ny-point y transforms */
+    int32_t fft_z;       /* of the nz-point z transforms */
 } vf_tiles;
 
 /* The tiles a grid launches with.  A new grid takes the process-wide tile cache's entry for its (nx, ny, nz,
- * precision) if there is one, else (4, 32, 8, 16), the autotuner's choice for a 256 x 128 x 128 room on GB300. */
+ * precision) if there is one, else (4, 32, 8, 16, 0, 0, 0): the z-chunks the autotuner chose for a 256 x 128 x 128
+ * room on GB300 and the default FFT schedules. */
 int vf_get_tiles(const vf_grid* g, vf_tiles* out);
 
-/* Set a grid's tiles (VF_EINVAL if a chunk is out of range; the grid is unchanged then).  Takes effect at the next
- * vf_step (the step graph is captured again). */
+/* Set a grid's tiles (VF_EINVAL if a chunk is out of range or an FFT index is not a candidate of its length; the
+ * grid is unchanged then).  Takes effect at the next vf_step (the step graph is captured again).  Waits. */
 int vf_set_tiles(vf_grid* g, const vf_tiles* t);
 
+/* Radix schedule `index` of the generic FFT passes for a transform of length n: writes its radices (each 2, 3, 4,
+ * 5, 8 or 16, product n, applied in this order) to radices[0 .. count-1] and returns count; returns 0 when index is
+ * past the last candidate (or n is not 2-3-5 smooth), VF_EINVAL for a NULL radices, index < 0 or max_radices too
+ * small (16 always suffices).  Candidate 0 is the default: as few power-of-two passes as possible, then the 3s and
+ * 5s; the others (at most 8 in all) split the power-of-two part into radix-16, radix-8 or radix-4 passes (radix-2
+ * too when it is at most 8), or run the default's small radices first, with the odd factors last or first.  Host
+ * only. */
+int vf_fft_schedules(int32_t n, int32_t index, int32_t* radices, int32_t max_radices);
+
 /* Autotuner: time every chunk in {4, 8, 16, 32} for each kernel family on this grid's own arrays (reps launches
- * each after one warm-up, CUDA events on the grid's stream, the least mean time wins), set the winners on the grid,
- * store them in the tile cache under the grid's (nx, ny, nz, precision) and copy them to *chosen (may be NULL).
- * Only scratch arrays are written: the state, the pressure, the history and the step count are unchanged.  Waits;
- * reps in [1, 1000].  Other work on the GPU at the same time perturbs the timings. */
+ * each after one warm-up, CUDA events on the grid's stream, the least mean time wins); then, for a grid on the
+ * generic FFT path, every candidate radix schedule of each axis in turn (x, then y, then z, the others held at their
+ * best so far), timed as one Poisson solve (FFT, 1/lambda, inverse FFT) of a scratch array.  Sets the winners on the
+ * grid, stores them in the tile cache under the grid's (nx, ny, nz, precision) and copies them to *chosen (may be
+ * NULL).  Only scratch arrays are written: the state, the pressure, the history and the step count are unchanged
+ * (the next steps may differ from an untuned grid's in the last bits if another FFT schedule won).  Waits; reps in
+ * [1, 1000].  Other work on the GPU at the same time perturbs the timings. */
 int vf_autotune(vf_grid* g, int32_t reps, vf_tiles* chosen);
 
 /* Tile cache: look up (1 found and *out set, 0 not found), or forget every entry. */

@@ -17,6 +17,7 @@
 #include <string>
 #include <vector>
 
+#include "fft_plan.h"
 #include "grid.h"
 
 using vf::FftAxis;
@@ -401,6 +402,46 @@ cudaError_t mask_fields(vf_grid* g)
     return Kernels<T>::apply_mask(g->q, g->mask, g->N, g->stream);
 }
 
+// Lengths of the three FFT axes: the x half length nx/2, ny, nz.
+void fft_lengths(const vf_grid* g, int len[3])
+{
+    len[0] = g->d.nx / 2;
+    len[1] = g->d.ny;
+    len[2] = g->d.nz;
+}
+
+// Every index names a candidate schedule of its axis length.
+bool fft_indices_valid(const vf_grid* g, const int idx[3])
+{
+    int len[3];
+    fft_lengths(g, len);
+    for (int a = 0; a < 3; ++a)
+        if (idx[a] < 0 || idx[a] >= (int)vf::fft_schedules(len[a]).size()) return false;
+    return true;
+}
+
+// Switch the generic FFT passes to the schedules idx (valid indices): rebuild the three axes and, once the tables
+// exist, the digit-reversal tables of the in-place y and z transforms (same sizes, copied over the old ones).  The
+// step graphs are dropped.  Stream-ordered copies; waits for them, since the host tables die here.
+int set_fft_sched(vf_grid* g, const int idx[3])
+{
+    int len[3];
+    fft_lengths(g, len);
+    for (int a = 0; a < 3; ++a) g->fft_sched[a] = idx[a];
+    g->ax = vf::make_fft_axis_sched(len[0], idx[0]);
+    g->ay = vf::make_fft_axis_sched(len[1], idx[1]);
+    g->az = vf::make_fft_axis_sched(len[2], idx[2]);
+    drop_graphs(g);
+    if (!g->krev_y || !g->krev_z) return VF_OK;
+    std::vector<int> ry(g->d.ny), rz(g->d.nz);
+    vf::digit_reversal(g->ay, ry.data());
+    vf::digit_reversal(g->az, rz.data());
+    VF_CK(cudaMemcpyAsync(g->krev_y, ry.data(), ry.size() * sizeof(int), cudaMemcpyHostToDevice, g->stream));
+    VF_CK(cudaMemcpyAsync(g->krev_z, rz.data(), rz.size() * sizeof(int), cudaMemcpyHostToDevice, g->stream));
+    VF_CK(cudaStreamSynchronize(g->stream));
+    return VF_OK;
+}
+
 }  // namespace
 
 namespace vf_engine {
@@ -537,6 +578,13 @@ int vf_create_grid(const vf_grid_desc* d, vf_grid** out)
         vf_tiles t{};
         if (vf_tile_cache_lookup(d->nx, d->ny, d->nz, d->precision, &t) == 1) {
             g->zc[0] = t.zc_stage; g->zc[1] = t.zc_div; g->zc[2] = t.zc_project; g->zc[3] = t.zc_filter;
+            const int idx[3] = {t.fft_x, t.fft_y, t.fft_z};
+            if (fft_indices_valid(g, idx)) {
+                for (int a = 0; a < 3; ++a) g->fft_sched[a] = idx[a];
+                g->ax = vf::make_fft_axis_sched(M, idx[0]);
+                g->ay = vf::make_fft_axis_sched(d->ny, idx[1]);
+                g->az = vf::make_fft_axis_sched(d->nz, idx[2]);
+            }
         }
     }
     const FlowConsts<float> kf = flow_consts<float>(g);
@@ -1251,16 +1299,52 @@ int autotune_t(vf_grid* g, int reps, vf_tiles* best)
     best->zc_div = chosen[1];
     best->zc_project = chosen[2];
     best->zc_filter = chosen[3];
+    // FFT radix schedules (generic passes only): each axis in turn, the others at their best so far, timed as one
+    // Poisson solve of the scratch array qa into qb (no Eq. 9 correction)
+    int sched[3] = {g->fft_sched[0], g->fft_sched[1], g->fft_sched[2]};
+    if (!g->reg) {
+        int len[3];
+        fft_lengths(g, len);
+        for (int axis = 0; axis < 3; ++axis) {
+            const int nc = (int)vf::fft_schedules(len[axis]).size();
+            float best_ms = 0.f;
+            int pick = sched[axis];
+            for (int c = 0; c < nc; ++c) {
+                int trial[3] = {sched[0], sched[1], sched[2]};
+                trial[axis] = c;
+                int rc = set_fft_sched(g, trial);
+                if (rc) return rc;
+                const PoissonArgs<T> pa = poisson_args<T>(g, (T*)g->qa, (T*)g->qb, 0);
+                auto launch = [&]() -> cudaError_t { return Kernels<T>::poisson_iteration(pa, 1, st); };
+                float ms = 0.f;
+                const cudaError_t e = time_launches(st, reps, launch, &ms);
+                if (e != cudaSuccess) return fail_cuda(g, e, "vf_autotune");
+                if (best_ms == 0.f || ms < best_ms) {
+                    best_ms = ms;
+                    pick = c;
+                }
+            }
+            sched[axis] = pick;
+        }
+        const int rc = set_fft_sched(g, sched);
+        if (rc) return rc;
+    }
+    best->fft_x = sched[0];
+    best->fft_y = sched[1];
+    best->fft_z = sched[2];
     return VF_OK;
 }
 
-void apply_tiles(vf_grid* g, const vf_tiles& t)
+int apply_tiles(vf_grid* g, const vf_tiles& t)
 {
     g->zc[vf::kZcStage] = t.zc_stage;
     g->zc[vf::kZcDiv] = t.zc_div;
     g->zc[vf::kZcProject] = t.zc_project;
     g->zc[vf::kZcFilter] = t.zc_filter;
     drop_graphs(g);
+    const int idx[3] = {t.fft_x, t.fft_y, t.fft_z};
+    if (idx[0] == g->fft_sched[0] && idx[1] == g->fft_sched[1] && idx[2] == g->fft_sched[2]) return VF_OK;
+    return set_fft_sched(g, idx);
 }
 
 }  // namespace
@@ -1274,6 +1358,9 @@ int vf_get_tiles(const vf_grid* g, vf_tiles* out)
     out->zc_div = g->zc[vf::kZcDiv];
     out->zc_project = g->zc[vf::kZcProject];
     out->zc_filter = g->zc[vf::kZcFilter];
+    out->fft_x = g->fft_sched[0];
+    out->fft_y = g->fft_sched[1];
+    out->fft_z = g->fft_sched[2];
     return VF_OK;
 }
 
@@ -1282,9 +1369,21 @@ int vf_set_tiles(vf_grid* g, const vf_tiles* t)
     int rc = check(g);
     if (rc) return rc;
     if (!t || !tiles_valid(*t)) return set_err(g, VF_EINVAL, "vf_set_tiles: chunk out of range");
+    const int idx[3] = {t->fft_x, t->fft_y, t->fft_z};
+    if (!fft_indices_valid(g, idx)) return set_err(g, VF_EINVAL, "vf_set_tiles: FFT schedule index out of range");
     VF_CK(cudaStreamSynchronize(g->stream));
-    apply_tiles(g, *t);
-    return VF_OK;
+    return apply_tiles(g, *t);
+}
+
+int vf_fft_schedules(int32_t n, int32_t index, int32_t* radices, int32_t max_radices)
+{
+    if (!radices || index < 0 || max_radices < 1) return VF_EINVAL;
+    const std::vector<std::vector<int>> c = vf::fft_schedules(n);
+    if (index >= (int)c.size()) return 0;
+    const std::vector<int>& r = c[index];
+    if ((int)r.size() > max_radices) return VF_EINVAL;
+    for (size_t i = 0; i < r.size(); ++i) radices[i] = r[i];
+    return (int)r.size();
 }
 
 int vf_autotune(vf_grid* g, int32_t reps, vf_tiles* chosen)
@@ -1297,7 +1396,7 @@ int vf_autotune(vf_grid* g, int32_t reps, vf_tiles* chosen)
     rc = g->fp64 ? autotune_t<double>(g, reps, &t) : autotune_t<float>(g, reps, &t);
     if (rc) return rc;
     VF_CK(cudaStreamSynchronize(g->stream));
-    apply_tiles(g, t);
+    if ((rc = apply_tiles(g, t))) return rc;
     {
         std::lock_guard<std::mutex> lock(tile_mutex());
         tile_cache()[TileKey{g->d.nx, g->d.ny, g->d.nz, g->d.precision}] = t;

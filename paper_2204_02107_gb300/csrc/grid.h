@@ -74,6 +74,7 @@ struct vf_grid {
 
     int zc[vf::kZcKinds] = {4, 32, 8, 16};  // z-chunks (vf_tiles): stage, divergence, projection, filter
 
+    int fft_sched[3] = {0, 0, 0};          // radix schedule index per axis (vf_tiles fft_x, fft_y, fft_z)
     vf::FftAxis ax{}, ay{}, az{};
     int rows_per_block = 1, cols_per_block = 16;
 

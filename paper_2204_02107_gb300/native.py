@@ -48,7 +48,7 @@ class VfBatchDesc(C.Structure):
 
 class VfTiles(C.Structure):
     _fields_ = [("zc_stage", C.c_int32), ("zc_div", C.c_int32), ("zc_project", C.c_int32),
-                ("zc_filter", C.c_int32)]
+                ("zc_filter", C.c_int32), ("fft_x", C.c_int32), ("fft_y", C.c_int32), ("fft_z", C.c_int32)]
 
     def to_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -104,6 +104,7 @@ _SIGNATURES = {
     "vf_get_tiles": (C.c_int, [C.c_void_p, C.POINTER(VfTiles)]),
     "vf_set_tiles": (C.c_int, [C.c_void_p, C.POINTER(VfTiles)]),
     "vf_autotune": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(VfTiles)]),
+    "vf_fft_schedules": (C.c_int, [C.c_int32, C.c_int32, C.POINTER(C.c_int32), C.c_int32]),
     "vf_tile_cache_lookup": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.POINTER(VfTiles)]),
     "vf_tile_cache_clear": (C.c_int, []),
     "vf_batch_create": (C.c_int, [C.POINTER(VfBatchDesc), C.POINTER(C.c_void_p)]),
@@ -498,17 +499,21 @@ class Grid:
         return {lib().vf_phase_name(i).decode(): (ms[i], cnt[i]) for i in range(N_PHASES) if cnt[i] > 0}
 
     def tiles(self):
-        """The launch tiles (z-chunks per kernel family) of this grid."""
+        """The launch tiles of this grid: z-chunks per kernel family and the FFT radix schedule per axis."""
         t = VfTiles()
         self._check(lib().vf_get_tiles(self._h, C.byref(t)), "vf_get_tiles")
         return t.to_dict()
 
-    def set_tiles(self, zc_stage, zc_div, zc_project, zc_filter):
-        t = VfTiles(zc_stage, zc_div, zc_project, zc_filter)
+    def set_tiles(self, zc_stage, zc_div, zc_project, zc_filter, fft_x=None, fft_y=None, fft_z=None):
+        """Set the z-chunks; FFT schedule indices left as None keep the grid's current ones."""
+        cur = self.tiles()
+        fft = [cur[k] if v is None else v for k, v in (("fft_x", fft_x), ("fft_y", fft_y), ("fft_z", fft_z))]
+        t = VfTiles(zc_stage, zc_div, zc_project, zc_filter, *fft)
         self._check(lib().vf_set_tiles(self._h, C.byref(t)), "vf_set_tiles")
 
     def autotune(self, reps=5):
-        """Time every z-chunk per kernel family on this grid, keep the fastest and cache it for the shape."""
+        """Time every z-chunk per kernel family on this grid, then (generic FFT path) every radix schedule per
+        axis; keep the fastest and cache them for the shape."""
         t = VfTiles()
         self._check(lib().vf_autotune(self._h, int(reps), C.byref(t)), "vf_autotune")
         return t.to_dict()
@@ -517,6 +522,19 @@ class Grid:
         """Solve L p = f on the device (f, p: contiguous CUDA tensors in the grid's precision)."""
         self._check(lib().vf_poisson_solve(self._h, C.c_void_p(f.data_ptr()), C.c_void_p(p.data_ptr())),
                     "vf_poisson_solve")
+
+
+def fft_schedules(n):
+    """Candidate radix schedules of the generic FFT passes for length n (``vf_fft_schedules``), default first."""
+    out = []
+    buf = (C.c_int32 * 16)()
+    while True:
+        k = lib().vf_fft_schedules(int(n), len(out), buf, 16)
+        if k < 0:
+            raise VentflowError(k, "vf_fft_schedules")
+        if k == 0:
+            return out
+        out.append([buf[i] for i in range(k)])
 
 
 def measure_fp64_rate():

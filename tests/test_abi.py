@@ -98,3 +98,33 @@ def test_host_metrics_match_oracle(lib):
         assert p == pytest.approx(V.infection_probability(q), rel=1e-12)
     with pytest.raises(native.VentflowError):
         native.wells_riley(1.0, 1.2, -1.0, 0.5)
+
+
+def test_fft_schedules(lib):
+    """Radix schedules of the generic FFT passes: every candidate factors n into radices the kernels implement,
+    candidates are distinct, at most 8, and candidate 0 is the documented default (fewest power-of-two passes,
+    then the 3s and 5s)."""
+    default = {8: [8], 16: [16], 32: [4, 8], 64: [8, 8], 128: [16, 8], 256: [16, 16], 12: [4, 3],
+               20: [4, 5], 36: [4, 3, 3], 72: [8, 3, 3], 80: [16, 5], 96: [4, 8, 3], 120: [8, 3, 5],
+               160: [4, 8, 5], 192: [8, 8, 3], 1024: [16, 8, 8]}
+    for n in range(2, 1025):
+        cands = native.fft_schedules(n)
+        m = n
+        for p in (2, 3, 5):
+            while m % p == 0:
+                m //= p
+        if m != 1:
+            assert cands == [], n
+            continue
+        assert 1 <= len(cands) <= 8, n
+        assert len({tuple(c) for c in cands}) == len(cands), n
+        for c in cands:
+            assert int(np.prod(c)) == n and set(c) <= {2, 3, 4, 5, 8, 16}, (n, c)
+        if n in default:
+            assert cands[0] == default[n], (n, cands[0])
+    # several schedules for the mixed lengths of the batch rooms
+    assert all(len(native.fft_schedules(n)) >= 3 for n in (36, 40, 48, 60, 72, 80, 96))
+    buf = (ctypes.c_int32 * 2)()
+    assert lib.vf_fft_schedules(1024, 0, buf, 2) == native.VF_EINVAL      # three radices do not fit in two
+    assert lib.vf_fft_schedules(64, -1, buf, 2) == native.VF_EINVAL
+    assert lib.vf_fft_schedules(64, 99, buf, 2) == 0

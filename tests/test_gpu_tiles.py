@@ -3,19 +3,21 @@
 A tile changes how the stencil kernels are split into CTAs, never what a cell computes: the fields after any
 number of steps are bitwise the same under every tiling, including chunks that leave a ragged last chunk along z
 and chunks larger than nz.  The reductions are summed per CTA, so only their last bits may follow the filter's
-chunk; the histogram is exact.  The autotuner writes scratch arrays only and its choice is cached per shape."""
+chunk; the histogram is exact.  The autotuner writes scratch arrays only and its choice is cached per shape; on the
+generic FFT path it also picks the FFT radix schedules, which change the rounding order only."""
 import numpy as np
 import pytest
 
 from oracle import flow as F
 from paper_2204_02107_gb300 import native, rooms
-from gpu_helpers import FIELD_NAMES, field_errors, gpu_grid, load_state, read_state, require_gpu
+from gpu_helpers import FIELD_NAMES, field_errors, gpu_grid, load_state, read_state, rel_l2, require_gpu
 from gpu_helpers import room_case as oracle_case
 
 pytestmark = pytest.mark.gpu
 
 ALL = FIELD_NAMES + ("p",)
-DEFAULT = {"zc_stage": 4, "zc_div": 32, "zc_project": 8, "zc_filter": 16}
+DEFAULT = {"zc_stage": 4, "zc_div": 32, "zc_project": 8, "zc_filter": 16, "fft_x": 0, "fft_y": 0, "fft_z": 0}
+ZC = ("zc_stage", "zc_div", "zc_project", "zc_filter")
 # Reductions under another filter chunk are summed in another order.  FP32: the kinetic energy is a plain float sum
 # of at most 64 non-negative terms per thread before the float-float and FP64 stages, so its relative change is
 # below 64 * 2^-24 < 4e-6; the scalar inventories are compensated (float-float) sums, good to ~2^-44 of the sum.
@@ -105,7 +107,7 @@ def test_autotune_keeps_state_and_caches_choice(torch, precision):
     hist_before = g.history()
     info_before = g.info()
     chosen = g.autotune(reps=3)
-    assert set(chosen.values()) <= {4, 8, 16, 32}
+    assert {chosen[k] for k in ZC} <= {4, 8, 16, 32}
     assert g.tiles() == chosen
     assert native.tile_cache_lookup(room.nx, room.ny, room.nz, precision) == chosen
     for n in ALL:
@@ -114,14 +116,22 @@ def test_autotune_keeps_state_and_caches_choice(torch, precision):
     hist_after = g.history()
     assert len(hist_after) == len(hist_before)
     assert [h["ke"] for h in hist_after] == [h["ke"] for h in hist_before]
-    # stepping on: the same fields as a grid that never autotuned
+    # stepping on: the same fields as a grid that never autotuned and switches to the chosen FFT schedules after
+    # the same 5 steps (the z-chunks change no field value; another FFT schedule only the rounding order)
     g.step(7, reduce_every=1)
     tuned = {n: g.read_field(n) for n in ALL}
     g.close()
     native.tile_cache_clear()
-    ref, _ = run(room, precision, None, steps=12)
+    g2 = native.room_grid(room, precision=precision)
+    g2.step(5, reduce_every=1)
+    g2.set_tiles(8, 8, 8, 16, chosen["fft_x"], chosen["fft_y"], chosen["fft_z"])
+    g2.step(7, reduce_every=1)
     for n in ALL:
-        assert np.array_equal(tuned[n], ref[n]), n
+        assert np.array_equal(g2.read_field(n), tuned[n]), n
+    g2.close()
+    untuned, _ = run(room, precision, None, steps=12)
+    for n in ALL:
+        assert rel_l2(tuned[n], untuned[n]) < (1e-12 if precision == "fp64" else 1e-5), n
 
 
 def test_new_grid_takes_cached_tiles(torch):
