@@ -231,11 +231,29 @@ def run_reference(args):
         return 0
     from oracle import flow as F
     from paper_2204_02107_gb300 import rooms
-    room = rooms.single_room(128, 64, 64)
-    prm = F.Params(nx=room.nx, ny=room.ny, nz=room.nz, lx=room.lx, ly=room.ly, lz=room.lz, nu=rooms.NU_AIR,
-                   dt=room.dt, u_set=(room.u_in, 0.0, 0.0), c_set=0.0, filter=True, n_pressure_iters=4)
-    geom = F.Geometry(room.beta, room.S, room.room)
-    st = F.zero_state(prm, c=room.initial_c())
+
+    def case(nx, ny, nz):
+        room = rooms.single_room(nx, ny, nz)
+        prm = F.Params(nx=room.nx, ny=room.ny, nz=room.nz, lx=room.lx, ly=room.ly, lz=room.lz, nu=rooms.NU_AIR,
+                       dt=room.dt, u_set=(room.u_in, 0.0, 0.0), c_set=0.0, filter=True, n_pressure_iters=4)
+        return room, prm, F.Geometry(room.beta, room.S, room.room), F.zero_state(prm, c=room.initial_c())
+
+    # the sample: the largest room of the ladder whose estimated warm-up + timed steps fit the time budget, the
+    # estimate scaled by cells from one timed step of the smallest room (per-cell cost falls with size, so the
+    # estimate errs long)
+    ladder = [(128, 64, 64), (64, 32, 32), (32, 16, 16)]
+    budget_s = 150.0
+    room, prm, geom, st = case(*ladder[-1])
+    st, _ = F.step(st, geom, prm)
+    t0 = time.perf_counter()
+    F.step(st, geom, prm)
+    per_cell = (time.perf_counter() - t0) / room.cells
+    pick = ladder[-1]
+    for shape in ladder:
+        if per_cell * shape[0] * shape[1] * shape[2] * (args.steps + args.warmup) <= budget_s:
+            pick = shape
+            break
+    room, prm, geom, st = case(*pick)
     for _ in range(args.warmup):
         st, _ = F.step(st, geom, prm)
     t0 = time.perf_counter()
@@ -243,12 +261,14 @@ def run_reference(args):
         st, _ = F.step(st, geom, prm)
     el = time.perf_counter() - t0
     value = room.cells * args.steps / el / 1e9
-    sample = ("each step one full FP64 oracle step of the same room construction at 128x64x64 (1/8 of the cells "
-              "of the 256x128x128 room), numpy on one host core")
+    frac = room.cells / (256 * 128 * 128)
+    sample = (f"each step one full FP64 oracle step of the same room construction at {pick[0]}x{pick[1]}x{pick[2]} "
+              f"({frac:.4g} of the cells of the 256x128x128 room; the largest of 128x64x64, 64x32x32, 32x16x16 "
+              f"whose {args.steps} + {args.warmup} steps fit about {budget_s:.0f} s), numpy on one host core")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3 / max(1, args.steps),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": "single room 256x128x128 (sampled at 128x64x64)",
+            "data": "synthetic", "config": {"workload": f"single room 256x128x128 (sampled at {pick[0]}x{pick[1]}x{pick[2]})",
                                             "cells": room.cells, "parallelism": "none (host oracle)"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
