@@ -219,58 +219,125 @@ def cpu_baseline_oracle(room, precision_note, steps=1):
     for _ in range(steps):
         st, _ = F.step(st, geom, prm)
     dt = time.perf_counter() - t0
-    return {"value": room.cells * steps / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{steps} full FP64 step(s) of the {room.nx}x{room.ny}x{room.nz} room ({precision_note}); "
-                      f"numpy element-wise ops and numpy.fft run on one core"}
+    single = {"value": room.cells * steps / dt / 1e9, "unit": UNIT, "cores": 1,
+              "sample": f"{steps} full FP64 step(s) of the {room.nx}x{room.ny}x{room.nz} room ({precision_note}); "
+                        f"numpy element-wise ops and numpy.fft run on one core"}
+    # every host core: one copy of a 128x64x64 room of the same construction per core, 3 timed steps after 1
+    procs = host_cores()
+    value, _ = oracle_all_cores((128, 64, 64), 3, 1, procs)
+    return {"value": value, "unit": UNIT, "cores": procs, "kind": "oracle",
+            "sample": f"{procs} independent copies (one process per host core, one thread each) of the room "
+                      f"construction at 128x64x64 (1/8 of the cells), 3 full FP64 steps each ({precision_note}) "
+                      f"after 1 warm-up step, timed from a common barrier to the slowest process",
+            "single_core_full_size": single}
 
 
-def run_reference(args):
-    """--impl reference: the oracle on the host cores, on a bounded sample of the workload."""
-    world, rank, _ = dist_setup()
-    if rank != 0:
-        return 0
+def oracle_room(nx, ny, nz):
+    """The oracle's inputs for the single-room construction at nx x ny x nz (filter on, 4 pressure iterations)."""
     from oracle import flow as F
     from paper_2204_02107_gb300 import rooms
+    room = rooms.single_room(nx, ny, nz)
+    prm = F.Params(nx=room.nx, ny=room.ny, nz=room.nz, lx=room.lx, ly=room.ly, lz=room.lz, nu=rooms.NU_AIR,
+                   dt=room.dt, u_set=(room.u_in, 0.0, 0.0), c_set=0.0, filter=True, n_pressure_iters=4)
+    return room, prm, F.Geometry(room.beta, room.S, room.room), F.zero_state(prm, c=room.initial_c())
 
-    def case(nx, ny, nz):
-        room = rooms.single_room(nx, ny, nz)
-        prm = F.Params(nx=room.nx, ny=room.ny, nz=room.nz, lx=room.lx, ly=room.ly, lz=room.lz, nu=rooms.NU_AIR,
-                       dt=room.dt, u_set=(room.u_in, 0.0, 0.0), c_set=0.0, filter=True, n_pressure_iters=4)
-        return room, prm, F.Geometry(room.beta, room.S, room.room), F.zero_state(prm, c=room.initial_c())
 
-    # the sample: the largest room of the ladder whose estimated warm-up + timed steps fit the time budget, the
-    # estimate scaled by cells from one timed step of the smallest room (per-cell cost falls with size, so the
-    # estimate errs long)
+def oracle_worker(shape, steps, warmup, barrier, queue):
+    """One host process: warm-up oracle steps, a barrier shared by every process, then ``steps`` timed steps; puts
+    the elapsed seconds of the timed steps (or the error) on the queue."""
+    try:
+        from oracle import flow as F
+        room, prm, geom, st = oracle_room(*shape)
+        for _ in range(warmup):
+            st, _ = F.step(st, geom, prm)
+        barrier.wait(timeout=900)
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            st, _ = F.step(st, geom, prm)
+        queue.put(("ok", time.perf_counter() - t0))
+    except Exception as e:   # reported by the parent
+        queue.put(("error", repr(e)))
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_all_cores(shape, steps, warmup, procs):
+    """The oracle as it stands, one independent copy of the room per host core (spawned processes, one thread
+    each), the timed steps started together after a barrier: whole-host cell-updates/s = procs x cells x steps /
+    the slowest process's time, like the max over ranks of the GPU arm."""
+    import multiprocessing as mp
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[var] = "1"
+    ctx = mp.get_context("spawn")
+    barrier, queue = ctx.Barrier(procs), ctx.Queue()
+    ps = [ctx.Process(target=oracle_worker, args=(shape, steps, warmup, barrier, queue)) for _ in range(procs)]
+    for p in ps:
+        p.start()
+    import queue as queue_mod
+    results = []
+    while len(results) < procs:   # a process that dies without reporting ends the wait
+        try:
+            results.append(queue.get(timeout=1.0))
+        except queue_mod.Empty:
+            if not any(p.is_alive() for p in ps) and queue.empty():
+                for p in ps:
+                    p.join(timeout=1)
+                raise RuntimeError("an oracle process exited without a result")
+    for p in ps:
+        p.join(timeout=60)
+    errors = [r[1] for r in results if r[0] != "ok"]
+    if errors:
+        raise RuntimeError(f"oracle process failed: {errors[0]}")
+    el = max(r[1] for r in results)
+    cells = shape[0] * shape[1] * shape[2]
+    return procs * cells * steps / el / 1e9, el
+
+
+def pick_oracle_sample(steps_total, budget_s, slowdown):
+    """Largest room of the ladder whose steps_total oracle steps fit budget_s, estimated from one timed step of the
+    smallest room scaled by cells and by ``slowdown`` (per-cell cost falls with size, so the estimate errs long)."""
+    from oracle import flow as F
     ladder = [(128, 64, 64), (64, 32, 32), (32, 16, 16)]
-    budget_s = 150.0
-    room, prm, geom, st = case(*ladder[-1])
+    room, prm, geom, st = oracle_room(*ladder[-1])
     st, _ = F.step(st, geom, prm)
     t0 = time.perf_counter()
     F.step(st, geom, prm)
     per_cell = (time.perf_counter() - t0) / room.cells
-    pick = ladder[-1]
     for shape in ladder:
-        if per_cell * shape[0] * shape[1] * shape[2] * (args.steps + args.warmup) <= budget_s:
-            pick = shape
-            break
-    room, prm, geom, st = case(*pick)
-    for _ in range(args.warmup):
-        st, _ = F.step(st, geom, prm)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        st, _ = F.step(st, geom, prm)
-    el = time.perf_counter() - t0
-    value = room.cells * args.steps / el / 1e9
-    frac = room.cells / (256 * 128 * 128)
-    sample = (f"each step one full FP64 oracle step of the same room construction at {pick[0]}x{pick[1]}x{pick[2]} "
-              f"({frac:.4g} of the cells of the 256x128x128 room; the largest of 128x64x64, 64x32x32, 32x16x16 "
-              f"whose {args.steps} + {args.warmup} steps fit about {budget_s:.0f} s), numpy on one host core")
+        if per_cell * slowdown * shape[0] * shape[1] * shape[2] * steps_total <= budget_s:
+            return shape
+    return ladder[-1]
+
+
+def run_reference(args):
+    """--impl reference: the oracle on every host core (one copy of the sample room per core), on a bounded sample
+    of the workload sized so that the warm-up and timed steps end within a few minutes."""
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return 0
+    procs = host_cores()
+    budget_s = 150.0
+    pick = pick_oracle_sample(args.steps + args.warmup, budget_s, slowdown=2.0)   # 2: cores share memory
+    value, el = oracle_all_cores(pick, args.steps, args.warmup, procs)
+    cells = pick[0] * pick[1] * pick[2]
+    frac = cells / (256 * 128 * 128)
+    sample = (f"each step {procs} independent full FP64 oracle steps (one process per host core) of the same room "
+              f"construction at {pick[0]}x{pick[1]}x{pick[2]} ({frac:.4g} of the cells of the 256x128x128 room; "
+              f"the largest of 128x64x64, 64x32x32, 32x16x16 whose {args.steps} + {args.warmup} steps fit about "
+              f"{budget_s:.0f} s); numpy, one thread per process")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3 / max(1, args.steps),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": f"single room 256x128x128 (sampled at {pick[0]}x{pick[1]}x{pick[2]})",
-                                            "cells": room.cells, "parallelism": "none (host oracle)"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "data": "synthetic",
+            "config": {"workload": f"single room 256x128x128 (sampled at {pick[0]}x{pick[1]}x{pick[2]}, "
+                                   f"one copy per host core)", "cells": cells * procs,
+                       "parallelism": f"{procs} host processes (host oracle)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": procs, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
