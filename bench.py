@@ -224,7 +224,11 @@ def cpu_baseline_oracle(room, precision_note, steps=1):
                         f"numpy element-wise ops and numpy.fft run on one core"}
     # every host core: one copy of a 128x64x64 room of the same construction per core, 3 timed steps after 1
     procs = host_cores()
-    value, _ = oracle_all_cores((128, 64, 64), 3, 1, procs)
+    try:
+        value, _ = oracle_all_cores((128, 64, 64), 3, 1, procs)
+    except Exception as e:   # keep the measured single-core figure rather than lose the line
+        return {"value": single["value"], "unit": UNIT, "cores": 1, "kind": "oracle", "sample": single["sample"],
+                "all_cores_error": repr(e)}
     return {"value": value, "unit": UNIT, "cores": procs, "kind": "oracle",
             "sample": f"{procs} independent copies (one process per host core, one thread each) of the room "
                       f"construction at 128x64x64 (1/8 of the cells), 3 full FP64 steps each ({precision_note}) "
@@ -323,7 +327,20 @@ def run_reference(args):
     procs = host_cores()
     budget_s = 150.0
     pick = pick_oracle_sample(args.steps + args.warmup, budget_s, slowdown=2.0)   # 2: cores share memory
-    value, el = oracle_all_cores(pick, args.steps, args.warmup, procs)
+    try:
+        value, el = oracle_all_cores(pick, args.steps, args.warmup, procs)
+    except Exception as e:   # one process in this one instead of no line
+        print(f"all-core oracle run failed ({e!r}); timing this process alone", file=sys.stderr)
+        from oracle import flow as F
+        procs = 1
+        room, prm, geom, st = oracle_room(*pick)
+        for _ in range(args.warmup):
+            st, _ = F.step(st, geom, prm)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            st, _ = F.step(st, geom, prm)
+        el = time.perf_counter() - t0
+        value = room.cells * args.steps / el / 1e9
     cells = pick[0] * pick[1] * pick[2]
     frac = cells / (256 * 128 * 128)
     sample = (f"each step {procs} independent full FP64 oracle steps (one process per host core) of the same room "
