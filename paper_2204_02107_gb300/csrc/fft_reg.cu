@@ -1,5 +1,6 @@
 // Register-resident passes of the FFT Poisson solve (Sec. 2.2, Eqs. 7-9) for grids whose axis lengths are all
-// 16 G with G in {1, 2, 4, 8, 16} (nx = 32 G_x) and whose (y, z) plane fits in shared memory.
+// 16 G with G in {1, 2, 4, 8, 16} (nx = 32 G_x); the (y, z) work is one whole-plane kernel when the plane of one kx
+// fits in shared memory, else the tile mode further down.
 //
 // A transform of n = 16 G points is done by G threads of one warp.  Thread t holds x[t + G m] (m = 0..15),
 // does a 16-point DFT in registers, multiplies by W_n^(t k1), exchanges through a slice of shared memory that
