@@ -1,7 +1,8 @@
 """Pins of the oracle's Lagrangian particles (Sec. 2.3).
 
 Fixed by: the interpolation's exactness on cell values and on linear fields; the paper's printed sedimentation
-times; the closed form of the implicit-Euler recurrence; relaxation to a uniform flow; deposition on a floor."""
+times; the closed form of the implicit-Euler recurrence; relaxation to a uniform flow; deposition on a floor; the
+drag law at Reynolds numbers with integer 2/3 powers and one step at a slip Reynolds number of 27."""
 import json
 import os
 
@@ -106,3 +107,31 @@ def test_deposits_on_a_floor():
     assert dep[0] and np.all(vel == 0.0)
     k = int(np.floor(pos[0, 2] / prm.h[2] + 0.5))
     assert beta[k, 4, 4] == 1.0 and pos[0, 2] < 0.7    # stopped in the last fluid cell above the floor
+
+
+def test_drag_law_special_values():
+    """C_d = 1 + Re_p^(2/3) / 6 (Sec. 2.3) at Reynolds numbers whose 2/3 power is an integer: Stokes drag at 0,
+    5/3 at 8, 5/2 at 27, 1 + 100/6 at 1000 (a wrong exponent or coefficient misses all but the first)."""
+    re = np.array([0.0, 8.0, 27.0, 1000.0])
+    assert P.drag_coefficient(re) == pytest.approx([1.0, 5.0 / 3.0, 2.5, 1.0 + 100.0 / 6.0], rel=1e-14)
+
+
+def test_step_uses_drag_at_the_start_of_step_slip():
+    """A particle at rest in a uniform stream whose slip Reynolds number is 27: one implicit Euler step gives
+    u_p' = a U / (1 + a) with a = dt C_d / tau_p and C_d = 5/2 taken at the starting slip (the reading of Sec. 2.3's
+    implicit Euler with a nonlinear drag); dropping the Re correction (C_d = 1) or taking C_d at the new slip
+    fails this."""
+    prm = prm_box()
+    d = 100e-6
+    U = 27.0 * NU / d                               # slip Reynolds number U d / nu = 27
+    u = np.full(prm.shape, U)
+    zero = np.zeros(prm.shape)
+    tau = RHO_P * d * d / (18.0 * RHO_F * NU)       # Sec. 2.3's relaxation time
+    dt = 0.05 * tau
+    a = dt * 2.5 / tau
+    pos, vel, dep = P.particle_step(np.array([[1.0, 1.0, 2.0]]), np.zeros((1, 3)), np.array([d]),
+                                    np.zeros(1, dtype=bool), u, zero, zero, np.ones(prm.shape), prm, dt, RHO_P,
+                                    RHO_F, (0.0, 0.0, 0.0))
+    assert vel[0, 0] == pytest.approx(a * U / (1.0 + a), rel=1e-12)
+    assert vel[0, 1] == 0.0 and vel[0, 2] == 0.0
+    assert pos[0, 0] == pytest.approx(1.0 + dt * a * U / (1.0 + a), rel=1e-12)
