@@ -305,7 +305,9 @@ int vf_batch_sync(vf_batch* b);
 /* Wait for enqueued steps; write up to max_slots finished slots to done_slots, their total to *n_done. */
 int vf_batch_poll(vf_batch* b, int32_t* done_slots, int32_t max_slots, int32_t* n_done);
 
-/* The grid of a slot (NULL if empty): read its fields and history with the vf_grid calls after vf_batch_poll. */
+/* The grid of a slot (NULL if empty): read its fields and history with the vf_grid calls after vf_batch_poll.  The
+ * batch's step graph holds the slot's launch shapes: do not change them through this handle (vf_set_tiles,
+ * vf_autotune) while the slot is in the batch. */
 vf_grid* vf_batch_grid(vf_batch* b, int32_t slot);
 
 /* Free a slot and its memory (waits for enqueued steps). */
