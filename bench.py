@@ -589,9 +589,11 @@ def bench_fft_vs_cufft(stream, nx=256, ny=128, nz=128, lengths=(10.0, 5.0, 5.0),
             "cufft_path": "torch.fft.rfftn, multiply by 1/lambda, torch.fft.irfftn on the same stream"}
 
 
-def e2e_run(room, precision, steps, stream):
+def e2e_run(room, precision, steps, stream, per_step=False):
     """End to end through the C ABI with pinned host buffers: grid creation, mask / inflow / region / scalar
-    upload, ``steps`` steps with a reduction record each, then the records and all five fields read back."""
+    upload, ``steps`` steps with a reduction record each, then the records and all five fields read back.
+    per_step: every step is its own vf_step(1) followed by vf_history(1), which copies that step's record to the
+    host and so waits for the step (a caller monitoring every step)."""
     import torch
     from paper_2204_02107_gb300 import native
     n = room.cells
@@ -614,8 +616,14 @@ def e2e_run(room, precision, steps, stream):
     g.set_inflow(S, (room.u_in, 0.0, 0.0), 0.0)
     g.set_region(region)
     g.set_field("c", c0)
-    g.step(steps, reduce_every=1)
-    hist = g.history(steps)
+    if per_step:
+        hist = []
+        for _ in range(steps):
+            g.step(1, reduce_every=1)
+            hist += g.history(1)
+    else:
+        g.step(steps, reduce_every=1)
+        hist = g.history(steps)
     for name, out in zip(("u", "v", "w", "c", "p"), outs):
         native.lib().vf_read_field(g._h, native.FIELDS[name], native.C.c_void_p(out.ctypes.data), 0,
                                    native.VF_HOST)
@@ -623,11 +631,14 @@ def e2e_run(room, precision, steps, stream):
     el = time.perf_counter() - t0
     g.close()
     h2d = 3 * n + 4 * n
-    d2h = 5 * 4 * n + len(hist) * native.C.sizeof(native.VfReduce)
+    d2h = 5 * 4 * n + len(hist) * native.C.sizeof(native.VfReduce) + (8 * steps if per_step else 8)
+    what = ("create grid + upload mask, forcing region, room region, scalar (pinned host) + steps with per-step FP64 "
+            "reductions + read back the reduction records and u, v, w, c, p")
+    if per_step:
+        what += "; each step launched alone and its record read back (a host wait) before the next"
     return {"value": n * steps / el / 1e9, "unit": UNIT, "h2d_bytes_per_step": h2d / steps,
-            "d2h_bytes_per_step": d2h / steps, "seconds": el,
-            "what": "create grid + upload mask, forcing region, room region, scalar (pinned host) + steps with "
-                    "per-step FP64 reductions + read back the reduction records and u, v, w, c, p"}
+            "d2h_bytes_per_step": d2h / steps, "seconds": el, "steps": steps, "records_read": len(hist),
+            "last_record_step": hist[-1]["step"] if hist else None, "what": what}
 
 
 def main():
@@ -738,6 +749,10 @@ def main():
     fp64_achieved = None if fp64_flops is None else fp64_flops * cells / (fp64_ms / args.fp64_steps / 1e3) / 1e9
 
     e2e = e2e_run(room, "fp32", args.steps, stream)
+    try:
+        e2e_each = e2e_run(room, "fp32", min(args.steps, 500), stream, per_step=True)
+    except Exception as e:   # an extra figure: never costs the line
+        e2e_each = {"error": repr(e)}
     g.close()
     extras = {"fft_vs_cufft": bench_fft_vs_cufft(stream)}
     if not args.no_extras and world == 1:
@@ -772,6 +787,7 @@ def main():
                               "frac": None if fp64_achieved is None else fp64_achieved / fp64_peak,
                               "flops_per_cell_step": fp64_flops}},
         "e2e": e2e,
+        "e2e_result_read_every_step": e2e_each,
         "gpu_launches": int(round(sum(n for _, n in phases.values()) / prof_steps)) * args.steps,
         "clocks": clocks.summary(),
         "last_record": {k: hist[-1][k] for k in ("step", "ke", "c_room", "div_max", "u_max")} if hist else None,
