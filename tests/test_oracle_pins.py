@@ -444,3 +444,46 @@ def test_region_force_closed_forms():
     f = F.region_force(st, geom, prm, region)
     # convection of u(y) alone vanishes (v = w = 0, d/dx u = 0); diffusion: nu * 2 * 3.0 per cell
     assert f[0] == pytest.approx(prm.nu * 6.0 * 18 * prm.cell_volume, rel=1e-10)
+
+
+def test_reductions_closed_forms():
+    """The diagnostics (Sec. 3.3) of a state whose sums have closed forms over whole periods: u = A sin(2 pi x/lx),
+    v = B cos(2 pi z/lz), w = C; c = c0 everywhere except three room cells at -0.01, 1.0 and 1.02.  Then
+    KE = V (A^2/2 + B^2/2 + C^2) / 2, D u = a cos(2 pi x/lx) with a = A sin(2 pi/nx)/hx (v and w carry no
+    divergence), so div_max = |a| and div_l2 = |a| sqrt(V/2); u_max = max(|A|, |B|, |C|); the scalar sums are
+    counts times the values, and every room cell falls in bin floor(64 c0) except c = 1 (last bin, by the min rule)
+    and the two cells outside [0, 1]."""
+    nx, ny, nz = 16, 12, 10
+    prm = F.Params(nx=nx, ny=ny, nz=nz, lx=1.6, ly=0.9, lz=1.3, nu=0.0, dt=1.0)
+    hx, hy, hz = prm.h
+    dV = hx * hy * hz
+    vol = prm.lx * prm.ly * prm.lz
+    A, B, C, c0 = 0.7, -0.45, 0.2, 0.41
+    i = np.arange(nx)
+    k = np.arange(nz)
+    u = np.broadcast_to(A * np.sin(2 * math.pi * i / nx)[None, None, :], prm.shape).copy()
+    v = np.broadcast_to(B * np.cos(2 * math.pi * k / nz)[:, None, None], prm.shape).copy()
+    w = np.full(prm.shape, C)
+    c = np.full(prm.shape, c0)
+    room = np.zeros(prm.shape)
+    room[:, :, : nx // 2] = 1.0                       # x < 8: the room
+    c[3, 4, 2], c[5, 6, 1], c[7, 2, 5] = -0.01, 1.0, 1.02
+    st = F.State(u, v, w, c, np.zeros(prm.shape))
+    rec = F.reductions(st, F.Geometry(np.ones(prm.shape), np.zeros(prm.shape), room), prm)
+    a = A * math.sin(2 * math.pi / nx) / hx
+    n_room = (nx // 2) * ny * nz
+    v_room = n_room * dV
+    assert rec['ke'] == pytest.approx(0.5 * vol * (A * A / 2 + B * B / 2 + C * C), rel=1e-13)
+    assert rec['div_max'] == pytest.approx(abs(a), rel=1e-13)
+    assert rec['div_l2'] == pytest.approx(abs(a) * math.sqrt(vol / 2), rel=1e-13)
+    assert rec['u_max'] == pytest.approx(max(abs(A), abs(B), abs(C)), rel=1e-15)
+    odd = [-0.01, 1.0, 1.02]
+    assert rec['v_room'] == pytest.approx(v_room, rel=1e-14)
+    assert rec['c_total'] == pytest.approx(dV * ((nx * ny * nz - 3) * c0 + sum(odd)), rel=1e-13)
+    assert rec['c_room'] == pytest.approx(dV * ((n_room - 3) * c0 + sum(odd)), rel=1e-13)
+    assert rec['c2_room'] == pytest.approx(dV * ((n_room - 3) * c0 * c0 + sum(x * x for x in odd)), rel=1e-13)
+    want = np.zeros(64, dtype=np.int64)
+    want[int(64 * c0)] = n_room - 3
+    want[63] = 1
+    assert np.array_equal(rec['hist'], want)
+    assert (rec['hist_under'], rec['hist_over']) == (1, 1)
