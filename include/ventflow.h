@@ -243,10 +243,11 @@ int vf_get_tiles(const vf_grid* g, vf_tiles* out);
  * grid is unchanged then).  Takes effect at the next vf_step (the step graph is captured again).  Waits. */
 int vf_set_tiles(vf_grid* g, const vf_tiles* t);
 
-/* Radix schedule `index` of the generic FFT passes for a transform of length n: writes its radices (each 2, 3, 4,
- * 5, 8 or 16, product n, applied in this order) to radices[0 .. count-1] and returns count; returns 0 when index is
- * past the last candidate (or n is not 2-3-5 smooth), VF_EINVAL for a NULL radices, index < 0 or max_radices too
- * small (16 always suffices).  Candidate 0 is the default: as few power-of-two passes as possible, then the 3s and
+/* Radix schedule `index` of the generic FFT passes for a transform of length n (an implementation choice; the paper
+ * has no counterpart beyond its use of the FFT in Sec. 2.2): writes its radices (each 2, 3, 4, 5, 8 or 16, product
+ * n, applied in this order) to radices[0 .. count-1] and returns count; returns 0 when index is past the last
+ * candidate (or n is not 2-3-5 smooth), VF_EINVAL for a NULL radices, index < 0 or max_radices too small (16
+ * always suffices).  Candidate 0 is the default: as few power-of-two passes as possible, then the 3s and
  * 5s; the others (at most 8 in all) split the power-of-two part into radix-16, radix-8 or radix-4 passes (radix-2
  * too when it is at most 8), or run the default's small radices first, with the odd factors last or first.  Host
  * only. */
