@@ -19,6 +19,7 @@ import hashlib
 import json
 import math
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -153,19 +154,27 @@ def dist_barrier(world):
         dist.barrier()
 
 
+def code_text(text):
+    """Source text without its comments, whitespace runs collapsed: what the compiler reads of it."""
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
 def source_digest(path, end_marker=None):
-    """SHA-256 of a source file, or of its text up to the first line that starts with ``end_marker`` (the part a
-    kernel and the helpers above it are compiled from); None when the file or the marker is missing."""
+    """SHA-256 of the code of a source file (comments and layout aside), or of its text up to the first line that
+    starts with ``end_marker`` (the part a kernel and the helpers above it are compiled from); None when the file or
+    the marker is missing."""
     full = os.path.join(ROOT, path)
     if not os.path.exists(full):
         return None
-    data = open(full, "rb").read()
+    data = open(full, encoding="utf-8").read()
     if end_marker:
-        cut = data.find(b"\n" + end_marker.encode())
+        cut = data.find("\n" + end_marker)
         if cut < 0:
             return None
         data = data[:cut + 1]
-    return hashlib.sha256(data).hexdigest()
+    return hashlib.sha256(code_text(data).encode()).hexdigest()
 
 
 def traffic_record(kernel, tiles):
@@ -201,8 +210,7 @@ def fp64_flop_record():
     with open(path) as f:
         rec = json.load(f)
     for src, digest in rec.get("sources", {}).items():
-        full = os.path.join(ROOT, src)
-        if not os.path.exists(full) or hashlib.sha256(open(full, "rb").read()).hexdigest() != digest:
+        if source_digest(src) != digest:
             return None
     return rec.get("flops_per_cell_step")
 
