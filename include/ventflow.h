@@ -205,7 +205,7 @@ int vf_region_force(vf_grid* g, double force[3]);
  * time is read from the device (waits for the enqueued steps). */
 int vf_info(const vf_grid* g, double* t, int64_t* step, int64_t* cells, int64_t* device_bytes);
 
-/* Solve L p = f once with the grid's FFT Poisson solver (Sec. 2.2, one pass of steps a6-a8): forward 3D FFT,
+/* Solve L p = f once with the grid's FFT Poisson solver (Sec. 2.2, one pass of step 3 above): forward 3D FFT,
  * division by lambda (null modes -> 0), inverse 3D FFT.  f and p are device arrays of nx*ny*nz values in the
  * grid's precision (double for VF_FP64, float otherwise); they may alias.  Uses the grid's spectrum buffer as
  * scratch; stream-ordered on the grid's stream, returns without waiting. */

@@ -87,7 +87,7 @@ __device__ __forceinline__ void sigma_flush(double s, unsigned long long* out)
 }
 
 // ------------------------------------------------------------------------------------------------------------
-// RK4 stage (a1 + a2 + a3)
+// RK4 stage: momentum and scalar right-hand sides and the stage combine (Sec. 2.1, Eqs. 2-4)
 // ------------------------------------------------------------------------------------------------------------
 // k_i = beta [ -sum_j q4h_j ((U_j Q_i)^+ - (U_j Q_i)^- + U_j^0 (Q_i^+ - Q_i^-))          (skew convection)
 //              + nu sum_j ih2_j (Q_i^+ - 2 Q_i^0 + Q_i^-)                                  (diffusion)
@@ -262,7 +262,7 @@ k_stage(StageArgs<T> a, FlowConsts<T> k)
 }
 
 // ------------------------------------------------------------------------------------------------------------
-// Divergence r = sum_j delta_j u_j / dt (a4; divided by dt because the solver works on p / rho)
+// Divergence r = sum_j delta_j u_j / dt (Eq. 9; divided by dt because the solver works on p / rho)
 // ------------------------------------------------------------------------------------------------------------
 constexpr int kDivGroup = 4;
 
@@ -322,7 +322,7 @@ __global__ void __launch_bounds__(TX * TY) k_div(const void* __restrict__ q, T* 
 }
 
 // ------------------------------------------------------------------------------------------------------------
-// Projection u = beta (u* - dt G p) with p = p / rho (a9); c* passes through.  Ticks the device step counter.
+// Projection u = beta (u* - dt G p) with p = p / rho (Eq. 8); c* passes through.  Ticks the device step counter.
 // ------------------------------------------------------------------------------------------------------------
 constexpr int kProjectGroup = 2;
 
@@ -403,7 +403,7 @@ __global__ void __launch_bounds__(TX * TY) k_project(const void* __restrict__ qs
 }
 
 // ------------------------------------------------------------------------------------------------------------
-// Reductions (a11).  Each thread accumulates the cells it visits: compensated (TwoSum) sums for the scalar
+// Reductions (Sec. 3.3).  Each thread accumulates the cells it visits: compensated (TwoSum) sums for the scalar
 // inventories, plain per-thread sums of at most 64 terms for energy and squared divergence, an exact room-cell
 // count, and the histogram as runs of equal bins (shared atomics only when a run ends).  The CTA epilogue
 // combines the warps and writes one partial per quantity; the last CTA to finish (atomic ticket) adds the partials
@@ -838,9 +838,9 @@ k_reduce_state(const void* __restrict__ q, const uint8_t* __restrict__ mask, int
 }
 
 // ------------------------------------------------------------------------------------------------------------
-// Sixth-order filter q <- beta (q + pi^-6 sum_j S6_j q), S6 = (1, -6, 15, -20, 15, -6, 1) (a10, Eq. 6).
+// Sixth-order filter q <- beta (q + pi^-6 sum_j S6_j q), S6 = (1, -6, 15, -20, 15, -6, 1) (Eq. 6).
 // DIVSTAT: also the divergence of the filter's input (the projected velocity, after the projection and before the
-// filter) for the reductions (a11): per warp the sum of d^2 and max |d| into r.div_partial, no CTA barrier.
+// filter) for the reductions (Sec. 3.3): per warp the sum of d^2 and max |d| into r.div_partial, no CTA barrier.
 // ------------------------------------------------------------------------------------------------------------
 template <typename T, bool DIVSTAT, bool SIGMA>
 __global__ void __launch_bounds__(TX * TY, sizeof(T) == 4 ? 4 : 2)

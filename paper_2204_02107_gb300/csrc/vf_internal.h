@@ -203,8 +203,8 @@ struct PoissonArgs {
     FastDiv nx_div;           // i -> i / nx (cell index -> row, correction kernel)
     int rows_per_block;       // rows of the x passes per CTA
     int cols_per_block;       // kx columns of the y / z tile passes per CTA
-    // register path (every axis length 16 G with G in 1, 2, 4, 8, 16 and the plane in shared memory): the
-    // transforms are held in registers, G threads per sequence
+    // register path (every axis length 16 G with G in 1, 2, 4, 8, 16): the transforms are held in registers, G
+    // threads per sequence; whole-plane kernel when the (y, z) plane of one kx fits in shared memory, else tile mode
     int reg;
     int gx, gy, gz;           // M / 16, ny / 16, nz / 16
     int reg_sp;               // complex stride between the z rows of the shared plane

@@ -28,7 +28,7 @@ def grid_coords(prm):
 BASE = F.Params(nx=24, ny=20, nz=18, lx=2.4, ly=3.0, lz=1.8, nu=0.0, dt=1e-2, filter=False, n_pressure_iters=1)
 
 
-# ---------------------------------------------------------------- operators: exact symbols on Fourier modes (P2)
+# ---------------------------------------------------------------- operators: exact symbols on Fourier modes
 
 @pytest.mark.parametrize("d", [0, 1, 2])
 @pytest.mark.parametrize("k", [1, 3, 7])
@@ -70,7 +70,7 @@ def test_filter_symbol():
     np.testing.assert_allclose(ratio, 1 - 3 * 64 / math.pi ** 6, atol=1e-13)
 
 
-# ---------------------------------------------------------------- skew-symmetric convection conserves energy (P11)
+# ---------------------------------------------------------------- skew-symmetric convection conserves energy
 
 def test_skew_symmetric_convection_conserves_energy():
     """sum_cells u . N(u) = 0 for a random, non-solenoidal periodic field (summation by parts of the skew form)."""
@@ -184,7 +184,7 @@ def test_forcing_and_body_force():
     np.testing.assert_allclose(new3.w, -0.6 * 0.05, atol=1e-15)
 
 
-# ---------------------------------------------------------------- Poisson solve (P3)
+# ---------------------------------------------------------------- Poisson solve
 
 def test_poisson_manufactured_modes():
     """p = random combination of non-null modes, f = lambda(k) p_k mode by mode (closed form) -> solve returns p;
@@ -228,7 +228,7 @@ def test_poisson_null_modes_dropped():
     assert F.null_modes(prm).sum() == 8
 
 
-# ---------------------------------------------------------------- beta-iteration vs brute-force projection (P4)
+# ---------------------------------------------------------------- beta-iteration vs brute-force projection
 
 def central_gradient_matrix(shape, h):
     """Dense (3N x N) matrix of the periodic central gradient, built from index arithmetic alone."""
@@ -294,7 +294,7 @@ def test_beta_iteration_residual_decreases():
 
 
 def test_unmasked_projection_divergence_free():
-    """P5: beta = 1, random u*: one iteration is exact; max|D u| * h / max|u| at round-off."""
+    """beta = 1, random u*: one iteration is exact; max|D u| * h / max|u| at round-off."""
     prm = F.Params(nx=16, ny=12, nz=10, lx=1.6, ly=1.2, lz=1.0, nu=0.0, dt=1.0)
     g = F.open_geometry(prm)
     us = rooms.random_fields(prm.shape, seed=8, count=3)
@@ -306,7 +306,7 @@ def test_unmasked_projection_divergence_free():
 # ---------------------------------------------------------------- whole steps
 
 def test_taylor_green_decay():
-    """P6: Taylor-Green on a periodic 32^3 grid of [0, 2 pi)^3, nu = 0.01, dt = 1e-3, 100 steps: the amplitude
+    """Taylor-Green on a periodic 32^3 grid of [0, 2 pi)^3, nu = 0.01, dt = 1e-3, 100 steps: the amplitude
     sqrt(E/E0) follows exp(-3 nu t) (Stokes decay of |k|^2 = 3) to 1e-4, and the field stays divergence-free."""
     n = 32
     prm = F.Params(nx=n, ny=n, nz=n, lx=2 * math.pi, ly=2 * math.pi, lz=2 * math.pi, nu=0.01, dt=1e-3,
@@ -338,7 +338,7 @@ def channel_case(ny=16, b=1e-3, nu=0.05):
 
 
 def test_poiseuille_fixed_point():
-    """P7: the analytic channel profile U(y) = (b/2nu) y (D - y) (Sec. 3.1.1) is a discrete steady state: central
+    """the analytic channel profile U(y) = (b/2nu) y (D - y) (Sec. 3.1.1) is a discrete steady state: central
     second differences are exact on quadratics and the walls sit where U = 0."""
     prm, g, U = channel_case()
     z = np.zeros(prm.shape)
@@ -375,7 +375,7 @@ def small_room_case(seed=2, nx=40, ny=24, nz=20, steps=0):
 
 
 def test_masking_exact_zero_in_solids():
-    """P8: u, v, w, c are exactly zero in every solid cell after every step."""
+    """u, v, w, c are exactly zero in every solid cell after every step."""
     prm, g, st = small_room_case()
     solid = g.beta == 0
     for _ in range(5):
@@ -386,7 +386,7 @@ def test_masking_exact_zero_in_solids():
 
 
 def test_scalar_budget_closes():
-    """P9: the flux-form scalar transport is conservative: over one step the change of the total inventory equals
+    """the flux-form scalar transport is conservative: over one step the change of the total inventory equals
     the RK-weighted forcing inventory minus what the re-mask after the filter removes from solid cells."""
     prm, g, st = small_room_case()
     for _ in range(3):
