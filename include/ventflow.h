@@ -112,7 +112,8 @@ typedef struct vf_grid vf_grid;
 
 /* ---- grid lifecycle ------------------------------------------------------------------------------------- */
 
-/* Fill *d with defaults: 64^3 unit box, nu = 1.6e-5, alpha_c = nu, dt = 1e-3, tau_f = dt, no body force,
+/* Fill *d with defaults (the case parameters of Sec. 2.4; nu of air, Tab. 3): 64^3 unit box, nu = 1.6e-5,
+ * alpha_c = nu, dt = 1e-3, tau_f = dt, no body force,
  * 4 pressure iterations, filter on, FP32_MIXED, 4096 history records, own stream, default allocator. */
 int vf_grid_desc_default(vf_grid_desc* d);
 
@@ -121,12 +122,14 @@ int vf_grid_desc_default(vf_grid_desc* d);
  * grid is ready to step once vf_set_mask has been called.  *out receives the handle (NULL on failure). */
 int vf_create_grid(const vf_grid_desc* d, vf_grid** out);
 
-/* Release everything the grid owns (waits for its stream first).  NULL is accepted. */
+/* Release everything the grid owns (waits for its stream first).  NULL is accepted.  (Resource handling: no
+ * counterpart in the paper.) */
 int vf_destroy(vf_grid* g);
 
 /* ---- inputs (Sec. 2.1: beta, S, u_set, c_set; Sec. 3.3: the room region) ----------------------------------- */
 
-/* beta: nx*ny*nz bytes in `mem`, nonzero = fluid, 0 = solid.  Fields are re-masked (set to zero in solids). */
+/* The binary mask beta of Sec. 2.1 (Eq. 4): nx*ny*nz bytes in `mem`, nonzero = fluid, 0 = solid.  Fields are
+ * re-masked (set to zero in solids). */
 int vf_set_mask(vf_grid* g, const uint8_t* beta, int mem);
 
 /* S: nx*ny*nz bytes, nonzero = forcing region (cells outside the fluid are ignored); u_set[3] and c_set are the
@@ -154,42 +157,49 @@ int vf_set_inflow_values(vf_grid* g, const void* S, int is_fp64, const double u_
  * vf_set_inflow_tanh and vf_set_inflow_values return to constant targets. */
 int vf_set_inflow_field(vf_grid* g, const void* S, const void* targets, int is_fp64, int mem);
 
-/* room: nx*ny*nz bytes, nonzero = counted in c_room, c2_room, v_room and the histogram. */
+/* The room whose CO2 inventory, volume and concentration distribution Sec. 3.3 evaluates: room is nx*ny*nz bytes
+ * in `mem`, nonzero = counted in c_room, c2_room, v_room and the histogram. */
 int vf_set_region(vf_grid* g, const uint8_t* room, int mem);
 
-/* Overwrite one field from nx*ny*nz values (double if is_fp64, else float) in `mem`.  VF_P takes the pressure
+/* Overwrite one field of the state of Sec. 2.1 (u, v, w, c, p) from nx*ny*nz values (double if is_fp64, else
+ * float) in `mem`.  VF_P takes the pressure
  * divided by density p/rho (the warm start of the next pressure solve); u, v, w, c are multiplied by beta on the
  * way in. */
 int vf_set_field(vf_grid* g, int field, const void* src, int is_fp64, int mem);
 
-/* Set the simulated time and step counter of the current state (used when restoring a saved state). */
+/* Set the simulated time and step counter of the current state (with vf_set_field, restores a saved state; no
+ * counterpart in the paper, which only writes its fields out, Sec. 2.4). */
 int vf_set_time(vf_grid* g, double t, int64_t step);
 
 /* ---- stepping -------------------------------------------------------------------------------------------- */
 
-/* Enqueue n time steps on the grid's stream and return without waiting.  Every `reduce_every`-th step (counted
- * from step 0; 0 = never) also records the reductions of the new state into the device history.  Steps replay a
- * captured CUDA graph of one step unless the environment variable VF_NO_GRAPH is set. */
+/* Enqueue n time steps (Sec. 2.1-2.2, steps 1-6 above) on the grid's stream and return without waiting.  Every
+ * `reduce_every`-th step (counted from step 0; 0 = never) also records the reductions of the new state into the
+ * device history.  Steps replay a captured CUDA graph of one step unless the environment variable VF_NO_GRAPH is
+ * set. */
 int vf_step(vf_grid* g, int64_t n, int32_t reduce_every);
 
-/* Wait for all work enqueued on the grid. */
+/* Wait for all work enqueued on the grid (no counterpart in the paper). */
 int vf_sync(vf_grid* g);
 
 /* ---- outputs --------------------------------------------------------------------------------------------- */
 
-/* Copy one field (nx*ny*nz values, double if as_fp64 else float) into dst in `mem`, after all enqueued steps.
+/* Copy one field of the state of Sec. 2.1 (nx*ny*nz values, double if as_fp64 else float) into dst in `mem`,
+ * after all enqueued steps.
  * VF_P is the pressure divided by density, p/rho [m^2/s^2]; the library stores exactly this value, so reading
  * and writing it back restores the state bit for bit. */
 int vf_read_field(vf_grid* g, int field, void* dst, int as_fp64, int mem);
 
-/* Compute the reductions of the current state (waits).  Returns VF_ENONFINITE if a field holds NaN/Inf. */
+/* Compute the reductions (the Sec. 3.3 diagnostics of vf_reduce) of the current state (waits).  Returns
+ * VF_ENONFINITE if a field holds NaN/Inf. */
 int vf_reductions(vf_grid* g, vf_reduce* out);
 
-/* Copy the per-step reduction records taken by vf_step (oldest first, at most max_records of the most recent)
+/* Copy the per-step reduction records (Sec. 3.3 time series) taken by vf_step (oldest first, at most
+ * max_records of the most recent)
  * into out[]; *count receives the number copied.  Waits for enqueued steps. */
 int vf_history(vf_grid* g, vf_reduce* out, int64_t max_records, int64_t* count);
 
-/* Forget the recorded history. */
+/* Forget the recorded history (of the Sec. 3.3 time series). */
 int vf_clear_history(vf_grid* g);
 
 /* Immersed-boundary force on a solid region (the drag of the cube-in-channel case, Sec. 3.1.2).  region: nx*ny*nz
@@ -201,7 +211,8 @@ int vf_set_force_region(vf_grid* g, const uint8_t* region, int mem);
  * density]: the rate at which the mask removes momentum there, the force the fluid exerts on the body.  Waits. */
 int vf_region_force(vf_grid* g, double force[3]);
 
-/* Simulated time, step count, cell count and bytes of device memory held by the grid.  With a dynamic time step the
+/* Simulated time, step count, cell count and bytes of device memory held by the grid (bookkeeping: no
+ * counterpart in the paper).  With a dynamic time step the
  * time is read from the device (waits for the enqueued steps). */
 int vf_info(const vf_grid* g, double* t, int64_t* step, int64_t* cells, int64_t* device_bytes);
 
@@ -268,6 +279,8 @@ int vf_tile_cache_lookup(int32_t nx, int32_t ny, int32_t nz, int32_t precision, 
 int vf_tile_cache_clear(void);
 
 /* ---- batched rooms and continuous batching (many rooms advanced together) --------------------------------- */
+/* The paper runs one case at a time; batching and serving many rooms has no counterpart there.  Each room's step is
+ * the step of Sec. 2.1-2.2 exactly as vf_step runs it. */
 
 /* Device bytes vf_create_grid will allocate for a description (used for admission by memory budget). */
 int64_t vf_grid_bytes(const vf_grid_desc* d);
@@ -358,12 +371,12 @@ int vf_particles_set(vf_grid* g, int64_t n, const double* pos, const double* vel
  * (1 = deposited); any of them may be NULL. */
 int vf_particles_read(vf_grid* g, double* pos, double* vel, int32_t* deposited);
 
-/* Number of particles of the grid. */
+/* Number of particles of the grid (Sec. 2.3). */
 int vf_particles_count(const vf_grid* g, int64_t* n);
 
 /* ---- measurement ----------------------------------------------------------------------------------------- */
 
-/* Kernel phases of one step, in launch order. */
+/* Kernel phases of one step, in launch order (measurement: no counterpart in the paper). */
 #define VF_PHASE_STAGE1 0       /* RK4 stage 1: k1, acc = q + dt/6 k1, q2 = q + dt/2 k1 */
 #define VF_PHASE_STAGE2 1       /* RK4 stage 2 */
 #define VF_PHASE_STAGE3 2       /* RK4 stage 3 */
@@ -397,6 +410,7 @@ int vf_measure_fp64_rate(double* gflops);
 const char* vf_phase_name(int phase);
 
 /* ---- status ---------------------------------------------------------------------------------------------- */
+/* Status and binding helpers (no counterpart in the paper). */
 
 const char* vf_status_string(int status);
 
@@ -407,7 +421,8 @@ const char* vf_last_error(const vf_grid* g);
 
 /* ---- host-side ventilation metrics (Sec. 3.3.2, 3.4), from a reduction series -------------------------------- */
 
-/* ACH [1/h] from the least-squares slope of ln c(t) (fresh air c = 0): ACH = -3600 d ln c / dt, t in seconds. */
+/* ACH [1/h] from the least-squares slope of ln c(t) (fresh air c = 0; the decay of Sec. 3.3.2 with C1 = 0):
+ * ACH = -3600 d ln c / dt, t in seconds. */
 int vf_ach_log_slope(const double* t_seconds, const double* c_mean, int64_t n, double* ach_per_hour);
 
 /* Three-parameter fit c(t) = C0 exp(-ACH t) + C1 (Sec. 3.3.2): ACH [1/h], C0, C1. */
