@@ -278,6 +278,16 @@ int vf_autotune(vf_grid* g, int32_t reps, vf_tiles* chosen);
 int vf_tile_cache_lookup(int32_t nx, int32_t ny, int32_t nz, int32_t precision, vf_tiles* out);
 int vf_tile_cache_clear(void);
 
+/* Tile cache contents, so that tuned tiles can be saved and restored across processes (host only, no device
+ * work): the number of entries; entry i in (nx, ny, nz, precision) order, key[4] = {nx, ny, nz, precision} and its
+ * tiles (VF_EINVAL for i out of range or a NULL pointer); and storing tiles under a key as vf_autotune does,
+ * replacing an entry (VF_EINVAL for a chunk out of range, an unknown precision or an FFT index that is not a
+ * candidate of its axis length; VF_ESIZE for sizes vf_create_grid rejects).  Grids created afterwards take the
+ * stored tiles. */
+int64_t vf_tile_cache_size(void);
+int vf_tile_cache_entry(int64_t i, int32_t key[4], vf_tiles* out);
+int vf_tile_cache_insert(int32_t nx, int32_t ny, int32_t nz, int32_t precision, const vf_tiles* t);
+
 /* ---- batched rooms and continuous batching (many rooms advanced together) --------------------------------- */
 /* The paper runs one case at a time; batching and serving many rooms has no counterpart there.  Each room's step is
  * the step of Sec. 2.1-2.2 exactly as vf_step runs it. */

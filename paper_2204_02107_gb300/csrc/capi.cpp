@@ -12,6 +12,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <iterator>
 #include <map>
 #include <mutex>
 #include <string>
@@ -1418,6 +1419,40 @@ int vf_tile_cache_clear(void)
 {
     std::lock_guard<std::mutex> lock(tile_mutex());
     tile_cache().clear();
+    return VF_OK;
+}
+
+int64_t vf_tile_cache_size(void)
+{
+    std::lock_guard<std::mutex> lock(tile_mutex());
+    return (int64_t)tile_cache().size();
+}
+
+int vf_tile_cache_entry(int64_t i, int32_t key[4], vf_tiles* out)
+{
+    if (!key || !out) return VF_EINVAL;
+    std::lock_guard<std::mutex> lock(tile_mutex());
+    if (i < 0 || i >= (int64_t)tile_cache().size()) return VF_EINVAL;
+    auto it = tile_cache().begin();
+    std::advance(it, (long)i);
+    key[0] = it->first.nx;
+    key[1] = it->first.ny;
+    key[2] = it->first.nz;
+    key[3] = it->first.precision;
+    *out = it->second;
+    return VF_OK;
+}
+
+int vf_tile_cache_insert(int32_t nx, int32_t ny, int32_t nz, int32_t precision, const vf_tiles* t)
+{
+    if (!t || !tiles_valid(*t) || (precision != VF_FP64 && precision != VF_FP32_MIXED)) return VF_EINVAL;
+    if (!smooth235_even(nx) || !smooth235_even(ny) || !smooth235_even(nz)) return VF_ESIZE;
+    if ((long long)nx * ny * nz > (1LL << 31)) return VF_ESIZE;
+    const int len[3] = {nx / 2, ny, nz}, idx[3] = {t->fft_x, t->fft_y, t->fft_z};
+    for (int a = 0; a < 3; ++a)
+        if (idx[a] < 0 || idx[a] >= (int)vf::fft_schedules(len[a]).size()) return VF_EINVAL;
+    std::lock_guard<std::mutex> lock(tile_mutex());
+    tile_cache()[TileKey{nx, ny, nz, precision}] = *t;
     return VF_OK;
 }
 

@@ -105,6 +105,9 @@ _SIGNATURES = {
     "vf_set_tiles": (C.c_int, [C.c_void_p, C.POINTER(VfTiles)]),
     "vf_autotune": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(VfTiles)]),
     "vf_fft_schedules": (C.c_int, [C.c_int32, C.c_int32, C.POINTER(C.c_int32), C.c_int32]),
+    "vf_tile_cache_size": (C.c_int64, []),
+    "vf_tile_cache_entry": (C.c_int, [C.c_int64, C.POINTER(C.c_int32), C.POINTER(VfTiles)]),
+    "vf_tile_cache_insert": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.POINTER(VfTiles)]),
     "vf_tile_cache_lookup": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.POINTER(VfTiles)]),
     "vf_tile_cache_clear": (C.c_int, []),
     "vf_batch_create": (C.c_int, [C.POINTER(VfBatchDesc), C.POINTER(C.c_void_p)]),
@@ -555,6 +558,46 @@ def tile_cache_lookup(nx, ny, nz, precision="fp32"):
 
 def tile_cache_clear():
     lib().vf_tile_cache_clear()
+
+
+def tile_cache_entries():
+    """Every tile-cache entry: a list of ((nx, ny, nz, 'fp64' | 'fp32'), tiles dict) in key order."""
+    out = []
+    key = (C.c_int32 * 4)()
+    for i in range(int(lib().vf_tile_cache_size())):
+        t = VfTiles()
+        rc = lib().vf_tile_cache_entry(i, key, C.byref(t))
+        if rc != VF_OK:
+            raise VentflowError(rc, "vf_tile_cache_entry")
+        out.append(((key[0], key[1], key[2], "fp64" if key[3] == VF_FP64 else "fp32"), t.to_dict()))
+    return out
+
+
+def tile_cache_insert(nx, ny, nz, precision, tiles):
+    """Store tiles (a dict with the vf_tiles fields) for a shape and precision, as the autotuner does."""
+    t = VfTiles(**{name: int(tiles[name]) for name, _ in VfTiles._fields_})
+    rc = lib().vf_tile_cache_insert(int(nx), int(ny), int(nz), PRECISIONS[precision], C.byref(t))
+    if rc != VF_OK:
+        raise VentflowError(rc, "vf_tile_cache_insert")
+
+
+def tile_cache_save(path):
+    """Write the tile cache to a JSON file (a list of {"nx", "ny", "nz", "precision", "tiles"})."""
+    import json
+    entries = [{"nx": k[0], "ny": k[1], "nz": k[2], "precision": k[3], "tiles": t} for k, t in tile_cache_entries()]
+    with open(path, "w") as f:
+        json.dump(entries, f, indent=1)
+
+
+def tile_cache_load(path):
+    """Add the entries of a JSON file written by tile_cache_save to the tile cache (each checked by the library);
+    returns the number loaded."""
+    import json
+    with open(path) as f:
+        entries = json.load(f)
+    for e in entries:
+        tile_cache_insert(e["nx"], e["ny"], e["nz"], e["precision"], e["tiles"])
+    return len(entries)
 
 
 def poisson_solve_noalloc(nx, ny, nz, lx, ly, lz, f, p, stream=None):

@@ -128,3 +128,30 @@ def test_fft_schedules(lib):
     assert lib.vf_fft_schedules(1024, 0, buf, 2) == native.VF_EINVAL      # three radices do not fit in two
     assert lib.vf_fft_schedules(64, -1, buf, 2) == native.VF_EINVAL
     assert lib.vf_fft_schedules(64, 99, buf, 2) == 0
+
+
+def test_tile_cache_save_and_load(lib, tmp_path):
+    """The tile cache round-trips through JSON without a GPU; the library checks every stored entry."""
+    native.tile_cache_clear()
+    a = {"zc_stage": 8, "zc_div": 16, "zc_project": 4, "zc_filter": 32, "fft_x": 1, "fft_y": 2, "fft_z": 0}
+    b = {"zc_stage": 4, "zc_div": 32, "zc_project": 8, "zc_filter": 16, "fft_x": 0, "fft_y": 0, "fft_z": 0}
+    native.tile_cache_insert(96, 80, 72, "fp32", a)
+    native.tile_cache_insert(64, 64, 64, "fp64", b)
+    assert native.tile_cache_lookup(96, 80, 72, "fp32") == a
+    assert [k for k, _ in native.tile_cache_entries()] == [(64, 64, 64, "fp64"), (96, 80, 72, "fp32")]
+    path = tmp_path / "tiles.json"
+    native.tile_cache_save(path)
+    native.tile_cache_clear()
+    assert native.tile_cache_entries() == []
+    assert native.tile_cache_load(path) == 2
+    assert native.tile_cache_lookup(96, 80, 72, "fp32") == a and native.tile_cache_lookup(64, 64, 64, "fp64") == b
+    bad = [((96, 80, 72), dict(a, zc_stage=3), native.VF_EINVAL),                  # chunk below the minimum
+           ((96, 80, 72), dict(a, fft_x=len(native.fft_schedules(48))), native.VF_EINVAL),   # not a candidate
+           ((98, 80, 72), a, native.VF_ESIZE)]                                     # 98 = 2 * 7^2
+    for (nx, ny, nz), tiles, code in bad:
+        with pytest.raises(native.VentflowError) as e:
+            native.tile_cache_insert(nx, ny, nz, "fp32", tiles)
+        assert e.value.code == code
+    key = (ctypes.c_int32 * 4)()
+    assert lib.vf_tile_cache_entry(5, key, ctypes.byref(native.VfTiles())) == native.VF_EINVAL
+    native.tile_cache_clear()
