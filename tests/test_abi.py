@@ -155,3 +155,49 @@ def test_tile_cache_save_and_load(lib, tmp_path):
     key = (ctypes.c_int32 * 4)()
     assert lib.vf_tile_cache_entry(5, key, ctypes.byref(native.VfTiles())) == native.VF_EINVAL
     native.tile_cache_clear()
+
+
+C_CLIENT = r"""
+#include <stdio.h>
+#include <string.h>
+#include "ventflow.h"
+
+int main(void)
+{
+    vf_grid_desc d;
+    int64_t sizes[4];
+    int32_t rad[16];
+    if (vf_grid_desc_default(&d) != VF_OK || d.n_pressure_iters != 4 || d.precision != VF_FP32_MIXED) return 1;
+    if (vf_abi_sizes(sizes) != VF_OK) return 2;
+    if (sizes[0] != (int64_t)sizeof(vf_grid_desc) || sizes[1] != (int64_t)sizeof(vf_reduce) ||
+        sizes[2] != (int64_t)sizeof(vf_batch_desc) || sizes[3] != (int64_t)sizeof(vf_tiles)) return 3;
+    if (vf_fft_schedules(96, 0, rad, 16) != 3 || rad[0] * rad[1] * rad[2] != 96) return 4;
+    if (strcmp(vf_status_string(VF_ESIZE), "VF_ESIZE") != 0) return 5;
+    d.nx = 14;   /* 14 = 2 x 7: rejected before any device work */
+    vf_grid* g = NULL;
+    if (vf_create_grid(&d, &g) != VF_ESIZE || g != NULL) return 6;
+    printf("ok\n");
+    return 0;
+}
+"""
+
+
+def test_header_is_plain_c_and_links(lib, tmp_path):
+    """The header compiles as C11 with warnings as errors, and a C program linked against the library sees the
+    same struct sizes as the library and calls its host-only entry points (no GPU needed)."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "client.c"
+    src.write_text(C_CLIENT)
+    exe = tmp_path / "client"
+    libdir = os.path.dirname(B.LIB_PATH)
+    cmd = [gcc, "-std=c11", "-Wall", "-Wextra", "-Werror", "-I", os.path.join(ROOT, "include"), str(src), "-o",
+           str(exe), "-L", libdir, "-l:" + os.path.basename(B.LIB_PATH), "-Wl,-rpath," + libdir]
+    subprocess.run(cmd, check=True, capture_output=True, text=True)
+    env = dict(os.environ)
+    env["LD_LIBRARY_PATH"] = ":".join(p for p in ("/usr/local/cuda/lib64", env.get("LD_LIBRARY_PATH", "")) if p)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, env=env, timeout=60)
+    assert out.returncode == 0 and out.stdout.strip() == "ok", (out.returncode, out.stdout, out.stderr)
