@@ -12,6 +12,7 @@ from __future__ import annotations
 
 import collections
 import dataclasses
+import os
 import time
 
 import numpy as np
@@ -52,14 +53,24 @@ def room_result(req, grid, room, arrival, start, finish):
 class Server:
     """Continuous batching over a ``native.Batch``."""
 
-    def __init__(self, hbm_budget_bytes=120 << 30, max_slots=64, chunk_steps=50, precision="fp32"):
-        self.batch = native.Batch(max_slots=max_slots, hbm_budget_bytes=hbm_budget_bytes, reduce_every=1)
+    def __init__(self, hbm_budget_bytes=120 << 30, max_slots=64, chunk_steps=50, precision="fp32", autotune=0,
+                 tile_cache_path=None):
+        """autotune > 0: the first room of each shape is autotuned with that many reps when admitted.
+        tile_cache_path: a JSON tile cache (``native.tile_cache_save``) loaded now if the file exists and written
+        back by close(), so tuned tiles outlive the server."""
+        self.tile_cache_path = tile_cache_path
+        if tile_cache_path is not None and os.path.exists(tile_cache_path):
+            native.tile_cache_load(tile_cache_path)
+        self.batch = native.Batch(max_slots=max_slots, hbm_budget_bytes=hbm_budget_bytes, reduce_every=1,
+                                  autotune=autotune)
         self.chunk = chunk_steps
         self.precision = precision
         self.max_slots = max_slots
 
     def close(self):
         self.batch.close()
+        if self.tile_cache_path is not None:
+            native.tile_cache_save(self.tile_cache_path)
 
     def run(self, requests, realtime=True):
         """Serve a trace (dicts from ``rooms.request_trace``); returns the list of Results in completion order.

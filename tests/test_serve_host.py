@@ -136,3 +136,18 @@ def test_summary_counts_and_percentiles():
     assert s["makespan_s"] == pytest.approx(9.0)       # first arrival 0, last finish 4 + 5
     assert s["solves_per_hour"] == pytest.approx(5 / 9.0 * 3600)
     assert s["gcell_updates_per_s"] == pytest.approx(5 * 1000 * 10 / 9.0 / 1e9)
+
+
+def test_server_keeps_its_tuned_tiles_across_restarts(monkeypatch, tmp_path):
+    monkeypatch.setattr(native, "Batch", FakeBatch)
+    native.tile_cache_clear()
+    path = str(tmp_path / "tiles.json")
+    tiles = {"zc_stage": 8, "zc_div": 16, "zc_project": 8, "zc_filter": 32, "fft_x": 1, "fft_y": 0, "fft_z": 2}
+    srv = serve.Server(tile_cache_path=path)             # no file yet: nothing to load
+    native.tile_cache_insert(96, 64, 64, "fp32", tiles)  # what an admission autotune leaves in the cache
+    srv.close()                                          # writes the cache
+    native.tile_cache_clear()
+    srv = serve.Server(tile_cache_path=path)             # a restarted server loads it
+    assert native.tile_cache_lookup(96, 64, 64, "fp32") == tiles
+    srv.close()
+    native.tile_cache_clear()
