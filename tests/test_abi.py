@@ -201,3 +201,26 @@ def test_header_is_plain_c_and_links(lib, tmp_path):
     env["LD_LIBRARY_PATH"] = ":".join(p for p in ("/usr/local/cuda/lib64", env.get("LD_LIBRARY_PATH", "")) if p)
     out = subprocess.run([str(exe)], capture_output=True, text=True, env=env, timeout=60)
     assert out.returncode == 0 and out.stdout.strip() == "ok", (out.returncode, out.stdout, out.stderr)
+
+
+def test_batch_and_solver_arguments_rejected_before_any_device_call(lib):
+    """Batch descriptions, the allocation-free solve's sizes and NULL handles are checked on the host first."""
+    h = ctypes.c_void_p()
+    for fields in ({"max_slots": 0}, {"hbm_budget_bytes": 0}, {"reduce_every": -1}, {"autotune": -1},
+                   {"autotune": 1001}):
+        d = native.VfBatchDesc(4, 1 << 30, 1, None, 0)
+        for k, v in fields.items():
+            setattr(d, k, v)
+        assert lib.vf_batch_create(ctypes.byref(d), ctypes.byref(h)) == native.VF_EINVAL, fields
+    assert lib.vf_batch_create(None, ctypes.byref(h)) == native.VF_EINVAL
+    # sizes beyond the static scratch, or not 2-3-5 smooth, are refused before the device is touched
+    f = ctypes.c_void_p(16)
+    big = lib.vf_poisson_noalloc_max_cells(native.VF_FP64)
+    assert big > 0 and lib.vf_poisson_noalloc_max_cells(7) == 0
+    assert lib.vf_poisson_solve_noalloc(512, 128, 128, 1.0, 1.0, 1.0, native.VF_FP64, f, f, None) == native.VF_ESIZE
+    assert lib.vf_poisson_solve_noalloc(14, 8, 8, 1.0, 1.0, 1.0, native.VF_FP64, f, f, None) == native.VF_ESIZE
+    # NULL grid handles
+    assert lib.vf_step(None, 1, 0) == native.VF_EINVAL
+    assert lib.vf_sync(None) == native.VF_EINVAL
+    t = native.VfTiles()
+    assert lib.vf_get_tiles(None, ctypes.byref(t)) == native.VF_EINVAL
