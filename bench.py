@@ -6,10 +6,12 @@ projection, filter, FP64 reductions): the single room of 256 x 128 x 128 cells (
 state (about 0.3 GB) is larger than L2, so no flush is needed between steps.
 
 Our arm prints one JSON line with the device-timed throughput, the end-to-end throughput through the C ABI with
-host buffers, the roofline of the dominant kernel (per-kernel CUDA-event times from vf_profile_steps), the FP64
-form's throughput, clocks sampled during the timed region and the oracle timed on the host cores.
+host buffers (also with every step's record read before the next step), the roofline of the dominant kernel
+(per-kernel CUDA-event times from vf_profile_steps), the FP64 form's throughput, one FFT Poisson solve against
+cuFFT, the large-room, batch, serving and next-row legs, clocks sampled during the timed region and the oracle
+timed on the host cores (one process per core, and one full-size step on one core).
 
-``--impl reference`` times the FP64 CPU oracle as it stands on the host cores (the only other place this script
+``--impl reference`` times the FP64 CPU oracle as it stands on every host core (the only other place this script
 runs it), on a bounded sample of the same workload.
 """
 from __future__ import annotations
