@@ -46,7 +46,7 @@ extern "C" {
 /* ---- status codes ---------------------------------------------------------------------------------------- */
 #define VF_OK 0
 #define VF_EINVAL (-1)      /* bad argument (null pointer, bad enum, non-positive length, ...) */
-#define VF_ESIZE (-2)       /* grid size not even, < 8, or with a prime factor other than 2, 3, 5 */
+#define VF_ESIZE (-2)       /* grid size not even, < 8, with a prime factor other than 2, 3, 5, or over 2^30 cells */
 #define VF_ENOMEM (-3)      /* allocation failed, or a batch is over its memory budget */
 #define VF_ECUDA (-4)       /* a CUDA runtime call failed (sticky for the grid) */
 #define VF_ESTATE (-5)      /* call not valid in the current state (e.g. step before set_mask) */
@@ -67,7 +67,7 @@ typedef struct vf_allocator {
 
 /* Grid description (Sec. 2.4: the case parameters).  Fill with vf_grid_desc_default, then override. */
 typedef struct vf_grid_desc {
-    int32_t nx, ny, nz;          /* cells per axis: each even, >= 8, of the form 2^a 3^b 5^c */
+    int32_t nx, ny, nz;          /* cells per axis: each even, >= 8, of the form 2^a 3^b 5^c; nx*ny*nz <= 2^30 */
     double lx, ly, lz;           /* box lengths [m]; h_j = l_j / n_j */
     double nu;                   /* kinematic viscosity [m^2/s] */
     double alpha_c;              /* scalar diffusivity [m^2/s]; < 0 -> nu */

@@ -53,6 +53,10 @@ int fail_cuda(vf_grid* g, cudaError_t e, const char* what)
         if (e_ != cudaSuccess) return fail_cuda(g, e_, #call);       \
     } while (0)
 
+// Largest grid: cell indices and the index arithmetic of the kernels (offsets of up to a few thousand cells past
+// an index) stay far inside 32-bit integers.
+constexpr long long kMaxCells = 1LL << 30;
+
 bool smooth235_even(int n)
 {
     if (n < 8 || n % 2) return false;
@@ -522,7 +526,7 @@ int vf_create_grid(const vf_grid_desc* d, vf_grid** out)
     if (d->precision != VF_FP64 && d->precision != VF_FP32_MIXED) return VF_EINVAL;
     if (d->n_pressure_iters < 0 || d->history_capacity < 1) return VF_EINVAL;
     if (!(d->courant_max >= 0.0)) return VF_EINVAL;
-    if ((long long)d->nx * d->ny * d->nz > (1LL << 31)) return VF_ESIZE;
+    if ((long long)d->nx * d->ny * d->nz > kMaxCells) return VF_ESIZE;
 
     vf_grid* g = new vf_grid();
     g->d = *d;
@@ -1447,7 +1451,7 @@ int vf_tile_cache_insert(int32_t nx, int32_t ny, int32_t nz, int32_t precision, 
 {
     if (!t || !tiles_valid(*t) || (precision != VF_FP64 && precision != VF_FP32_MIXED)) return VF_EINVAL;
     if (!smooth235_even(nx) || !smooth235_even(ny) || !smooth235_even(nz)) return VF_ESIZE;
-    if ((long long)nx * ny * nz > (1LL << 31)) return VF_ESIZE;
+    if ((long long)nx * ny * nz > kMaxCells) return VF_ESIZE;
     const int len[3] = {nx / 2, ny, nz}, idx[3] = {t->fft_x, t->fft_y, t->fft_z};
     for (int a = 0; a < 3; ++a)
         if (idx[a] < 0 || idx[a] >= (int)vf::fft_schedules(len[a]).size()) return VF_EINVAL;

@@ -70,6 +70,17 @@ def test_bad_sizes_rejected_before_any_device_call(lib, n):
     assert not h.value
 
 
+@pytest.mark.parametrize("shape", [(2048, 1024, 1024), (1152, 1024, 1024), (4096, 512, 1024)])
+def test_grids_over_two_to_the_thirty_cells_rejected(lib, shape):
+    d = native.default_desc()
+    d.nx, d.ny, d.nz = shape
+    h = ctypes.c_void_p()
+    assert lib.vf_create_grid(ctypes.byref(d), ctypes.byref(h)) == native.VF_ESIZE
+    assert not h.value
+    t = native.VfTiles(4, 32, 8, 16, 0, 0, 0)
+    assert lib.vf_tile_cache_insert(*shape, native.VF_FP32_MIXED, ctypes.byref(t)) == native.VF_ESIZE
+
+
 def test_bad_arguments_rejected(lib):
     d = native.default_desc()
     d.dt = 0.0
