@@ -176,14 +176,31 @@ def _is_tensor(x):
     return type(x).__module__.startswith("torch")
 
 
+def _device_tensor(x, dtypes, n, what):
+    """Check that x is a contiguous CUDA tensor whose dtype name is in ``dtypes`` ('float64', 'float32',
+    'uint8') with n elements (n None: any count) before its address goes to the library, which would otherwise
+    read past a smaller buffer or through a host pointer."""
+    if not _is_tensor(x) or not x.is_cuda:
+        raise TypeError(f"{what}: expected a CUDA tensor")
+    name = str(x.dtype).replace("torch.", "")
+    if name not in dtypes:
+        raise TypeError(f"{what}: dtype {name} not one of {', '.join(dtypes)}")
+    if not x.is_contiguous():
+        raise ValueError(f"{what}: tensor must be contiguous")
+    if n is not None and x.numel() != n:
+        raise ValueError(f"{what}: expected {n} elements, got {x.numel()}")
+    return x
+
+
 def _pointer(x, dtype, n):
-    """(pointer, mem, keepalive) for a numpy array (host) or CUDA torch tensor (device) of n values."""
+    """(pointer, mem, keepalive) for a numpy array (host) or CUDA torch tensor (device) of n values; a device
+    tensor must hold elements of ``dtype`` (None: float64 or float32)."""
     if _is_tensor(x):
         if not x.is_cuda:
             x = x.detach().cpu().numpy()
         else:
-            if not x.is_contiguous() or x.numel() != n:
-                raise ValueError(f"device array must be contiguous with {n} elements")
+            want = ("float64", "float32") if dtype is None else (np.dtype(dtype).name,)
+            _device_tensor(x, want, n, "device array")
             return C.c_void_p(x.data_ptr()), VF_DEVICE, x
     a = np.ascontiguousarray(x, dtype=dtype)
     if a.size != n:
@@ -469,6 +486,7 @@ class Grid:
     def read_field_into(self, name, tensor):
         """Device-to-device read into a contiguous CUDA tensor (float64 or float32)."""
         import torch
+        _device_tensor(tensor, ("float64", "float32"), self.n, "read_field_into")
         ptr, mem, _keep = _pointer(tensor, None, self.n)
         self._check(lib().vf_read_field(self._h, FIELDS[name], ptr, 1 if tensor.dtype == torch.float64 else 0, mem),
                     "vf_read_field")
@@ -523,6 +541,9 @@ class Grid:
 
     def poisson_solve(self, f, p):
         """Solve L p = f on the device (f, p: contiguous CUDA tensors in the grid's precision)."""
+        want = ("float64",) if self.precision == "fp64" else ("float32",)
+        _device_tensor(f, want, self.n, "poisson_solve f")
+        _device_tensor(p, want, self.n, "poisson_solve p")
         self._check(lib().vf_poisson_solve(self._h, C.c_void_p(f.data_ptr()), C.c_void_p(p.data_ptr())),
                     "vf_poisson_solve")
 
@@ -600,10 +621,30 @@ def tile_cache_load(path):
     return len(entries)
 
 
+def _noalloc_sizes_accepted(nx, ny, nz, precision):
+    """The size rules vf_poisson_solve_noalloc states: even, >= 8, 2-3-5 smooth, at most its cell limit, every FFT
+    length (nx/2 + 1, ny, nz) at most 1024."""
+    def smooth(n):
+        if n < 8 or n % 2:
+            return False
+        for q in (2, 3, 5):
+            while n % q == 0:
+                n //= q
+        return n == 1
+    return (all(smooth(int(v)) for v in (nx, ny, nz)) and nx * ny * nz <= lib().vf_poisson_noalloc_max_cells(precision)
+            and max(nx // 2 + 1, ny, nz) <= 1024)
+
+
 def poisson_solve_noalloc(nx, ny, nz, lx, ly, lz, f, p, stream=None):
     """Solve L p = f without any device allocation (f, p: contiguous CUDA tensors, float64 or float32)."""
-    import torch
-    precision = VF_FP64 if f.dtype == torch.float64 else VF_FP32_MIXED
+    _device_tensor(f, ("float64", "float32"), None, "poisson_solve_noalloc f")
+    dt = str(f.dtype).replace("torch.", "")
+    _device_tensor(p, (dt,), None, "poisson_solve_noalloc p")
+    precision = VF_FP64 if dt == "float64" else VF_FP32_MIXED
+    if _noalloc_sizes_accepted(nx, ny, nz, precision):   # sizes the call refuses never reach the arrays
+        for x, what in ((f, "f"), (p, "p")):
+            if x.numel() != nx * ny * nz:
+                raise ValueError(f"poisson_solve_noalloc {what}: expected {nx * ny * nz} elements, got {x.numel()}")
     rc = lib().vf_poisson_solve_noalloc(nx, ny, nz, lx, ly, lz, precision, C.c_void_p(f.data_ptr()),
                                         C.c_void_p(p.data_ptr()), C.c_void_p(stream) if stream else None)
     if rc != VF_OK:
