@@ -283,6 +283,8 @@ class Batch:
         ps = _pointer(S, np.uint8, n) if S is not None else (None, mem, None)
         pr = _pointer(room, np.uint8, n) if room is not None else (None, mem, None)
         pc = _pointer(c0, np.float64, n) if c0 is not None else (None, mem, None)
+        if len({p[1] for p in (ps, pr, pc)} | {mem}) != 1:
+            raise ValueError("beta, S, room and c0 must all be host arrays or all CUDA tensors")
         us = (C.c_double * 3)(*u_set)
         slot = C.c_int32()
         rc = lib().vf_batch_add(self._h, C.byref(desc), pb, ps[0], pr[0], us, float(c_set), pc[0], 1, int(steps),

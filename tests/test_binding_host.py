@@ -91,3 +91,19 @@ def test_noalloc_checks_arrays_only_for_sizes_it_accepts(fake_lib):
     assert len(fake_lib.calls) == 2
     native.poisson_solve_noalloc(72, 36, 20, 1.0, 1.0, 1.0, FakeCudaTensor(n), FakeCudaTensor(n))
     assert fake_lib.calls[-1] == (72, 36, 20)
+
+
+def test_batch_add_refuses_mixed_host_and_device_inputs(monkeypatch):
+    calls = []
+    b = native.Batch.__new__(native.Batch)            # no device batch: the check comes before the library call
+    b._h, b._desc = None, {}
+    monkeypatch.setattr(native, "lib", lambda: type("L", (), {"vf_batch_add": lambda *a: calls.append(a)})())
+    desc = native.VfGridDesc()
+    desc.nx, desc.ny, desc.nz = 8, 8, 8
+    n = 512
+    host = __import__("numpy").ones(n, dtype="uint8")
+    with pytest.raises(ValueError):
+        b.add(desc, host, host, (1.0, 0.0, 0.0), 0.0, 10, room=host, c0=FakeCudaTensor(n))
+    with pytest.raises(TypeError):                 # a device c0 must be float64 (the call passes is_fp64 = 1)
+        b.add(desc, FakeCudaTensor(n, "uint8"), None, (1.0, 0.0, 0.0), 0.0, 10, c0=FakeCudaTensor(n, "float32"))
+    assert calls == []
