@@ -1,7 +1,7 @@
 // Step engine and C ABI of the ventilation-flow library (declared in include/ventflow.h).
 //
-// A grid owns every device buffer of one room: the state q = (u, v, w, c), two RK4 stage states and the RK4
-// accumulator, the pressure p / rho (kept between steps as the warm start of Eq. 9; the paper's p carries a factor
+// A grid owns every device buffer of one room: the state q = (u, v, w, c), three RK4 stage states (q2, q3, q4 in
+// the buffers qa, qb, acc; no accumulator is carried between stages), the pressure p / rho (kept between steps as the warm start of Eq. 9; the paper's p carries a factor
 // dt, so the solver works on D u* / dt and the projection subtracts dt G p), the divergence r, the half
 // spectrum, a staging buffer for host/device transfers, the packed mask and the FFT tables.  A step is a fixed
 // sequence of kernel launches on the grid's stream; it is captured once into a CUDA graph and replayed.
