@@ -205,11 +205,34 @@ RK4_NODES = (0.0, 0.5, 0.5, 1.0)
 RK4_WEIGHTS = (1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0)
 
 
+def room_outflow_rate(c, u, v, w, geom: Geometry, prm: Params):
+    """Rate at which the scalar leaves the room region through its boundary (the outlet and inlet openings of a
+    ventilated room, Sec. 3.3): over every face between a room cell and a cell outside the room, the face flux of
+    Eq. 3 in the flux form of scalar_rhs -- convective beta_f (u_j c |_i + u_j c |_{i+1}) / 2 minus diffusive
+    alpha_c beta_f (c_{i+1} - c_i) / h_j -- times the face area dV / h_j, counted positive out of the room."""
+    vel = (u, v, w)
+    h = prm.h
+    room = geom.room
+    total = 0.0
+    for j in range(3):
+        ax = AXES[j]
+        beta_face = geom.beta * shift(geom.beta, 1, ax)
+        uc = vel[j] * c
+        flux = beta_face * (0.5 * (uc + shift(uc, 1, ax)) - prm.alpha * (shift(c, 1, ax) - c) / h[j])  # i -> i+1
+        room_next = shift(room, 1, ax)
+        # +1 where the face leads out of the room (i inside, i+1 outside), -1 where it leads in
+        sign = room * (1.0 - room_next) - (1.0 - room) * room_next
+        total += prm.cell_volume / h[j] * float(np.sum(sign * flux))
+    return total
+
+
 def rk4_predictor(q, geom, prm, record=None):
     """Classic RK4 over (u, v, w, c) with no pressure term inside the stages: returns q* (Sec. 2.1).
 
-    If ``record`` is a dict, the RK-weighted forcing inventory dt * sum_s b_s sum_cells k_forcing,s * dV of the
-    scalar is stored in record['forcing'] (the scalar budget term of the relaxation source)."""
+    If ``record`` is a dict, the scalar budget terms of the step are stored in it, each the RK-weighted sum
+    dt * sum_s b_s X_s over the four stage states: 'forcing', the inventory the relaxation source adds
+    (X_s = sum_cells beta S (c_set - c_s) / tau_f dV); 'forcing_room', the same over the room cells; 'outflow',
+    what leaves the room through its boundary (X_s = room_outflow_rate at stage state s)."""
     dt = prm.dt
     ks = []
     stage_q = q
@@ -218,8 +241,13 @@ def rk4_predictor(q, geom, prm, record=None):
             stage_q = [qn + RK4_NODES[s] * dt * k for qn, k in zip(q, ks[-1])]
         ks.append(stage_rhs(stage_q, geom, prm))
         if record is not None:
-            forcing = float(np.sum(geom.beta * geom.S * (prm.c_set - stage_q[3]) / prm.tau)) * prm.cell_volume
-            record['forcing'] = record.get('forcing', 0.0) + dt * RK4_WEIGHTS[s] * forcing
+            src = geom.beta * geom.S * (prm.c_set - stage_q[3]) / prm.tau
+            weight = dt * RK4_WEIGHTS[s]
+            record['forcing'] = record.get('forcing', 0.0) + weight * float(np.sum(src)) * prm.cell_volume
+            record['forcing_room'] = (record.get('forcing_room', 0.0)
+                                      + weight * float(np.sum(geom.room * src)) * prm.cell_volume)
+            record['outflow'] = record.get('outflow', 0.0) + weight * room_outflow_rate(
+                stage_q[3], stage_q[0], stage_q[1], stage_q[2], geom, prm)
     return [qn + dt * sum(b * k[f] for b, k in zip(RK4_WEIGHTS, ks)) for f, qn in enumerate(q)]
 
 
@@ -369,11 +397,14 @@ def step(state: State, geom: Geometry, prm: Params, with_budget=False):
         budget['c_star_total'] = prm.cell_volume * float(np.sum(cs))
     if prm.filter:
         if budget is not None:
-            unmasked = cs + sum(sixth_difference(cs, ax) for ax in AXES) / math.pi ** 6
-            budget['mask_loss'] = prm.cell_volume * float(np.sum((1.0 - geom.beta) * unmasked))
+            # what the filter adds before the re-mask: removed again in solids, kept in the room's fluid cells
+            change = sum(sixth_difference(cs, ax) for ax in AXES) / math.pi ** 6
+            budget['mask_loss'] = prm.cell_volume * float(np.sum((1.0 - geom.beta) * (cs + change)))
+            budget['filter_room'] = prm.cell_volume * float(np.sum(geom.room * geom.beta * change))
         u, v, w, c = (filter6(f, geom) for f in (u, v, w, c))
     elif budget is not None:
         budget['mask_loss'] = 0.0
+        budget['filter_room'] = 0.0
     new = State(u, v, w, c, p, state.t + prm.dt, state.step + 1)
     # the step's divergence diagnostic measures the projection: D u right after it, before the filter (Sec. 2.2)
     rec = reductions(new, geom, prm, div_velocity=projected)

@@ -397,10 +397,62 @@ def test_scalar_budget_closes():
     assert abs(rec['c_star_total'] - before - rec['forcing']) < 1e-12 * before
     assert abs(after - rec['c_star_total'] + rec['mask_loss']) < 1e-12 * before
     assert rec['forcing'] != 0.0
-    # a plausible mistake -- convective flux without face weights -- leaks through solid faces
+    # the re-mask after the filter is the only loss: with the filter off nothing is removed from the solids
     prm_nofilter = prm.with_(filter=False)
     _, rec2 = F.step(st, g, prm_nofilter, with_budget=True)
     assert rec2['mask_loss'] == 0.0
+
+
+def test_room_outflow_closed_form():
+    """outflow rate of a slab room x in [a, b) across a uniform flow U along x: c = 1 in the room, c_L in the
+    cell before it and c_R in the cell after it.  Per (y, z) row the two x faces give
+    A [U (c_R - c_L) / 2 + alpha (2 - c_R - c_L) / h] (face area A = dV / h); the slab spans y and z, so no other
+    face leaves it.  A solid cell behind a face closes that face."""
+    prm = F.Params(nx=16, ny=6, nz=5, lx=1.6, ly=0.9, lz=1.0, nu=0.0, alpha_c=0.003, dt=1e-3)
+    a, b, U, cL, cR = 5, 11, 0.7, 0.25, -0.4
+    room = np.zeros(prm.shape)
+    room[:, :, a:b] = 1.0
+    c = np.full(prm.shape, 3.0)              # cells away from the room's faces do not count
+    c[:, :, a:b] = 1.0
+    c[:, :, a - 1] = cL
+    c[:, :, b] = cR
+    u = np.full(prm.shape, U)
+    z = np.zeros(prm.shape)
+    g = F.Geometry(np.ones(prm.shape), np.zeros(prm.shape), room)
+    hx = prm.h[0]
+    A = prm.cell_volume / hx
+    rows = prm.ny * prm.nz
+    want = rows * A * (U * (cR - cL) / 2 + prm.alpha * (2 - cR - cL) / hx)
+    got = F.room_outflow_rate(c, u, z, z, g, prm)
+    assert abs(got - want) < 1e-13 * abs(want)
+    # the same room with the cells behind its right face solid: only the left face is left
+    beta = np.ones(prm.shape)
+    beta[:, :, b] = 0.0
+    g2 = F.Geometry(beta, np.zeros(prm.shape), room)
+    want2 = rows * A * (-U * (cL + 1) / 2 + prm.alpha * (1 - cL) / hx)
+    assert abs(F.room_outflow_rate(c * beta, u * beta, z, z, g2, prm) - want2) < 1e-13 * abs(want2)
+
+
+def test_room_budget_closes():
+    """over one step the room inventory changes by the forcing inside the room, minus what leaves the room
+    through its openings, plus what the filter moves across the room's boundary: the flux form makes every
+    interior face cancel.  A wrong sign, area or diffusive term of the outflow breaks the balance."""
+    prm, g, st = small_room_case()
+    u, v, w = rooms.random_fields(prm.shape, 4, count=3, scale=0.3, beta=g.beta)
+    st = F.State(u, v, w, st.c, st.p)
+    for _ in range(2):
+        st, rec0 = F.step(st, g, prm)
+    new, rec = F.step(st, g, prm, with_budget=True)
+    change = rec['c_room'] - rec0['c_room']
+    balance = rec['forcing_room'] - rec['outflow'] + rec['filter_room']
+    assert abs(change - balance) < 1e-12 * rec['c_room']
+    assert abs(rec['outflow']) > 1e-6 * rec['c_room'] and rec['forcing_room'] == 0.0
+    # with the inlet region counted as room the forcing acts inside it, and the balance still closes
+    g2 = F.Geometry(g.beta, g.S, np.maximum(g.room, g.S))
+    _, r1 = F.step(st, g2, prm, with_budget=True)
+    assert r1['forcing_room'] != 0.0
+    before = prm.cell_volume * float(np.sum(g2.room * st.c))
+    assert abs(r1['c_room'] - before - (r1['forcing_room'] - r1['outflow'] + r1['filter_room'])) < 1e-12 * before
 
 
 def test_histogram_brute_force():
