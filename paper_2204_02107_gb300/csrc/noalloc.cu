@@ -27,10 +27,10 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratch
 
 std::mutex g_setup_mutex;
 void* g_scratch_ptr[kMaxDevices] = {};
-cudaError_t g_setup_status[kMaxDevices] = {};
-bool g_setup_done[kMaxDevices] = {};
 
-// Device address of the scratch array on the current device, looked up on the first call for that device.
+// Device address of the scratch array on the current device, looked up on the first successful call for that
+// device.  Only a successful lookup is kept: a failed one (for example a first call made during stream capture)
+// is tried again by the next call.
 cudaError_t scratch_on_current_device(void** out)
 {
     int dev = -1;
@@ -38,14 +38,26 @@ cudaError_t scratch_on_current_device(void** out)
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_setup_done[dev]) {
+    if (!g_scratch_ptr[dev]) {
         void* p = nullptr;
-        g_setup_status[dev] = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            cudaGetLastError();   // clear the lookup's error so the caller's next CUDA call does not see it
+            return e != cudaSuccess ? e : cudaErrorInvalidSymbol;
+        }
         g_scratch_ptr[dev] = p;
-        g_setup_done[dev] = true;
     }
     *out = g_scratch_ptr[dev];
-    return g_setup_status[dev];
+    return cudaSuccess;
+}
+
+// Error return once work may be queued on st: wait for that work (its status is not needed) so that nothing of
+// this call is still using the shared array when the caller's next call starts.
+int drain_and_fail(cudaStream_t st)
+{
+    cudaStreamSynchronize(st);
+    cudaGetLastError();
+    return VF_ECUDA;
 }
 
 bool smooth235_even(int n)
@@ -97,11 +109,11 @@ int solve(int nx, int ny, int nz, double lx, double ly, double lz, const void* f
     for (int t = 0; t < 4; ++t)
         if (cudaMemcpyAsync(dtw + (size_t)t * kMaxAxis, tw[t], tw_len[t] * sizeof(C2), cudaMemcpyHostToDevice, st) !=
             cudaSuccess)
-            return VF_ECUDA;
+            return drain_and_fail(st);
     for (int j = 0; j < 3; ++j)
         if (cudaMemcpyAsync(dlam + (size_t)j * kMaxAxis, lam[j], lam_len[j] * sizeof(T), cudaMemcpyHostToDevice,
                             st) != cudaSuccess)
-            return VF_ECUDA;
+            return drain_and_fail(st);
 
     vf::PoissonArgs<T> a{};
     a.nx = nx; a.ny = ny; a.nz = nz; a.M = M;
@@ -128,8 +140,8 @@ int solve(int nx, int ny, int nz, double lx, double ly, double lz, const void* f
     const int per_cta = sizeof(T) == 8 ? 1024 : 2048;   // complex values per CTA in the x passes
     a.rows_per_block = per_cta / M > 0 ? per_cta / M : 1;
     a.cols_per_block = (int)tb;
-    if (vf::Kernels<T>::poisson_prepare(a) != cudaSuccess) return VF_ECUDA;
-    if (vf::Kernels<T>::poisson_iteration(a, 1, st) != cudaSuccess) return VF_ECUDA;
+    if (vf::Kernels<T>::poisson_prepare(a) != cudaSuccess) return drain_and_fail(st);
+    if (vf::Kernels<T>::poisson_iteration(a, 1, st) != cudaSuccess) return drain_and_fail(st);
     // the stack tables must stay alive until their copies have been consumed
     if (cudaStreamSynchronize(st) != cudaSuccess) return VF_ECUDA;
     return VF_OK;

@@ -44,8 +44,8 @@ def test_binding_covers_header(lib):
 
 
 def test_struct_sizes_match_header(lib):
-    # vf_reduce: 11 scalars + 64 + 2 counters, all 8 bytes
-    assert ctypes.sizeof(native.VfReduce) == 8 * (11 + 64 + 2)
+    # vf_reduce: 11 scalars + 64 + 2 counters + 5 budget terms, all 8 bytes
+    assert ctypes.sizeof(native.VfReduce) == 8 * (11 + 64 + 2 + 5)
     sizes = (ctypes.c_int64 * 4)()
     assert lib.vf_abi_sizes(sizes) == 0
     assert list(sizes) == [ctypes.sizeof(native.VfGridDesc), ctypes.sizeof(native.VfReduce),
@@ -230,6 +230,12 @@ def test_batch_and_solver_arguments_rejected_before_any_device_call(lib):
     assert big > 0 and lib.vf_poisson_noalloc_max_cells(7) == 0
     assert lib.vf_poisson_solve_noalloc(512, 128, 128, 1.0, 1.0, 1.0, native.VF_FP64, f, f, None) == native.VF_ESIZE
     assert lib.vf_poisson_solve_noalloc(14, 8, 8, 1.0, 1.0, 1.0, native.VF_FP64, f, f, None) == native.VF_ESIZE
+    # the y and z passes' shared-memory bound: ny or nz above 581 (FP64) / 592 (FP32), whatever the cell count
+    for prec in (native.VF_FP64, native.VF_FP32_MIXED):
+        assert lib.vf_poisson_solve_noalloc(8, 600, 8, 1.0, 1.0, 1.0, prec, f, f, None) == native.VF_ESIZE
+        assert lib.vf_poisson_solve_noalloc(8, 8, 600, 1.0, 1.0, 1.0, prec, f, f, None) == native.VF_ESIZE
+        assert not native._noalloc_sizes_accepted(8, 600, 8, prec)
+    assert native._noalloc_sizes_accepted(8, 576, 8, native.VF_FP64)
     # NULL grid handles
     assert lib.vf_step(None, 1, 0) == native.VF_EINVAL
     assert lib.vf_sync(None) == native.VF_EINVAL
