@@ -106,6 +106,17 @@ typedef struct vf_reduce {
     int64_t hist_under;          /* room cells with c < 0 */
     int64_t hist_over;           /* room cells with c > 1 */
     double dt;                   /* time step that produced the state (the grid's dt for vf_reductions) */
+    /* Scalar budget of the step that produced the state (Eqs. 3-4 in flux form, the room inventory of
+     * Sec. 3.3), in units of c m^3; records taken by vf_step only (vf_reductions leaves them 0).  Each stage
+     * term is the RK4-weighted sum dt sum_s b_s X_s over the four stage states s.  With c_total and c_room of
+     * the previous record they close: c_total' = c_total + budget_forcing - budget_mask_loss and
+     * c_room' = c_room + budget_forcing_room - budget_outflow + budget_filter_room. */
+    double budget_forcing;       /* X_s = sum over fluid cells dV S (c_set - c_s) / tau_f */
+    double budget_forcing_room;  /* the same over the room cells */
+    double budget_outflow;       /* X_s = scalar flux out of the room through its faces to non-room fluid cells
+                                    (convective minus diffusive face flux of Eq. 3 times the face area) */
+    double budget_mask_loss;     /* scalar the filter puts into solid cells, removed again by the re-mask */
+    double budget_filter_room;   /* change of the room inventory by the filter (Eq. 6) */
 } vf_reduce;
 
 typedef struct vf_grid vf_grid;
@@ -352,8 +363,9 @@ const char* vf_batch_last_error(const vf_batch* b);
  *   nx, ny, nz, lx, ly, lz: sizes and box lengths as in vf_grid_desc;  precision: VF_FP64 (f, p are double) or
  *   VF_FP32_MIXED (float);  f, p: caller-owned device arrays of nx*ny*nz values (may alias);  stream: a
  *   cudaStream_t or NULL.  Returns after p is written.
- * Limits: nx*ny*nz <= vf_poisson_noalloc_max_cells(precision) (4,194,304 in FP64, 8,388,608 in FP32) and every
- * FFT length (nx/2 + 1, ny, nz) <= 1024; larger sizes return VF_ESIZE.
+ * Limits: nx*ny*nz <= vf_poisson_noalloc_max_cells(precision) (4,194,304 in FP64, 8,388,608 in FP32), every
+ * FFT length (nx/2 + 1, ny, nz) <= 1024, and ny, nz <= 581 in FP64 or <= 592 in FP32 (the y and z passes keep
+ * three tiles and a twiddle table of the longer axis in one CTA's shared memory); larger sizes return VF_ESIZE.
  * The first call on a device looks up the array's device address (once per device, with that device current);
  * make that first call before any stream capture.  Every call reuses the same array and leaves its contents
  * behind; calls that overlap on the GPU (several streams or threads at once) race on it. */
@@ -404,7 +416,8 @@ int vf_particles_count(const vf_grid* g, int64_t* n);
 #define VF_PHASE_FFT_YZ_SOLVE 14 /* per-kx plane: y, z FFTs, division by lambda, inverse z, y FFTs */
 #define VF_PHASE_ADJUST_DT 15   /* dynamic time step: dt from the Courant rate of the current state */
 #define VF_PHASE_PARTICLES 16   /* Lagrangian particles (Sec. 2.3) in the new velocity */
-#define VF_N_PHASES 17
+#define VF_PHASE_BUDGET 17      /* scalar budget of the RK4 stages (steps that write a reduction record) */
+#define VF_N_PHASES 18
 
 /* Run n steps like vf_step but with direct launches bracketed by CUDA events on the grid's stream; adds the
  * elapsed milliseconds of every phase to phase_ms[VF_N_PHASES] and its launch count to launches[VF_N_PHASES]

@@ -197,6 +197,20 @@ vf::ReduceArgsDev reduce_args(const vf_grid* g)
     return r;
 }
 
+vf::BudgetConsts budget_consts(const vf_grid* g)
+{
+    const vf_grid_desc& d = g->d;
+    vf::BudgetConsts b{};
+    const double h[3] = {d.lx / d.nx, d.ly / d.ny, d.lz / d.nz};
+    b.dV = h[0] * h[1] * h[2];
+    b.dt = d.dt;
+    b.inv_tau = 1.0 / (d.tau_f > 0 ? d.tau_f : d.dt);
+    b.alpha = d.alpha_c < 0 ? d.nu : d.alpha_c;
+    b.cset = g->cset;
+    for (int j = 0; j < 3; ++j) b.ih[j] = 1.0 / h[j];
+    return b;
+}
+
 int pressure_iters(const vf_grid* g)
 {
     if (g->d.n_pressure_iters <= 0) return 0;
@@ -231,6 +245,15 @@ cudaError_t enqueue_step_t(vf_grid* g, cudaStream_t st, bool with_reduce, const 
     a.qs = g->qb; a.out = g->acc;
     if ((e = Kernels<T>::stage(3, a, k, st)) != cudaSuccess) return e;
     mark(VF_PHASE_STAGE3);
+    if (with_reduce) {
+        // scalar budget of the four stage states q_n, q2, q3, q4 (all still in place until stage 4)
+        StageArgs<T> b = a;
+        b.q2 = g->qa; b.q3 = g->qb;
+        if ((e = Kernels<T>::budget(b, g->acc, k, budget_consts(g), g->budget_partial, g->budget_done, g->budget_out,
+                                    st)) != cudaSuccess)
+            return e;
+        mark(VF_PHASE_BUDGET);
+    }
     a.qs = g->acc; a.q2 = g->qa; a.q3 = g->qb; a.out = g->qa;
     if ((e = Kernels<T>::stage(4, a, k, st)) != cudaSuccess) return e;
     mark(VF_PHASE_STAGE4);
@@ -253,7 +276,9 @@ cudaError_t enqueue_step_t(vf_grid* g, cudaStream_t st, bool with_reduce, const 
     if (g->d.filter) {
         // with the filter on, the filter records the divergence of its input (the projected velocity) and the
         // flat reduction of the filtered state follows
-        const vf::ReduceArgsDev ra = reduce_args(g);
+        vf::ReduceArgsDev ra = reduce_args(g);
+        ra.budget = g->budget_out;
+        ra.filter_budget = 1;
         if ((e = Kernels<T>::filter(g->qb, g->q, g->mask, k, with_reduce ? &ra : nullptr, st, sigma_out)) !=
             cudaSuccess)
             return e;
@@ -263,7 +288,9 @@ cudaError_t enqueue_step_t(vf_grid* g, cudaStream_t st, bool with_reduce, const 
             mark(VF_PHASE_REDUCE);
         }
     } else if (with_reduce) {
-        if ((e = Kernels<T>::reduce(g->q, g->mask, k, reduce_args(g), 1, st)) != cudaSuccess) return e;
+        vf::ReduceArgsDev ra = reduce_args(g);
+        ra.budget = g->budget_out;
+        if ((e = Kernels<T>::reduce(g->q, g->mask, k, ra, 1, st)) != cudaSuccess) return e;
         mark(VF_PHASE_REDUCE);
     }
     if (g->particles.n > 0) {
@@ -478,10 +505,11 @@ size_t grid_bytes(const vf_grid_desc& d)
     k.zc[vf::kZcFilter] = vf::kZChunkMin;
     const size_t ndiv = (size_t)Kernels<float>::filter_warps(k);
     size_t b = 4 * r256(4 * N * esz) + 5 * r256(N * esz) + r256(N * 4) + r256(N * 8) + 2 * r256(N);
-    b += r256(nred * vf::kRedSlots * 8) + r256(ndiv * 2 * 8) + r256((vf::kHistBins + 2) * 8) + r256(4) +
+    b += r256(nred * vf::kRedSlots * 8) + r256(ndiv * vf::kDivRecord * 8) + r256((vf::kHistBins + 2) * 8) + r256(4) +
          r256(sizeof(vf_reduce));
     b += r256((size_t)d.history_capacity * sizeof(vf_reduce)) + r256(16) + r256(4) + r256(8);
     b += r256(sizeof(vf::DtCtl)) + r256(3 * sizeof(double));
+    b += r256(vf::kBudgetBlocks * vf::kBudgetTerms * 8) + r256(4) + r256(vf::kBudgetTerms * 8);
     b += r256(M * cpx) + r256(d.ny * cpx) + r256(d.nz * cpx) + r256((M + 1) * cpx);
     b += r256(M * esz) + r256(d.ny * esz) + r256(d.nz * esz) + r256(d.ny * 4) + r256(d.nz * 4);
     return b;
@@ -555,7 +583,7 @@ int vf_create_grid(const vf_grid_desc* d, vf_grid** out)
     const int M = d->nx / 2;
     {
         // the FFT passes keep up to three tiles of their batch and a twiddle table in shared memory (at most
-        // 227 KB per CTA): ny, nz <= 593 in FP32 and <= 581 in FP64
+        // 227 KB per CTA): ny, nz <= 592 in FP32 and <= 581 in FP64
         const size_t cplx = g->fp64 ? 16 : 8, tb = g->fp64 ? 8 : 16, limit = 227 * 1024;
         const size_t n = (size_t)std::max(d->ny, d->nz);
         if ((3 * tb * n + n) * cplx > limit || 4 * (size_t)M * cplx > limit) return fail(VF_ESIZE);
@@ -600,7 +628,8 @@ int vf_create_grid(const vf_grid_desc* d, vf_grid** out)
         kmin.zc[vf::kZcFilter] = vf::kZChunkMin;
         g->ndiv = Kernels<float>::filter_warps(kmin);
     }
-    if (!(g->div_partial = (double*)galloc(g, (size_t)g->ndiv * 2 * sizeof(double)))) return fail(VF_ENOMEM);
+    if (!(g->div_partial = (double*)galloc(g, (size_t)g->ndiv * vf::kDivRecord * sizeof(double))))
+        return fail(VF_ENOMEM);
     if (!(g->hist_accum = (unsigned long long*)galloc(g, (vf::kHistBins + 2) * sizeof(unsigned long long))))
         return fail(VF_ENOMEM);
     if (!(g->red_done = (unsigned int*)galloc(g, sizeof(unsigned int)))) return fail(VF_ENOMEM);
@@ -611,6 +640,10 @@ int vf_create_grid(const vf_grid_desc* d, vf_grid** out)
     if (!(g->solid_count = (unsigned long long*)galloc(g, sizeof(unsigned long long)))) return fail(VF_ENOMEM);
     if (!(g->dtctl = (vf::DtCtl*)galloc(g, sizeof(vf::DtCtl)))) return fail(VF_ENOMEM);
     if (!(g->force_acc = (double*)galloc(g, 3 * sizeof(double)))) return fail(VF_ENOMEM);
+    if (!(g->budget_partial = (double*)galloc(g, vf::kBudgetBlocks * vf::kBudgetTerms * sizeof(double))))
+        return fail(VF_ENOMEM);
+    if (!(g->budget_done = (unsigned int*)galloc(g, sizeof(unsigned int)))) return fail(VF_ENOMEM);
+    if (!(g->budget_out = (double*)galloc(g, vf::kBudgetTerms * sizeof(double)))) return fail(VF_ENOMEM);
     {
         // the control block starts at the given dt (constants with the same formulas as the adjust kernel)
         g->dynamic = d->courant_max > 0.0;
@@ -692,6 +725,7 @@ int vf_set_mask(vf_grid* g, const uint8_t* beta, int mem)
     VF_CK(cudaStreamSynchronize(g->stream));
     g->has_solid = solids > 0;
     VF_CK(vf::build_stencil_mask(g->mask, g->smask, g->d.nx, g->d.ny, g->d.nz, g->stream));
+    VF_CK(vf::mask_mark_budget(g->mask, g->d.nx, g->d.ny, g->d.nz, g->stream));
     VF_CK(cudaStreamSynchronize(g->stream));
     g->mask_set = true;
     g->sigma_stale = true;   // the fields were re-masked
@@ -709,6 +743,7 @@ int vf_set_inflow(vf_grid* g, const uint8_t* S, const double u_set[3], double c_
         if (rc) return rc;
         VF_CK(vf::mask_merge(g->mask, (const uint8_t*)src, vf::kBitS, g->N, g->stream));
         VF_CK(vf::build_stencil_mask(g->mask, g->smask, g->d.nx, g->d.ny, g->d.nz, g->stream));
+        VF_CK(vf::mask_mark_budget(g->mask, g->d.nx, g->d.ny, g->d.nz, g->stream));
         VF_CK(cudaStreamSynchronize(g->stream));
     }
     for (int j = 0; j < 3; ++j) g->uset[j] = u_set[j];
@@ -741,6 +776,7 @@ int vf_set_inflow_tanh(vf_grid* g, const double center[3], const double width[3]
     if (g->fp64) VF_CK(Kernels<double>::tanh_source((double*)g->sval, g->mask, w, n[0], n[1], n[2], g->stream));
     else VF_CK(Kernels<float>::tanh_source((float*)g->sval, g->mask, w, n[0], n[1], n[2], g->stream));
     VF_CK(vf::build_stencil_mask(g->mask, g->smask, n[0], n[1], n[2], g->stream));
+    VF_CK(vf::mask_mark_budget(g->mask, n[0], n[1], n[2], g->stream));
     VF_CK(cudaStreamSynchronize(g->stream));
     for (int j = 0; j < 3; ++j) g->uset[j] = u_set[j];
     g->cset = c_set;
@@ -766,6 +802,7 @@ int vf_set_inflow_values(vf_grid* g, const void* S, int is_fp64, const double u_
         VF_CK(Kernels<float>::source_bits(g->mask, (const float*)g->sval, g->N, g->stream));
     }
     VF_CK(vf::build_stencil_mask(g->mask, g->smask, g->d.nx, g->d.ny, g->d.nz, g->stream));
+    VF_CK(vf::mask_mark_budget(g->mask, g->d.nx, g->d.ny, g->d.nz, g->stream));
     VF_CK(cudaStreamSynchronize(g->stream));
     for (int j = 0; j < 3; ++j) g->uset[j] = u_set[j];
     g->cset = c_set;
@@ -794,6 +831,7 @@ int vf_set_inflow_field(vf_grid* g, const void* S, const void* targets, int is_f
         VF_CK(Kernels<float>::source_bits(g->mask, (const float*)g->sval, g->N, g->stream));
     }
     VF_CK(vf::build_stencil_mask(g->mask, g->smask, g->d.nx, g->d.ny, g->d.nz, g->stream));
+    VF_CK(vf::mask_mark_budget(g->mask, g->d.nx, g->d.ny, g->d.nz, g->stream));
     for (int comp = 0; comp < 4; ++comp) {
         // one component at a time through the staging buffer (N values)
         VF_CK(cudaStreamSynchronize(g->stream));
@@ -849,6 +887,7 @@ int vf_set_region(vf_grid* g, const uint8_t* room, int mem)
     const void* src = stage_input(g, room, g->N, mem, &rc);
     if (rc) return rc;
     VF_CK(vf::mask_merge(g->mask, (const uint8_t*)src, vf::kBitRoom, g->N, g->stream));
+    VF_CK(vf::mask_mark_budget(g->mask, g->d.nx, g->d.ny, g->d.nz, g->stream));
     VF_CK(cudaStreamSynchronize(g->stream));
     return VF_OK;
 }
@@ -1156,7 +1195,7 @@ const char* vf_phase_name(int phase)
     static const char* names[VF_N_PHASES] = {"stage1", "stage2", "stage3", "stage4", "div", "fft_x_fwd",
                                              "fft_y_fwd", "fft_z_solve", "fft_y_inv", "fft_x_inv", "project",
                                              "filter", "reduce", "poisson_rhs", "fft_yz_solve", "adjust_dt",
-                                             "particles"};
+                                             "particles", "budget"};
     if (phase < 0 || phase >= VF_N_PHASES) return "unknown";
     return names[phase];
 }

@@ -605,11 +605,14 @@ __device__ __forceinline__ void red_init(RedShared<T>& sh)
 // CTA partials (quantity-major, partial[q * nblocks + cta]), the histogram counters, the ticket, and in the last
 // CTA the final sums and the record.  Quantities 0-5 are sums, 6-7 maxima.  SPLIT_C: slot 2 holds the scalar over
 // the non-room cells (total = slot 2 + slot 3).  Every thread of a CTA of TX * TY threads calls it once.
+// quantities 6 and 7 of the reduction slots are maxima, the others sums
+__device__ __forceinline__ bool red_is_max(int q) { return q == 6 || q == 7; }
+
 template <typename T, bool SPLIT_C>
 __device__ void red_tail(RedShared<T>& sh, const ReduceArgsDev& r, int to_history)
 {
     constexpr int NW = TX * TY / 32;
-    static_assert(NW == kRedSlots, "one warp per reduced quantity in the final pass");
+    static_assert(NW <= kRedSlots && kRedSlots <= 2 * NW, "one or two reduced quantities per warp in the final pass");
     static_assert(TX * TY >= kHistBins + 2, "one thread per histogram counter in the final pass");
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     const int lane = tid & 31, wid = tid >> 5;
@@ -619,7 +622,7 @@ __device__ void red_tail(RedShared<T>& sh, const ReduceArgsDev& r, int to_histor
     const long long bid = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
     if (tid < kRedSlots) {
         Part<T> v = sh.red[tid][0];
-        for (int i = 1; i < NW; ++i) v = (tid < 6) ? v.plus(sh.red[tid][i]) : v.maxw(sh.red[tid][i]);
+        for (int i = 1; i < NW; ++i) v = red_is_max(tid) ? v.maxw(sh.red[tid][i]) : v.plus(sh.red[tid][i]);
         part[(long long)tid * nblocks + bid] = v;
     }
     for (int i = tid; i < kHistBins + 2; i += TX * TY)
@@ -640,9 +643,9 @@ __device__ void red_tail(RedShared<T>& sh, const ReduceArgsDev& r, int to_histor
         if (r.dyn) { t_end = r.dyn->t_end; dt_dyn = r.dyn->dt; }
     }
     if (tid < kHistBins + 2) sh.hist_total[tid] = (long long)atomicExch(r.hist_accum + tid, 0ull);
-    {
+    for (int qq = wid; qq < kRedSlots; qq += NW) {
         constexpr int kInFlight = 16;
-        const int qq = wid;
+        const bool mx = red_is_max(qq);
         const Part<T>* src = part + (long long)qq * nblocks;
         Part<T> v = Part<T>::of(T(0));   // a sum starts from 0, and so does a maximum (of non-negative values)
         for (int c0 = 0; c0 < nblocks; c0 += 32 * kInFlight) {
@@ -653,9 +656,9 @@ __device__ void red_tail(RedShared<T>& sh, const ReduceArgsDev& r, int to_histor
                 pv[u] = b < nblocks ? ld_part(src + b) : Part<T>::of(T(0));
             }
 #pragma unroll
-            for (int u = 0; u < kInFlight; ++u) v = (qq < 6) ? v.plus(pv[u]) : v.maxw(pv[u]);
+            for (int u = 0; u < kInFlight; ++u) v = mx ? v.maxw(pv[u]) : v.plus(pv[u]);
         }
-        v = (qq < 6) ? warp_sum(v) : Part<T>::of(warp_maxT(v.s));
+        v = mx ? Part<T>::of(warp_maxT(v.s)) : warp_sum(v);
         if (lane == 0) sh.fin[qq] = v.value();
     }
     __syncthreads();
@@ -684,6 +687,12 @@ __device__ void red_tail(RedShared<T>& sh, const ReduceArgsDev& r, int to_histor
             dst->v_room = r.dV * sh.fin[5];
             dst->div_max = sh.fin[6];
             dst->u_max = sh.fin[7];
+            // scalar budget of the step: the stage terms of k_budget, the filter's terms from its records
+            dst->budget_forcing = r.budget ? r.budget[0] : 0.0;
+            dst->budget_forcing_room = r.budget ? r.budget[1] : 0.0;
+            dst->budget_outflow = r.budget ? r.budget[2] : 0.0;
+            dst->budget_mask_loss = r.filter_budget ? r.dV * sh.fin[8] : 0.0;
+            dst->budget_filter_room = r.filter_budget ? r.dV * sh.fin[9] : 0.0;
         }
     }
     __syncthreads();
@@ -714,6 +723,8 @@ __device__ void red_finish(CellStats<T>& cs, RedShared<T>& sh, const ReduceArgsD
         sh.red[5][wid] = Part<T>::of((T)vr);   // at most 32 x 64 cells: exact
         sh.red[6][wid] = Part<T>::of(dmax);
         sh.red[7][wid] = Part<T>::of(umax);
+        sh.red[8][wid] = Part<T>::of(T(0));   // no filter records
+        sh.red[9][wid] = Part<T>::of(T(0));
     }
     red_tail<T, false>(sh, r, to_history);
 }
@@ -809,18 +820,23 @@ k_reduce_state(const void* __restrict__ q, const uint8_t* __restrict__ mask, int
             for (int f = 0; f < 4; ++f) cur[u][f] = nxt[u][f];
         }
     }
-    // the filter's divergence records, folded in record order per thread
-    Part<T> d2 = Part<T>::of(T(0));
+    // the filter's records (divergence, mask loss, room change), folded in record order per thread
+    Part<T> d2 = Part<T>::of(T(0)), ml = Part<T>::of(T(0)), fr = Part<T>::of(T(0));
     T dmax = T(0);
     const Part<T>* rec = reinterpret_cast<const Part<T>*>(r.div_partial);
     for (int j = blockIdx.x * kRedThreads + tid; j < r.div_count; j += gridDim.x * kRedThreads) {
-        d2 = d2.plus(ld_part(rec + 2 * (long long)j));
-        dmax = fmax(dmax, ld_part(rec + 2 * (long long)j + 1).s);
+        const Part<T>* rj = rec + kDivRecord * (long long)j;
+        d2 = d2.plus(ld_part(rj));
+        dmax = fmax(dmax, ld_part(rj + 1).s);
+        ml = ml.plus(ld_part(rj + 2));
+        fr = fr.plus(ld_part(rj + 3));
     }
     cs.run.flush(sh.hist);
     const Part<T> ke = warp_sum(Part<T>::of(cs.ke));
     const Part<T> cn = warp_sum(cs.cn), cr = warp_sum(cs.cr), c2 = warp_sum(cs.c2);
     d2 = warp_sum(d2);
+    ml = warp_sum(ml);
+    fr = warp_sum(fr);
     const int vr = __reduce_add_sync(0xffffffffu, cs.vr);
     const T umax = warp_maxT(cs.umax);
     dmax = warp_maxT(dmax);
@@ -833,6 +849,8 @@ k_reduce_state(const void* __restrict__ q, const uint8_t* __restrict__ mask, int
         sh.red[5][wid] = Part<T>::of((T)vr);   // at most 32 x 64 cells: exact
         sh.red[6][wid] = Part<T>::of(dmax);
         sh.red[7][wid] = Part<T>::of(umax);
+        sh.red[8][wid] = ml;
+        sh.red[9][wid] = fr;
     }
     red_tail<T, true>(sh, r, to_history);
 }
@@ -840,7 +858,9 @@ k_reduce_state(const void* __restrict__ q, const uint8_t* __restrict__ mask, int
 // ------------------------------------------------------------------------------------------------------------
 // Sixth-order filter q <- beta (q + pi^-6 sum_j S6_j q), S6 = (1, -6, 15, -20, 15, -6, 1) (Eq. 6).
 // DIVSTAT: also the divergence of the filter's input (the projected velocity, after the projection and before the
-// filter) for the reductions (Sec. 3.3): per warp the sum of d^2 and max |d| into r.div_partial, no CTA barrier.
+// filter) for the reductions (Sec. 3.3), and the filter's share of the scalar budget: per warp the sum of d^2,
+// max |d|, the sum over solid cells of the unmasked filtered scalar (what the re-mask removes) and the sum over
+// fluid room cells of the filter's change of the scalar, into r.div_partial (kDivRecord values), no CTA barrier.
 // ------------------------------------------------------------------------------------------------------------
 template <typename T, bool DIVSTAT, bool SIGMA>
 __global__ void __launch_bounds__(TX * TY, sizeof(T) == 4 ? 4 : 2)
@@ -849,7 +869,7 @@ k_filter(const void* __restrict__ in, void* __restrict__ out, const uint8_t* __r
 {
     pdl_enter();
     T smax = T(0);   // SIGMA: Courant rate of the filtered velocity (the step's final state)
-    T d2 = T(0), dmax = T(0);
+    T d2 = T(0), dmax = T(0), mloss = T(0), froom = T(0);
     const int x = blockIdx.x * TX + threadIdx.x;
     const int y = blockIdx.y * TY + threadIdx.y;
     if (x < k.nx && y < k.ny) {
@@ -899,6 +919,9 @@ k_filter(const void* __restrict__ in, void* __restrict__ out, const uint8_t* __r
             if (DIVSTAT) {
                 d2 += div * div;
                 dmax = fmax(dmax, fabs(div));
+                const T change = k.filt * acc[3];
+                if (!(m0 & kBitBeta)) mloss += zw[3][3] + change;
+                else if (m0 & kBitRoom) froom += change;
             }
             if (SIGMA) smax = fmax(smax, sigma_cell(o[0], o[1], o[2], k.ih));
         }
@@ -907,15 +930,139 @@ k_filter(const void* __restrict__ in, void* __restrict__ out, const uint8_t* __r
     if (DIVSTAT) {
         const Part<T> s = warp_sum(Part<T>::of(d2));
         const T m = warp_maxT(dmax);
+        const Part<T> ml = warp_sum(Part<T>::of(mloss)), fr = warp_sum(Part<T>::of(froom));
         const int tid = threadIdx.y * TX + threadIdx.x;
         if ((tid & 31) == 0) {
             const long long bid = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
             const long long w = bid * (TX * TY / 32) + (tid >> 5);
-            Part<T>* rec = reinterpret_cast<Part<T>*>(r.div_partial);
-            rec[2 * w] = s;
-            rec[2 * w + 1] = Part<T>::of(m);
+            Part<T>* rec = reinterpret_cast<Part<T>*>(r.div_partial) + kDivRecord * w;
+            rec[0] = s;
+            rec[1] = Part<T>::of(m);
+            rec[2] = ml;
+            rec[3] = fr;
         }
     }
+}
+
+// ------------------------------------------------------------------------------------------------------------
+// Scalar budget of the RK4 stages (Eqs. 3-4 in flux form; the room inventory of Sec. 3.3).  At every cell with
+// the budget bit and for each stage state q_s (q_n, q2, q3, q4) with its RK4 weight b_s: the relaxation source
+// S (c_set - c_s) / tau_f of a fluid forcing cell (and again if the cell is in the room), and for a fluid room
+// cell the flux of Eq. 3 through each face to a fluid neighbour outside the room -- convective
+// (u_j c |_i + u_j c |_nb) / 2 minus diffusive alpha_c (c_nb - c_i) / h_j, counted out of the room -- times the face
+// area dV / h_j.  Each CTA takes a fixed contiguous chunk of the mask, 16 cells per thread and load; the cells of
+// the budget are few (the openings of a room), so their arithmetic is in double.  The last CTA (atomic ticket)
+// adds the CTA partials in CTA order and scales by dt.
+// ------------------------------------------------------------------------------------------------------------
+constexpr int kBudgetThreads = 256;
+
+template <typename T>
+__device__ __forceinline__ double ld_comp(const void* q, size_t i, int comp)
+{
+    return (double)__ldcg(reinterpret_cast<const T*>(q) + 4 * i + comp);
+}
+
+template <typename T, bool DYN>
+__global__ void __launch_bounds__(kBudgetThreads)
+k_budget(StageArgs<T> a, const void* __restrict__ q4, FlowConsts<T> k, BudgetConsts bc, size_t chunk,
+         double* partial, unsigned int* done, double* out)
+{
+    pdl_enter();
+    const int nx = k.nx, ny = k.ny, nz = k.nz;
+    const size_t n = (size_t)nx * ny * nz, plane = (size_t)nx * ny;
+    const double inv_tau = DYN ? k.dyn->inv_tau : bc.inv_tau;
+    const double bw[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
+    const void* qs[4] = {a.qn, a.q2, a.q3, q4};
+    double f_all = 0.0, f_room = 0.0, outflow = 0.0;
+    auto cell = [&](size_t i, uint8_t m) {
+        if (!(m & kBitBeta)) return;
+        if (m & kBitS) {
+            const double S = a.sval ? (double)a.sval[i] : 1.0;
+            const double cset = a.target ? ld_comp<T>(a.target, i, 3) : bc.cset;
+            double f = 0.0;
+#pragma unroll
+            for (int s = 0; s < 4; ++s) f += bw[s] * (S * (cset - ld_comp<T>(qs[s], i, 3)) * inv_tau);
+            f_all += f;
+            if (m & kBitRoom) f_room += f;
+        }
+        if (!(m & kBitRoom)) return;
+        const int x = (int)(i % nx), y = (int)((i / nx) % ny), z = (int)(i / plane);
+        const long long ii = (long long)i, pl = (long long)plane;
+        const size_t nbs[6] = {(size_t)(ii - x + wrap(x - 1, nx)), (size_t)(ii - x + wrap(x + 1, nx)),
+                               (size_t)(ii + (long long)(wrap(y - 1, ny) - y) * nx),
+                               (size_t)(ii + (long long)(wrap(y + 1, ny) - y) * nx),
+                               (size_t)(ii + (long long)(wrap(z - 1, nz) - z) * pl),
+                               (size_t)(ii + (long long)(wrap(z + 1, nz) - z) * pl)};
+#pragma unroll
+        for (int d = 0; d < 6; ++d) {
+            const size_t nb = nbs[d];
+            const uint8_t mn = a.mask[nb];
+            if (!(mn & kBitBeta) || (mn & kBitRoom)) continue;
+            const int j = d >> 1;
+            const double sgn = (d & 1) ? 1.0 : -1.0;   // face at +h_j / 2 or -h_j / 2
+            double fl = 0.0;
+#pragma unroll
+            for (int s = 0; s < 4; ++s) {
+                const double ui = ld_comp<T>(qs[s], i, j), ci = ld_comp<T>(qs[s], i, 3);
+                const double un = ld_comp<T>(qs[s], nb, j), cn = ld_comp<T>(qs[s], nb, 3);
+                // outward flux: sgn times the flux along +j through the face
+                fl += bw[s] * (sgn * 0.5 * (ui * ci + un * cn) - bc.alpha * (cn - ci) * bc.ih[j]);
+            }
+            outflow += fl * bc.ih[j];
+        }
+    };
+    const size_t lo = (size_t)blockIdx.x * chunk, hi = lo + chunk < n ? lo + chunk : n;
+    for (size_t i0 = lo + 16 * (size_t)threadIdx.x; i0 < hi; i0 += 16 * (size_t)kBudgetThreads) {
+        if (i0 + 16 <= n) {
+            const uint4 w = __ldg(reinterpret_cast<const uint4*>(a.mask + i0));
+            if (!((w.x | w.y | w.z | w.w) & 0x20202020u)) continue;   // no budget bit in these 16 cells
+            const uint32_t words[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll 1
+            for (int b = 0; b < 16; ++b) {
+                const uint8_t m = (uint8_t)(words[b >> 2] >> (8 * (b & 3)));
+                if (m & kBitBudget) cell(i0 + b, m);
+            }
+        } else {
+            for (size_t i = i0; i < n; ++i) {
+                const uint8_t m = a.mask[i];
+                if (m & kBitBudget) cell(i, m);
+            }
+        }
+    }
+    // CTA sums (fixed butterfly, then warps in order), the partial of this CTA, the ticket
+    __shared__ double wsum[kBudgetTerms][kBudgetThreads / 32];
+    __shared__ bool is_last;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    double v[kBudgetTerms] = {f_all, f_room, outflow};
+#pragma unroll
+    for (int t = 0; t < kBudgetTerms; ++t) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[t] += __shfl_xor_sync(0xffffffffu, v[t], o);
+        if (lane == 0) wsum[t][wid] = v[t];
+    }
+    __syncthreads();
+    if (tid < kBudgetTerms) {
+        double c = 0.0;
+        for (int w = 0; w < kBudgetThreads / 32; ++w) c += wsum[tid][w];
+        partial[(size_t)blockIdx.x * kBudgetTerms + tid] = c;
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) is_last = atomicAdd(done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    if (wid < kBudgetTerms) {
+        double c = 0.0;
+        for (unsigned b = lane; b < gridDim.x; b += 32) c += __ldcg(partial + (size_t)b * kBudgetTerms + wid);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+        if (lane == 0) {
+            const double dt = DYN ? k.dyn->dt : bc.dt;
+            out[wid] = dt * bc.dV * c;   // the outflow's face area dV / h_j: 1 / h_j is already in it
+        }
+    }
+    if (tid == 0) *done = 0u;
 }
 
 // ------------------------------------------------------------------------------------------------------------
@@ -1150,6 +1297,28 @@ __global__ void k_mark_near_solid(uint8_t* mask, int nx, int ny, int nz)
     }
 }
 
+// budget bit of every cell: a fluid forcing cell, or a fluid room cell with a fluid axis neighbour outside the room
+__global__ void k_mark_budget(uint8_t* mask, int nx, int ny, int nz)
+{
+    const size_t n = (size_t)nx * ny * nz;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(i % nx), y = (int)((i / nx) % ny), z = (int)(i / ((size_t)nx * ny));
+        const size_t plane = (size_t)nx * ny, row = (size_t)y * nx, zb = (size_t)z * plane;
+        const uint8_t m = mask[i];
+        bool flag = false;
+        if (m & kBitBeta) {
+            flag = (m & kBitS) != 0;
+            if (!flag && (m & kBitRoom)) {
+                auto open = [&](size_t j) { return (mask[j] & (kBitBeta | kBitRoom)) == kBitBeta; };
+                flag = open(zb + row + wrap(x - 1, nx)) || open(zb + row + wrap(x + 1, nx)) ||
+                       open(zb + (size_t)wrap(y - 1, ny) * nx + x) || open(zb + (size_t)wrap(y + 1, ny) * nx + x) ||
+                       open((size_t)wrap(z - 1, nz) * plane + row + x) || open((size_t)wrap(z + 1, nz) * plane + row + x);
+            }
+        }
+        mask[i] = (uint8_t)((m & ~kBitBudget) | (flag ? kBitBudget : 0));
+    }
+}
+
 __global__ void k_near_counts(const uint8_t* __restrict__ mask, size_t n, int* counts)
 {
     __shared__ int warp_tot[kListChunk / 32];
@@ -1261,6 +1430,19 @@ cudaError_t Kernels<T>::filter(const void* in, void* out, const uint8_t* mask, c
     auto kern = r ? (sigma ? k_filter<T, true, true> : k_filter<T, true, false>)
                   : (sigma ? k_filter<T, false, true> : k_filter<T, false, false>);
     return launch_pdl(kern, g, b, 0, st, in, out, mask, k, ra, sigma);
+}
+
+template <typename T>
+cudaError_t Kernels<T>::budget(const StageArgs<T>& a, const void* q4, const FlowConsts<T>& k, const BudgetConsts& b,
+                               double* partial, unsigned int* done, double* out, cudaStream_t st)
+{
+    const size_t n = (size_t)k.nx * k.ny * k.nz;
+    // chunk: a multiple of 16 cells, so every 16-byte mask load of a CTA is aligned and inside its chunk
+    size_t chunk = (n + kBudgetBlocks - 1) / kBudgetBlocks;
+    chunk = (chunk + 15) & ~(size_t)15;
+    const unsigned blocks = (unsigned)((n + chunk - 1) / chunk);
+    auto kern = k.dyn ? k_budget<T, true> : k_budget<T, false>;
+    return launch_pdl(kern, dim3(blocks), dim3(kBudgetThreads), 0, st, a, q4, k, b, chunk, partial, done, out);
 }
 
 template <typename T>
@@ -1420,6 +1602,12 @@ cudaError_t mask_count_solid(const uint8_t* mask, size_t n, unsigned long long* 
 cudaError_t mask_mark_near_solid(uint8_t* mask, int nx, int ny, int nz, cudaStream_t st)
 {
     k_mark_near_solid<<<elementwise_blocks((size_t)nx * ny * nz), 256, 0, st>>>(mask, nx, ny, nz);
+    return cudaGetLastError();
+}
+
+cudaError_t mask_mark_budget(uint8_t* mask, int nx, int ny, int nz, cudaStream_t st)
+{
+    k_mark_budget<<<elementwise_blocks((size_t)nx * ny * nz), 256, 0, st>>>(mask, nx, ny, nz);
     return cudaGetLastError();
 }
 

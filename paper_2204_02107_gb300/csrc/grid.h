@@ -55,7 +55,10 @@ struct vf_grid {
     int* krev_z = nullptr;
 
     double* red_partial = nullptr;
-    double* div_partial = nullptr;       // the filter's per-warp divergence records
+    double* div_partial = nullptr;       // the filter's per-warp records (divergence, mask loss, room change)
+    double* budget_partial = nullptr;    // k_budget: CTA partials, ticket and the step's stage budget terms
+    unsigned int* budget_done = nullptr;
+    double* budget_out = nullptr;
     unsigned long long* hist_accum = nullptr;
     unsigned int* red_done = nullptr;
     vf_reduce* red_out = nullptr;

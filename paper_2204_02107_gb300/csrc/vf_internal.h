@@ -21,6 +21,9 @@ constexpr uint8_t kBitS = 2u;
 constexpr uint8_t kBitRoom = 4u;
 constexpr uint8_t kBitNearSolid = 8u;
 constexpr uint8_t kBitForce = 16u;   // cells whose immersed-boundary force vf_region_force sums
+// cells that enter the scalar budget of the stages: fluid forcing cells, and fluid room cells with a fluid axis
+// neighbour outside the room (a face of the room's boundary); derived from beta, S and the room bits
+constexpr uint8_t kBitBudget = 32u;
 
 // Stencil mask of the stage kernels: one byte per cell with its own beta and S bits and the beta of its six axis
 // neighbours, so a cell's stencil reads one byte instead of five.
@@ -241,7 +244,7 @@ constexpr int kPlaneThreads = 512;
 // Reduction scratch: per-CTA partial sums and histogram counts, and the output records.
 struct ReduceArgsDev {
     double* partial;          // [kRedSlots * nblocks], quantity-major
-    double* div_partial;      // the filter's divergence records, {sum d^2, max |d|} per warp
+    double* div_partial;      // the filter's records, kDivRecord per warp
     int div_count;            // records k_reduce_state folds (set by its launcher)
     unsigned long long* hist_accum;   // [kHistBins + 2], zero between launches
     unsigned int* done;       // CTAs finished in the current launch, zero between launches
@@ -255,8 +258,24 @@ struct ReduceArgsDev {
     double dt;
     double t0;                // simulated time at step 0
     const DtCtl* dyn;         // dynamic time step: time and dt of the record from here (nullptr: t0 + step dt)
+    // scalar budget of the step (nullptr: the record's budget fields are 0): the stage terms k_budget left in
+    // budget[0..kBudgetTerms), and whether the filter's records carry its mask loss and room change
+    const double* budget;
+    int filter_budget;
 };
-constexpr int kRedSlots = 8;   // ke, div2, c_total, c_room, c2_room, v_room, div_max, u_max
+// ke, div2, c_total, c_room, c2_room, v_room, div_max, u_max, filter mask loss, filter room change
+constexpr int kRedSlots = 10;
+// The filter's record per warp: sum d^2, max |d| (divergence of its input), the scalar it puts into solid cells
+// (removed by the re-mask) and its change of the room cells' scalar.
+constexpr int kDivRecord = 4;
+// Scalar budget of the RK4 stages (k_budget): forcing, forcing in the room, outflow from the room.
+constexpr int kBudgetTerms = 3;
+constexpr int kBudgetBlocks = 256;   // CTAs of k_budget (fixed, so the sum order is too)
+// Constants of k_budget in double: cell volume, fixed dt and 1 / tau_f (a dynamic step takes them from DtCtl),
+// alpha_c, the forcing target c_set and 1 / h_j.
+struct BudgetConsts {
+    double dV, dt, inv_tau, alpha, cset, ih[3];
+};
 
 // Called after each launch of a step when a step is profiled (pass = VF phase id, see vf_phase_name).
 struct LaunchHook {
@@ -315,6 +334,10 @@ struct Kernels {
     // r != nullptr: also the divergence records of the projected velocity (r->div_partial) for reduce_state
     static cudaError_t filter(const void* in, void* out, const uint8_t* mask, const FlowConsts<T>& k,
                               const ReduceArgsDev* r, cudaStream_t st, unsigned long long* sigma = nullptr);
+    // scalar budget of the four stage states (q_n, q2, q3, q4) at the kBitBudget cells, RK4-weighted, into
+    // out[kBudgetTerms]; partial: kBudgetBlocks * kBudgetTerms doubles; done: a zeroed ticket counter
+    static cudaError_t budget(const StageArgs<T>& a, const void* q4, const FlowConsts<T>& k, const BudgetConsts& b,
+                              double* partial, unsigned int* done, double* out, cudaStream_t st);
     static int filter_warps(const FlowConsts<T>& k);   // divergence records one filter launch writes
     // reductions of the filtered state q with the divergence records of the filter launched before it with the same
     // k; max_blocks: the partial slots of r (reduce_blocks)
@@ -352,6 +375,7 @@ cudaError_t mask_merge(uint8_t* mask, const uint8_t* src, uint8_t bit, size_t n,
 cudaError_t mask_fill(uint8_t* mask, uint8_t value, size_t n, cudaStream_t st);
 cudaError_t mask_count_solid(const uint8_t* mask, size_t n, unsigned long long* d_count, cudaStream_t st);
 cudaError_t mask_mark_near_solid(uint8_t* mask, int nx, int ny, int nz, cudaStream_t st);
+cudaError_t mask_mark_budget(uint8_t* mask, int nx, int ny, int nz, cudaStream_t st);
 // Ordered list of the cells whose near-solid bit is set: per-chunk counts, then (after a host-side exclusive
 // scan into offsets) the cell indices in ascending order.
 constexpr int kListChunk = 1024;

@@ -20,7 +20,7 @@ VF_OK, VF_EINVAL, VF_ESIZE, VF_ENOMEM, VF_ECUDA, VF_ESTATE, VF_ENONFINITE, VF_ET
 VF_FP64, VF_FP32_MIXED = 0, 1
 VF_HOST, VF_DEVICE = 0, 1
 FIELDS = {"u": 0, "v": 1, "w": 2, "c": 3, "p": 4}
-N_PHASES = 17
+N_PHASES = 18
 PRECISIONS = {"fp64": VF_FP64, "fp32": VF_FP32_MIXED, "fp32_mixed": VF_FP32_MIXED}
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -58,7 +58,10 @@ class VfReduce(C.Structure):
     _fields_ = [("t", C.c_double), ("step", C.c_int64), ("ke", C.c_double), ("div_max", C.c_double),
                 ("div_l2", C.c_double), ("u_max", C.c_double), ("c_total", C.c_double), ("c_room", C.c_double),
                 ("c2_room", C.c_double), ("v_room", C.c_double), ("hist", C.c_int64 * 64),
-                ("hist_under", C.c_int64), ("hist_over", C.c_int64), ("dt", C.c_double)]
+                ("hist_under", C.c_int64), ("hist_over", C.c_int64), ("dt", C.c_double),
+                ("budget_forcing", C.c_double), ("budget_forcing_room", C.c_double),
+                ("budget_outflow", C.c_double), ("budget_mask_loss", C.c_double),
+                ("budget_filter_room", C.c_double)]
 
     def to_dict(self):
         d = {name: getattr(self, name) for name, _ in self._fields_ if name != "hist"}
@@ -625,7 +628,7 @@ def tile_cache_load(path):
 
 def _noalloc_sizes_accepted(nx, ny, nz, precision):
     """The size rules vf_poisson_solve_noalloc states: even, >= 8, 2-3-5 smooth, at most its cell limit, every FFT
-    length (nx/2 + 1, ny, nz) at most 1024."""
+    length (nx/2 + 1, ny, nz) at most 1024, ny and nz at most 581 (FP64) or 592 (FP32)."""
     def smooth(n):
         if n < 8 or n % 2:
             return False
@@ -633,8 +636,9 @@ def _noalloc_sizes_accepted(nx, ny, nz, precision):
             while n % q == 0:
                 n //= q
         return n == 1
+    yz_max = 581 if precision == VF_FP64 else 592
     return (all(smooth(int(v)) for v in (nx, ny, nz)) and nx * ny * nz <= lib().vf_poisson_noalloc_max_cells(precision)
-            and max(nx // 2 + 1, ny, nz) <= 1024)
+            and max(nx // 2 + 1, ny, nz) <= 1024 and max(ny, nz) <= yz_max)
 
 
 def poisson_solve_noalloc(nx, ny, nz, lx, ly, lz, f, p, stream=None):
