@@ -56,7 +56,6 @@ PHASE_BYTES_PER_CELL = {
     "reduce": 4 * F32 + 1,       # read u, v, w, c, mask
     "adjust_dt": None,           # one thread: the dynamic time step's control block
     "particles": None,           # per particle, not per cell
-    "budget": 1,                 # scans the mask (1 byte per cell); reads states only at the few budget cells
 }
 # kernel function of each phase (phases of one function are one roofline row)
 PHASE_KERNEL = {"stage1": "k_stage", "stage2": "k_stage", "stage3": "k_stage", "stage4": "k_stage",

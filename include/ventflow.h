@@ -416,8 +416,7 @@ int vf_particles_count(const vf_grid* g, int64_t* n);
 #define VF_PHASE_FFT_YZ_SOLVE 14 /* per-kx plane: y, z FFTs, division by lambda, inverse z, y FFTs */
 #define VF_PHASE_ADJUST_DT 15   /* dynamic time step: dt from the Courant rate of the current state */
 #define VF_PHASE_PARTICLES 16   /* Lagrangian particles (Sec. 2.3) in the new velocity */
-#define VF_PHASE_BUDGET 17      /* scalar budget of the RK4 stages (steps that write a reduction record) */
-#define VF_N_PHASES 18
+#define VF_N_PHASES 17
 
 /* Run n steps like vf_step but with direct launches bracketed by CUDA events on the grid's stream; adds the
  * elapsed milliseconds of every phase to phase_ms[VF_N_PHASES] and its launch count to launches[VF_N_PHASES]

@@ -197,10 +197,20 @@ vf::ReduceArgsDev reduce_args(const vf_grid* g)
     return r;
 }
 
-vf::BudgetConsts budget_consts(const vf_grid* g)
+// Budget CTAs of a recorded step's stage 3 and 4 launches: about one CTA per 256 (cell, stage state) items, at
+// least one, at most one z slice of the stage grid.
+template <typename T>
+vf::BudgetArgs budget_args(const vf_grid* g, const FlowConsts<T>& k)
 {
     const vf_grid_desc& d = g->d;
-    vf::BudgetConsts b{};
+    vf::BudgetArgs b{};
+    b.n = g->n_budget;
+    b.cap = Kernels<T>::budget_cta_capacity(k);
+    b.ctas = (int)std::min<long long>(b.cap, std::max<long long>(1, (2LL * g->n_budget + 255) / 256));
+    b.list = g->budget_list;
+    b.partial = g->budget_partial;
+    b.done = g->budget_done;
+    b.out = g->budget_out;
     const double h[3] = {d.lx / d.nx, d.ly / d.ny, d.lz / d.nz};
     b.dV = h[0] * h[1] * h[2];
     b.dt = d.dt;
@@ -209,6 +219,45 @@ vf::BudgetConsts budget_consts(const vf_grid* g)
     b.cset = g->cset;
     for (int j = 0; j < 3; ++j) b.ih[j] = 1.0 / h[j];
     return b;
+}
+
+// Ordered list of the cells whose mask has `bit`: per-chunk counts, host exclusive scan, fill (synchronous).
+cudaError_t cell_list(vf_grid* g, uint8_t bit, int* list, int* count)
+{
+    const size_t chunks = (g->N + vf::kListChunk - 1) / vf::kListChunk;
+    int* d_counts = (int*)g->staging;
+    cudaError_t e;
+    if ((e = vf::mask_list_counts(g->mask, g->N, bit, d_counts, g->stream)) != cudaSuccess) return e;
+    std::vector<int> counts(chunks);
+    if ((e = cudaMemcpyAsync(counts.data(), d_counts, chunks * sizeof(int), cudaMemcpyDeviceToHost, g->stream)) !=
+            cudaSuccess ||
+        (e = cudaStreamSynchronize(g->stream)) != cudaSuccess)
+        return e;
+    int total = 0;
+    for (size_t c = 0; c < chunks; ++c) {
+        const int n = counts[c];
+        counts[c] = total;
+        total += n;
+    }
+    if ((e = cudaMemcpyAsync(d_counts, counts.data(), chunks * sizeof(int), cudaMemcpyHostToDevice, g->stream)) !=
+            cudaSuccess ||
+        (e = vf::mask_list_fill(g->mask, g->N, bit, d_counts, list, g->stream)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(g->stream)) != cudaSuccess)
+        return e;
+    *count = total;
+    return cudaSuccess;
+}
+
+void drop_graphs(vf_grid* g);
+
+// The budget bit of every cell (from beta, S and the room bits) and the list of those cells; the step graphs
+// carry the list's length, so they are rebuilt.
+cudaError_t budget_cells(vf_grid* g)
+{
+    cudaError_t e = vf::mask_mark_budget(g->mask, g->d.nx, g->d.ny, g->d.nz, g->stream);
+    if (e == cudaSuccess) e = cell_list(g, vf::kBitBudget, g->budget_list, &g->n_budget);
+    if (e == cudaSuccess) drop_graphs(g);
+    return e;
 }
 
 int pressure_iters(const vf_grid* g)
@@ -243,16 +292,21 @@ cudaError_t enqueue_step_t(vf_grid* g, cudaStream_t st, bool with_reduce, const 
     if ((e = Kernels<T>::stage(2, a, k, st)) != cudaSuccess) return e;
     mark(VF_PHASE_STAGE2);
     a.qs = g->qb; a.out = g->acc;
+    if (with_reduce) {
+        // scalar budget: extra CTAs of stage 3 read q_n and q2, those of stage 4 q3 and q4 (none is written by
+        // the launch that reads it)
+        a.bud = budget_args(g, k);
+        a.bud.slot = 0;
+        a.bud.qa = g->q; a.bud.wa = 1.0 / 6.0;
+        a.bud.qb = g->qa; a.bud.wb = 1.0 / 3.0;
+    }
     if ((e = Kernels<T>::stage(3, a, k, st)) != cudaSuccess) return e;
     mark(VF_PHASE_STAGE3);
     if (with_reduce) {
-        // scalar budget of the four stage states q_n, q2, q3, q4 (all still in place until stage 4)
-        StageArgs<T> b = a;
-        b.q2 = g->qa; b.q3 = g->qb;
-        if ((e = Kernels<T>::budget(b, g->acc, k, budget_consts(g), g->budget_partial, g->budget_done, g->budget_out,
-                                    st)) != cudaSuccess)
-            return e;
-        mark(VF_PHASE_BUDGET);
+        a.bud.ctas_prev = a.bud.ctas;
+        a.bud.slot = 1;
+        a.bud.qa = g->qb; a.bud.wa = 1.0 / 3.0;
+        a.bud.qb = g->acc; a.bud.wb = 1.0 / 6.0;
     }
     a.qs = g->acc; a.q2 = g->qa; a.q3 = g->qb; a.out = g->qa;
     if ((e = Kernels<T>::stage(4, a, k, st)) != cudaSuccess) return e;
@@ -509,7 +563,8 @@ size_t grid_bytes(const vf_grid_desc& d)
          r256(sizeof(vf_reduce));
     b += r256((size_t)d.history_capacity * sizeof(vf_reduce)) + r256(16) + r256(4) + r256(8);
     b += r256(sizeof(vf::DtCtl)) + r256(3 * sizeof(double));
-    b += r256(vf::kBudgetBlocks * vf::kBudgetTerms * 8) + r256(4) + r256(vf::kBudgetTerms * 8);
+    b += r256(2 * (size_t)Kernels<float>::budget_cta_capacity(k) * vf::kBudgetTerms * 8) + r256(N * 4) + r256(4) +
+         r256(vf::kBudgetTerms * 8);
     b += r256(M * cpx) + r256(d.ny * cpx) + r256(d.nz * cpx) + r256((M + 1) * cpx);
     b += r256(M * esz) + r256(d.ny * esz) + r256(d.nz * esz) + r256(d.ny * 4) + r256(d.nz * 4);
     return b;
@@ -640,8 +695,10 @@ int vf_create_grid(const vf_grid_desc* d, vf_grid** out)
     if (!(g->solid_count = (unsigned long long*)galloc(g, sizeof(unsigned long long)))) return fail(VF_ENOMEM);
     if (!(g->dtctl = (vf::DtCtl*)galloc(g, sizeof(vf::DtCtl)))) return fail(VF_ENOMEM);
     if (!(g->force_acc = (double*)galloc(g, 3 * sizeof(double)))) return fail(VF_ENOMEM);
-    if (!(g->budget_partial = (double*)galloc(g, vf::kBudgetBlocks * vf::kBudgetTerms * sizeof(double))))
+    if (!(g->budget_partial = (double*)galloc(g, 2 * (size_t)Kernels<float>::budget_cta_capacity(kf) *
+                                                     vf::kBudgetTerms * sizeof(double))))
         return fail(VF_ENOMEM);
+    if (!(g->budget_list = (int*)galloc(g, g->N * sizeof(int)))) return fail(VF_ENOMEM);
     if (!(g->budget_done = (unsigned int*)galloc(g, sizeof(unsigned int)))) return fail(VF_ENOMEM);
     if (!(g->budget_out = (double*)galloc(g, vf::kBudgetTerms * sizeof(double)))) return fail(VF_ENOMEM);
     {
@@ -700,32 +757,14 @@ int vf_set_mask(vf_grid* g, const uint8_t* beta, int mem)
     VF_CK(vf::mask_merge(g->mask, (const uint8_t*)src, vf::kBitBeta, g->N, g->stream));
     VF_CK(vf::mask_mark_near_solid(g->mask, g->d.nx, g->d.ny, g->d.nz, g->stream));
     VF_CK(g->fp64 ? mask_fields<double>(g) : mask_fields<float>(g));
-    {
-        // ordered list of the cells next to a solid: per-chunk counts, host exclusive scan, fill
-        const size_t chunks = (g->N + vf::kListChunk - 1) / vf::kListChunk;
-        int* d_counts = (int*)g->staging;
-        VF_CK(vf::mask_near_counts(g->mask, g->N, d_counts, g->stream));
-        std::vector<int> counts(chunks);
-        VF_CK(cudaMemcpyAsync(counts.data(), d_counts, chunks * sizeof(int), cudaMemcpyDeviceToHost, g->stream));
-        VF_CK(cudaStreamSynchronize(g->stream));
-        int total = 0;
-        for (size_t c = 0; c < chunks; ++c) {
-            const int n = counts[c];
-            counts[c] = total;
-            total += n;
-        }
-        VF_CK(cudaMemcpyAsync(d_counts, counts.data(), chunks * sizeof(int), cudaMemcpyHostToDevice, g->stream));
-        VF_CK(vf::mask_near_fill(g->mask, g->N, d_counts, g->near_list, g->stream));
-        VF_CK(cudaStreamSynchronize(g->stream));
-        g->n_near = total;
-    }
+    if (cudaError_t e = cell_list(g, vf::kBitNearSolid, g->near_list, &g->n_near)) return fail_cuda(g, e, "near-solid list");
     VF_CK(vf::mask_count_solid(g->mask, g->N, g->solid_count, g->stream));
     unsigned long long solids = 0;
     VF_CK(cudaMemcpyAsync(&solids, g->solid_count, sizeof(solids), cudaMemcpyDeviceToHost, g->stream));
     VF_CK(cudaStreamSynchronize(g->stream));
     g->has_solid = solids > 0;
     VF_CK(vf::build_stencil_mask(g->mask, g->smask, g->d.nx, g->d.ny, g->d.nz, g->stream));
-    VF_CK(vf::mask_mark_budget(g->mask, g->d.nx, g->d.ny, g->d.nz, g->stream));
+    VF_CK(budget_cells(g));
     VF_CK(cudaStreamSynchronize(g->stream));
     g->mask_set = true;
     g->sigma_stale = true;   // the fields were re-masked
@@ -743,7 +782,7 @@ int vf_set_inflow(vf_grid* g, const uint8_t* S, const double u_set[3], double c_
         if (rc) return rc;
         VF_CK(vf::mask_merge(g->mask, (const uint8_t*)src, vf::kBitS, g->N, g->stream));
         VF_CK(vf::build_stencil_mask(g->mask, g->smask, g->d.nx, g->d.ny, g->d.nz, g->stream));
-        VF_CK(vf::mask_mark_budget(g->mask, g->d.nx, g->d.ny, g->d.nz, g->stream));
+        VF_CK(budget_cells(g));
         VF_CK(cudaStreamSynchronize(g->stream));
     }
     for (int j = 0; j < 3; ++j) g->uset[j] = u_set[j];
@@ -776,7 +815,7 @@ int vf_set_inflow_tanh(vf_grid* g, const double center[3], const double width[3]
     if (g->fp64) VF_CK(Kernels<double>::tanh_source((double*)g->sval, g->mask, w, n[0], n[1], n[2], g->stream));
     else VF_CK(Kernels<float>::tanh_source((float*)g->sval, g->mask, w, n[0], n[1], n[2], g->stream));
     VF_CK(vf::build_stencil_mask(g->mask, g->smask, n[0], n[1], n[2], g->stream));
-    VF_CK(vf::mask_mark_budget(g->mask, n[0], n[1], n[2], g->stream));
+    VF_CK(budget_cells(g));
     VF_CK(cudaStreamSynchronize(g->stream));
     for (int j = 0; j < 3; ++j) g->uset[j] = u_set[j];
     g->cset = c_set;
@@ -802,7 +841,7 @@ int vf_set_inflow_values(vf_grid* g, const void* S, int is_fp64, const double u_
         VF_CK(Kernels<float>::source_bits(g->mask, (const float*)g->sval, g->N, g->stream));
     }
     VF_CK(vf::build_stencil_mask(g->mask, g->smask, g->d.nx, g->d.ny, g->d.nz, g->stream));
-    VF_CK(vf::mask_mark_budget(g->mask, g->d.nx, g->d.ny, g->d.nz, g->stream));
+    VF_CK(budget_cells(g));
     VF_CK(cudaStreamSynchronize(g->stream));
     for (int j = 0; j < 3; ++j) g->uset[j] = u_set[j];
     g->cset = c_set;
@@ -831,7 +870,7 @@ int vf_set_inflow_field(vf_grid* g, const void* S, const void* targets, int is_f
         VF_CK(Kernels<float>::source_bits(g->mask, (const float*)g->sval, g->N, g->stream));
     }
     VF_CK(vf::build_stencil_mask(g->mask, g->smask, g->d.nx, g->d.ny, g->d.nz, g->stream));
-    VF_CK(vf::mask_mark_budget(g->mask, g->d.nx, g->d.ny, g->d.nz, g->stream));
+    VF_CK(budget_cells(g));
     for (int comp = 0; comp < 4; ++comp) {
         // one component at a time through the staging buffer (N values)
         VF_CK(cudaStreamSynchronize(g->stream));
@@ -887,7 +926,7 @@ int vf_set_region(vf_grid* g, const uint8_t* room, int mem)
     const void* src = stage_input(g, room, g->N, mem, &rc);
     if (rc) return rc;
     VF_CK(vf::mask_merge(g->mask, (const uint8_t*)src, vf::kBitRoom, g->N, g->stream));
-    VF_CK(vf::mask_mark_budget(g->mask, g->d.nx, g->d.ny, g->d.nz, g->stream));
+    VF_CK(budget_cells(g));
     VF_CK(cudaStreamSynchronize(g->stream));
     return VF_OK;
 }
@@ -1195,7 +1234,7 @@ const char* vf_phase_name(int phase)
     static const char* names[VF_N_PHASES] = {"stage1", "stage2", "stage3", "stage4", "div", "fft_x_fwd",
                                              "fft_y_fwd", "fft_z_solve", "fft_y_inv", "fft_x_inv", "project",
                                              "filter", "reduce", "poisson_rhs", "fft_yz_solve", "adjust_dt",
-                                             "particles", "budget"};
+                                             "particles"};
     if (phase < 0 || phase >= VF_N_PHASES) return "unknown";
     return names[phase];
 }

@@ -166,6 +166,116 @@ __device__ __forceinline__ void stage_cell(const StageArgs<T>& a, const FlowCons
     }
 }
 
+// ------------------------------------------------------------------------------------------------------------
+// Scalar budget CTAs of the stage 3 and stage 4 launches (Eqs. 3-4 in flux form; the room inventory of Sec. 3.3).
+// For every cell of the budget list and each of the launch's two stage states q_s (RK4 weight b_s): the relaxation
+// source S (c_set - c_s) / tau_f of a fluid forcing cell (and again if the cell is in the room), and for a fluid
+// room cell the flux of Eq. 3 through each face to a fluid neighbour outside the room -- convective
+// (u_j c |_i + u_j c |_nb) / 2 minus diffusive alpha_c (c_nb - c_i) / h_j, counted out of the room -- times the face
+// area dV / h_j.  A thread takes one (cell, state) item at a time and issues all of its loads (the cell's and its
+// six neighbours' 4-vectors and mask bytes) before using them; the arithmetic is in double.  Each CTA leaves its
+// partial sums; the last budget CTA of stage 4 (atomic ticket) adds both launches' partials in CTA order and
+// scales by dt and dV.
+// ------------------------------------------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void ld4_cg(const void* base, size_t i, double q[4])
+{
+    if constexpr (sizeof(T) == 4) {
+        const float4 v = __ldcg(reinterpret_cast<const float4*>(base) + i);
+        q[0] = v.x; q[1] = v.y; q[2] = v.z; q[3] = v.w;
+    } else {
+        const double2* p = reinterpret_cast<const double2*>(base) + 2 * i;
+        const double2 a = __ldcg(p), b = __ldcg(p + 1);
+        q[0] = a.x; q[1] = a.y; q[2] = b.x; q[3] = b.y;
+    }
+}
+
+template <typename T, bool DYN>
+__device__ __noinline__ void budget_cta(const StageArgs<T>& a, const FlowConsts<T>& k, int cta)
+{
+    const BudgetArgs& B = a.bud;
+    const int nx = k.nx, ny = k.ny, nz = k.nz;
+    const long long plane = (long long)nx * ny;
+    const double inv_tau = DYN ? k.dyn->inv_tau : B.inv_tau;
+    const int tid = threadIdx.x + TX * threadIdx.y;
+    double f_all = 0.0, f_room = 0.0, outflow = 0.0;
+    const long long items = 2LL * (B.n > 0 ? B.n : 0);
+    for (long long j = (long long)cta * (TX * TY) + tid; j < items; j += (long long)B.ctas * (TX * TY)) {
+        const long long i = B.list[j >> 1];
+        const void* q = (j & 1) ? B.qb : B.qa;
+        const double w = (j & 1) ? B.wb : B.wa;
+        const int x = (int)(i % nx), y = (int)((i / nx) % ny), z = (int)(i / plane);
+        const long long nb[6] = {i - x + wrap(x - 1, nx), i - x + wrap(x + 1, nx),
+                                 i + (long long)(wrap(y - 1, ny) - y) * nx, i + (long long)(wrap(y + 1, ny) - y) * nx,
+                                 i + (long long)(wrap(z - 1, nz) - z) * plane,
+                                 i + (long long)(wrap(z + 1, nz) - z) * plane};
+        const uint8_t m = a.mask[i];
+        uint8_t mn[6];
+        double qc[4], qn[6][4];
+        ld4_cg<T>(q, (size_t)i, qc);
+#pragma unroll
+        for (int d = 0; d < 6; ++d) {
+            mn[d] = a.mask[nb[d]];
+            ld4_cg<T>(q, (size_t)nb[d], qn[d]);
+        }
+        if (!(m & kBitBeta)) continue;
+        if (m & kBitS) {
+            const double S = a.sval ? (double)a.sval[i] : 1.0;
+            const double cset = a.target ? (double)__ldcg(reinterpret_cast<const T*>(a.target) + 4 * i + 3) : B.cset;
+            const double f = w * (S * (cset - qc[3]) * inv_tau);
+            f_all += f;
+            if (m & kBitRoom) f_room += f;
+        }
+        if (m & kBitRoom) {
+#pragma unroll
+            for (int d = 0; d < 6; ++d) {
+                if ((mn[d] & (kBitBeta | kBitRoom)) != kBitBeta) continue;   // a solid or room neighbour
+                const int jx = d >> 1;
+                const double sgn = (d & 1) ? 1.0 : -1.0;   // face at +h_j / 2 or -h_j / 2
+                const double flux = sgn * 0.5 * (qc[jx] * qc[3] + qn[d][jx] * qn[d][3]) -
+                                    B.alpha * (qn[d][3] - qc[3]) * B.ih[jx];
+                outflow += w * flux * B.ih[jx];
+            }
+        }
+    }
+    __shared__ double wsum[kBudgetTerms][TX * TY / 32];
+    __shared__ bool is_last;
+    const int lane = tid & 31, wid = tid >> 5;
+    double v[kBudgetTerms] = {f_all, f_room, outflow};
+#pragma unroll
+    for (int t = 0; t < kBudgetTerms; ++t) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[t] += __shfl_xor_sync(0xffffffffu, v[t], o);
+        if (lane == 0) wsum[t][wid] = v[t];
+    }
+    __syncthreads();
+    if (tid < kBudgetTerms) {
+        double c = 0.0;
+        for (int ww = 0; ww < TX * TY / 32; ++ww) c += wsum[tid][ww];
+        B.partial[((size_t)B.slot * B.cap + cta) * kBudgetTerms + tid] = c;
+    }
+    if (B.slot == 0) return;
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) is_last = atomicAdd(B.done, 1u) == (unsigned)(B.ctas - 1);
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    if (wid < kBudgetTerms) {
+        double c = 0.0;
+        for (int b = lane; b < B.ctas_prev; b += 32) c += __ldcg(B.partial + (size_t)b * kBudgetTerms + wid);
+        for (int b = lane; b < B.ctas; b += 32)
+            c += __ldcg(B.partial + ((size_t)B.cap + b) * kBudgetTerms + wid);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+        if (lane == 0) {
+            const double dt = DYN ? k.dyn->dt : B.dt;
+            B.out[wid] = dt * B.dV * c;   // the outflow's face area dV / h_j: its 1 / h_j is already in c
+        }
+    }
+    if (tid == 0) *B.done = 0u;
+}
+
 // Stage 4 reads three own states (q_n, q2, q3): prefetching them too takes 80 registers (3 CTAs per SM).
 #ifndef VF_STAGE_PREFETCH_OWN4
 #define VF_STAGE_PREFETCH_OWN4 0
@@ -177,6 +287,17 @@ __global__ void __launch_bounds__(TX * TY, sizeof(T) == 4 ? 4 : 1)
 k_stage(StageArgs<T> a, FlowConsts<T> k)
 {
     pdl_enter();
+    int bz = blockIdx.z;
+    if constexpr (STAGE >= 3) {
+        if (a.bud.n >= 0) {   // the first z slice of the grid holds the budget CTAs
+            if (bz == 0) {
+                const int cta = blockIdx.x + gridDim.x * blockIdx.y;
+                if (cta < a.bud.ctas) budget_cta<T, DYN>(a, k, cta);
+                return;
+            }
+            --bz;
+        }
+    }
     const int x = blockIdx.x * TX + threadIdx.x;
     const int y = blockIdx.y * TY + threadIdx.y;
     if (x >= k.nx || y >= k.ny) return;
@@ -191,7 +312,7 @@ k_stage(StageArgs<T> a, FlowConsts<T> k)
     const int nx = k.nx, ny = k.ny, nz = k.nz;
     const int plane = nx * ny;
     const int zc = k.zc[kZcStage];
-    const int z0 = blockIdx.z * zc;
+    const int z0 = bz * zc;
     const int z1 = min(z0 + zc, nz);
     const int xm = wrap(x - 1, nx), xp = wrap(x + 1, nx);
     const int rowc = y * nx, rowm = wrap(y - 1, ny) * nx, rowp = wrap(y + 1, ny) * nx;
@@ -945,127 +1066,6 @@ k_filter(const void* __restrict__ in, void* __restrict__ out, const uint8_t* __r
 }
 
 // ------------------------------------------------------------------------------------------------------------
-// Scalar budget of the RK4 stages (Eqs. 3-4 in flux form; the room inventory of Sec. 3.3).  At every cell with
-// the budget bit and for each stage state q_s (q_n, q2, q3, q4) with its RK4 weight b_s: the relaxation source
-// S (c_set - c_s) / tau_f of a fluid forcing cell (and again if the cell is in the room), and for a fluid room
-// cell the flux of Eq. 3 through each face to a fluid neighbour outside the room -- convective
-// (u_j c |_i + u_j c |_nb) / 2 minus diffusive alpha_c (c_nb - c_i) / h_j, counted out of the room -- times the face
-// area dV / h_j.  Each CTA takes a fixed contiguous chunk of the mask, 16 cells per thread and load; the cells of
-// the budget are few (the openings of a room), so their arithmetic is in double.  The last CTA (atomic ticket)
-// adds the CTA partials in CTA order and scales by dt.
-// ------------------------------------------------------------------------------------------------------------
-constexpr int kBudgetThreads = 256;
-
-template <typename T>
-__device__ __forceinline__ double ld_comp(const void* q, size_t i, int comp)
-{
-    return (double)__ldcg(reinterpret_cast<const T*>(q) + 4 * i + comp);
-}
-
-template <typename T, bool DYN>
-__global__ void __launch_bounds__(kBudgetThreads)
-k_budget(StageArgs<T> a, const void* __restrict__ q4, FlowConsts<T> k, BudgetConsts bc, size_t chunk,
-         double* partial, unsigned int* done, double* out)
-{
-    pdl_enter();
-    const int nx = k.nx, ny = k.ny, nz = k.nz;
-    const size_t n = (size_t)nx * ny * nz, plane = (size_t)nx * ny;
-    const double inv_tau = DYN ? k.dyn->inv_tau : bc.inv_tau;
-    const double bw[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
-    const void* qs[4] = {a.qn, a.q2, a.q3, q4};
-    double f_all = 0.0, f_room = 0.0, outflow = 0.0;
-    auto cell = [&](size_t i, uint8_t m) {
-        if (!(m & kBitBeta)) return;
-        if (m & kBitS) {
-            const double S = a.sval ? (double)a.sval[i] : 1.0;
-            const double cset = a.target ? ld_comp<T>(a.target, i, 3) : bc.cset;
-            double f = 0.0;
-#pragma unroll
-            for (int s = 0; s < 4; ++s) f += bw[s] * (S * (cset - ld_comp<T>(qs[s], i, 3)) * inv_tau);
-            f_all += f;
-            if (m & kBitRoom) f_room += f;
-        }
-        if (!(m & kBitRoom)) return;
-        const int x = (int)(i % nx), y = (int)((i / nx) % ny), z = (int)(i / plane);
-        const long long ii = (long long)i, pl = (long long)plane;
-        const size_t nbs[6] = {(size_t)(ii - x + wrap(x - 1, nx)), (size_t)(ii - x + wrap(x + 1, nx)),
-                               (size_t)(ii + (long long)(wrap(y - 1, ny) - y) * nx),
-                               (size_t)(ii + (long long)(wrap(y + 1, ny) - y) * nx),
-                               (size_t)(ii + (long long)(wrap(z - 1, nz) - z) * pl),
-                               (size_t)(ii + (long long)(wrap(z + 1, nz) - z) * pl)};
-#pragma unroll
-        for (int d = 0; d < 6; ++d) {
-            const size_t nb = nbs[d];
-            const uint8_t mn = a.mask[nb];
-            if (!(mn & kBitBeta) || (mn & kBitRoom)) continue;
-            const int j = d >> 1;
-            const double sgn = (d & 1) ? 1.0 : -1.0;   // face at +h_j / 2 or -h_j / 2
-            double fl = 0.0;
-#pragma unroll
-            for (int s = 0; s < 4; ++s) {
-                const double ui = ld_comp<T>(qs[s], i, j), ci = ld_comp<T>(qs[s], i, 3);
-                const double un = ld_comp<T>(qs[s], nb, j), cn = ld_comp<T>(qs[s], nb, 3);
-                // outward flux: sgn times the flux along +j through the face
-                fl += bw[s] * (sgn * 0.5 * (ui * ci + un * cn) - bc.alpha * (cn - ci) * bc.ih[j]);
-            }
-            outflow += fl * bc.ih[j];
-        }
-    };
-    const size_t lo = (size_t)blockIdx.x * chunk, hi = lo + chunk < n ? lo + chunk : n;
-    for (size_t i0 = lo + 16 * (size_t)threadIdx.x; i0 < hi; i0 += 16 * (size_t)kBudgetThreads) {
-        if (i0 + 16 <= n) {
-            const uint4 w = __ldg(reinterpret_cast<const uint4*>(a.mask + i0));
-            if (!((w.x | w.y | w.z | w.w) & 0x20202020u)) continue;   // no budget bit in these 16 cells
-            const uint32_t words[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll 1
-            for (int b = 0; b < 16; ++b) {
-                const uint8_t m = (uint8_t)(words[b >> 2] >> (8 * (b & 3)));
-                if (m & kBitBudget) cell(i0 + b, m);
-            }
-        } else {
-            for (size_t i = i0; i < n; ++i) {
-                const uint8_t m = a.mask[i];
-                if (m & kBitBudget) cell(i, m);
-            }
-        }
-    }
-    // CTA sums (fixed butterfly, then warps in order), the partial of this CTA, the ticket
-    __shared__ double wsum[kBudgetTerms][kBudgetThreads / 32];
-    __shared__ bool is_last;
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    double v[kBudgetTerms] = {f_all, f_room, outflow};
-#pragma unroll
-    for (int t = 0; t < kBudgetTerms; ++t) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v[t] += __shfl_xor_sync(0xffffffffu, v[t], o);
-        if (lane == 0) wsum[t][wid] = v[t];
-    }
-    __syncthreads();
-    if (tid < kBudgetTerms) {
-        double c = 0.0;
-        for (int w = 0; w < kBudgetThreads / 32; ++w) c += wsum[tid][w];
-        partial[(size_t)blockIdx.x * kBudgetTerms + tid] = c;
-    }
-    __threadfence();
-    __syncthreads();
-    if (tid == 0) is_last = atomicAdd(done, 1u) == gridDim.x - 1;
-    __syncthreads();
-    if (!is_last) return;
-    __threadfence();
-    if (wid < kBudgetTerms) {
-        double c = 0.0;
-        for (unsigned b = lane; b < gridDim.x; b += 32) c += __ldcg(partial + (size_t)b * kBudgetTerms + wid);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-        if (lane == 0) {
-            const double dt = DYN ? k.dyn->dt : bc.dt;
-            out[wid] = dt * bc.dV * c;   // the outflow's face area dV / h_j: 1 / h_j is already in it
-        }
-    }
-    if (tid == 0) *done = 0u;
-}
-
-// ------------------------------------------------------------------------------------------------------------
 // Smooth source mask (Eq. 5): S = prod_j (1 - tanh(B_j [d_j / (W_j/2) - (W_j/2) / d_j])) / 2, d_j the
 // minimum-image distance from the cell centre i h_j to c_j; the factor is its limit 1 where d_j = 0.  Evaluated
 // in double, stored in the grid's precision; the mask's S bit marks S > 0.
@@ -1319,14 +1319,14 @@ __global__ void k_mark_budget(uint8_t* mask, int nx, int ny, int nz)
     }
 }
 
-__global__ void k_near_counts(const uint8_t* __restrict__ mask, size_t n, int* counts)
+__global__ void k_list_counts(const uint8_t* __restrict__ mask, size_t n, uint8_t bit, int* counts)
 {
     __shared__ int warp_tot[kListChunk / 32];
     const size_t base = (size_t)blockIdx.x * kListChunk;
     int local = 0;
     for (int t = threadIdx.x; t < kListChunk; t += blockDim.x) {
         const size_t i = base + t;
-        if (i < n && (mask[i] & kBitNearSolid)) ++local;
+        if (i < n && (mask[i] & bit)) ++local;
     }
     for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(0xffffffffu, local, o);
     if ((threadIdx.x & 31) == 0) warp_tot[threadIdx.x >> 5] = local;
@@ -1339,7 +1339,8 @@ __global__ void k_near_counts(const uint8_t* __restrict__ mask, size_t n, int* c
 }
 
 // each chunk writes its flagged cells in ascending order from its offset (ballot + popcount prefix per warp)
-__global__ void k_near_fill(const uint8_t* __restrict__ mask, size_t n, const int* __restrict__ offsets, int* list)
+__global__ void k_list_fill(const uint8_t* __restrict__ mask, size_t n, uint8_t bit, const int* __restrict__ offsets,
+                            int* list)
 {
     __shared__ int warp_tot[32];
     __shared__ int running;
@@ -1349,7 +1350,7 @@ __global__ void k_near_fill(const uint8_t* __restrict__ mask, size_t n, const in
     __syncthreads();
     for (int r = 0; r < kListChunk; r += blockDim.x) {
         const size_t i = base + r + threadIdx.x;
-        const bool flag = i < n && (mask[i] & kBitNearSolid);
+        const bool flag = i < n && (mask[i] & bit);
         const unsigned bal = __ballot_sync(0xffffffffu, flag);
         if (lane == 0) warp_tot[wid] = __popc(bal);
         __syncthreads();
@@ -1390,9 +1391,21 @@ bool pdl_on()
 // launchers
 // ------------------------------------------------------------------------------------------------------------
 template <typename T>
+int Kernels<T>::budget_cta_capacity(const FlowConsts<T>& k)
+{
+    const dim3 g = flow_grid(k, kZcStage);
+    return (int)(g.x * g.y);
+}
+
+template <typename T>
 cudaError_t Kernels<T>::stage(int s, const StageArgs<T>& a, const FlowConsts<T>& k, cudaStream_t st)
 {
-    const dim3 g = flow_grid(k, kZcStage), b(TX, TY);
+    dim3 g = flow_grid(k, kZcStage);
+    const dim3 b(TX, TY);
+    if (s >= 3 && a.bud.n >= 0) {
+        if (a.bud.ctas < 1 || a.bud.ctas > (int)(g.x * g.y) || a.bud.ctas > a.bud.cap) return cudaErrorInvalidValue;
+        g.z += 1;   // the budget slice
+    }
     const bool dyn = k.dyn != nullptr;
     switch (s) {
         case 1: return launch_pdl(dyn ? k_stage<T, 1, true> : k_stage<T, 1, false>, g, b, 0, st, a, k);
@@ -1430,19 +1443,6 @@ cudaError_t Kernels<T>::filter(const void* in, void* out, const uint8_t* mask, c
     auto kern = r ? (sigma ? k_filter<T, true, true> : k_filter<T, true, false>)
                   : (sigma ? k_filter<T, false, true> : k_filter<T, false, false>);
     return launch_pdl(kern, g, b, 0, st, in, out, mask, k, ra, sigma);
-}
-
-template <typename T>
-cudaError_t Kernels<T>::budget(const StageArgs<T>& a, const void* q4, const FlowConsts<T>& k, const BudgetConsts& b,
-                               double* partial, unsigned int* done, double* out, cudaStream_t st)
-{
-    const size_t n = (size_t)k.nx * k.ny * k.nz;
-    // chunk: a multiple of 16 cells, so every 16-byte mask load of a CTA is aligned and inside its chunk
-    size_t chunk = (n + kBudgetBlocks - 1) / kBudgetBlocks;
-    chunk = (chunk + 15) & ~(size_t)15;
-    const unsigned blocks = (unsigned)((n + chunk - 1) / chunk);
-    auto kern = k.dyn ? k_budget<T, true> : k_budget<T, false>;
-    return launch_pdl(kern, dim3(blocks), dim3(kBudgetThreads), 0, st, a, q4, k, b, chunk, partial, done, out);
 }
 
 template <typename T>
@@ -1611,15 +1611,16 @@ cudaError_t mask_mark_budget(uint8_t* mask, int nx, int ny, int nz, cudaStream_t
     return cudaGetLastError();
 }
 
-cudaError_t mask_near_counts(const uint8_t* mask, size_t n, int* chunk_counts, cudaStream_t st)
+cudaError_t mask_list_counts(const uint8_t* mask, size_t n, uint8_t bit, int* chunk_counts, cudaStream_t st)
 {
-    k_near_counts<<<(unsigned)((n + kListChunk - 1) / kListChunk), 256, 0, st>>>(mask, n, chunk_counts);
+    k_list_counts<<<(unsigned)((n + kListChunk - 1) / kListChunk), 256, 0, st>>>(mask, n, bit, chunk_counts);
     return cudaGetLastError();
 }
 
-cudaError_t mask_near_fill(const uint8_t* mask, size_t n, const int* chunk_offsets, int* list, cudaStream_t st)
+cudaError_t mask_list_fill(const uint8_t* mask, size_t n, uint8_t bit, const int* chunk_offsets, int* list,
+                           cudaStream_t st)
 {
-    k_near_fill<<<(unsigned)((n + kListChunk - 1) / kListChunk), 256, 0, st>>>(mask, n, chunk_offsets, list);
+    k_list_fill<<<(unsigned)((n + kListChunk - 1) / kListChunk), 256, 0, st>>>(mask, n, bit, chunk_offsets, list);
     return cudaGetLastError();
 }
 

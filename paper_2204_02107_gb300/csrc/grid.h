@@ -56,9 +56,11 @@ struct vf_grid {
 
     double* red_partial = nullptr;
     double* div_partial = nullptr;       // the filter's per-warp records (divergence, mask loss, room change)
-    double* budget_partial = nullptr;    // k_budget: CTA partials, ticket and the step's stage budget terms
+    double* budget_partial = nullptr;    // scalar budget: CTA partials of stages 3 and 4, ticket, the step's terms
     unsigned int* budget_done = nullptr;
     double* budget_out = nullptr;
+    int* budget_list = nullptr;          // cells with the budget bit, ascending (capacity N)
+    int n_budget = 0;
     unsigned long long* hist_accum = nullptr;
     unsigned int* red_done = nullptr;
     vf_reduce* red_out = nullptr;

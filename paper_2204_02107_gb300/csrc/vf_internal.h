@@ -73,6 +73,27 @@ struct FlowConsts {
     const DtCtl* dyn;   // dynamic time step: dt-dependent constants come from here (nullptr: the fields above)
 };
 
+// Scalar budget of a step's four stage states (Eqs. 3-4 in flux form, the room inventory of Sec. 3.3), computed
+// by extra CTAs of the stage 3 and stage 4 launches on steps that write a reduction record: stage 3's read q_n and
+// q2, stage 4's q3 and q4, none of which that launch writes.  The CTA partials of both launches are added in CTA
+// order by the last budget CTA of stage 4 (atomic ticket).
+struct BudgetArgs {
+    int n = -1;               // cells in the list; < 0: no budget CTAs in this launch
+    int ctas = 0;             // budget CTAs of this launch (at least 1 when n >= 0)
+    int ctas_prev = 0;        // budget CTAs of the stage 3 launch (stage 4 adds their partials too)
+    int slot = 0;             // 0: stage 3 launch, 1: stage 4 launch
+    int cap = 0;              // CTA partials per slot
+    const int* list = nullptr;        // cells with the budget bit, ascending
+    const void* qa = nullptr;         // the two stage states of this launch and their RK4 weights
+    const void* qb = nullptr;
+    double wa = 0.0, wb = 0.0;
+    double* partial = nullptr;        // [2][cap][kBudgetTerms]
+    unsigned int* done = nullptr;     // ticket of stage 4's budget CTAs, zero between launches
+    double* out = nullptr;            // [kBudgetTerms] of the step, scaled by dt and dV
+    double dV = 0.0, dt = 0.0, inv_tau = 0.0, alpha = 0.0, cset = 0.0, ih[3] = {0.0, 0.0, 0.0};   // in double;
+                                      // a dynamic step takes dt and 1 / tau_f from DtCtl
+};
+
 // Pointers of one RK4 stage.  Every state array holds one 4-vector (u, v, w, c) of T per cell (16 bytes for
 // float, 32 for double): q_s (stencil input), q_n, the stage states q2, q3 (read by stage 4) and the output.
 template <typename T>
@@ -87,6 +108,7 @@ struct StageArgs {
     const T* sval;      // smooth forcing region S in [0, 1] at the cells whose S bit is set (nullptr: S = 1 there)
     const void* target; // per-cell forcing targets (u, v, w, c)_set as a 4-vector array (nullptr: the constants;
                         // when given, the constants are 0 and S beta target / tau_f is added at the S cells)
+    BudgetArgs bud;     // stages 3 and 4 of a recorded step: the scalar budget CTAs
 };
 
 // One smooth source window of Eq. 5 on a grid: centre c_j, half widths W_j / 2, sharpness B_j, cell size h_j and
@@ -268,14 +290,8 @@ constexpr int kRedSlots = 10;
 // The filter's record per warp: sum d^2, max |d| (divergence of its input), the scalar it puts into solid cells
 // (removed by the re-mask) and its change of the room cells' scalar.
 constexpr int kDivRecord = 4;
-// Scalar budget of the RK4 stages (k_budget): forcing, forcing in the room, outflow from the room.
+// Scalar budget of the RK4 stages: forcing, forcing in the room, outflow from the room.
 constexpr int kBudgetTerms = 3;
-constexpr int kBudgetBlocks = 256;   // CTAs of k_budget (fixed, so the sum order is too)
-// Constants of k_budget in double: cell volume, fixed dt and 1 / tau_f (a dynamic step takes them from DtCtl),
-// alpha_c, the forcing target c_set and 1 / h_j.
-struct BudgetConsts {
-    double dV, dt, inv_tau, alpha, cset, ih[3];
-};
 
 // Called after each launch of a step when a step is profiled (pass = VF phase id, see vf_phase_name).
 struct LaunchHook {
@@ -325,7 +341,9 @@ struct RegFft {
 
 template <typename T>
 struct Kernels {
+    // s = 3, 4 with a.bud.n >= 0: plus a.bud.ctas budget CTAs (a first z slice of the grid)
     static cudaError_t stage(int s, const StageArgs<T>& a, const FlowConsts<T>& k, cudaStream_t st);
+    static int budget_cta_capacity(const FlowConsts<T>& k);   // CTAs one z slice of the stage grid has
     static cudaError_t divergence(const void* qstar, T* r, const FlowConsts<T>& k, cudaStream_t st);
     // u = beta (u* - dt G p), c* passes through; ticks the device step counter
     // sigma != nullptr: also the Courant rate of the written velocity into *sigma (atomic max of double bits)
@@ -334,10 +352,6 @@ struct Kernels {
     // r != nullptr: also the divergence records of the projected velocity (r->div_partial) for reduce_state
     static cudaError_t filter(const void* in, void* out, const uint8_t* mask, const FlowConsts<T>& k,
                               const ReduceArgsDev* r, cudaStream_t st, unsigned long long* sigma = nullptr);
-    // scalar budget of the four stage states (q_n, q2, q3, q4) at the kBitBudget cells, RK4-weighted, into
-    // out[kBudgetTerms]; partial: kBudgetBlocks * kBudgetTerms doubles; done: a zeroed ticket counter
-    static cudaError_t budget(const StageArgs<T>& a, const void* q4, const FlowConsts<T>& k, const BudgetConsts& b,
-                              double* partial, unsigned int* done, double* out, cudaStream_t st);
     static int filter_warps(const FlowConsts<T>& k);   // divergence records one filter launch writes
     // reductions of the filtered state q with the divergence records of the filter launched before it with the same
     // k; max_blocks: the partial slots of r (reduce_blocks)
@@ -376,10 +390,11 @@ cudaError_t mask_fill(uint8_t* mask, uint8_t value, size_t n, cudaStream_t st);
 cudaError_t mask_count_solid(const uint8_t* mask, size_t n, unsigned long long* d_count, cudaStream_t st);
 cudaError_t mask_mark_near_solid(uint8_t* mask, int nx, int ny, int nz, cudaStream_t st);
 cudaError_t mask_mark_budget(uint8_t* mask, int nx, int ny, int nz, cudaStream_t st);
-// Ordered list of the cells whose near-solid bit is set: per-chunk counts, then (after a host-side exclusive
-// scan into offsets) the cell indices in ascending order.
+// Ordered list of the cells whose mask has a given bit (the near-solid cells, the budget cells): per-chunk
+// counts, then (after a host-side exclusive scan into offsets) the cell indices in ascending order.
 constexpr int kListChunk = 1024;
-cudaError_t mask_near_counts(const uint8_t* mask, size_t n, int* chunk_counts, cudaStream_t st);
-cudaError_t mask_near_fill(const uint8_t* mask, size_t n, const int* chunk_offsets, int* list, cudaStream_t st);
+cudaError_t mask_list_counts(const uint8_t* mask, size_t n, uint8_t bit, int* chunk_counts, cudaStream_t st);
+cudaError_t mask_list_fill(const uint8_t* mask, size_t n, uint8_t bit, const int* chunk_offsets, int* list,
+                           cudaStream_t st);
 
 }  // namespace vf

@@ -20,7 +20,7 @@ VF_OK, VF_EINVAL, VF_ESIZE, VF_ENOMEM, VF_ECUDA, VF_ESTATE, VF_ENONFINITE, VF_ET
 VF_FP64, VF_FP32_MIXED = 0, 1
 VF_HOST, VF_DEVICE = 0, 1
 FIELDS = {"u": 0, "v": 1, "w": 2, "c": 3, "p": 4}
-N_PHASES = 18
+N_PHASES = 17
 PRECISIONS = {"fp64": VF_FP64, "fp32": VF_FP32_MIXED, "fp32_mixed": VF_FP32_MIXED}
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
