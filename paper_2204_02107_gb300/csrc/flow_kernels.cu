@@ -989,27 +989,90 @@ k_filter(const void* __restrict__ in, void* __restrict__ out, const uint8_t* __r
          ReduceArgsDev r, unsigned long long* sigma_out)
 {
     pdl_enter();
+    // x / y neighbours from a shared-memory tile of the current plane: the CTA's TX x TY cells and a 3-cell halo
+    // ring (periodic), double buffered; the ring of the next plane arrives by cp.async while the current plane is
+    // filtered, the interior is each thread's own z-window register.  The z neighbours stay in registers.
+    // Three buffers in FP32 (a buffer is refilled two planes after it was read, so one CTA barrier per plane
+    // suffices); two in FP64 (within the static shared-memory limit: a second barrier guards the refill).
+    constexpr int HW = TX + 6, HH = TY + 6, V = 4 * (int)sizeof(T) / 16;   // 16-byte pieces per 4-vector
+    constexpr int NB = sizeof(T) == 4 ? 3 : 2;
+    __shared__ __align__(16) T tile[NB][HH][HW][4];
     T smax = T(0);   // SIGMA: Courant rate of the filtered velocity (the step's final state)
     T d2 = T(0), dmax = T(0), mloss = T(0), froom = T(0);
-    const int x = blockIdx.x * TX + threadIdx.x;
-    const int y = blockIdx.y * TY + threadIdx.y;
-    if (x < k.nx && y < k.ny) {
-        const int nx = k.nx, ny = k.ny, nz = k.nz;
-        const int plane = nx * ny;
-        const int z0 = blockIdx.z * k.zc[kZcFilter], z1 = min(z0 + k.zc[kZcFilter], nz);
-        const int yc = y * nx;
-        // z window of 7 planes of the 4-vector, in registers
-        T zw[7][4];
+    const int nx = k.nx, ny = k.ny, nz = k.nz;
+    const int plane = nx * ny;
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int x = x0 + tx, y = y0 + ty;
+    const bool act = x < nx && y < ny;
+    const int wx = min(TX, nx - x0), wy = min(TY, ny - y0);   // cells of this (possibly ragged) tile
+    const int W = wx + 6, H = wy + 6;
+    const int z0 = blockIdx.z * k.zc[kZcFilter], z1 = min(z0 + k.zc[kZcFilter], nz);
+    // The halo ring: tile cell (sx, sy) holds cell (x0 + sx - 3, y0 + sy - 3), wrapped.  The ring has at most
+    // 2 (TX + TY + 6) * 3 <= 2 TX TY cells; thread tid owns ring cells tid and tid + TX TY (in ring order), whose
+    // in-plane cell index and shared-memory offset are found once.
+    constexpr int kRingMax = 2;
+    int ring_cell[kRingMax];
+    uint32_t ring_smem[kRingMax];
+    {
+        const int n_ring = W * H - wx * wy;
+        for (int o = 0; o < kRingMax; ++o) {
+            const int j = tid + o * TX * TY;
+            ring_cell[o] = -1;
+            ring_smem[o] = 0u;
+            if (j >= n_ring) continue;
+            // ring order: the 3 rows above, then 3 + 3 cells on each interior row, then the 3 rows below
+            int sx, sy;
+            if (j < 3 * W) { sy = j / W; sx = j - sy * W; }
+            else if (j < 3 * W + 6 * wy) { const int q = j - 3 * W; sy = 3 + q / 6; const int c = q - (q / 6) * 6; sx = c < 3 ? c : wx + c; }
+            else { const int q = j - 3 * W - 6 * wy; sy = wy + 3 + q / W; sx = q - (q / W) * W; }
+            ring_cell[o] = wrap(y0 + sy - 3, ny) * nx + wrap(x0 + sx - 3, nx);
+            ring_smem[o] = (uint32_t)__cvta_generic_to_shared(&tile[0][sy][sx][0]);
+        }
+    }
+    constexpr uint32_t kTileBytes = (uint32_t)sizeof(tile[0]);
+    auto ring = [&](int zz, int b) {
+        const size_t zb = (size_t)zz * plane;
 #pragma unroll
-        for (int m = 0; m < 6; ++m) ld4(in, wrap(z0 + m - 3, nz) * plane + yc + x, zw[m + 1]);
-        for (int z = z0; z < z1; ++z) {
-            const int zb = z * plane;
-            const int ic = zb + yc + x;
+        for (int o = 0; o < kRingMax; ++o) {
+            if (ring_cell[o] < 0) continue;
+            const char* src = reinterpret_cast<const char*>(in) + (zb + ring_cell[o]) * 4 * sizeof(T);
+            const uint32_t dst = ring_smem[o] + (uint32_t)b * kTileBytes;
 #pragma unroll
-            for (int m = 0; m < 6; ++m)
+            for (int v = 0; v < V; ++v)
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst + 16u * v), "l"(src + 16 * v)
+                             : "memory");
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    const int yc = (act ? y : 0) * nx, xa = act ? x : 0;
+    // z window of 7 planes of the 4-vector, in registers
+    T zw[7][4] = {};
+    if (act) {
 #pragma unroll
-                for (int f = 0; f < 4; ++f) zw[m][f] = zw[m + 1][f];
-            ld4(in, wrap(z + 3, nz) * plane + yc + x, zw[6]);
+        for (int m = 0; m < 6; ++m) ld4(in, wrap(z0 + m - 3, nz) * plane + yc + xa, zw[m + 1]);
+    }
+    if (z0 < z1) ring(z0, 0);
+    int s = 0;
+    for (int z = z0; z < z1; ++z) {
+        const int zb = z * plane;
+        const int ic = zb + yc + xa;
+#pragma unroll
+        for (int m = 0; m < 6; ++m)
+#pragma unroll
+            for (int f = 0; f < 4; ++f) zw[m][f] = zw[m + 1][f];
+        if (act) ld4(in, wrap(z + 3, nz) * plane + yc + xa, zw[6]);
+        if (NB == 2) __syncthreads();           // every read of the other buffer (plane z - 1) is done
+        const int sn = s + 1 == NB ? 0 : s + 1;
+        if (z + 1 < z1) ring(z + 1, sn);
+        else asm volatile("cp.async.commit_group;" ::: "memory");   // an empty group keeps the wait count uniform
+        if (act) {
+#pragma unroll
+            for (int f = 0; f < 4; ++f) tile[s][ty + 3][tx + 3][f] = zw[3][f];
+        }
+        asm volatile("cp.async.wait_group 1;" ::: "memory");   // this thread's ring copies of plane z
+        __syncthreads();
+        if (act) {
             // sum of the three sixth differences: sum_m S6[m] (q_x[m] + q_y[m] + q_z[m]); centre weight -20 x 3
             T acc[4];
 #pragma unroll
@@ -1022,10 +1085,13 @@ k_filter(const void* __restrict__ in, void* __restrict__ out, const uint8_t* __r
             for (int d = 3; d >= 1; --d) {
                 const T cf = coef[3 - d];
                 T a[4], b[4], c[4], e[4];
-                ld4(in, zb + yc + wrap(x - d, nx), a);
-                ld4(in, zb + yc + wrap(x + d, nx), b);
-                ld4(in, zb + wrap(y - d, ny) * nx + x, c);
-                ld4(in, zb + wrap(y + d, ny) * nx + x, e);
+#pragma unroll
+                for (int f = 0; f < 4; ++f) {
+                    a[f] = tile[s][ty + 3][tx + 3 - d][f];
+                    b[f] = tile[s][ty + 3][tx + 3 + d][f];
+                    c[f] = tile[s][ty + 3 - d][tx + 3][f];
+                    e[f] = tile[s][ty + 3 + d][tx + 3][f];
+                }
 #pragma unroll
                 for (int f = 0; f < 4; ++f) acc[f] += cf * ((a[f] + b[f]) + (c[f] + e[f]));
                 if (DIVSTAT && d == 1)
@@ -1046,13 +1112,14 @@ k_filter(const void* __restrict__ in, void* __restrict__ out, const uint8_t* __r
             }
             if (SIGMA) smax = fmax(smax, sigma_cell(o[0], o[1], o[2], k.ih));
         }
+        s = sn;
     }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
     if (SIGMA) sigma_flush((double)smax, sigma_out);
     if (DIVSTAT) {
         const Part<T> s = warp_sum(Part<T>::of(d2));
         const T m = warp_maxT(dmax);
         const Part<T> ml = warp_sum(Part<T>::of(mloss)), fr = warp_sum(Part<T>::of(froom));
-        const int tid = threadIdx.y * TX + threadIdx.x;
         if ((tid & 31) == 0) {
             const long long bid = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
             const long long w = bid * (TX * TY / 32) + (tid >> 5);
