@@ -102,7 +102,7 @@ void free_particles(vf_grid* g)
 
 void release_all(vf_grid* g)
 {
-    for (int i = 0; i < 2; ++i)
+    for (int i = 0; i < 4; ++i)
         if (g->gexec[i]) { cudaGraphExecDestroy(g->gexec[i]); g->gexec[i] = nullptr; }
     g->graph_ok = false;
     free_particles(g);
@@ -266,8 +266,35 @@ int pressure_iters(const vf_grid* g)
     return g->has_solid ? g->d.n_pressure_iters : 1;
 }
 
+// The reduction record of the grid's current state (the step that just ended): the flat reduction of the filtered
+// state with the filter's records, or the standalone reduction when the filter is off.
 template <typename T>
-cudaError_t enqueue_step_t(vf_grid* g, cudaStream_t st, bool with_reduce, const vf::LaunchHook* hook)
+cudaError_t enqueue_reduction_t(vf_grid* g, cudaStream_t st)
+{
+    const FlowConsts<T> k = flow_consts<T>(g);
+    vf::ReduceArgsDev ra = reduce_args(g);
+    ra.budget = g->budget_out;
+    if (g->d.filter) {
+        ra.filter_budget = 1;
+        return Kernels<T>::reduce_state(g->q, g->mask, k, ra, 1, g->nred, st);
+    }
+    return Kernels<T>::reduce(g->q, g->mask, k, ra, 1, st);
+}
+
+cudaError_t enqueue_reduction(vf_grid* g, cudaStream_t st)
+{
+    return g->fp64 ? enqueue_reduction_t<double>(g, st) : enqueue_reduction_t<float>(g, st);
+}
+
+// Step launches.  with_reduce: this step writes a reduction record (budget CTAs in stages 3 and 4, the filter's
+// records); lag: its reduction kernel is not launched here but by the next step (reduce_prev) or a flush.
+// reduce_prev: the previous step's record is reduced on the side stream while stages 1 and 2 run (they write
+// only the stage states qa and qb; the reduction reads q, the filter's records and the budget terms, which nothing
+// before stage 3 writes), joined before stage 3.  Not with a dynamic time step, whose adjust kernel rewrites the
+// time the record reads.
+template <typename T>
+cudaError_t enqueue_step_t(vf_grid* g, cudaStream_t st, bool with_reduce, const vf::LaunchHook* hook, bool lag = false,
+                           bool reduce_prev = false)
 {
     auto mark = [&](int phase) { if (hook) (*hook)(phase); };
     const FlowConsts<T> k = flow_consts<T>(g);
@@ -277,6 +304,14 @@ cudaError_t enqueue_step_t(vf_grid* g, cudaStream_t st, bool with_reduce, const 
     if (g->dynamic) {
         if ((e = vf::adjust_dt(g->dtctl, st)) != cudaSuccess) return e;
         mark(VF_PHASE_ADJUST_DT);
+    }
+    if (reduce_prev) {
+        if (g->dynamic) return cudaErrorInvalidValue;
+        if ((e = cudaEventRecord(g->ev_fork, st)) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(g->side_stream, g->ev_fork, 0)) != cudaSuccess ||
+            (e = enqueue_reduction_t<T>(g, g->side_stream)) != cudaSuccess ||
+            (e = cudaEventRecord(g->ev_join, g->side_stream)) != cudaSuccess)
+            return e;
     }
     StageArgs<T> a{};
     a.mask = g->mask;
@@ -292,6 +327,7 @@ cudaError_t enqueue_step_t(vf_grid* g, cudaStream_t st, bool with_reduce, const 
     if ((e = Kernels<T>::stage(2, a, k, st)) != cudaSuccess) return e;
     mark(VF_PHASE_STAGE2);
     a.qs = g->qb; a.out = g->acc;
+    if (reduce_prev && (e = cudaStreamWaitEvent(st, g->ev_join, 0)) != cudaSuccess) return e;
     if (with_reduce) {
         // scalar budget: extra CTAs of stage 3 read q_n and q2, those of stage 4 q3 and q4 (none is written by
         // the launch that reads it)
@@ -337,14 +373,9 @@ cudaError_t enqueue_step_t(vf_grid* g, cudaStream_t st, bool with_reduce, const 
             cudaSuccess)
             return e;
         mark(VF_PHASE_FILTER);
-        if (with_reduce) {
-            if ((e = Kernels<T>::reduce_state(g->q, g->mask, k, ra, 1, g->nred, st)) != cudaSuccess) return e;
-            mark(VF_PHASE_REDUCE);
-        }
-    } else if (with_reduce) {
-        vf::ReduceArgsDev ra = reduce_args(g);
-        ra.budget = g->budget_out;
-        if ((e = Kernels<T>::reduce(g->q, g->mask, k, ra, 1, st)) != cudaSuccess) return e;
+    }
+    if (with_reduce && !lag) {
+        if ((e = enqueue_reduction_t<T>(g, st)) != cudaSuccess) return e;
         mark(VF_PHASE_REDUCE);
     }
     if (g->particles.n > 0) {
@@ -356,10 +387,11 @@ cudaError_t enqueue_step_t(vf_grid* g, cudaStream_t st, bool with_reduce, const 
     return cudaSuccess;
 }
 
-cudaError_t enqueue_step(vf_grid* g, cudaStream_t st, bool with_reduce, const vf::LaunchHook* hook = nullptr)
+cudaError_t enqueue_step(vf_grid* g, cudaStream_t st, bool with_reduce, const vf::LaunchHook* hook = nullptr,
+                         bool lag = false, bool reduce_prev = false)
 {
-    return g->fp64 ? enqueue_step_t<double>(g, st, with_reduce, hook)
-                   : enqueue_step_t<float>(g, st, with_reduce, hook);
+    return g->fp64 ? enqueue_step_t<double>(g, st, with_reduce, hook, lag, reduce_prev)
+                   : enqueue_step_t<float>(g, st, with_reduce, hook, lag, reduce_prev);
 }
 
 // Event recorder behind vf_profile_steps: one event after every launch, tagged with its phase.
@@ -382,18 +414,23 @@ struct PhaseRecorder {
 
 void drop_graphs(vf_grid* g)
 {
-    for (int i = 0; i < 2; ++i)
+    for (int i = 0; i < 4; ++i)
         if (g->gexec[i]) { cudaGraphExecDestroy(g->gexec[i]); g->gexec[i] = nullptr; }
     g->graph_ok = false;
 }
 
+// Step graphs: variant bit 0 = the step writes a record, bit 1 = the previous step's record is reduced alongside
+// stages 1-2 (the record of a recorded step is then left to the next step or a flush: lagged).  Variants 2 and 3
+// exist only for a fixed time step.
 int capture_graphs(vf_grid* g)
 {
     drop_graphs(g);
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < 4; ++i) {
+        if (i >= 2 && g->dynamic) continue;
         cudaGraph_t graph = nullptr;
         VF_CK(cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeRelaxed));
-        cudaError_t e = enqueue_step(g, g->cap_stream, i == 1);
+        const bool lagged = !g->dynamic;
+        cudaError_t e = enqueue_step(g, g->cap_stream, (i & 1) != 0, nullptr, lagged && (i & 1), (i & 2) != 0);
         cudaError_t e2 = cudaStreamEndCapture(g->cap_stream, &graph);
         if (e != cudaSuccess) { if (graph) cudaGraphDestroy(graph); return fail_cuda(g, e, "capture step"); }
         if (e2 != cudaSuccess) return fail_cuda(g, e2, "cudaStreamEndCapture");
@@ -624,6 +661,9 @@ int vf_create_grid(const vf_grid_desc* d, vf_grid** out)
         release_all(g);
         if (g->own_stream && g->stream) cudaStreamDestroy(g->stream);
         if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
+        if (g->side_stream) cudaStreamDestroy(g->side_stream);
+        if (g->ev_fork) cudaEventDestroy(g->ev_fork);
+        if (g->ev_join) cudaEventDestroy(g->ev_join);
         delete g;
         return code;
     };
@@ -634,6 +674,10 @@ int vf_create_grid(const vf_grid_desc* d, vf_grid** out)
         g->own_stream = true;
     }
     if (cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking) != cudaSuccess) return fail(VF_ECUDA);
+    if (cudaStreamCreateWithFlags(&g->side_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&g->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&g->ev_join, cudaEventDisableTiming) != cudaSuccess)
+        return fail(VF_ECUDA);
 
     const int M = d->nx / 2;
     {
@@ -742,6 +786,9 @@ int vf_destroy(vf_grid* g)
     if (g->stream) cudaStreamSynchronize(g->stream);
     release_all(g);
     if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
+    if (g->side_stream) cudaStreamDestroy(g->side_stream);
+    if (g->ev_fork) cudaEventDestroy(g->ev_fork);
+    if (g->ev_join) cudaEventDestroy(g->ev_join);
     if (g->own_stream && g->stream) cudaStreamDestroy(g->stream);
     delete g;
     return VF_OK;
@@ -977,13 +1024,19 @@ int vf_step(vf_grid* g, int64_t n, int32_t reduce_every)
         if (rc) return rc;
     }
     if (n > 0) VF_CK(vf_engine::refresh_sigma(g, g->stream));
+    // with graphs and a fixed time step a recorded step's reduction runs alongside the next step's stages 1-2;
+    // the last pending one is launched before returning, so the records are the same as with no lag
+    const bool lag = g->use_graph && !g->dynamic;
+    bool pending = false;
     for (int64_t i = 0; i < n; ++i) {
         const int64_t s = g->step + 1;
         const bool red = reduce_every > 0 && (s % reduce_every) == 0;
-        if (g->use_graph) VF_CK(cudaGraphLaunch(g->gexec[red ? 1 : 0], g->stream));
+        if (g->use_graph) VF_CK(cudaGraphLaunch(g->gexec[(red ? 1 : 0) | (lag && pending ? 2 : 0)], g->stream));
         else VF_CK(enqueue_step(g, g->stream, red));
+        pending = lag && red;
         g->step = s;
     }
+    if (pending) VF_CK(enqueue_reduction(g, g->stream));
     return VF_OK;
 }
 

@@ -83,7 +83,9 @@ struct vf_grid {
     vf::FftAxis ax{}, ay{}, az{};
     int rows_per_block = 1, cols_per_block = 16;
 
-    cudaGraphExec_t gexec[2]{nullptr, nullptr};
+    cudaGraphExec_t gexec[4]{nullptr, nullptr, nullptr, nullptr};   // step graphs (see capture_graphs)
+    cudaStream_t side_stream = nullptr;  // the previous step's reduction alongside stages 1-2
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     bool graph_ok = false;
     bool use_graph = true;
 
