@@ -150,6 +150,11 @@ __device__ __forceinline__ void dft(C* v)
     else dft16<C, INV>(v);
 }
 
+// 1 / (lambda N) factor of the eigenvalue division, -invN / sum: in FP32 the fast division (two multiplies by an
+// approximate reciprocal, within 2 ulp), in FP64 the correctly rounded one
+__device__ __forceinline__ float inv_lambda(float invN, float sum) { return __fdividef(-invN, sum); }
+__device__ __forceinline__ double inv_lambda(double invN, double sum) { return -invN / sum; }
+
 template <typename C>
 __device__ __forceinline__ void stage_table(C* dst, const void* src, int n)
 {

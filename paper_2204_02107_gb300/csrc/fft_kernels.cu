@@ -226,7 +226,7 @@ __global__ void __launch_bounds__(256) k_fft_z_solve(PoissonArgs<T> A)
         T s = T(0);
         if (kx < M) {
             const bool null = (kx == 0) && ky_null && ((kz == 0) || (2 * kz == n));
-            if (!null) s = A.invN / -(__ldg(A.lamx + kx) + ly + __ldg(A.lamz + kz));
+            if (!null) s = inv_lambda(A.invN, __ldg(A.lamx + kx) + ly + __ldg(A.lamz + kz));
         }
         mid[kz * TB + b] = cscale(v, s);
     };
@@ -417,7 +417,7 @@ __global__ void __launch_bounds__(kPlaneThreads) k_fft_yz_solve(PoissonArgs<T> A
         const int pz = (int)fdiv((uint32_t)i, A.ny_div), py = i - pz * ny;
         const int ky = ky_of[py], kz = kz_of[pz];
         const bool null = (kx == 0) && (ky == 0 || 2 * ky == ny) && (kz == 0 || 2 * kz == nz);
-        const T s = null ? T(0) : A.invN / -(lx + __ldg(A.lamy + ky) + __ldg(A.lamz + kz));
+        const T s = null ? T(0) : inv_lambda(A.invN, lx + __ldg(A.lamy + ky) + __ldg(A.lamz + kz));
         const int q = pz * SP + padded(py);
         plane[q] = cscale(plane[q], s);
     }

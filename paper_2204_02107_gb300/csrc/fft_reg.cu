@@ -110,8 +110,10 @@ __device__ __forceinline__ void reg_inv(C v[16], int t, const C* tw, BUF buf)
 // x passes: 128-thread CTAs in both precisions (FP32: 1024 CTAs over 8 per SM balance the SMs better than 512 over
 // 4, measured 12.5 / 12.4 vs 12.8 / 13.3 us per pass on the 256 x 128 x 128 room)
 template <typename T> __host__ __device__ constexpr int x_threads() { return 128; }
+// (y, z) plane kernel: 512 threads in FP32 (up to 128 registers a thread; with 1024 threads the 64-register cap
+// spills the transforms: 15.7 against 18.2 us per launch on the 256 x 128 x 128 room)
 #ifndef VF_REG_YZ_THREADS
-#define VF_REG_YZ_THREADS 1024
+#define VF_REG_YZ_THREADS 512
 #endif
 template <typename T> __host__ __device__ constexpr int yz_threads() { return sizeof(T) == 4 ? VF_REG_YZ_THREADS : 512; }
 
@@ -363,7 +365,7 @@ __global__ void __launch_bounds__(yz_threads<T>()) k_reg_yz_solve(PoissonArgs<T>
                 for (int k2 = 0; k2 < GZ; ++k2) {
                     const int kz = RegShape<GZ>::freq(t, q, k2);
                     const bool null = ky_null && (kz == 0 || 2 * kz == NZ);
-                    const T s = null ? T(0) : A.invN / -(lxy + __ldg(A.lamz + kz));
+                    const T s = null ? T(0) : inv_lambda(A.invN, lxy + __ldg(A.lamz + kz));
                     v[q * GZ + k2] = cscale(v[q * GZ + k2], s);
                 }
             reg_inv<C, GZ>(v, t, twz, buf);
@@ -514,7 +516,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? VF_ZTILE_MIN_CTAS : 2) k
         for (int k2 = 0; k2 < GZ; ++k2) {
             const int kz = RegShape<GZ>::freq(t, q, k2);
             const bool null = ky_null && (kz == 0 || 2 * kz == NZ);
-            const T s = null ? T(0) : A.invN / -(lxy + __ldg(A.lamz + kz));
+            const T s = null ? T(0) : inv_lambda(A.invN, lxy + __ldg(A.lamz + kz));
             v[q * GZ + k2] = cscale(v[q * GZ + k2], s);
         }
     reg_inv<C, GZ>(v, t, twz, buf);
