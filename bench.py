@@ -187,20 +187,22 @@ def traffic_record(kernel, tiles):
         return None
     with open(path) as f:
         rec = json.load(f)
-    entry = rec.get("kernels", {}).get(kernel)
-    if not entry:
+    entries = rec.get("kernels", {}).get(kernel)
+    if not entries:
         return None
-    digest = source_digest(entry["source"], entry.get("source_end_marker"))
-    if digest is None or digest != entry.get("source_sha256"):
-        return None
-    for hdr, hdr_digest in (entry.get("headers") or {}).items():
-        if source_digest(hdr) != hdr_digest:
+    if isinstance(entries, dict):
+        entries = [entries]
+    for entry in entries:   # one capture per launch tiling
+        if any(tiles.get(key) != value for key, value in (entry.get("tiles") or {}).items()):
+            continue
+        digest = source_digest(entry["source"], entry.get("source_end_marker"))
+        if digest is None or digest != entry.get("source_sha256"):
             return None
-    for key, value in (entry.get("tiles") or {}).items():
-        if tiles.get(key) != value:
-            return None
-    scale = entry.get("scale_to_full", 1.0)
-    return entry["dram_bytes_per_launch"] * scale
+        for hdr, hdr_digest in (entry.get("headers") or {}).items():
+            if source_digest(hdr) != hdr_digest:
+                return None
+        return entry["dram_bytes_per_launch"] * entry.get("scale_to_full", 1.0)
+    return None
 
 
 def fp64_flop_record():
