@@ -89,10 +89,13 @@ def strouhal_and_drag(cc, warm, meas, every=5, fevery=50):
 
 
 def test_strouhal_and_drag_against_table2(torch):
-    """30 cells per obstacle side, Re_ob = 84: about 22 shedding periods of development, 11 measured."""
+    """30 cells per obstacle side, Re_ob = 84: about 22 shedding periods of development, 11 measured.  The drag
+    coefficient agrees with Tab. 2 to 3 % (and converges towards it with resolution); the Strouhal number is 7.5 %
+    above the paper's at every resolution from 30 to 60 cells per side and under every change of the forcing strip,
+    channel length, nz, filter and pressure iterations tried, so its band holds that systematic offset."""
     cc = rooms.cube_channel(30)
     st, cd, periods = strouhal_and_drag(cc, 24000, 12000)
     tab = GOLDEN["cube_in_channel"]
     assert periods >= 8
-    assert abs(st - tab["strouhal_30"]) / tab["strouhal_30"] < 0.10, st
-    assert abs(cd - tab["drag_30"]) / tab["drag_30"] < 0.10, cd
+    assert abs(st - tab["strouhal_30"]) / tab["strouhal_30"] < 0.085, st
+    assert abs(cd - tab["drag_30"]) / tab["drag_30"] < 0.04, cd
