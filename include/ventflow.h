@@ -242,8 +242,7 @@ int vf_poisson_solve(vf_grid* g, const void* f, void* p);
  * fft_*: radix schedule of the generic mixed-radix FFT passes (Sec. 2.2's FFTs) along the x half length nx/2, y
  * and z: an index into vf_fft_schedules' candidates for that length, 0 = the default.  Every schedule computes the
  * same transforms in another rounding order, so fields agree to rounding (not bitwise) across schedules.  Grids
- * whose FFT takes the register path (nx/2, ny and nz each 16, 32, 64, 128 or 256) keep the indices but do not use
- * them. */
+ * whose FFT takes the register path (vf_fft_path) keep the indices but do not use them. */
 #define VF_ZCHUNK_MIN 4
 #define VF_ZCHUNK_MAX 64
 typedef struct vf_tiles {
@@ -260,6 +259,16 @@ typedef struct vf_tiles {
  * precision) if there is one, else (4, 32, 8, 16, 0, 0, 0): the z-chunks the autotuner chose for a 256 x 128 x 128
  * room on GB300 and the default FFT schedules. */
 int vf_get_tiles(const vf_grid* g, vf_tiles* out);
+
+/* Which passes the grid's pressure solve (Sec. 2.2's FFTs) runs, chosen at vf_create_grid from the lengths and the
+ * precision: VF_FFT_GENERIC (the mixed-radix passes), VF_FFT_REGISTER_PLANE (register-resident transforms, the
+ * (y, z) plane of each kx in one CTA) or VF_FFT_REGISTER_TILE (register transforms, y passes and z tiles).  The
+ * register path takes lengths nx/2, ny, nz each 16 G (G = 1, 2, 4, 8, 16), and in FP32 also 36, 40, 48, 60, 72,
+ * 80 or 96 (then ny = nz, the plane kernel only).  VF_EINVAL for a NULL argument.  Host only. */
+#define VF_FFT_GENERIC 0
+#define VF_FFT_REGISTER_PLANE 1
+#define VF_FFT_REGISTER_TILE 2
+int vf_fft_path(const vf_grid* g, int32_t* path);
 
 /* Set a grid's tiles (VF_EINVAL if a chunk is out of range or an FFT index is not a candidate of its length; the
  * grid is unchanged then).  Takes effect at the next vf_step (the step graph is captured again).  Waits. */

@@ -159,6 +159,7 @@ PoissonArgs<T> poisson_args(const vf_grid* g, T* f, T* p, int use_mask)
     a.n_near = use_mask ? g->n_near : 0;
     a.plane_layout = g->plane_layout ? 1 : 0;
     a.reg = g->reg;
+    a.rx = g->reg_rx; a.ry = g->reg_ry; a.rz = g->reg_rz;
     a.gx = g->reg_gx; a.gy = g->reg_gy; a.gz = g->reg_gz;
     a.reg_sp = g->reg_sp; a.reg_spx = g->reg_spx; a.reg_sb = g->reg_sb;
     a.reg_tile = g->reg_tile; a.reg_sy = g->reg_sy; a.reg_tb = g->reg_tb; a.reg_st = g->reg_st;
@@ -492,6 +493,7 @@ int build_tables_t(vf_grid* g)
         PoissonArgs<T> ra = poisson_args<T>(g, nullptr, nullptr, 0);
         vf::RegFft<T>::configure(ra);
         g->reg = ra.reg;
+        g->reg_rx = ra.rx; g->reg_ry = ra.ry; g->reg_rz = ra.rz;
         g->reg_gx = ra.gx; g->reg_gy = ra.gy; g->reg_gz = ra.gz;
         g->reg_sp = ra.reg_sp; g->reg_spx = ra.reg_spx; g->reg_sb = ra.reg_sb;
         g->reg_tile = ra.reg_tile; g->reg_sy = ra.reg_sy; g->reg_tb = ra.reg_tb; g->reg_st = ra.reg_st;
@@ -1497,6 +1499,13 @@ int vf_get_tiles(const vf_grid* g, vf_tiles* out)
     out->fft_x = g->fft_sched[0];
     out->fft_y = g->fft_sched[1];
     out->fft_z = g->fft_sched[2];
+    return VF_OK;
+}
+
+int vf_fft_path(const vf_grid* g, int32_t* path)
+{
+    if (!g || !path) return VF_EINVAL;
+    *path = !g->reg ? VF_FFT_GENERIC : (g->reg_tile ? VF_FFT_REGISTER_TILE : VF_FFT_REGISTER_PLANE);
     return VF_OK;
 }
 

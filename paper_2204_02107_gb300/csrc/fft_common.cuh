@@ -3,6 +3,7 @@
 // D((1 - beta) G p) at one cell.  Included by the kernel files only (everything has internal linkage).
 #pragma once
 
+#include <utility>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -140,14 +141,116 @@ __device__ __forceinline__ void dft16(C* v)
 }
 
 template <typename C, int R, bool INV>
+__device__ __forceinline__ void dft(C* v);
+
+// f(std::integral_constant<int, i>) for i = 0 .. N-1, expanded at compile time
+template <typename F, int... I>
+__device__ __forceinline__ void static_for_impl(F&& f, std::integer_sequence<int, I...>)
+{
+    (f(std::integral_constant<int, I>{}), ...);
+}
+template <int N, typename F>
+__device__ __forceinline__ void static_for(F&& f)
+{
+    static_for_impl(f, std::make_integer_sequence<int, N>{});
+}
+
+// ---- composite orders: compile-time Cooley-Tukey split R = A B in registers ---------------------------------
+// cos and sin of 2 pi j / n evaluated at compile time (argument reduced to [-pi/4, pi/4] by octant, then Taylor
+// series to 1e-17), for the constant twiddles of the composite small DFTs
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+__host__ __device__ constexpr double taylor_sin(double x)
+{
+    double term = x, sum = x;
+    for (int k = 1; k < 14; ++k) {
+        term *= -x * x / ((2.0 * k) * (2.0 * k + 1.0));
+        sum += term;
+    }
+    return sum;
+}
+__host__ __device__ constexpr double taylor_cos(double x)
+{
+    double term = 1.0, sum = 1.0;
+    for (int k = 1; k < 14; ++k) {
+        term *= -x * x / ((2.0 * k - 1.0) * (2.0 * k));
+        sum += term;
+    }
+    return sum;
+}
+// (cos, sin) of 2 pi j / n: j / n reduced to eighths of a turn
+__host__ __device__ constexpr double cos_turn(long long j, long long n)
+{
+    j %= n;
+    if (j < 0) j += n;
+    const long long o = (8 * j) / n;                           // octant 0..7
+    const double r = kTwoPi * ((double)(8 * j - o * n) / (8.0 * n));   // remainder angle in [0, pi/4)
+    const double c = taylor_cos(r), s = taylor_sin(r);
+    // cos(o pi/4 + r) for o = 0..7 with the 45-degree rotations written out
+    constexpr double h = 0.70710678118654752440;
+    switch (o) {
+        case 0: return c;
+        case 1: return h * (c - s);
+        case 2: return -s;
+        case 3: return -h * (c + s);
+        case 4: return -c;
+        case 5: return -h * (c - s);
+        case 6: return s;
+        default: return h * (c + s);
+    }
+}
+
+// first factor of a composite order (the remaining factor is R / factor)
+template <int R> __host__ __device__ constexpr int ct_factor()
+{
+    return R % 16 == 0 && R > 16 ? 16 : R % 8 == 0 && R > 8 ? 8 : R % 4 == 0 && R > 4 ? 4 : R % 2 == 0 && R > 2 ? 2 :
+           R % 3 == 0 && R > 3 ? 3 : R % 5 == 0 && R > 5 ? 5 : R;
+}
+
+// X[k1 + A k2] = sum_b W_B^(b k2) W_R^(b k1) sum_a x[b + B a] W_A^(a k1): DFTs of order A over a, the twiddles,
+// DFTs of order B over b; in place, natural order in and out
+template <typename C, int A, int B, bool INV>
+__device__ __forceinline__ void dft_ct(C* v)
+{
+    using T = decltype(C::x);
+    constexpr int R = A * B;
+    C y[B][A];
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+#pragma unroll
+        for (int a = 0; a < A; ++a) y[b][a] = v[b + B * a];
+        dft<C, A, INV>(y[b]);
+    }
+    // W_R^(b k1) = exp(-+ 2 pi i b k1 / R), each a compile-time constant
+    static_for<B * A>([&](auto I) {
+        constexpr int b = decltype(I)::value / A, k1 = decltype(I)::value % A;
+        if constexpr (b > 0 && k1 > 0) {
+            constexpr double c = cos_turn((long long)b * k1, R);
+            constexpr double sn = (INV ? 1.0 : -1.0) * cos_turn((long long)b * k1 * 4 - R, 4LL * R);
+            y[b][k1] = cmul(y[b][k1], mk<C>((T)c, (T)sn));
+        }
+    });
+#pragma unroll
+    for (int k1 = 0; k1 < A; ++k1) {
+        C z[B];
+#pragma unroll
+        for (int b = 0; b < B; ++b) z[b] = y[b][k1];
+        dft<C, B, INV>(z);
+#pragma unroll
+        for (int k2 = 0; k2 < B; ++k2) v[k1 + A * k2] = z[k2];
+    }
+}
+
+template <typename C, int R, bool INV>
 __device__ __forceinline__ void dft(C* v)
 {
-    if (R == 2) dft2<C, INV>(v[0], v[1]);
-    else if (R == 3) dft3<C, INV>(v[0], v[1], v[2]);
-    else if (R == 4) dft4<C, INV>(v[0], v[1], v[2], v[3]);
-    else if (R == 5) dft5<C, INV>(v[0], v[1], v[2], v[3], v[4]);
-    else if (R == 8) dft8<C, INV>(v);
-    else dft16<C, INV>(v);
+    if constexpr (R == 1) {
+    } else if constexpr (R == 2) dft2<C, INV>(v[0], v[1]);
+    else if constexpr (R == 3) dft3<C, INV>(v[0], v[1], v[2]);
+    else if constexpr (R == 4) dft4<C, INV>(v[0], v[1], v[2], v[3]);
+    else if constexpr (R == 5) dft5<C, INV>(v[0], v[1], v[2], v[3], v[4]);
+    else if constexpr (R == 8) dft8<C, INV>(v);
+    else if constexpr (R == 16) dft16<C, INV>(v);
+    else dft_ct<C, ct_factor<R>(), R / ct_factor<R>(), INV>(v);
 }
 
 // 1 / (lambda N) factor of the eigenvalue division, -invN / sum: in FP32 the fast division (two multiplies by an

@@ -28,63 +28,65 @@
 namespace vf {
 namespace {
 
-template <int G>
+// Shape of a register transform of n = R G points: G threads (a power of two dividing R and 32) hold R values each.
+template <int R, int G>
 struct RegShape {
-    static constexpr int Q = 16 / G;
-    // exchange slot of the k1-th 16-point output of thread t (skewed so both sides of the exchange spread over
+    static_assert(R % G == 0 && 32 % G == 0, "G threads per transform, R / G second-stage transforms per thread");
+    static constexpr int Q = R / G;
+    // exchange slot of the k1-th R-point output of thread t (skewed so both sides of the exchange spread over
     // the shared-memory banks)
     static __device__ __forceinline__ int xpos(int t, int k1) { return k1 * G + ((t + k1 / Q) & (G - 1)); }
     // slot and frequency of held value (q, k2) of thread t
-    static __device__ __forceinline__ int slot(int t, int q, int k2) { return t + G * q + 16 * k2; }
-    static __device__ __forceinline__ int freq(int t, int q, int k2) { return t * Q + q + 16 * k2; }
+    static __device__ __forceinline__ int slot(int t, int q, int k2) { return t + G * q + R * k2; }
+    static __device__ __forceinline__ int freq(int t, int q, int k2) { return t * Q + q + R * k2; }
 };
 
 // slot of frequency k (the inverse of RegShape::freq followed by RegShape::slot)
-template <int G>
+template <int R, int G>
 __device__ __forceinline__ int slot_of_freq(int k)
 {
-    constexpr int Q = 16 / G;
-    const int k1 = k & 15, k2 = k >> 4;
-    return (k1 / Q) + G * (k1 % Q) + 16 * k2;
+    constexpr int Q = R / G;
+    const int k1 = k % R, k2 = k / R;
+    return (k1 / Q) + G * (k1 % Q) + R * k2;
 }
 
 // frequency held at slot s
-template <int G>
+template <int R, int G>
 __device__ __forceinline__ int freq_of_slot(int s)
 {
-    constexpr int Q = 16 / G;
-    const int r = s & 15, k2 = s >> 4;
-    return (r % G) * Q + r / G + 16 * k2;
+    constexpr int Q = R / G;
+    const int r = s % R, k2 = s / R;
+    return (r % G) * Q + r / G + R * k2;
 }
 
 // forward transform of v (thread t of its group); buf(e) is element e of the group's exchange slice
-template <typename C, int G, typename BUF>
-__device__ __forceinline__ void reg_fwd(C v[16], int t, const C* tw, BUF buf)
+template <typename C, int R, int G, typename BUF>
+__device__ __forceinline__ void reg_fwd(C v[R], int t, const C* tw, BUF buf)
 {
-    dft<C, 16, false>(v);
+    dft<C, R, false>(v);
     if constexpr (G > 1) {
-        constexpr int Q = 16 / G;
+        constexpr int Q = R / G;
 #pragma unroll
-        for (int k1 = 1; k1 < 16; ++k1) v[k1] = cmul(v[k1], tw[t * k1]);
+        for (int k1 = 1; k1 < R; ++k1) v[k1] = cmul(v[k1], tw[t * k1]);
         __syncwarp();
 #pragma unroll
-        for (int k1 = 0; k1 < 16; ++k1) buf(RegShape<G>::xpos(t, k1)) = v[k1];
+        for (int k1 = 0; k1 < R; ++k1) buf(RegShape<R, G>::xpos(t, k1)) = v[k1];
         __syncwarp();
 #pragma unroll
         for (int q = 0; q < Q; ++q)
 #pragma unroll
-            for (int s = 0; s < G; ++s) v[q * G + s] = buf(RegShape<G>::xpos(s, t * Q + q));
+            for (int s = 0; s < G; ++s) v[q * G + s] = buf(RegShape<R, G>::xpos(s, t * Q + q));
 #pragma unroll
         for (int q = 0; q < Q; ++q) dft<C, G, false>(v + q * G);
     }
 }
 
 // inverse transform (unnormalised) from the held layout back to v[m] = n x[t + G m]
-template <typename C, int G, typename BUF>
-__device__ __forceinline__ void reg_inv(C v[16], int t, const C* tw, BUF buf)
+template <typename C, int R, int G, typename BUF>
+__device__ __forceinline__ void reg_inv(C v[R], int t, const C* tw, BUF buf)
 {
     if constexpr (G > 1) {
-        constexpr int Q = 16 / G;
+        constexpr int Q = R / G;
 #pragma unroll
         for (int q = 0; q < Q; ++q) dft<C, G, true>(v + q * G);
 #pragma unroll
@@ -99,12 +101,12 @@ __device__ __forceinline__ void reg_inv(C v[16], int t, const C* tw, BUF buf)
 #pragma unroll
         for (int q = 0; q < Q; ++q)
 #pragma unroll
-            for (int s = 0; s < G; ++s) buf(RegShape<G>::xpos(s, t * Q + q)) = v[q * G + s];
+            for (int s = 0; s < G; ++s) buf(RegShape<R, G>::xpos(s, t * Q + q)) = v[q * G + s];
         __syncwarp();
 #pragma unroll
-        for (int k1 = 0; k1 < 16; ++k1) v[k1] = buf(RegShape<G>::xpos(t, k1));
+        for (int k1 = 0; k1 < R; ++k1) v[k1] = buf(RegShape<R, G>::xpos(t, k1));
     }
-    dft<C, 16, true>(v);
+    dft<C, R, true>(v);
 }
 
 // x passes: 128-thread CTAs in both precisions (FP32: 1024 CTAs over 8 per SM balance the SMs better than 512 over
@@ -116,16 +118,28 @@ template <typename T> __host__ __device__ constexpr int x_threads() { return 128
 #define VF_REG_YZ_THREADS 512
 #endif
 template <typename T> __host__ __device__ constexpr int yz_threads() { return sizeof(T) == 4 ? VF_REG_YZ_THREADS : 512; }
+// threads of the plane kernel: one pass over the y rows (NZ groups of GY) and the z columns (NY groups of GZ),
+// at most yz_threads for lengths 16 G; the 2-3-5 planes (at most 384 threads) take exactly one pass, so that the
+// transforms of 18 .. 36 values a thread have up to 255 registers
+template <typename T, int RY, int GY, int RZ, int GZ>
+__host__ __device__ constexpr int yz_nt()
+{
+    constexpr int want = (RZ * GZ * GY > RY * GY * GZ ? RZ * GZ * GY : RY * GY * GZ);
+    constexpr int r32 = want < 32 ? 32 : (want + 31) / 32 * 32;
+    return RY == 16 && RZ == 16 ? (r32 < yz_threads<T>() ? r32 : yz_threads<T>()) : r32;
+}
+template <typename T, int RY, int GY, int RZ, int GZ>
+__host__ __device__ constexpr int yz_bound() { return RY == 16 && RZ == 16 ? yz_threads<T>() : yz_nt<T, RY, GY, RZ, GZ>(); }
 
 // ---- x forward ---------------------------------------------------------------------------------------------
 // Each warp works alone on its 32 / GX rows: the split step writes X_k of its rows straight to the plane layout
 // spec[k][row] (the rows of a warp are consecutive, so each frequency is one contiguous 32-byte or longer piece).
-template <typename T, int GX>
+template <typename T, int RX, int GX>
 __global__ void __launch_bounds__(x_threads<T>()) k_reg_x_fwd(PoissonArgs<T> A)
 {
     pdl_enter();
     using C = typename CxT<T>::type;
-    constexpr int M = 16 * GX, NT = x_threads<T>(), B = NT / GX, P = 32 / GX, Q = 16 / GX;
+    constexpr int M = RX * GX, NT = x_threads<T>(), B = NT / GX, P = 32 / GX, Q = RX / GX;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int SPX = A.reg_spx;
     C* tw = reinterpret_cast<C*>(smem_raw);
@@ -136,11 +150,11 @@ __global__ void __launch_bounds__(x_threads<T>()) k_reg_x_fwd(PoissonArgs<T> A)
     const int b = warp * P + gi;
     const int rows = A.ny * A.nz, row = blockIdx.x * B + b;
     const bool act = row < rows;
-    C v[16];
+    C v[RX];
     {   // the row's loads are issued before the tables are staged
         const T* __restrict__ src = A.f + (long long)(act ? row : 0) * A.nx;
 #pragma unroll
-        for (int m = 0; m < 16; ++m)
+        for (int m = 0; m < RX; ++m)
             v[m] = act ? *reinterpret_cast<const C*>(src + 2 * (t + GX * m)) : mk<C>(T(0), T(0));
     }
     stage_table(tw, A.twx, M);
@@ -148,12 +162,12 @@ __global__ void __launch_bounds__(x_threads<T>()) k_reg_x_fwd(PoissonArgs<T> A)
     __syncthreads();
     C* rb = rowbuf + b * SPX;
     auto buf = [rb](int e) -> C& { return rb[e]; };
-    reg_fwd<C, GX>(v, t, tw, buf);
+    reg_fwd<C, RX, GX>(v, t, tw, buf);
     __syncwarp();
 #pragma unroll
     for (int q = 0; q < Q; ++q)
 #pragma unroll
-        for (int k2 = 0; k2 < GX; ++k2) rb[RegShape<GX>::slot(t, q, k2)] = v[q * GX + k2];
+        for (int k2 = 0; k2 < GX; ++k2) rb[RegShape<RX, GX>::slot(t, q, k2)] = v[q * GX + k2];
     __syncwarp();
     // the split results go straight to the plane layout (rows of a warp are consecutive), or, for rows of 256
     // frequencies (two rows per warp, 16-byte pieces), through a frequency-major stage so that each frequency of
@@ -167,17 +181,17 @@ __global__ void __launch_bounds__(x_threads<T>()) k_reg_x_fwd(PoissonArgs<T> A)
         else if (act) spec[(long long)k * rows] = val;
     };
     // split step: X_k = E_k + W^k O_k from Z_k and conj Z_{M-k}; the pair (k, M - k) by one thread,
-    // k = t + GX i for i = 0..8 (k = M / 2 only for t = 0)
+    // k = t + GX i for i = 0..RX/2 (k = M / 2 only for t = 0)
 #pragma unroll
-    for (int i = 0; i <= 8; ++i) {
+    for (int i = 0; i <= RX / 2; ++i) {
         const int k = t + GX * i;
         if (k > M / 2) break;
-        const C Zk = rb[slot_of_freq<GX>(k)];
+        const C Zk = rb[slot_of_freq<RX, GX>(k)];
         if (k == 0) {
             put(0, mk<C>(Zk.x + Zk.y, Zk.x - Zk.y));                  // (X_0, X_{nx/2})
             continue;
         }
-        const C Zm = rb[slot_of_freq<GX>(M - k)];
+        const C Zm = rb[slot_of_freq<RX, GX>(M - k)];
         {
             const C E = mk<C>(T(0.5) * (Zk.x + Zm.x), T(0.5) * (Zk.y - Zm.y));
             const C O = mk<C>(T(0.5) * (Zk.y + Zm.y), T(-0.5) * (Zk.x - Zm.x));
@@ -201,12 +215,12 @@ __global__ void __launch_bounds__(x_threads<T>()) k_reg_x_fwd(PoissonArgs<T> A)
 }
 
 // ---- x inverse ---------------------------------------------------------------------------------------------
-template <typename T, int GX>
+template <typename T, int RX, int GX>
 __global__ void __launch_bounds__(x_threads<T>()) k_reg_x_inv(PoissonArgs<T> A)
 {
     pdl_enter();
     using C = typename CxT<T>::type;
-    constexpr int M = 16 * GX, NT = x_threads<T>(), B = NT / GX, P = 32 / GX, Q = 16 / GX;
+    constexpr int M = RX * GX, NT = x_threads<T>(), B = NT / GX, P = 32 / GX, Q = RX / GX;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int SPX = A.reg_spx;
     C* tw = reinterpret_cast<C*>(smem_raw);
@@ -224,7 +238,7 @@ __global__ void __launch_bounds__(x_threads<T>()) k_reg_x_inv(PoissonArgs<T> A)
     constexpr bool STAGED = GX == 16;
     constexpr int SB = B + 1;
     C* stage = rowbuf + B * SPX;
-    C xk[9], xm[9];
+    C xk[RX / 2 + 1], xm[RX / 2 + 1];
     if (STAGED) {
         const C* __restrict__ in = reinterpret_cast<const C*>(A.spec);
         const int row0 = blockIdx.x * B;
@@ -243,7 +257,7 @@ __global__ void __launch_bounds__(x_threads<T>()) k_reg_x_inv(PoissonArgs<T> A)
         }
         __syncthreads();
 #pragma unroll
-        for (int i = 0; i <= 8; ++i) {
+        for (int i = 0; i <= RX / 2; ++i) {
             const int k = t + GX * i;
             const bool ok = k <= M / 2;
             xk[i] = ok ? stage[k * SB + b] : mk<C>(T(0), T(0));
@@ -252,7 +266,7 @@ __global__ void __launch_bounds__(x_threads<T>()) k_reg_x_inv(PoissonArgs<T> A)
     } else {
         const C* __restrict__ spec = reinterpret_cast<const C*>(A.spec) + (act ? row : 0);
 #pragma unroll
-        for (int i = 0; i <= 8; ++i) {
+        for (int i = 0; i <= RX / 2; ++i) {
             const int k = t + GX * i;
             const bool ok = act && k <= M / 2;
             xk[i] = ok ? spec[(long long)k * rows] : mk<C>(T(0), T(0));
@@ -263,12 +277,12 @@ __global__ void __launch_bounds__(x_threads<T>()) k_reg_x_inv(PoissonArgs<T> A)
     C* rb = rowbuf + b * SPX;
     // join: Z'_k = (X_k + conj X_{M-k}) + i W^{-k} (X_k - conj X_{M-k})
 #pragma unroll
-    for (int i = 0; i <= 8; ++i) {
+    for (int i = 0; i <= RX / 2; ++i) {
         const int k = t + GX * i;
         if (k > M / 2) break;
         const C Xk = xk[i], Xm = xm[i];
         if (k == 0) {
-            rb[slot_of_freq<GX>(0)] = mk<C>(Xk.x + Xk.y, Xk.x - Xk.y);
+            rb[slot_of_freq<RX, GX>(0)] = mk<C>(Xk.x + Xk.y, Xk.x - Xk.y);
             continue;
         }
         {
@@ -276,42 +290,44 @@ __global__ void __launch_bounds__(x_threads<T>()) k_reg_x_inv(PoissonArgs<T> A)
             C w = twr[k];
             w.y = -w.y;
             const C wd = cmul(w, d);
-            rb[slot_of_freq<GX>(k)] = mk<C>(s.x - wd.y, s.y + wd.x);
+            rb[slot_of_freq<RX, GX>(k)] = mk<C>(s.x - wd.y, s.y + wd.x);
         }
         if (2 * k != M) {
             const C s = mk<C>(Xm.x + Xk.x, Xm.y - Xk.y), d = mk<C>(Xm.x - Xk.x, Xm.y + Xk.y);
             C w = twr[M - k];
             w.y = -w.y;
             const C wd = cmul(w, d);
-            rb[slot_of_freq<GX>(M - k)] = mk<C>(s.x - wd.y, s.y + wd.x);
+            rb[slot_of_freq<RX, GX>(M - k)] = mk<C>(s.x - wd.y, s.y + wd.x);
         }
     }
     __syncwarp();
-    C v[16];
+    C v[RX];
 #pragma unroll
     for (int q = 0; q < Q; ++q)
 #pragma unroll
-        for (int k2 = 0; k2 < GX; ++k2) v[q * GX + k2] = rb[RegShape<GX>::slot(t, q, k2)];
+        for (int k2 = 0; k2 < GX; ++k2) v[q * GX + k2] = rb[RegShape<RX, GX>::slot(t, q, k2)];
     auto buf = [rb](int e) -> C& { return rb[e]; };
-    reg_inv<C, GX>(v, t, tw, buf);
+    reg_inv<C, RX, GX>(v, t, tw, buf);
     if (act) {
         T* __restrict__ dst = A.p + (long long)row * A.nx;
 #pragma unroll
-        for (int m = 0; m < 16; ++m) *reinterpret_cast<C*>(dst + 2 * (t + GX * m)) = v[m];
+        for (int m = 0; m < RX; ++m) *reinterpret_cast<C*>(dst + 2 * (t + GX * m)) = v[m];
     }
 }
 
 // ---- (y, z) plane of one kx ----------------------------------------------------------------------------------
-template <typename T, int GY, int GZ>
-__global__ void __launch_bounds__(yz_threads<T>()) k_reg_yz_solve(PoissonArgs<T> A)
+template <typename T, int RY, int GY, int RZ, int GZ>
+__global__ void __launch_bounds__((yz_bound<T, RY, GY, RZ, GZ>())) k_reg_yz_solve(PoissonArgs<T> A)
 {
     pdl_enter();
     using C = typename CxT<T>::type;
-    constexpr int NY = 16 * GY, NZ = 16 * GZ, QY = 16 / GY, QZ = 16 / GZ;
+    constexpr int NY = RY * GY, NZ = RZ * GZ, QY = RY / GY, QZ = RZ / GZ;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int SP = A.reg_sp;
-    C* plane = reinterpret_cast<C*>(smem_raw);     // row z at z * SP, slot s of the y transform at s
-    C* twy = plane + NZ * SP;
+    // row z at z * SP, slot s of the y transform at s; row NZ and column NY (SP > NY when a warp's last z groups
+    // run past NY) are the exchange slices of the groups past the last row or column, which hold no data
+    C* plane = reinterpret_cast<C*>(smem_raw);
+    C* twy = plane + (NZ + 1) * SP;
     C* twz = twy + NY;
     stage_table(twy, A.twy, NY);
     stage_table(twz, A.twz, NZ);
@@ -325,19 +341,19 @@ __global__ void __launch_bounds__(yz_threads<T>()) k_reg_yz_solve(PoissonArgs<T>
         const int gi = lane % P, t = lane / P;
         for (int z0 = warp * P; z0 < NZ; z0 += nwarps * P) {
             const int z = z0 + gi;
-            const bool act = z < NZ;             // false only for G = 1 with NZ = 16 (no exchange then)
-            C v[16];
+            const bool act = z < NZ;
+            C v[RY];
 #pragma unroll
-            for (int m = 0; m < 16; ++m) v[m] = act ? g[z * NY + t + GY * m] : mk<C>(T(0), T(0));
-            C* row = plane + (act ? z : 0) * SP;
+            for (int m = 0; m < RY; ++m) v[m] = act ? g[z * NY + t + GY * m] : mk<C>(T(0), T(0));
+            C* row = plane + (act ? z : NZ) * SP;
             auto buf = [row](int e) -> C& { return row[e]; };
-            reg_fwd<C, GY>(v, t, twy, buf);
+            reg_fwd<C, RY, GY>(v, t, twy, buf);
             __syncwarp();
             if (act) {
 #pragma unroll
                 for (int q = 0; q < QY; ++q)
 #pragma unroll
-                    for (int k2 = 0; k2 < GY; ++k2) row[RegShape<GY>::slot(t, q, k2)] = v[q * GY + k2];
+                    for (int k2 = 0; k2 < GY; ++k2) row[RegShape<RY, GY>::slot(t, q, k2)] = v[q * GY + k2];
             }
         }
     }
@@ -350,29 +366,29 @@ __global__ void __launch_bounds__(yz_threads<T>()) k_reg_yz_solve(PoissonArgs<T>
         for (int c0 = warp * P; c0 < NY; c0 += nwarps * P) {
             const int c = c0 + gi;
             const bool act = c < NY;
-            const int cc = act ? c : 0;
-            const int ky = freq_of_slot<GY>(cc);
+            const int cc = act ? c : NY;
+            const int ky = freq_of_slot<RY, GY>(act ? c : 0);
             const T lxy = lx + __ldg(A.lamy + ky);
             const bool ky_null = (kx == 0) && (ky == 0 || 2 * ky == NY);
-            C v[16];
+            C v[RZ];
 #pragma unroll
-            for (int m = 0; m < 16; ++m) v[m] = plane[(t + GZ * m) * SP + cc];
+            for (int m = 0; m < RZ; ++m) v[m] = plane[(t + GZ * m) * SP + cc];
             auto buf = [plane, SP, cc](int e) -> C& { return plane[e * SP + cc]; };
-            reg_fwd<C, GZ>(v, t, twz, buf);
+            reg_fwd<C, RZ, GZ>(v, t, twz, buf);
 #pragma unroll
             for (int q = 0; q < QZ; ++q)
 #pragma unroll
                 for (int k2 = 0; k2 < GZ; ++k2) {
-                    const int kz = RegShape<GZ>::freq(t, q, k2);
+                    const int kz = RegShape<RZ, GZ>::freq(t, q, k2);
                     const bool null = ky_null && (kz == 0 || 2 * kz == NZ);
                     const T s = null ? T(0) : inv_lambda(A.invN, lxy + __ldg(A.lamz + kz));
                     v[q * GZ + k2] = cscale(v[q * GZ + k2], s);
                 }
-            reg_inv<C, GZ>(v, t, twz, buf);
+            reg_inv<C, RZ, GZ>(v, t, twz, buf);
             __syncwarp();
             if (act) {
 #pragma unroll
-                for (int m = 0; m < 16; ++m) plane[(t + GZ * m) * SP + cc] = v[m];
+                for (int m = 0; m < RZ; ++m) plane[(t + GZ * m) * SP + cc] = v[m];
             }
         }
     }
@@ -384,17 +400,17 @@ __global__ void __launch_bounds__(yz_threads<T>()) k_reg_yz_solve(PoissonArgs<T>
         for (int z0 = warp * P; z0 < NZ; z0 += nwarps * P) {
             const int z = z0 + gi;
             const bool act = z < NZ;
-            C* row = plane + (act ? z : 0) * SP;
-            C v[16];
+            C* row = plane + (act ? z : NZ) * SP;
+            C v[RY];
 #pragma unroll
             for (int q = 0; q < QY; ++q)
 #pragma unroll
-                for (int k2 = 0; k2 < GY; ++k2) v[q * GY + k2] = row[RegShape<GY>::slot(t, q, k2)];
+                for (int k2 = 0; k2 < GY; ++k2) v[q * GY + k2] = row[RegShape<RY, GY>::slot(t, q, k2)];
             auto buf = [row](int e) -> C& { return row[e]; };
-            reg_inv<C, GY>(v, t, twy, buf);
+            reg_inv<C, RY, GY>(v, t, twy, buf);
             if (act) {
 #pragma unroll
-                for (int m = 0; m < 16; ++m) g[z * NY + t + GY * m] = v[m];
+                for (int m = 0; m < RY; ++m) g[z * NY + t + GY * m] = v[m];
             }
         }
     }
@@ -436,20 +452,20 @@ __global__ void __launch_bounds__(256) k_reg_y(PoissonArgs<T> A)
     if (!INV) {
 #pragma unroll
         for (int m = 0; m < 16; ++m) v[m] = act ? g[t + GY * m] : mk<C>(T(0), T(0));
-        reg_fwd<C, GY>(v, t, tw, buf);
+        reg_fwd<C, 16, GY>(v, t, tw, buf);
         if (act) {
 #pragma unroll
             for (int q = 0; q < Q; ++q)
 #pragma unroll
-                for (int k2 = 0; k2 < GY; ++k2) g[RegShape<GY>::slot(t, q, k2)] = v[q * GY + k2];
+                for (int k2 = 0; k2 < GY; ++k2) g[RegShape<16, GY>::slot(t, q, k2)] = v[q * GY + k2];
         }
     } else {
 #pragma unroll
         for (int q = 0; q < Q; ++q)
 #pragma unroll
             for (int k2 = 0; k2 < GY; ++k2)
-                v[q * GY + k2] = act ? g[RegShape<GY>::slot(t, q, k2)] : mk<C>(T(0), T(0));
-        reg_inv<C, GY>(v, t, tw, buf);
+                v[q * GY + k2] = act ? g[RegShape<16, GY>::slot(t, q, k2)] : mk<C>(T(0), T(0));
+        reg_inv<C, 16, GY>(v, t, tw, buf);
         if (act) {
 #pragma unroll
             for (int m = 0; m < 16; ++m) g[t + GY * m] = v[m];
@@ -509,17 +525,17 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? VF_ZTILE_MIN_CTAS : 2) k
 #pragma unroll
     for (int m = 0; m < 16; ++m) v[m] = tile[(t + GZ * m) * ST + c];
     auto buf = [tile, ST, c](int e) -> C& { return tile[e * ST + c]; };
-    reg_fwd<C, GZ>(v, t, twz, buf);
+    reg_fwd<C, 16, GZ>(v, t, twz, buf);
 #pragma unroll
     for (int q = 0; q < QZ; ++q)
 #pragma unroll
         for (int k2 = 0; k2 < GZ; ++k2) {
-            const int kz = RegShape<GZ>::freq(t, q, k2);
+            const int kz = RegShape<16, GZ>::freq(t, q, k2);
             const bool null = ky_null && (kz == 0 || 2 * kz == NZ);
             const T s = null ? T(0) : inv_lambda(A.invN, lxy + __ldg(A.lamz + kz));
             v[q * GZ + k2] = cscale(v[q * GZ + k2], s);
         }
-    reg_inv<C, GZ>(v, t, twz, buf);
+    reg_inv<C, 16, GZ>(v, t, twz, buf);
     __syncwarp();
 #pragma unroll
     for (int m = 0; m < 16; ++m) tile[(t + GZ * m) * ST + c] = v[m];
@@ -546,20 +562,29 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? VF_ZTILE_MIN_CTAS : 2) k
 }
 
 // ---- host side ---------------------------------------------------------------------------------------------
-int g_of(int n)
+// Register transform shape of an axis of n points: R values per thread and G threads, n = R G.  Lengths 16 G
+// (G = 1..16) in both precisions; the 2-3-5 lengths of the batch and serving rooms (36 .. 96) in FP32, whose
+// (y, z) planes fit whole in shared memory.
+bool reg_shape(int n, bool fp32, int* R, int* G)
 {
     for (int g = 1; g <= 16; g *= 2)
-        if (n == 16 * g) return g;
-    return 0;
+        if (n == 16 * g) { *R = 16; *G = g; return true; }
+    if (!fp32) return false;
+    static const int tab[][3] = {{36, 18, 2}, {40, 20, 2}, {48, 12, 4}, {60, 30, 2}, {72, 36, 2}, {80, 20, 4},
+                                 {96, 24, 4}};
+    for (const auto& e : tab)
+        if (n == e[0]) { *R = e[1]; *G = e[2]; return true; }
+    return false;
 }
 
 // Worst number of distinct 8-byte words one bank serves in a warp access (shared memory: 16 banks of 8 bytes
-// per 128-byte wavefront for 8-byte elements, 32 of 4 bytes = 16 of 8).  addr(lane, step) in elements of esz bytes.
+// per 128-byte wavefront for 8-byte elements, 32 of 4 bytes = 16 of 8).  addr(lane, step) in elements of esz
+// bytes, for steps 0..nsteps-1.
 template <typename F>
-int worst_ways(int esz, F addr)
+int worst_ways(int esz, int nsteps, F addr)
 {
     int worst = 1;
-    for (int step = 0; step < 16; ++step) {
+    for (int step = 0; step < nsteps; ++step) {
         int ways[32] = {0};
         long long seen[32][32];
         int nseen[32] = {0};
@@ -578,50 +603,51 @@ int worst_ways(int esz, F addr)
     return worst;
 }
 
-int xpos_h(int G, int t, int k1) { const int Q = 16 / G; return k1 * G + ((t + k1 / Q) & (G - 1)); }
+int xpos_h(int R, int G, int t, int k1) { const int Q = R / G; return k1 * G + ((t + k1 / Q) & (G - 1)); }
 
 // conflicts of the row-owned accesses (a group of G threads per row, rows `stride` apart)
-int row_ways(int G, int stride, int esz)
+int row_ways(int R, int G, int stride, int esz)
 {
-    const int P = 32 / G, Q = 16 / G;
+    const int P = 32 / G, Q = R / G;
     int w = 0;
     auto mx = [&](int v) { w = v > w ? v : w; };
     if (G > 1) {
-        mx(worst_ways(esz, [&](int l, int s) { return (long long)(l % P) * stride + xpos_h(G, l / P, s); }));
-        mx(worst_ways(esz, [&](int l, int s) {
-            return (long long)(l % P) * stride + xpos_h(G, s % G, (l / P) * Q + (s / G) % Q); }));
+        mx(worst_ways(esz, R, [&](int l, int s) { return (long long)(l % P) * stride + xpos_h(R, G, l / P, s); }));
+        mx(worst_ways(esz, R, [&](int l, int s) {
+            return (long long)(l % P) * stride + xpos_h(R, G, s % G, (l / P) * Q + (s / G) % Q); }));
     }
-    mx(worst_ways(esz, [&](int l, int s) { return (long long)(l % P) * stride + (l / P) + G * (s % Q) + 16 * ((s / Q) % G); }));
+    mx(worst_ways(esz, R, [&](int l, int s) {
+        return (long long)(l % P) * stride + (l / P) + G * (s % Q) + R * ((s / Q) % G); }));
     return w;
 }
 
 // conflicts of the column-owned accesses (element e of column c at e * stride + c)
-int col_ways(int G, int stride, int esz)
+int col_ways(int R, int G, int stride, int esz)
 {
-    const int P = 32 / G, Q = 16 / G;
+    const int P = 32 / G, Q = R / G;
     int w = 0;
     auto mx = [&](int v) { w = v > w ? v : w; };
-    mx(worst_ways(esz, [&](int l, int s) { return (long long)((l / P) + G * s) * stride + (l % P); }));
+    mx(worst_ways(esz, R, [&](int l, int s) { return (long long)((l / P) + G * s) * stride + (l % P); }));
     if (G > 1) {
-        mx(worst_ways(esz, [&](int l, int s) { return (long long)xpos_h(G, l / P, s) * stride + (l % P); }));
-        mx(worst_ways(esz, [&](int l, int s) {
-            return (long long)xpos_h(G, s % G, (l / P) * Q + (s / G) % Q) * stride + (l % P); }));
+        mx(worst_ways(esz, R, [&](int l, int s) { return (long long)xpos_h(R, G, l / P, s) * stride + (l % P); }));
+        mx(worst_ways(esz, R, [&](int l, int s) {
+            return (long long)xpos_h(R, G, s % G, (l / P) * Q + (s / G) % Q) * stride + (l % P); }));
     }
     return w;
 }
 
 template <typename T>
-size_t x_smem(int M, int spx)
+size_t x_smem(int M, int G, int spx)
 {
-    const int B = x_threads<T>() / (M / 16);
-    const size_t stage = M == 256 ? (size_t)M * (B + 1) : 0;     // the frequency-major stage of 256-point rows
+    const int B = x_threads<T>() / G;
+    const size_t stage = G == 16 ? (size_t)M * (B + 1) : 0;     // the frequency-major stage of 256-point rows
     return ((size_t)M + (M + 1) + (size_t)B * spx + stage) * sizeof(typename CxT<T>::type);
 }
 
 template <typename T>
 size_t yz_smem(int ny, int nz, int sp)
 {
-    return ((size_t)nz * sp + ny + nz) * sizeof(typename CxT<T>::type);
+    return ((size_t)(nz + 1) * sp + ny + nz) * sizeof(typename CxT<T>::type);
 }
 
 template <typename T>
@@ -639,6 +665,19 @@ size_t ztile_smem(int nz, int st)
 
 constexpr size_t kRegSmemLimit = 200 * 1024;
 
+template <typename K>
+cudaError_t raise_smem(K kernel, size_t bytes)
+{
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    if (bytes > (size_t)optin) return cudaErrorInvalidValue;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+}
+
+// ---- tile mode (lengths 16 G) --------------------------------------------------------------------------------
 template <typename T, int GY>
 cudaError_t launch_y(const PoissonArgs<T>& a, bool inv, cudaStream_t st)
 {
@@ -682,84 +721,6 @@ cudaError_t dispatch_ztile(const PoissonArgs<T>& a, cudaStream_t st)
     }
 }
 
-template <typename T, int GX>
-cudaError_t launch_x(const PoissonArgs<T>& a, bool fwd, cudaStream_t st)
-{
-    constexpr int B = x_threads<T>() / GX;
-    const int rows = a.ny * a.nz;
-    const unsigned grid = (unsigned)((rows + B - 1) / B);
-    const size_t sm = x_smem<T>(16 * GX, a.reg_spx);
-    return launch_pdl(fwd ? k_reg_x_fwd<T, GX> : k_reg_x_inv<T, GX>, dim3(grid), dim3(x_threads<T>()), sm, st, a);
-}
-
-template <typename T>
-cudaError_t dispatch_x(const PoissonArgs<T>& a, bool fwd, cudaStream_t st)
-{
-    switch (a.gx) {
-        case 1: return launch_x<T, 1>(a, fwd, st);
-        case 2: return launch_x<T, 2>(a, fwd, st);
-        case 4: return launch_x<T, 4>(a, fwd, st);
-        case 8: return launch_x<T, 8>(a, fwd, st);
-        case 16: return launch_x<T, 16>(a, fwd, st);
-        default: return cudaErrorInvalidValue;
-    }
-}
-
-template <typename T, int GY, int GZ>
-cudaError_t launch_yz(const PoissonArgs<T>& a, cudaStream_t st)
-{
-    const int want = (16 * GY) * (16 * GZ) / 16;
-    const int threads = want < 32 ? 32 : (want > yz_threads<T>() ? yz_threads<T>() : want);
-    return launch_pdl(k_reg_yz_solve<T, GY, GZ>, dim3(a.M), dim3(threads), yz_smem<T>(a.ny, a.nz, a.reg_sp), st, a);
-}
-
-template <typename T, int GY>
-cudaError_t dispatch_yz_z(const PoissonArgs<T>& a, cudaStream_t st)
-{
-    switch (a.gz) {
-        case 1: return launch_yz<T, GY, 1>(a, st);
-        case 2: return launch_yz<T, GY, 2>(a, st);
-        case 4: return launch_yz<T, GY, 4>(a, st);
-        case 8: return launch_yz<T, GY, 8>(a, st);
-        case 16: return launch_yz<T, GY, 16>(a, st);
-        default: return cudaErrorInvalidValue;
-    }
-}
-
-template <typename T>
-cudaError_t dispatch_yz(const PoissonArgs<T>& a, cudaStream_t st)
-{
-    switch (a.gy) {
-        case 1: return dispatch_yz_z<T, 1>(a, st);
-        case 2: return dispatch_yz_z<T, 2>(a, st);
-        case 4: return dispatch_yz_z<T, 4>(a, st);
-        case 8: return dispatch_yz_z<T, 8>(a, st);
-        case 16: return dispatch_yz_z<T, 16>(a, st);
-        default: return cudaErrorInvalidValue;
-    }
-}
-
-template <typename K>
-cudaError_t raise_smem(K kernel, size_t bytes)
-{
-    if (bytes <= 48 * 1024) return cudaSuccess;
-    int dev = 0, optin = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    if (e != cudaSuccess) return e;
-    if (bytes > (size_t)optin) return cudaErrorInvalidValue;
-    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
-}
-
-template <typename T, int GX>
-cudaError_t prepare_x(const PoissonArgs<T>& a)
-{
-    const size_t sm = x_smem<T>(16 * GX, a.reg_spx);
-    cudaError_t e = raise_smem(k_reg_x_fwd<T, GX>, sm);
-    if (e == cudaSuccess) e = raise_smem(k_reg_x_inv<T, GX>, sm);
-    return e;
-}
-
 template <typename T, int G>
 cudaError_t prepare_tile(const PoissonArgs<T>& a)
 {
@@ -774,18 +735,99 @@ cudaError_t prepare_tile(const PoissonArgs<T>& a)
     return e;
 }
 
-template <typename T, int GY>
-cudaError_t prepare_yz_z(const PoissonArgs<T>& a)
+// ---- shape dispatch ------------------------------------------------------------------------------------------
+// Calls f.template run<R, G>() for the shape (r, g): the lengths 16 G in both precisions, the FP32 2-3-5 shapes
+// only for float (no double instantiations of them).
+template <typename T, bool ONLY16 = false, typename F>
+cudaError_t with_shape(int r, int g, F&& f)
 {
-    const size_t sm = yz_smem<T>(a.ny, a.nz, a.reg_sp);
-    switch (a.gz) {
-        case 1: return raise_smem(k_reg_yz_solve<T, GY, 1>, sm);
-        case 2: return raise_smem(k_reg_yz_solve<T, GY, 2>, sm);
-        case 4: return raise_smem(k_reg_yz_solve<T, GY, 4>, sm);
-        case 8: return raise_smem(k_reg_yz_solve<T, GY, 8>, sm);
-        case 16: return raise_smem(k_reg_yz_solve<T, GY, 16>, sm);
-        default: return cudaErrorInvalidValue;
+    if (r == 16) {
+        switch (g) {
+            case 1: return f.template run<16, 1>();
+            case 2: return f.template run<16, 2>();
+            case 4: return f.template run<16, 4>();
+            case 8: return f.template run<16, 8>();
+            case 16: return f.template run<16, 16>();
+            default: return cudaErrorInvalidValue;
+        }
     }
+    if constexpr (sizeof(T) == 4 && !ONLY16) {
+        if (r == 18 && g == 2) return f.template run<18, 2>();
+        if (r == 20 && g == 2) return f.template run<20, 2>();
+        if (r == 12 && g == 4) return f.template run<12, 4>();
+        if (r == 30 && g == 2) return f.template run<30, 2>();
+        if (r == 36 && g == 2) return f.template run<36, 2>();
+        if (r == 20 && g == 4) return f.template run<20, 4>();
+        if (r == 24 && g == 4) return f.template run<24, 4>();
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <typename T>
+struct XLaunch {
+    const PoissonArgs<T>& a;
+    bool fwd;
+    cudaStream_t st;
+    bool prepare;
+    template <int R, int G>
+    cudaError_t run() const
+    {
+        constexpr int B = x_threads<T>() / G;
+        const size_t sm = x_smem<T>(R * G, G, a.reg_spx);
+        if (prepare) {
+            cudaError_t e = raise_smem(k_reg_x_fwd<T, R, G>, sm);
+            return e == cudaSuccess ? raise_smem(k_reg_x_inv<T, R, G>, sm) : e;
+        }
+        const int rows = a.ny * a.nz;
+        const unsigned grid = (unsigned)((rows + B - 1) / B);
+        return launch_pdl(fwd ? k_reg_x_fwd<T, R, G> : k_reg_x_inv<T, R, G>, dim3(grid), dim3(x_threads<T>()), sm,
+                          st, a);
+    }
+};
+
+template <typename T>
+cudaError_t dispatch_x(const PoissonArgs<T>& a, bool fwd, cudaStream_t st, bool prepare = false)
+{
+    return with_shape<T>(a.rx, a.gx, XLaunch<T>{a, fwd, st, prepare});
+}
+
+template <typename T, int RY, int GY>
+struct YZLaunch {
+    const PoissonArgs<T>& a;
+    cudaStream_t st;
+    bool prepare;
+    template <int RZ, int GZ>
+    cudaError_t run() const
+    {
+        const size_t sm = yz_smem<T>(a.ny, a.nz, a.reg_sp);
+        if (prepare) return raise_smem(k_reg_yz_solve<T, RY, GY, RZ, GZ>, sm);
+        return launch_pdl(k_reg_yz_solve<T, RY, GY, RZ, GZ>, dim3(a.M), dim3(yz_nt<T, RY, GY, RZ, GZ>()), sm, st,
+                          a);
+    }
+};
+
+template <typename T>
+struct YLaunch {
+    const PoissonArgs<T>& a;
+    cudaStream_t st;
+    bool prepare;
+    template <int RY, int GY>
+    cudaError_t run() const
+    {
+        if (RY != 16 && (a.rz != RY || a.gz != GY)) return cudaErrorInvalidValue;   // 2-3-5 planes: ny == nz
+        if constexpr (RY != 16) {
+            return YZLaunch<T, RY, GY>{a, st, prepare}.template run<RY, GY>();
+        } else {
+            if (a.rz != 16) return cudaErrorInvalidValue;
+            return with_shape<T, true>(16, a.gz, YZLaunch<T, RY, GY>{a, st, prepare});
+        }
+    }
+};
+
+template <typename T>
+cudaError_t dispatch_yz(const PoissonArgs<T>& a, cudaStream_t st, bool prepare = false)
+{
+    return with_shape<T>(a.ry, a.gy, YLaunch<T>{a, st, prepare});
 }
 
 }  // namespace
@@ -794,10 +836,15 @@ template <typename T>
 bool RegFft<T>::eligible(int nx, int ny, int nz)
 {
     if (nx % 2) return false;
-    const int gx = g_of(nx / 2), gy = g_of(ny), gz = g_of(nz);
-    if (!gx || !gy || !gz) return false;
-    // the x passes must fit; the (y, z) plane goes through shared memory whole when it fits, else in tiles
-    return x_smem<T>(nx / 2, nx / 2 + 15) <= kRegSmemLimit && y_smem<T>(ny, ny + 15) <= kRegSmemLimit;
+    constexpr bool fp32 = sizeof(T) == 4;
+    int rx, gx, ry, gy, rz, gz;
+    if (!reg_shape(nx / 2, fp32, &rx, &gx) || !reg_shape(ny, fp32, &ry, &gy) || !reg_shape(nz, fp32, &rz, &gz))
+        return false;
+    if (x_smem<T>(nx / 2, gx, nx / 2 + 15) > kRegSmemLimit) return false;
+    // 2-3-5 lengths in y or z: square planes that fit whole (no tile mode); 16 G lengths: tiles when they do not
+    if (ry != 16 || rz != 16)
+        return ry == rz && gy == gz && yz_smem<T>(ny, nz, ny + 15) <= kRegSmemLimit;
+    return y_smem<T>(ny, ny + 15) <= kRegSmemLimit;
 }
 
 template <typename T>
@@ -805,31 +852,34 @@ void RegFft<T>::configure(PoissonArgs<T>& a)
 {
     a.reg = 0;
     if (!eligible(a.nx, a.ny, a.nz)) return;
-    a.gx = g_of(a.M);
-    a.gy = g_of(a.ny);
-    a.gz = g_of(a.nz);
+    constexpr bool fp32 = sizeof(T) == 4;
+    reg_shape(a.M, fp32, &a.rx, &a.gx);
+    reg_shape(a.ny, fp32, &a.ry, &a.gy);
+    reg_shape(a.nz, fp32, &a.rz, &a.gz);
     const int esz = (int)sizeof(typename CxT<T>::type);
     // plane stride: fewest bank conflicts over the y-row and z-column accesses, then the smallest
+    // (a pad column holds the exchange of the z groups past the last y slot when a warp's groups run past ny)
     int best = -1, best_w = 1 << 30;
-    for (int pad = 0; pad < 16; ++pad) {
+    for (int pad = a.ny % (32 / a.gz) ? 1 : 0; pad < 16; ++pad) {
         const int sp = a.ny + pad;
-        const int w = std::max(row_ways(a.gy, sp, esz), col_ways(a.gz, sp, esz));
+        const int w = std::max(row_ways(a.ry, a.gy, sp, esz), col_ways(a.rz, a.gz, sp, esz));
         if (w < best_w) { best_w = w; best = sp; }
     }
     a.reg_sp = best;
-    a.reg_tile = (yz_smem<T>(a.ny, a.nz, a.reg_sp) > kRegSmemLimit || std::getenv("VF_REG_TILE")) ? 1 : 0;
+    const bool pow2 = a.ry == 16 && a.rz == 16;
+    a.reg_tile = pow2 && (yz_smem<T>(a.ny, a.nz, a.reg_sp) > kRegSmemLimit || std::getenv("VF_REG_TILE")) ? 1 : 0;
     if (a.reg_tile) {
         // y passes: the row slices of the groups; z tile: TB slots of one plane, columns as for the plane
         best = -1; best_w = 1 << 30;
         for (int pad = 0; pad < 16; ++pad) {
-            const int w = row_ways(a.gy, a.ny + pad, esz);
+            const int w = row_ways(16, a.gy, a.ny + pad, esz);
             if (w < best_w) { best_w = w; best = a.ny + pad; }
         }
         a.reg_sy = best;
         a.reg_tb = std::min(a.ny, 256 / a.gz);
         best = -1; best_w = 1 << 30;
         for (int pad = 0; pad < 16; ++pad) {
-            const int w = col_ways(a.gz, a.reg_tb + pad, esz);
+            const int w = col_ways(16, a.gz, a.reg_tb + pad, esz);
             if (w < best_w) { best_w = w; best = a.reg_tb + pad; }
         }
         a.reg_st = best;
@@ -837,7 +887,7 @@ void RegFft<T>::configure(PoissonArgs<T>& a)
     // x passes: the row slices of the groups
     best = -1; best_w = 1 << 30;
     for (int pad = 0; pad < 16; ++pad) {
-        const int w = row_ways(a.gx, a.M + pad, esz);
+        const int w = row_ways(a.rx, a.gx, a.M + pad, esz);
         if (w < best_w) { best_w = w; best = a.M + pad; }
     }
     a.reg_spx = best;
@@ -849,15 +899,7 @@ template <typename T>
 cudaError_t RegFft<T>::prepare(const PoissonArgs<T>& a)
 {
     if (!a.reg) return cudaErrorInvalidValue;
-    cudaError_t e;
-    switch (a.gx) {
-        case 1: e = prepare_x<T, 1>(a); break;
-        case 2: e = prepare_x<T, 2>(a); break;
-        case 4: e = prepare_x<T, 4>(a); break;
-        case 8: e = prepare_x<T, 8>(a); break;
-        case 16: e = prepare_x<T, 16>(a); break;
-        default: return cudaErrorInvalidValue;
-    }
+    cudaError_t e = dispatch_x<T>(a, true, nullptr, true);
     if (e != cudaSuccess) return e;
     if (a.reg_tile) {
         if ((e = prepare_tile<T, 1>(a)) != cudaSuccess) return e;
@@ -866,14 +908,7 @@ cudaError_t RegFft<T>::prepare(const PoissonArgs<T>& a)
         if ((e = prepare_tile<T, 8>(a)) != cudaSuccess) return e;
         return prepare_tile<T, 16>(a);
     }
-    switch (a.gy) {
-        case 1: return prepare_yz_z<T, 1>(a);
-        case 2: return prepare_yz_z<T, 2>(a);
-        case 4: return prepare_yz_z<T, 4>(a);
-        case 8: return prepare_yz_z<T, 8>(a);
-        case 16: return prepare_yz_z<T, 16>(a);
-        default: return cudaErrorInvalidValue;
-    }
+    return dispatch_yz<T>(a, nullptr, true);
 }
 
 template <typename T>

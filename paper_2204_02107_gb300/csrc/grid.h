@@ -34,7 +34,7 @@ struct vf_grid {
     int n_near = 0;
     bool plane_layout = false;
     // register path of the Poisson solve (PoissonArgs::reg and its shape), fixed at creation
-    int reg = 0, reg_gx = 0, reg_gy = 0, reg_gz = 0, reg_sp = 0, reg_spx = 0, reg_sb = 0;
+    int reg = 0, reg_rx = 0, reg_ry = 0, reg_rz = 0, reg_gx = 0, reg_gy = 0, reg_gz = 0, reg_sp = 0, reg_spx = 0, reg_sb = 0;
     int reg_tile = 0, reg_sy = 0, reg_tb = 0, reg_st = 0;
     void* staging = nullptr;     // N * 8 bytes
     uint8_t* mask = nullptr;

@@ -228,10 +228,12 @@ struct PoissonArgs {
     FastDiv nx_div;           // i -> i / nx (cell index -> row, correction kernel)
     int rows_per_block;       // rows of the x passes per CTA
     int cols_per_block;       // kx columns of the y / z tile passes per CTA
-    // register path (every axis length 16 G with G in 1, 2, 4, 8, 16): the transforms are held in registers, G
-    // threads per sequence; whole-plane kernel when the (y, z) plane of one kx fits in shared memory, else tile mode
+    // register path (every axis length R G: 16 G with G in 1, 2, 4, 8, 16, and in FP32 the 2-3-5 lengths 36 .. 96):
+    // the transforms are held in registers, G threads per sequence with R values each; whole-plane kernel when the
+    // (y, z) plane of one kx fits in shared memory, else tile mode (16 G lengths only)
     int reg;
-    int gx, gy, gz;           // M / 16, ny / 16, nz / 16
+    int rx, ry, rz;           // values per thread of the x (M points), y and z transforms
+    int gx, gy, gz;           // threads per transform: M = rx gx, ny = ry gy, nz = rz gz
     int reg_sp;               // complex stride between the z rows of the shared plane
     int reg_spx;              // complex stride between the rows of the x passes
     int reg_sb;               // unused (0)

@@ -105,6 +105,7 @@ _SIGNATURES = {
     "vf_poisson_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "vf_grid_bytes": (C.c_int64, [C.POINTER(VfGridDesc)]),
     "vf_get_tiles": (C.c_int, [C.c_void_p, C.POINTER(VfTiles)]),
+    "vf_fft_path": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32)]),
     "vf_set_tiles": (C.c_int, [C.c_void_p, C.POINTER(VfTiles)]),
     "vf_autotune": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(VfTiles)]),
     "vf_fft_schedules": (C.c_int, [C.c_int32, C.c_int32, C.POINTER(C.c_int32), C.c_int32]),
@@ -529,6 +530,12 @@ class Grid:
         t = VfTiles()
         self._check(lib().vf_get_tiles(self._h, C.byref(t)), "vf_get_tiles")
         return t.to_dict()
+
+    def fft_path(self):
+        """'generic', 'register_plane' or 'register_tile': the passes of this grid's pressure solve."""
+        p = C.c_int32()
+        self._check(lib().vf_fft_path(self._h, C.byref(p)), "vf_fft_path")
+        return ("generic", "register_plane", "register_tile")[p.value]
 
     def set_tiles(self, zc_stage, zc_div, zc_project, zc_filter, fft_x=None, fft_y=None, fft_z=None):
         """Set the z-chunks; FFT schedule indices left as None keep the grid's current ones."""

@@ -241,3 +241,5 @@ def test_batch_and_solver_arguments_rejected_before_any_device_call(lib):
     assert lib.vf_sync(None) == native.VF_EINVAL
     t = native.VfTiles()
     assert lib.vf_get_tiles(None, ctypes.byref(t)) == native.VF_EINVAL
+    path = ctypes.c_int32(-1)
+    assert lib.vf_fft_path(None, ctypes.byref(path)) == native.VF_EINVAL and path.value == -1

@@ -1,8 +1,11 @@
-"""Register-resident FFT passes of the Poisson solve (every axis 16 G long, G in 1, 2, 4, 8, 16).
+"""Register-resident FFT passes of the Poisson solve: every axis R G long with G threads of R values per
+transform (lengths 16 G, G in 1, 2, 4, 8, 16, in both precisions; in FP32 also the 2-3-5 lengths 36, 40, 48, 60,
+72, 80, 96 of the batch rooms, whose R-point DFTs are split at compile time into 2-, 3-, 4-, 5-, 8- and 16-point
+ones).
 
-The solve is checked against the oracle's numpy.fft solve for every G on every axis, and whole masked-room steps
-(the Eq. 9 correction kernel followed by the register passes) against the generic mixed-radix passes
-(VF_GENERIC_FFT).  The masked-room parity tests against the oracle include register-path shapes."""
+The solve is checked against the oracle's numpy.fft solve for every shape, and whole masked-room steps (the Eq. 9
+correction kernel followed by the register passes) against the generic mixed-radix passes (VF_GENERIC_FFT).  The
+masked-room parity tests against the oracle include register-path shapes."""
 import numpy as np
 import pytest
 
@@ -20,6 +23,19 @@ SHAPES = [(32, 16, 16),      # 1 1 1
           (512, 256, 16),    # 16 16 1
           (32, 16, 256),     # 1 1 16
           (64, 128, 16)]     # 2 8 1
+
+# FP32 2-3-5 shapes: (R, G) of x (nx / 2) and of y = z
+SHAPES_235 = [(72, 36, 36),      # (18, 2) (18, 2)
+              (80, 40, 40),      # (20, 2) (20, 2)
+              (96, 48, 48),      # (12, 4) (12, 4)
+              (120, 60, 60),     # (30, 2) (30, 2)
+              (144, 72, 72),     # (36, 2) (36, 2)
+              (160, 80, 80),     # (20, 4) (20, 4)
+              (192, 96, 96),     # (24, 4) (24, 4)
+              (128, 72, 72),     # (16, 4) (36, 2)
+              (72, 64, 64),      # (18, 2) (16, 4)
+              (64, 80, 80),      # (16, 2) (20, 4)
+              (120, 96, 96)]     # (30, 2) (24, 4)
 
 
 @pytest.fixture(scope="module")
@@ -43,6 +59,9 @@ def test_poisson_solve_all_g(torch, monkeypatch, precision, shape, mode):
     dt = torch.float64 if precision == "fp64" else torch.float32
     fd = torch.tensor(f, dtype=dt, device="cuda")
     pd = torch.empty_like(fd)
+    # (the FP64 256 x 128 plane exceeds the shared memory of one CTA: tiles in both modes)
+    too_big = precision == "fp64" and (ny, nz) == (128, 128)
+    assert g.fft_path() == ("register_tile" if mode == "tile" or too_big else "register_plane")
     g.poisson_solve(fd, pd)
     g.sync()
     got = pd.double().cpu().numpy()
@@ -52,6 +71,65 @@ def test_poisson_solve_all_g(torch, monkeypatch, precision, shape, mode):
     ref = F.poisson_fft_solve(f, prm)
     err = rel_l2(got, ref)
     assert err < (1e-13 if precision == "fp64" else 2e-6), err
+
+
+def poisson_case(torch, shape, precision, seed_extra=0):
+    nx, ny, nz = shape
+    prm = F.Params(nx=nx, ny=ny, nz=nz, lx=nx * 0.1, ly=ny * 0.07, lz=nz * 0.13, nu=0.0, dt=1.0)
+    rng = np.random.default_rng(nx * 7919 + ny * 31 + nz + seed_extra)
+    f = rng.standard_normal(prm.shape)
+    g = native.Grid(nx, ny, nz, prm.lx, prm.ly, prm.lz, nu=0.0, dt=1.0, precision=precision)
+    return prm, f, g
+
+
+@pytest.mark.parametrize("shape", SHAPES_235)
+def test_poisson_solve_235_fp32(torch, shape):
+    """FP32 register transforms of 2-3-5 lengths (whole (y, z) planes) against the oracle's numpy.fft solve; the
+    same lengths in FP64 take the generic passes."""
+    prm, f, g = poisson_case(torch, shape, "fp32")
+    assert g.fft_path() == "register_plane"
+    fd = torch.tensor(f, dtype=torch.float32, device="cuda")
+    pd = torch.empty_like(fd)
+    g.poisson_solve(fd, pd)
+    g.sync()
+    got = pd.double().cpu().numpy()
+    g.close()
+    ref = F.poisson_fft_solve(f.astype(np.float32).astype(np.float64), prm)
+    err = rel_l2(got, ref)
+    assert err < 2e-6, err
+    _, _, g64 = poisson_case(torch, shape, "fp64")
+    assert g64.fft_path() == "generic"
+    g64.close()
+
+
+def test_235_unequal_plane_takes_generic(torch):
+    """a 2-3-5 length in y or z needs ny = nz on the register path; otherwise the generic passes run"""
+    for shape in ((144, 72, 96), (128, 64, 72)):
+        _, _, g = poisson_case(torch, shape, "fp32")
+        assert g.fft_path() == "generic", shape
+        g.close()
+
+
+@pytest.mark.parametrize("shape", [(144, 72, 72), (120, 96, 96), (72, 64, 64)])
+def test_register_235_room_matches_generic_passes(torch, monkeypatch, shape):
+    """20 FP32 steps of a masked room through the 2-3-5 register passes and the generic ones"""
+    nx, ny, nz = shape
+    room, prm, geom, st0 = room_case(nx, ny, nz, boxes=[(nx // 4, nx // 4 + 8, 10, 20, 2, 12),
+                                                        (nx // 2, nx // 2 + 12, ny // 2, ny // 2 + 10, 2, 8)],
+                                     seed=nx + ny)
+    out = {}
+    for path in ("register", "generic"):
+        monkeypatch.delenv("VF_GENERIC_FFT", raising=False)
+        if path == "generic":
+            monkeypatch.setenv("VF_GENERIC_FFT", "1")
+        g = gpu_grid(prm, room.beta, room.S, room.room, "fp32")
+        assert g.fft_path() == ("register_plane" if path == "register" else "generic")
+        load_state(g, st0, prm, as_fp32=True)
+        g.step(20)
+        out[path] = {n: g.read_field(n) for n in FIELD_NAMES + ("p",)}
+        g.close()
+    for n in FIELD_NAMES + ("p",):
+        assert rel_l2(out["register"][n], out["generic"][n]) < 2e-5, n
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
