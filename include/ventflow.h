@@ -327,8 +327,10 @@ typedef struct vf_batch_desc {
 } vf_batch_desc;
 
 /* Empty batch.  One batch step advances every running room by one time step through a single CUDA graph launch
- * with one independent branch per room (the rooms' kernels run concurrently); a room's arithmetic is the same as
- * alone, so its fields are bitwise identical alone and in any mix. */
+ * with independent lanes of rooms (the lanes' kernels run concurrently; the rooms of a lane one after another, as
+ * many lanes as keep the Poisson working set of the rooms in flight within L2, at least 8; the environment
+ * variable VF_BATCH_LANES, read when the graph is captured, sets the count, 0 = one lane per room); a room's
+ * arithmetic is the same as alone, so its fields are bitwise identical alone and in any mix. */
 int vf_batch_create(const vf_batch_desc* d, vf_batch** out);
 int vf_batch_destroy(vf_batch* b);
 

@@ -15,6 +15,7 @@
 #include <cuda_runtime_api.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -68,8 +69,34 @@ void drop_graphs(vf_batch* b)
 
 bool stepping(const vf_batch_slot& s) { return s.g && !s.done && s.remaining > 0; }
 
-// One graph per reduction variant: fork the batch stream to each stepping room's capture stream, enqueue its
-// step there, join back.
+long long cells_of(const vf_grid* g) { return (long long)g->d.nx * g->d.ny * g->d.nz; }
+
+// Rooms run in lanes: chains of rooms, each room's step after the previous room's of its lane.  As many lanes as
+// keep the Poisson working set of the rooms in flight (right-hand side, spectrum and pressure: 3 values a cell)
+// within 60 % of L2, so that each room's four solves find their spectrum still in L2, but at least 8, which keep
+// the SMs busy between the launches of a room; all rooms in parallel left the spectra of 64 rooms competing for
+// L2 (mixed 64-room batch on GB300: 8.0 Gcell/s with every room a branch, 8.3 / 8.7 / 8.8 / 8.7 / 8.6 / 8.3 with
+// 4 / 6 / 8 / 10 / 16 / 32 lanes; 64 rooms of 128 x 64 x 64: 9.1 all parallel, 9.4 with 12 lanes; 8 rooms of
+// 256 x 128 x 128: 11.1 all parallel, 10.9 with 2 lanes).  VF_BATCH_LANES overrides the count (0: every room its
+// own branch).
+int lane_count(const std::vector<vf_batch_slot*>& rooms)
+{
+    if (rooms.empty()) return 0;
+    if (const char* lv = std::getenv("VF_BATCH_LANES")) return std::max(0, std::atoi(lv));
+    int dev = 0, l2 = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) != cudaSuccess ||
+        l2 <= 0)
+        return 0;
+    double per_room = 0.0;
+    for (const vf_batch_slot* s : rooms)
+        per_room += (double)cells_of(s->g) * 3.0 * (s->g->d.precision == VF_FP32_MIXED ? 4.0 : 8.0);
+    per_room /= (double)rooms.size();
+    const int lanes = (int)(0.6 * l2 / per_room);
+    return std::min(std::max(8, lanes), (int)rooms.size());
+}
+
+// One graph per reduction variant: fork the batch stream into the lanes, enqueue each room's step on its capture
+// stream after the previous room of its lane (longest rooms first, each to the least loaded lane), join back.
 int capture(vf_batch* b)
 {
     drop_graphs(b);
@@ -77,14 +104,35 @@ int capture(vf_batch* b)
         cudaGraph_t graph = nullptr;
         VB_CK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeRelaxed));
         cudaError_t e = cudaEventRecord(b->fork, b->stream);
-        for (vf_batch_slot& s : b->slots) {
+        std::vector<vf_batch_slot*> order;
+        for (vf_batch_slot& s : b->slots)
+            if (stepping(s)) order.push_back(&s);
+        const int lanes = lane_count(order);
+        std::vector<cudaEvent_t> tail;
+        std::vector<long long> load;
+        if (lanes > 0) {
+            std::stable_sort(order.begin(), order.end(), [](const vf_batch_slot* a, const vf_batch_slot* c) {
+                return cells_of(a->g) > cells_of(c->g); });
+            tail.assign((size_t)lanes, b->fork);
+            load.assign((size_t)lanes, 0);
+        }
+        for (vf_batch_slot* sp : order) {
+            vf_batch_slot& s = *sp;
             if (e != cudaSuccess) break;
-            if (!stepping(s)) continue;
-            e = cudaStreamWaitEvent(s.g->cap_stream, b->fork, 0);
+            int l = -1;
+            if (lanes > 0) {
+                l = 0;
+                for (int i = 1; i < lanes; ++i) if (load[i] < load[l]) l = i;
+                load[l] += cells_of(s.g);
+            }
+            e = cudaStreamWaitEvent(s.g->cap_stream, l < 0 ? b->fork : tail[l], 0);
             if (e == cudaSuccess) e = vf_engine::enqueue_step(s.g, s.g->cap_stream, v == 1);
             if (e == cudaSuccess) e = cudaEventRecord(s.join, s.g->cap_stream);
-            if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, s.join, 0);
+            if (l >= 0) tail[l] = s.join;
+            else if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, s.join, 0);
         }
+        for (cudaEvent_t t : tail)
+            if (e == cudaSuccess && t != b->fork) e = cudaStreamWaitEvent(b->stream, t, 0);
         cudaError_t e2 = cudaStreamEndCapture(b->stream, &graph);
         if (e != cudaSuccess) { if (graph) cudaGraphDestroy(graph); return bfail(b, e, "batch capture"); }
         if (e2 != cudaSuccess) return bfail(b, e2, "cudaStreamEndCapture");
