@@ -12,6 +12,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstdlib>
+#include <type_traits>
 
 #include "launch.cuh"
 #include "vf_internal.h"
@@ -319,9 +320,11 @@ k_stage(StageArgs<T> a, FlowConsts<T> k)
 
     // z registers: the 4-vector at z-1, z, z+1 and the prefetched plane z+2; the stencil mask at z and z+1; the
     // cell's own q_n (and q2, q3 in stage 4) at z and, prefetched, at z+1 (stage 4 overwrites q2 with q* in place:
-    // the cell at z+1 is read before its owner thread writes it)
-    T qzm[4], q0[4], qzp[4], qn2[4];
-    T own[3][4] = {}, own_next[3][4] = {};   // q_n, q2, q3 of the cell
+    // the cell at z+1 is read before its owner thread writes it).  The 4-vectors form a ring of 4 slots (plane
+    // z + j - 1 in slot (P + j) mod 4 at phase P = (z - z0) mod 4) and the own states a ring of 2, so that with the
+    // loop unrolled over the 4 phases every slot index is a constant and nothing is copied as the window moves.
+    T Q[4][4] = {};
+    T own[2][3][4] = {};   // q_n, q2, q3 of the cell at z (slot P mod 2) and z+1
     constexpr int NOWN = STAGE == 1 ? 0 : (STAGE == 4 ? 3 : 1);
     constexpr bool PF = STAGE != 4 || kStagePrefetchOwn4;   // prefetched one plane ahead, else read in place
     const void* own_src[3] = {a.qn, a.q2, a.q3};
@@ -330,34 +333,34 @@ k_stage(StageArgs<T> a, FlowConsts<T> k)
         const int im = wrap(z0 - 1, nz) * plane + rowc + x;
         const int ic = z0 * plane + rowc + x;
         const int ip = wrap(z0 + 1, nz) * plane + rowc + x;
-        ld4(a.qs, im, qzm);
-        ld4(a.qs, ic, q0);
-        ld4(a.qs, ip, qzp);
+        ld4(a.qs, im, Q[0]);
+        ld4(a.qs, ic, Q[1]);
+        ld4(a.qs, ip, Q[2]);
         m0 = __ldg(a.smask + ic);
         mzp = __ldg(a.smask + ip);
         if (PF) {
 #pragma unroll
-            for (int o = 0; o < NOWN; ++o) ld4(own_src[o], ic, own[o]);
+            for (int o = 0; o < NOWN; ++o) ld4(own_src[o], ic, own[0][o]);
         }
     }
-#pragma unroll
-    for (int f = 0; f < 4; ++f) qn2[f] = T(0);
-    for (int z = z0; z < z1; ++z) {
+    auto body = [&](auto phase, int z) {
+        constexpr int P = decltype(phase)::value;
+        constexpr int OC = PF ? P % 2 : 0, ON = PF ? (P + 1) % 2 : 0;   // own-state slots at z and z+1
         const int zb = z * plane;
         const int ic = zb + rowc + x;
         uint8_t mn2 = 0;
         if (z + 1 < z1) {   // prefetch plane z+2 of the stencil state and the cell's own states at z+1
             const int i2 = wrap(z + 2, nz) * plane + rowc + x;
-            ld4(a.qs, i2, qn2);
+            ld4(a.qs, i2, Q[(P + 3) % 4]);
             mn2 = __ldg(a.smask + i2);
             if (PF) {
 #pragma unroll
-                for (int o = 0; o < NOWN; ++o) ld4(own_src[o], ic + plane, own_next[o]);
+                for (int o = 0; o < NOWN; ++o) ld4(own_src[o], ic + plane, own[ON][o]);
             }
         }
         if (!PF) {
 #pragma unroll
-            for (int o = 0; o < NOWN; ++o) ld4(own_src[o], ic, own[o]);
+            for (int o = 0; o < NOWN; ++o) ld4(own_src[o], ic, own[OC][o]);
         }
         T qm[3][4], qp[3][4];
         ld4(a.qs, zb + rowc + xm, qm[0]);
@@ -365,20 +368,36 @@ k_stage(StageArgs<T> a, FlowConsts<T> k)
         ld4(a.qs, zb + rowm + x, qm[1]);
         ld4(a.qs, zb + rowp + x, qp[1]);
 #pragma unroll
-        for (int f = 0; f < 4; ++f) { qm[2][f] = qzm[f]; qp[2][f] = qzp[f]; }
+        for (int f = 0; f < 4; ++f) { qm[2][f] = Q[P % 4][f]; qp[2][f] = Q[(P + 2) % 4][f]; }
         T o[4];
-        stage_cell<T, STAGE>(a, k, ic, q0, qm, qp, m0, own[0], own[1], own[2], dt2, dtf, dt6, inv_tau, o);
+        stage_cell<T, STAGE>(a, k, ic, Q[(P + 1) % 4], qm, qp, m0, own[OC][0], own[OC][1], own[OC][2], dt2, dtf,
+                             dt6, inv_tau, o);
         st4(a.out, ic, o);
-#pragma unroll
-        for (int f = 0; f < 4; ++f) { qzm[f] = q0[f]; q0[f] = qzp[f]; qzp[f] = qn2[f]; }
-        if (PF) {
-#pragma unroll
-            for (int o = 0; o < NOWN; ++o)
-#pragma unroll
-                for (int f = 0; f < 4; ++f) own[o][f] = own_next[o][f];
-        }
         m0 = mzp;
         mzp = mn2;
+    };
+    using I0 = std::integral_constant<int, 0>; using I1 = std::integral_constant<int, 1>;
+    using I2 = std::integral_constant<int, 2>; using I3 = std::integral_constant<int, 3>;
+    if constexpr (STAGE == 4) {
+        // stage 4 holds three own states: unrolled, its loads of later planes are scheduled early and spill under
+        // the 64-register bound, so its window moves by copies
+        for (int z = z0; z < z1; ++z) {
+            body(I0{}, z);
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+#pragma unroll
+                for (int f = 0; f < 4; ++f) Q[j][f] = Q[j + 1][f];
+        }
+    } else {
+        for (int z = z0; z < z1; z += 4) {
+            body(I0{}, z);
+            if (z + 1 >= z1) break;
+            body(I1{}, z + 1);
+            if (z + 2 >= z1) break;
+            body(I2{}, z + 2);
+            if (z + 3 >= z1) break;
+            body(I3{}, z + 3);
+        }
     }
 }
 
