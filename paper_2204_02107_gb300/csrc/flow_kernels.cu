@@ -24,6 +24,13 @@ namespace {
 // parameters per kernel family (FlowConsts::zc), chosen by the autotuner or the defaults.
 constexpr int TX = 32;
 constexpr int TY = 8;
+// rows of the filter's tile in FP32 (its shared-memory halo ring is 3 cells wide: the taller the tile, the fewer
+// ring cells per filtered cell; 16 rows took 54.7 against 48.4 us per launch on the 256 x 128 x 128 room, the
+// ring copies are not what bounds it); FP64 keeps TY within the static shared-memory limit
+#ifndef VF_FILTER_TY
+#define VF_FILTER_TY 8
+#endif
+template <typename T> __host__ __device__ constexpr int filter_ty() { return sizeof(T) == 4 ? VF_FILTER_TY : TY; }
 
 __device__ __forceinline__ void ld4(const void* base, int i, float q[4])
 {
@@ -1003,17 +1010,18 @@ k_reduce_state(const void* __restrict__ q, const uint8_t* __restrict__ mask, int
 // fluid room cells of the filter's change of the scalar, into r.div_partial (kDivRecord values), no CTA barrier.
 // ------------------------------------------------------------------------------------------------------------
 template <typename T, bool DIVSTAT, bool SIGMA>
-__global__ void __launch_bounds__(TX * TY, sizeof(T) == 4 ? 4 : 2)
+__global__ void __launch_bounds__(TX * filter_ty<T>(), sizeof(T) == 4 ? 32 / filter_ty<T>() : 2)
 k_filter(const void* __restrict__ in, void* __restrict__ out, const uint8_t* __restrict__ mask, FlowConsts<T> k,
          ReduceArgsDev r, unsigned long long* sigma_out)
 {
     pdl_enter();
-    // x / y neighbours from a shared-memory tile of the current plane: the CTA's TX x TY cells and a 3-cell halo
+    // x / y neighbours from a shared-memory tile of the current plane: the CTA's TX x FY cells and a 3-cell halo
     // ring (periodic), double buffered; the ring of the next plane arrives by cp.async while the current plane is
     // filtered, the interior is each thread's own z-window register.  The z neighbours stay in registers.
     // Three buffers in FP32 (a buffer is refilled two planes after it was read, so one CTA barrier per plane
     // suffices); two in FP64 (within the static shared-memory limit: a second barrier guards the refill).
-    constexpr int HW = TX + 6, HH = TY + 6, V = 4 * (int)sizeof(T) / 16;   // 16-byte pieces per 4-vector
+    constexpr int FY = filter_ty<T>();
+    constexpr int HW = TX + 6, HH = FY + 6, V = 4 * (int)sizeof(T) / 16;   // 16-byte pieces per 4-vector
     constexpr int NB = sizeof(T) == 4 ? 3 : 2;
     __shared__ __align__(16) T tile[NB][HH][HW][4];
     T smax = T(0);   // SIGMA: Courant rate of the filtered velocity (the step's final state)
@@ -1021,14 +1029,14 @@ k_filter(const void* __restrict__ in, void* __restrict__ out, const uint8_t* __r
     const int nx = k.nx, ny = k.ny, nz = k.nz;
     const int plane = nx * ny;
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * FY;
     const int x = x0 + tx, y = y0 + ty;
     const bool act = x < nx && y < ny;
-    const int wx = min(TX, nx - x0), wy = min(TY, ny - y0);   // cells of this (possibly ragged) tile
+    const int wx = min(TX, nx - x0), wy = min(FY, ny - y0);   // cells of this (possibly ragged) tile
     const int W = wx + 6, H = wy + 6;
     const int z0 = blockIdx.z * k.zc[kZcFilter], z1 = min(z0 + k.zc[kZcFilter], nz);
     // The halo ring: tile cell (sx, sy) holds cell (x0 + sx - 3, y0 + sy - 3), wrapped.  The ring has at most
-    // 2 (TX + TY + 6) * 3 <= 2 TX TY cells; thread tid owns ring cells tid and tid + TX TY (in ring order), whose
+    // 2 (TX + FY + 6) * 3 <= 2 TX FY cells; thread tid owns ring cells tid and tid + TX FY (in ring order), whose
     // in-plane cell index and shared-memory offset are found once.
     constexpr int kRingMax = 2;
     int ring_cell[kRingMax];
@@ -1036,7 +1044,7 @@ k_filter(const void* __restrict__ in, void* __restrict__ out, const uint8_t* __r
     {
         const int n_ring = W * H - wx * wy;
         for (int o = 0; o < kRingMax; ++o) {
-            const int j = tid + o * TX * TY;
+            const int j = tid + o * TX * FY;
             ring_cell[o] = -1;
             ring_smem[o] = 0u;
             if (j >= n_ring) continue;
@@ -1141,7 +1149,7 @@ k_filter(const void* __restrict__ in, void* __restrict__ out, const uint8_t* __r
         const Part<T> ml = warp_sum(Part<T>::of(mloss)), fr = warp_sum(Part<T>::of(froom));
         if ((tid & 31) == 0) {
             const long long bid = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
-            const long long w = bid * (TX * TY / 32) + (tid >> 5);
+            const long long w = bid * (TX * FY / 32) + (tid >> 5);
             Part<T>* rec = reinterpret_cast<Part<T>*>(r.div_partial) + kDivRecord * w;
             rec[0] = s;
             rec[1] = Part<T>::of(m);
@@ -1454,10 +1462,10 @@ __global__ void k_list_fill(const uint8_t* __restrict__ mask, size_t n, uint8_t 
 }
 
 template <typename T>
-inline dim3 flow_grid(const FlowConsts<T>& k, int kind)
+inline dim3 flow_grid(const FlowConsts<T>& k, int kind, int ty = TY)
 {
     const int zc = k.zc[kind];
-    return dim3((k.nx + TX - 1) / TX, (k.ny + TY - 1) / TY, (k.nz + zc - 1) / zc);
+    return dim3((k.nx + TX - 1) / TX, (k.ny + ty - 1) / ty, (k.nz + zc - 1) / zc);
 }
 
 inline int elementwise_blocks(size_t n) { return (int)std::min<size_t>((n + 255) / 256, 152 * 16); }
@@ -1524,7 +1532,7 @@ template <typename T>
 cudaError_t Kernels<T>::filter(const void* in, void* out, const uint8_t* mask, const FlowConsts<T>& k,
                                const ReduceArgsDev* r, cudaStream_t st, unsigned long long* sigma)
 {
-    const dim3 g = flow_grid(k, kZcFilter), b(TX, TY);
+    const dim3 g = flow_grid(k, kZcFilter, filter_ty<T>()), b(TX, filter_ty<T>());
     const ReduceArgsDev ra = r ? *r : ReduceArgsDev{};
     auto kern = r ? (sigma ? k_filter<T, true, true> : k_filter<T, true, false>)
                   : (sigma ? k_filter<T, false, true> : k_filter<T, false, false>);
@@ -1534,8 +1542,8 @@ cudaError_t Kernels<T>::filter(const void* in, void* out, const uint8_t* mask, c
 template <typename T>
 int Kernels<T>::filter_warps(const FlowConsts<T>& k)
 {
-    const dim3 g = flow_grid(k, kZcFilter);
-    return (int)(g.x * g.y * g.z) * (TX * TY / 32);
+    const dim3 g = flow_grid(k, kZcFilter, filter_ty<T>());
+    return (int)(g.x * g.y * g.z) * (TX * filter_ty<T>() / 32);
 }
 
 template <typename T>
