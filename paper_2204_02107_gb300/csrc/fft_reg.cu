@@ -41,6 +41,15 @@ struct RegShape {
     static __device__ __forceinline__ int freq(int t, int q, int k2) { return t * Q + q + R * k2; }
 };
 
+// Lanes of a warp split into 32 / G groups of G threads: for G = 4 a group's threads are adjacent lanes, else lane
+// i of group g is lane g + i 32 / G.  Shared memory serves an 8-byte access by half-warps (16-byte: by quarters),
+// each 128 bytes; with its threads adjacent, a 4-thread group's four consecutive elements and the next rows' lie
+// in one half-warp, which a row stride of 4 mod 16 elements spreads over all banks (the host's bank model picks
+// the stride for the mapping in use).
+template <int G> __host__ __device__ constexpr bool adjacent_groups() { return G == 4; }
+template <int G> __device__ __forceinline__ int group_of(int lane) { return adjacent_groups<G>() ? lane / G : lane % (32 / G); }
+template <int G> __device__ __forceinline__ int member_of(int lane) { return adjacent_groups<G>() ? lane % G : lane / (32 / G); }
+
 // slot of frequency k (the inverse of RegShape::freq followed by RegShape::slot)
 template <int R, int G>
 __device__ __forceinline__ int slot_of_freq(int k)
@@ -146,7 +155,7 @@ __global__ void __launch_bounds__(x_threads<T>()) k_reg_x_fwd(PoissonArgs<T> A)
     C* twr = tw + M;
     C* rowbuf = twr + (M + 1);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int gi = lane % P, t = lane / P;
+    const int gi = group_of<GX>(lane), t = member_of<GX>(lane);
     const int b = warp * P + gi;
     const int rows = A.ny * A.nz, row = blockIdx.x * B + b;
     const bool act = row < rows;
@@ -229,7 +238,7 @@ __global__ void __launch_bounds__(x_threads<T>()) k_reg_x_inv(PoissonArgs<T> A)
     stage_table(tw, A.twx, M);
     stage_table(twr, A.twr, M + 1);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int gi = lane % P, t = lane / P;
+    const int gi = group_of<GX>(lane), t = member_of<GX>(lane);
     const int b = warp * P + gi;
     const int rows = A.ny * A.nz, row = blockIdx.x * B + b;
     const bool act = row < rows;
@@ -338,7 +347,7 @@ __global__ void __launch_bounds__((yz_bound<T, RY, GY, RZ, GZ>())) k_reg_yz_solv
     // y forward: a group per z row, global memory -> registers -> shared plane (slots)
     {
         constexpr int P = 32 / GY;
-        const int gi = lane % P, t = lane / P;
+        const int gi = group_of<GY>(lane), t = member_of<GY>(lane);
         for (int z0 = warp * P; z0 < NZ; z0 += nwarps * P) {
             const int z = z0 + gi;
             const bool act = z < NZ;
@@ -361,7 +370,7 @@ __global__ void __launch_bounds__((yz_bound<T, RY, GY, RZ, GZ>())) k_reg_yz_solv
     // z: a group per column (y slot c): forward FFT, x 1 / (lambda N), inverse FFT, in place in the column
     {
         constexpr int P = 32 / GZ;
-        const int gi = lane % P, t = lane / P;
+        const int gi = group_of<GZ>(lane), t = member_of<GZ>(lane);
         const T lx = __ldg(A.lamx + kx);
         for (int c0 = warp * P; c0 < NY; c0 += nwarps * P) {
             const int c = c0 + gi;
@@ -396,7 +405,7 @@ __global__ void __launch_bounds__((yz_bound<T, RY, GY, RZ, GZ>())) k_reg_yz_solv
     // y inverse: a group per z row, shared plane -> registers -> global memory
     {
         constexpr int P = 32 / GY;
-        const int gi = lane % P, t = lane / P;
+        const int gi = group_of<GY>(lane), t = member_of<GY>(lane);
         for (int z0 = warp * P; z0 < NZ; z0 += nwarps * P) {
             const int z = z0 + gi;
             const bool act = z < NZ;
@@ -577,61 +586,80 @@ bool reg_shape(int n, bool fp32, int* R, int* G)
     return false;
 }
 
-// Worst number of distinct 8-byte words one bank serves in a warp access (shared memory: 16 banks of 8 bytes
-// per 128-byte wavefront for 8-byte elements, 32 of 4 bytes = 16 of 8).  addr(lane, step) in elements of esz
-// bytes, for steps 0..nsteps-1.
+// Shared-memory wavefronts of a warp access, worst over its steps: the warp's lanes are served in 128-byte phases
+// (all 32 lanes for 4-byte elements, half-warps for 8-byte, quarter-warps for 16-byte), a phase taking as many
+// wavefronts as the most distinct 4-byte words any of its 32 banks holds.  addr(lane, step) in elements of esz
+// bytes, for steps 0..nsteps-1; the ideal is 32 esz / 128 wavefronts.
 template <typename F>
 int worst_ways(int esz, int nsteps, F addr)
 {
+    const int per_phase = esz > 4 ? 128 / esz : 32;
     int worst = 1;
     for (int step = 0; step < nsteps; ++step) {
-        int ways[32] = {0};
-        long long seen[32][32];
-        int nseen[32] = {0};
-        for (int lane = 0; lane < 32; ++lane) {
-            const long long byte = addr(lane, step) * (long long)esz;
-            for (int w = 0; w < esz / 4; ++w) {
-                const long long word = byte / 4 + w;
-                const int bank = (int)(word % 32);
-                bool dup = false;
-                for (int i = 0; i < nseen[bank]; ++i) dup |= seen[bank][i] == word;
-                if (!dup && nseen[bank] < 32) { seen[bank][nseen[bank]++] = word; ways[bank]++; }
+        int total = 0;
+        for (int p0 = 0; p0 < 32; p0 += per_phase) {
+            int ways[32] = {0};
+            long long seen[32][32];
+            int nseen[32] = {0};
+            for (int lane = p0; lane < p0 + per_phase; ++lane) {
+                const long long byte = addr(lane, step) * (long long)esz;
+                for (int w = 0; w < esz / 4; ++w) {
+                    const long long word = byte / 4 + w;
+                    const int bank = (int)(word % 32);
+                    bool dup = false;
+                    for (int i = 0; i < nseen[bank]; ++i) dup |= seen[bank][i] == word;
+                    if (!dup && nseen[bank] < 32) { seen[bank][nseen[bank]++] = word; ways[bank]++; }
+                }
             }
+            int m = 1;
+            for (int i = 0; i < 32; ++i) m = ways[i] > m ? ways[i] : m;
+            total += m;
         }
-        for (int i = 0; i < 32; ++i) worst = ways[i] > worst ? ways[i] : worst;
+        worst = total > worst ? total : worst;
     }
     return worst;
 }
 
 int xpos_h(int R, int G, int t, int k1) { const int Q = R / G; return k1 * G + ((t + k1 / Q) & (G - 1)); }
 
-// conflicts of the row-owned accesses (a group of G threads per row, rows `stride` apart)
-int row_ways(int R, int G, int stride, int esz)
+// group and member of a lane (adjacent: a group's threads are adjacent lanes, the plane and x kernels for G = 4;
+// else member i of group g is lane g + i 32 / G)
+struct LaneMap {
+    int G;
+    bool adj;
+    int grp(int l) const { return adj ? l / G : l % (32 / G); }
+    int mem(int l) const { return adj ? l % G : l / (32 / G); }
+};
+
+// wavefronts of the row-owned accesses (a group of G threads per row, rows `stride` apart)
+int row_ways(int R, int G, int stride, int esz, bool adj)
 {
-    const int P = 32 / G, Q = R / G;
+    const int Q = R / G;
+    const LaneMap L{G, adj};
     int w = 0;
     auto mx = [&](int v) { w = v > w ? v : w; };
     if (G > 1) {
-        mx(worst_ways(esz, R, [&](int l, int s) { return (long long)(l % P) * stride + xpos_h(R, G, l / P, s); }));
+        mx(worst_ways(esz, R, [&](int l, int s) { return (long long)L.grp(l) * stride + xpos_h(R, G, L.mem(l), s); }));
         mx(worst_ways(esz, R, [&](int l, int s) {
-            return (long long)(l % P) * stride + xpos_h(R, G, s % G, (l / P) * Q + (s / G) % Q); }));
+            return (long long)L.grp(l) * stride + xpos_h(R, G, s % G, L.mem(l) * Q + (s / G) % Q); }));
     }
     mx(worst_ways(esz, R, [&](int l, int s) {
-        return (long long)(l % P) * stride + (l / P) + G * (s % Q) + R * ((s / Q) % G); }));
+        return (long long)L.grp(l) * stride + L.mem(l) + G * (s % Q) + R * ((s / Q) % G); }));
     return w;
 }
 
-// conflicts of the column-owned accesses (element e of column c at e * stride + c)
-int col_ways(int R, int G, int stride, int esz)
+// wavefronts of the column-owned accesses (element e of column c at e * stride + c)
+int col_ways(int R, int G, int stride, int esz, bool adj)
 {
-    const int P = 32 / G, Q = R / G;
+    const int Q = R / G;
+    const LaneMap L{G, adj};
     int w = 0;
     auto mx = [&](int v) { w = v > w ? v : w; };
-    mx(worst_ways(esz, R, [&](int l, int s) { return (long long)((l / P) + G * s) * stride + (l % P); }));
+    mx(worst_ways(esz, R, [&](int l, int s) { return (long long)(L.mem(l) + G * s) * stride + L.grp(l); }));
     if (G > 1) {
-        mx(worst_ways(esz, R, [&](int l, int s) { return (long long)xpos_h(R, G, l / P, s) * stride + (l % P); }));
+        mx(worst_ways(esz, R, [&](int l, int s) { return (long long)xpos_h(R, G, L.mem(l), s) * stride + L.grp(l); }));
         mx(worst_ways(esz, R, [&](int l, int s) {
-            return (long long)xpos_h(R, G, s % G, (l / P) * Q + (s / G) % Q) * stride + (l % P); }));
+            return (long long)xpos_h(R, G, s % G, L.mem(l) * Q + (s / G) % Q) * stride + L.grp(l); }));
     }
     return w;
 }
@@ -857,12 +885,13 @@ void RegFft<T>::configure(PoissonArgs<T>& a)
     reg_shape(a.ny, fp32, &a.ry, &a.gy);
     reg_shape(a.nz, fp32, &a.rz, &a.gz);
     const int esz = (int)sizeof(typename CxT<T>::type);
+    auto adj = [](int g) { return g == 4; };   // adjacent_groups<G>() of the plane and x kernels
     // plane stride: fewest bank conflicts over the y-row and z-column accesses, then the smallest
     // (a pad column holds the exchange of the z groups past the last y slot when a warp's groups run past ny)
     int best = -1, best_w = 1 << 30;
     for (int pad = a.ny % (32 / a.gz) ? 1 : 0; pad < 16; ++pad) {
         const int sp = a.ny + pad;
-        const int w = std::max(row_ways(a.ry, a.gy, sp, esz), col_ways(a.rz, a.gz, sp, esz));
+        const int w = std::max(row_ways(a.ry, a.gy, sp, esz, adj(a.gy)), col_ways(a.rz, a.gz, sp, esz, adj(a.gz)));
         if (w < best_w) { best_w = w; best = sp; }
     }
     a.reg_sp = best;
@@ -872,14 +901,14 @@ void RegFft<T>::configure(PoissonArgs<T>& a)
         // y passes: the row slices of the groups; z tile: TB slots of one plane, columns as for the plane
         best = -1; best_w = 1 << 30;
         for (int pad = 0; pad < 16; ++pad) {
-            const int w = row_ways(16, a.gy, a.ny + pad, esz);
+            const int w = row_ways(16, a.gy, a.ny + pad, esz, false);
             if (w < best_w) { best_w = w; best = a.ny + pad; }
         }
         a.reg_sy = best;
         a.reg_tb = std::min(a.ny, 256 / a.gz);
         best = -1; best_w = 1 << 30;
         for (int pad = 0; pad < 16; ++pad) {
-            const int w = col_ways(16, a.gz, a.reg_tb + pad, esz);
+            const int w = col_ways(16, a.gz, a.reg_tb + pad, esz, false);
             if (w < best_w) { best_w = w; best = a.reg_tb + pad; }
         }
         a.reg_st = best;
@@ -887,7 +916,7 @@ void RegFft<T>::configure(PoissonArgs<T>& a)
     // x passes: the row slices of the groups
     best = -1; best_w = 1 << 30;
     for (int pad = 0; pad < 16; ++pad) {
-        const int w = row_ways(a.rx, a.gx, a.M + pad, esz);
+        const int w = row_ways(a.rx, a.gx, a.M + pad, esz, adj(a.gx));
         if (w < best_w) { best_w = w; best = a.M + pad; }
     }
     a.reg_spx = best;
