@@ -691,6 +691,8 @@ def main():
     ap.add_argument("--extra-steps", type=int, default=30, help="timed steps of the large-room and batch legs")
     ap.add_argument("--serve-requests", type=int, default=256, help="requests of the serving leg (0: skip)")
     ap.add_argument("--no-extras", action="store_true", help="skip the large-room, batch and serving legs")
+    ap.add_argument("--extras", default="large_room,batch,next_rows,cube_wake,serve",
+                    help="comma list of the extra legs to run (large_room, batch, next_rows, cube_wake, serve)")
     ap.add_argument("--no-autotune", action="store_true", help="launch with the default tiles")
     ap.add_argument("--tiles", default=None, help="z-chunks stage,div,project,filter (skips the autotuner)")
     args = ap.parse_args()
@@ -799,12 +801,17 @@ def main():
         e2e_each = {"error": repr(e)}
     g.close()
     extras = {"fft_vs_cufft": bench_fft_vs_cufft(stream)}
-    if not args.no_extras and world == 1:
-        extras["large_room"] = bench_large_room(stream, args.extra_steps)
-        extras["batch"] = bench_batch(stream, args.extra_steps)
-        extras["next_rows"] = bench_next_rows(stream, max(args.extra_steps, 100))
-        extras["cube_wake"] = bench_cube_wake(stream)
-        if args.serve_requests > 0:
+    legs = set() if args.no_extras else {x.strip() for x in args.extras.split(",") if x.strip()}
+    if legs and world == 1:
+        if "large_room" in legs:
+            extras["large_room"] = bench_large_room(stream, args.extra_steps)
+        if "batch" in legs:
+            extras["batch"] = bench_batch(stream, args.extra_steps)
+        if "next_rows" in legs:
+            extras["next_rows"] = bench_next_rows(stream, max(args.extra_steps, 100))
+        if "cube_wake" in legs:
+            extras["cube_wake"] = bench_cube_wake(stream)
+        if "serve" in legs and args.serve_requests > 0:
             extras["serve"] = bench_serve(args.serve_requests)
             extras["serve"]["single_room_gcell_updates_per_s_for_context"] = value
 
