@@ -81,15 +81,19 @@ def test_masked_room_fp64_100_steps(torch, monkeypatch, shape, boxes, fft_path):
     g.close()
 
 
-@pytest.mark.parametrize("shape", [(40, 24, 20), (64, 36, 30), (64, 32, 32)])
+@pytest.mark.parametrize("shape", [(40, 24, 20), (64, 36, 30), (64, 32, 32), (72, 36, 36), (96, 48, 48),
+                                   (80, 40, 40)])
 def test_fp32_one_step_from_identical_state(torch, shape):
-    """FP32 bulk: one step from a state that is exactly representable in float, compared with the oracle."""
+    """FP32 bulk: one step from a state that is exactly representable in float, compared with the oracle (the
+    last three shapes on the register FFT's 2-3-5 lengths: 18 x 2, 12 x 4 and 20 x 2 points)."""
     room, prm, geom, st0 = room_case(*shape, boxes=[(10, 14, 6, 12, 2, 8)], seed=17)
     st, _ = F.run(st0, geom, prm, 3)
     st32 = F.State(*(getattr(st, n).astype(np.float32).astype(np.float64) for n in ("u", "v", "w", "c")),
                    (st.p / prm.dt).astype(np.float32).astype(np.float64) * prm.dt, st.t, st.step)
     ref, rec = F.step(st32.copy(), geom, prm)
     g = gpu_grid(prm, room.beta, room.S, room.room, "fp32")
+    if shape[1] == shape[2] and shape[1] in (36, 48, 40):
+        assert g.fft_path() == "register_plane"
     load_state(g, st32, prm, as_fp32=True)
     g.step(1)
     out = read_state(g, prm)

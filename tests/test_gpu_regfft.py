@@ -167,3 +167,18 @@ def test_masked_room_fp64_100_steps_tile_mode(torch, monkeypatch):
     errs = field_errors(read_state(g, prm), ref)
     g.close()
     assert max(errs.values()) < 1e-11, errs
+
+
+def test_masked_room_fp64_4_thread_groups(torch):
+    """FP64 register passes with 4-thread groups on every axis (128 x 64 x 64: x 64 = 16 x 4, y = z 64 = 16 x 4; the
+    groups on adjacent lanes, strides from the quarter-warp bank model) against the oracle over 40 steps."""
+    from gpu_helpers import field_errors, read_state
+    room, prm, geom, st0 = room_case(128, 64, 64, boxes=[(30, 40, 10, 20, 2, 12), (70, 90, 30, 44, 2, 8)], seed=9)
+    ref, _ = F.run(st0.copy(), geom, prm, 40)
+    g = gpu_grid(prm, room.beta, room.S, room.room, "fp64")
+    assert g.fft_path() == "register_plane"
+    load_state(g, st0, prm)
+    g.step(40)
+    errs = field_errors(read_state(g, prm), ref)
+    g.close()
+    assert max(errs.values()) < 1e-11, errs
