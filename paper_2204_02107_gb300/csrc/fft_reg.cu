@@ -28,16 +28,22 @@
 namespace vf {
 namespace {
 
-// Shape of a register transform of n = R G points: G threads (a power of two dividing R and 32) hold R values each.
+// Shape of a register transform of n = R G points: G threads (a power of two dividing 32) hold R values each for
+// the first stage, then Q = ceil(R / G) second-stage transforms of order G each, those of k1 = t Q + q.  Where G
+// does not divide R the last transforms of a thread may lie past R: they run on zeros and are not stored.
 template <int R, int G>
 struct RegShape {
-    static_assert(R % G == 0 && 32 % G == 0, "G threads per transform, R / G second-stage transforms per thread");
-    static constexpr int Q = R / G;
+    static_assert(32 % G == 0, "a transform's G threads lie in one warp");
+    static constexpr int Q = (R + G - 1) / G;
+    static constexpr bool EVEN = R % G == 0;
+    static constexpr int V = Q * G;   // values a thread holds after the exchange (R when G divides R)
     // exchange slot of the k1-th R-point output of thread t (skewed so both sides of the exchange spread over
     // the shared-memory banks)
     static __device__ __forceinline__ int xpos(int t, int k1) { return k1 * G + ((t + k1 / Q) & (G - 1)); }
-    // slot and frequency of held value (q, k2) of thread t
-    static __device__ __forceinline__ int slot(int t, int q, int k2) { return t + G * q + R * k2; }
+    // held value (q, k2) of thread t is a frequency (k1 = t Q + q < R)
+    static __device__ __forceinline__ bool valid(int t, int q) { return EVEN || t * Q + q < R; }
+    // slot and frequency of held value (q, k2) of thread t (slots in frequency order where G does not divide R)
+    static __device__ __forceinline__ int slot(int t, int q, int k2) { return EVEN ? t + G * q + R * k2 : t * Q + q + R * k2; }
     static __device__ __forceinline__ int freq(int t, int q, int k2) { return t * Q + q + R * k2; }
 };
 
@@ -54,6 +60,7 @@ template <int G> __device__ __forceinline__ int member_of(int lane) { return adj
 template <int R, int G>
 __device__ __forceinline__ int slot_of_freq(int k)
 {
+    if constexpr (!RegShape<R, G>::EVEN) return k;
     constexpr int Q = R / G;
     const int k1 = k % R, k2 = k / R;
     return (k1 / Q) + G * (k1 % Q) + R * k2;
@@ -63,45 +70,52 @@ __device__ __forceinline__ int slot_of_freq(int k)
 template <int R, int G>
 __device__ __forceinline__ int freq_of_slot(int s)
 {
+    if constexpr (!RegShape<R, G>::EVEN) return s;
     constexpr int Q = R / G;
     const int r = s % R, k2 = s / R;
     return (r % G) * Q + r / G + R * k2;
 }
 
-// forward transform of v (thread t of its group); buf(e) is element e of the group's exchange slice
+// forward transform of v[0 .. R) (thread t of its group) into the held layout v[0 .. V); buf(e) is element e of the
+// group's exchange slice
 template <typename C, int R, int G, typename BUF>
-__device__ __forceinline__ void reg_fwd(C v[R], int t, const C* tw, BUF buf)
+__device__ __forceinline__ void reg_fwd(C* v, int t, const C* tw, BUF buf)
 {
     dft<C, R, false>(v);
     if constexpr (G > 1) {
-        constexpr int Q = R / G;
+        using S = RegShape<R, G>;
+        constexpr int Q = S::Q;
 #pragma unroll
         for (int k1 = 1; k1 < R; ++k1) v[k1] = cmul(v[k1], tw[t * k1]);
         __syncwarp();
 #pragma unroll
-        for (int k1 = 0; k1 < R; ++k1) buf(RegShape<R, G>::xpos(t, k1)) = v[k1];
+        for (int k1 = 0; k1 < R; ++k1) buf(S::xpos(t, k1)) = v[k1];
         __syncwarp();
+        C zero;
+        zero.x = zero.y = decltype(zero.x)(0);
 #pragma unroll
         for (int q = 0; q < Q; ++q)
 #pragma unroll
-            for (int s = 0; s < G; ++s) v[q * G + s] = buf(RegShape<R, G>::xpos(s, t * Q + q));
+            for (int s = 0; s < G; ++s) v[q * G + s] = S::valid(t, q) ? buf(S::xpos(s, t * Q + q)) : zero;
 #pragma unroll
         for (int q = 0; q < Q; ++q) dft<C, G, false>(v + q * G);
     }
 }
 
-// inverse transform (unnormalised) from the held layout back to v[m] = n x[t + G m]
+// inverse transform (unnormalised) from the held layout v[0 .. V) back to v[m] = n x[t + G m], m < R
 template <typename C, int R, int G, typename BUF>
-__device__ __forceinline__ void reg_inv(C v[R], int t, const C* tw, BUF buf)
+__device__ __forceinline__ void reg_inv(C* v, int t, const C* tw, BUF buf)
 {
     if constexpr (G > 1) {
-        constexpr int Q = R / G;
+        using S = RegShape<R, G>;
+        constexpr int Q = S::Q;
 #pragma unroll
         for (int q = 0; q < Q; ++q) dft<C, G, true>(v + q * G);
 #pragma unroll
         for (int q = 0; q < Q; ++q)
 #pragma unroll
             for (int s = 1; s < G; ++s) {
+                if (!S::valid(t, q)) continue;
                 C w = tw[s * (t * Q + q)];
                 w.y = -w.y;
                 v[q * G + s] = cmul(v[q * G + s], w);
@@ -110,10 +124,11 @@ __device__ __forceinline__ void reg_inv(C v[R], int t, const C* tw, BUF buf)
 #pragma unroll
         for (int q = 0; q < Q; ++q)
 #pragma unroll
-            for (int s = 0; s < G; ++s) buf(RegShape<R, G>::xpos(s, t * Q + q)) = v[q * G + s];
+            for (int s = 0; s < G; ++s)
+                if (S::valid(t, q)) buf(S::xpos(s, t * Q + q)) = v[q * G + s];
         __syncwarp();
 #pragma unroll
-        for (int k1 = 0; k1 < R; ++k1) v[k1] = buf(RegShape<R, G>::xpos(t, k1));
+        for (int k1 = 0; k1 < R; ++k1) v[k1] = buf(S::xpos(t, k1));
     }
     dft<C, R, true>(v);
 }
@@ -148,7 +163,8 @@ __global__ void __launch_bounds__(x_threads<T>()) k_reg_x_fwd(PoissonArgs<T> A)
 {
     pdl_enter();
     using C = typename CxT<T>::type;
-    constexpr int M = RX * GX, NT = x_threads<T>(), B = NT / GX, P = 32 / GX, Q = RX / GX;
+    using SX = RegShape<RX, GX>;
+    constexpr int M = RX * GX, NT = x_threads<T>(), B = NT / GX, P = 32 / GX, Q = SX::Q;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int SPX = A.reg_spx;
     C* tw = reinterpret_cast<C*>(smem_raw);
@@ -159,7 +175,7 @@ __global__ void __launch_bounds__(x_threads<T>()) k_reg_x_fwd(PoissonArgs<T> A)
     const int b = warp * P + gi;
     const int rows = A.ny * A.nz, row = blockIdx.x * B + b;
     const bool act = row < rows;
-    C v[RX];
+    C v[SX::V];
     {   // the row's loads are issued before the tables are staged
         const T* __restrict__ src = A.f + (long long)(act ? row : 0) * A.nx;
 #pragma unroll
@@ -176,7 +192,8 @@ __global__ void __launch_bounds__(x_threads<T>()) k_reg_x_fwd(PoissonArgs<T> A)
 #pragma unroll
     for (int q = 0; q < Q; ++q)
 #pragma unroll
-        for (int k2 = 0; k2 < GX; ++k2) rb[RegShape<RX, GX>::slot(t, q, k2)] = v[q * GX + k2];
+        for (int k2 = 0; k2 < GX; ++k2)
+            if (SX::valid(t, q)) rb[SX::slot(t, q, k2)] = v[q * GX + k2];
     __syncwarp();
     // the split results go straight to the plane layout (rows of a warp are consecutive), or, for rows of 256
     // frequencies (two rows per warp, 16-byte pieces), through a frequency-major stage so that each frequency of
@@ -229,7 +246,8 @@ __global__ void __launch_bounds__(x_threads<T>()) k_reg_x_inv(PoissonArgs<T> A)
 {
     pdl_enter();
     using C = typename CxT<T>::type;
-    constexpr int M = RX * GX, NT = x_threads<T>(), B = NT / GX, P = 32 / GX, Q = RX / GX;
+    using SX = RegShape<RX, GX>;
+    constexpr int M = RX * GX, NT = x_threads<T>(), B = NT / GX, P = 32 / GX, Q = SX::Q;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int SPX = A.reg_spx;
     C* tw = reinterpret_cast<C*>(smem_raw);
@@ -310,11 +328,12 @@ __global__ void __launch_bounds__(x_threads<T>()) k_reg_x_inv(PoissonArgs<T> A)
         }
     }
     __syncwarp();
-    C v[RX];
+    C v[SX::V];
 #pragma unroll
     for (int q = 0; q < Q; ++q)
 #pragma unroll
-        for (int k2 = 0; k2 < GX; ++k2) v[q * GX + k2] = rb[RegShape<RX, GX>::slot(t, q, k2)];
+        for (int k2 = 0; k2 < GX; ++k2)
+            v[q * GX + k2] = SX::valid(t, q) ? rb[SX::slot(t, q, k2)] : mk<C>(T(0), T(0));
     auto buf = [rb](int e) -> C& { return rb[e]; };
     reg_inv<C, RX, GX>(v, t, tw, buf);
     if (act) {
@@ -330,7 +349,9 @@ __global__ void __launch_bounds__((yz_bound<T, RY, GY, RZ, GZ>())) k_reg_yz_solv
 {
     pdl_enter();
     using C = typename CxT<T>::type;
-    constexpr int NY = RY * GY, NZ = RZ * GZ, QY = RY / GY, QZ = RZ / GZ;
+    using SY = RegShape<RY, GY>;
+    using SZ = RegShape<RZ, GZ>;
+    constexpr int NY = RY * GY, NZ = RZ * GZ, QY = SY::Q, QZ = SZ::Q;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int SP = A.reg_sp;
     // row z at z * SP, slot s of the y transform at s; row NZ and column NY (SP > NY when a warp's last z groups
@@ -351,7 +372,7 @@ __global__ void __launch_bounds__((yz_bound<T, RY, GY, RZ, GZ>())) k_reg_yz_solv
         for (int z0 = warp * P; z0 < NZ; z0 += nwarps * P) {
             const int z = z0 + gi;
             const bool act = z < NZ;
-            C v[RY];
+            C v[SY::V];
 #pragma unroll
             for (int m = 0; m < RY; ++m) v[m] = act ? g[z * NY + t + GY * m] : mk<C>(T(0), T(0));
             C* row = plane + (act ? z : NZ) * SP;
@@ -362,7 +383,8 @@ __global__ void __launch_bounds__((yz_bound<T, RY, GY, RZ, GZ>())) k_reg_yz_solv
 #pragma unroll
                 for (int q = 0; q < QY; ++q)
 #pragma unroll
-                    for (int k2 = 0; k2 < GY; ++k2) row[RegShape<RY, GY>::slot(t, q, k2)] = v[q * GY + k2];
+                    for (int k2 = 0; k2 < GY; ++k2)
+                        if (SY::valid(t, q)) row[SY::slot(t, q, k2)] = v[q * GY + k2];
             }
         }
     }
@@ -379,7 +401,7 @@ __global__ void __launch_bounds__((yz_bound<T, RY, GY, RZ, GZ>())) k_reg_yz_solv
             const int ky = freq_of_slot<RY, GY>(act ? c : 0);
             const T lxy = lx + __ldg(A.lamy + ky);
             const bool ky_null = (kx == 0) && (ky == 0 || 2 * ky == NY);
-            C v[RZ];
+            C v[SZ::V];
 #pragma unroll
             for (int m = 0; m < RZ; ++m) v[m] = plane[(t + GZ * m) * SP + cc];
             auto buf = [plane, SP, cc](int e) -> C& { return plane[e * SP + cc]; };
@@ -388,7 +410,8 @@ __global__ void __launch_bounds__((yz_bound<T, RY, GY, RZ, GZ>())) k_reg_yz_solv
             for (int q = 0; q < QZ; ++q)
 #pragma unroll
                 for (int k2 = 0; k2 < GZ; ++k2) {
-                    const int kz = RegShape<RZ, GZ>::freq(t, q, k2);
+                    if (!SZ::valid(t, q)) continue;   // a transform past R: nothing to scale
+                    const int kz = SZ::freq(t, q, k2);
                     const bool null = ky_null && (kz == 0 || 2 * kz == NZ);
                     const T s = null ? T(0) : inv_lambda(A.invN, lxy + __ldg(A.lamz + kz));
                     v[q * GZ + k2] = cscale(v[q * GZ + k2], s);
@@ -410,11 +433,12 @@ __global__ void __launch_bounds__((yz_bound<T, RY, GY, RZ, GZ>())) k_reg_yz_solv
             const int z = z0 + gi;
             const bool act = z < NZ;
             C* row = plane + (act ? z : NZ) * SP;
-            C v[RY];
+            C v[SY::V];
 #pragma unroll
             for (int q = 0; q < QY; ++q)
 #pragma unroll
-                for (int k2 = 0; k2 < GY; ++k2) v[q * GY + k2] = row[RegShape<RY, GY>::slot(t, q, k2)];
+                for (int k2 = 0; k2 < GY; ++k2)
+                    v[q * GY + k2] = SY::valid(t, q) ? row[SY::slot(t, q, k2)] : mk<C>(T(0), T(0));
             auto buf = [row](int e) -> C& { return row[e]; };
             reg_inv<C, RY, GY>(v, t, twy, buf);
             if (act) {
@@ -573,13 +597,15 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? VF_ZTILE_MIN_CTAS : 2) k
 // ---- host side ---------------------------------------------------------------------------------------------
 // Register transform shape of an axis of n points: R values per thread and G threads, n = R G.  Lengths 16 G
 // (G = 1..16) in both precisions; the 2-3-5 lengths of the batch and serving rooms (36 .. 96) in FP32, whose
-// (y, z) planes fit whole in shared memory.
+// (y, z) planes fit whole in shared memory.  36, 60 and 72 take more threads than divide R (9 x 4, 15 x 4,
+// 9 x 8): short first-stage DFTs and four or eight threads per transform instead of 18, 30 or 36 values on two
+// threads (the 72 x 72 plane kernel: 36 x 2 held 36 values in up to 255 registers on 160 threads).
 bool reg_shape(int n, bool fp32, int* R, int* G)
 {
     for (int g = 1; g <= 16; g *= 2)
         if (n == 16 * g) { *R = 16; *G = g; return true; }
     if (!fp32) return false;
-    static const int tab[][3] = {{36, 18, 2}, {40, 20, 2}, {48, 12, 4}, {60, 30, 2}, {72, 36, 2}, {80, 20, 4},
+    static const int tab[][3] = {{36, 9, 4}, {40, 20, 2}, {48, 12, 4}, {60, 15, 4}, {72, 9, 8}, {80, 20, 4},
                                  {96, 24, 4}};
     for (const auto& e : tab)
         if (n == e[0]) { *R = e[1]; *G = e[2]; return true; }
@@ -602,7 +628,9 @@ int worst_ways(int esz, int nsteps, F addr)
             long long seen[32][32];
             int nseen[32] = {0};
             for (int lane = p0; lane < p0 + per_phase; ++lane) {
-                const long long byte = addr(lane, step) * (long long)esz;
+                const long long e = addr(lane, step);
+                if (e < 0) continue;   // this lane makes no access at this step
+                const long long byte = e * (long long)esz;
                 for (int w = 0; w < esz / 4; ++w) {
                     const long long word = byte / 4 + w;
                     const int bank = (int)(word % 32);
@@ -620,7 +648,15 @@ int worst_ways(int esz, int nsteps, F addr)
     return worst;
 }
 
-int xpos_h(int R, int G, int t, int k1) { const int Q = R / G; return k1 * G + ((t + k1 / Q) & (G - 1)); }
+int q_h(int R, int G) { return (R + G - 1) / G; }
+int xpos_h(int R, int G, int t, int k1) { const int Q = q_h(R, G); return k1 * G + ((t + k1 / Q) & (G - 1)); }
+// slot of held value (q, k2) of thread t, -1 past R (RegShape::slot)
+long long slot_h(int R, int G, int t, int q, int k2)
+{
+    const int Q = q_h(R, G);
+    if (t * Q + q >= R) return -1;
+    return R % G == 0 ? t + G * q + (long long)R * k2 : t * Q + q + (long long)R * k2;
+}
 
 // group and member of a lane (adjacent: a group's threads are adjacent lanes, the plane and x kernels for G = 4;
 // else member i of group g is lane g + i 32 / G)
@@ -634,32 +670,36 @@ struct LaneMap {
 // wavefronts of the row-owned accesses (a group of G threads per row, rows `stride` apart)
 int row_ways(int R, int G, int stride, int esz, bool adj)
 {
-    const int Q = R / G;
+    const int Q = q_h(R, G);
     const LaneMap L{G, adj};
     int w = 0;
     auto mx = [&](int v) { w = v > w ? v : w; };
     if (G > 1) {
+        // exchange: the R first-stage outputs written, then per held transform q the G sources read
         mx(worst_ways(esz, R, [&](int l, int s) { return (long long)L.grp(l) * stride + xpos_h(R, G, L.mem(l), s); }));
-        mx(worst_ways(esz, R, [&](int l, int s) {
-            return (long long)L.grp(l) * stride + xpos_h(R, G, s % G, L.mem(l) * Q + (s / G) % Q); }));
+        mx(worst_ways(esz, Q * G, [&](int l, int s) {
+            const int k1 = L.mem(l) * Q + s / G;
+            return k1 < R ? (long long)L.grp(l) * stride + xpos_h(R, G, s % G, k1) : -1LL; }));
     }
-    mx(worst_ways(esz, R, [&](int l, int s) {
-        return (long long)L.grp(l) * stride + L.mem(l) + G * (s % Q) + R * ((s / Q) % G); }));
+    mx(worst_ways(esz, Q * G, [&](int l, int s) {   // held values to and from their slots
+        const long long e = slot_h(R, G, L.mem(l), s % Q, s / Q);
+        return e < 0 ? -1LL : (long long)L.grp(l) * stride + e; }));
     return w;
 }
 
 // wavefronts of the column-owned accesses (element e of column c at e * stride + c)
 int col_ways(int R, int G, int stride, int esz, bool adj)
 {
-    const int Q = R / G;
+    const int Q = q_h(R, G);
     const LaneMap L{G, adj};
     int w = 0;
     auto mx = [&](int v) { w = v > w ? v : w; };
     mx(worst_ways(esz, R, [&](int l, int s) { return (long long)(L.mem(l) + G * s) * stride + L.grp(l); }));
     if (G > 1) {
         mx(worst_ways(esz, R, [&](int l, int s) { return (long long)xpos_h(R, G, L.mem(l), s) * stride + L.grp(l); }));
-        mx(worst_ways(esz, R, [&](int l, int s) {
-            return (long long)xpos_h(R, G, s % G, L.mem(l) * Q + (s / G) % Q) * stride + L.grp(l); }));
+        mx(worst_ways(esz, Q * G, [&](int l, int s) {
+            const int k1 = L.mem(l) * Q + s / G;
+            return k1 < R ? (long long)xpos_h(R, G, s % G, k1) * stride + L.grp(l) : -1LL; }));
     }
     return w;
 }
@@ -780,11 +820,11 @@ cudaError_t with_shape(int r, int g, F&& f)
         }
     }
     if constexpr (sizeof(T) == 4 && !ONLY16) {
-        if (r == 18 && g == 2) return f.template run<18, 2>();
+        if (r == 9 && g == 4) return f.template run<9, 4>();
         if (r == 20 && g == 2) return f.template run<20, 2>();
         if (r == 12 && g == 4) return f.template run<12, 4>();
-        if (r == 30 && g == 2) return f.template run<30, 2>();
-        if (r == 36 && g == 2) return f.template run<36, 2>();
+        if (r == 15 && g == 4) return f.template run<15, 4>();
+        if (r == 9 && g == 8) return f.template run<9, 8>();
         if (r == 20 && g == 4) return f.template run<20, 4>();
         if (r == 24 && g == 4) return f.template run<24, 4>();
     }

@@ -85,7 +85,7 @@ def test_masked_room_fp64_100_steps(torch, monkeypatch, shape, boxes, fft_path):
                                    (80, 40, 40)])
 def test_fp32_one_step_from_identical_state(torch, shape):
     """FP32 bulk: one step from a state that is exactly representable in float, compared with the oracle (the
-    last three shapes on the register FFT's 2-3-5 lengths: 18 x 2, 12 x 4 and 20 x 2 points)."""
+    last three shapes on the register FFT's 2-3-5 lengths: 9 x 4, 12 x 4 and 20 x 2 points)."""
     room, prm, geom, st0 = room_case(*shape, boxes=[(10, 14, 6, 12, 2, 8)], seed=17)
     st, _ = F.run(st0, geom, prm, 3)
     st32 = F.State(*(getattr(st, n).astype(np.float32).astype(np.float64) for n in ("u", "v", "w", "c")),

@@ -1,7 +1,7 @@
 """Register-resident FFT passes of the Poisson solve: every axis R G long with G threads of R values per
 transform (lengths 16 G, G in 1, 2, 4, 8, 16, in both precisions; in FP32 also the 2-3-5 lengths 36, 40, 48, 60,
 72, 80, 96 of the batch rooms, whose R-point DFTs are split at compile time into 2-, 3-, 4-, 5-, 8- and 16-point
-ones).
+ones, with G threads also where G does not divide R).
 
 The solve is checked against the oracle's numpy.fft solve for every shape, and whole masked-room steps (the Eq. 9
 correction kernel followed by the register passes) against the generic mixed-radix passes (VF_GENERIC_FFT).  The
@@ -24,18 +24,18 @@ SHAPES = [(32, 16, 16),      # 1 1 1
           (32, 16, 256),     # 1 1 16
           (64, 128, 16)]     # 2 8 1
 
-# FP32 2-3-5 shapes: (R, G) of x (nx / 2) and of y = z
-SHAPES_235 = [(72, 36, 36),      # (18, 2) (18, 2)
+# FP32 2-3-5 shapes: (R, G) of x (nx / 2) and of y = z; 9 x 4, 15 x 4 and 9 x 8 have more threads than divide R
+SHAPES_235 = [(72, 36, 36),      # (9, 4) (9, 4)
               (80, 40, 40),      # (20, 2) (20, 2)
               (96, 48, 48),      # (12, 4) (12, 4)
-              (120, 60, 60),     # (30, 2) (30, 2)
-              (144, 72, 72),     # (36, 2) (36, 2)
+              (120, 60, 60),     # (15, 4) (15, 4)
+              (144, 72, 72),     # (9, 8) (9, 8)
               (160, 80, 80),     # (20, 4) (20, 4)
               (192, 96, 96),     # (24, 4) (24, 4)
-              (128, 72, 72),     # (16, 4) (36, 2)
-              (72, 64, 64),      # (18, 2) (16, 4)
+              (128, 72, 72),     # (16, 4) (9, 8)
+              (72, 64, 64),      # (9, 4) (16, 4)
               (64, 80, 80),      # (16, 2) (20, 4)
-              (120, 96, 96)]     # (30, 2) (24, 4)
+              (120, 96, 96)]     # (15, 4) (24, 4)
 
 
 @pytest.fixture(scope="module")
