@@ -597,17 +597,23 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? VF_ZTILE_MIN_CTAS : 2) k
 // ---- host side ---------------------------------------------------------------------------------------------
 // Register transform shape of an axis of n points: R values per thread and G threads, n = R G.  Lengths 16 G
 // (G = 1..16) in both precisions; the 2-3-5 lengths of the batch and serving rooms (36 .. 96) in FP32, whose
-// (y, z) planes fit whole in shared memory.  36, 60 and 72 take more threads than divide R (9 x 4, 15 x 4,
-// 9 x 8): short first-stage DFTs and four or eight threads per transform instead of 18, 30 or 36 values on two
-// threads (the 72 x 72 plane kernel: 36 x 2 held 36 values in up to 255 registers on 160 threads).
-bool reg_shape(int n, bool fp32, int* R, int* G)
+// (y, z) planes fit whole in shared memory.  Some take more threads than divide R (9 x 4, 15 x 4, 9 x 8 and, along
+// x, 5 x 8, 6 x 8, 10 x 8, 12 x 8): short first-stage DFTs and four or eight threads per transform instead of up
+// to 36 values on two threads (the 72 x 72 plane kernel: 12.3 us instead of 16.4 with 36 x 2).  The x passes
+// prefer eight threads (32 points: 6.5 instead of 8.3 us per pass as 4 x 8, 64: 6.8 instead of 8.0 as 8 x 8, 96:
+// 9.2 instead of 10.3 as 12 x 8; 128 stays 16 x 8: 14 against 12.5 us as 8 x 16); the plane kernel prefers the
+// 4-thread groups of adjacent lanes (80 x 80 as 20 x 4: 12.6 us, as 10 x 8: 14.6).
+bool reg_shape(int n, bool fp32, int* R, int* G, bool x_axis = false)
 {
+    if (fp32 && x_axis && (n == 32 || n == 64)) { *R = n / 8; *G = 8; return true; }
     for (int g = 1; g <= 16; g *= 2)
         if (n == 16 * g) { *R = 16; *G = g; return true; }
     if (!fp32) return false;
-    static const int tab[][3] = {{36, 9, 4}, {40, 20, 2}, {48, 12, 4}, {60, 15, 4}, {72, 9, 8}, {80, 20, 4},
-                                 {96, 24, 4}};
-    for (const auto& e : tab)
+    static const int tab_yz[][3] = {{36, 9, 4}, {40, 20, 2}, {48, 12, 4}, {60, 15, 4}, {72, 9, 8}, {80, 20, 4},
+                                    {96, 24, 4}};
+    static const int tab_x[][3] = {{36, 9, 4}, {40, 5, 8}, {48, 6, 8}, {60, 15, 4}, {72, 9, 8}, {80, 10, 8},
+                                   {96, 12, 8}};
+    for (const auto& e : x_axis ? tab_x : tab_yz)
         if (n == e[0]) { *R = e[1]; *G = e[2]; return true; }
     return false;
 }
@@ -804,9 +810,12 @@ cudaError_t prepare_tile(const PoissonArgs<T>& a)
 }
 
 // ---- shape dispatch ------------------------------------------------------------------------------------------
-// Calls f.template run<R, G>() for the shape (r, g): the lengths 16 G in both precisions, the FP32 2-3-5 shapes
-// only for float (no double instantiations of them).
-template <typename T, bool ONLY16 = false, typename F>
+// Calls f.template run<R, G>() for the shape (r, g) of set SET: kShapes16 the lengths 16 G (both precisions),
+// kShapesYZ adds the FP32 2-3-5 shapes of the y and z axes, kShapesX those of the x axis (no double or unused
+// instantiations of them).
+constexpr int kShapes16 = 0, kShapesYZ = 1, kShapesX = 2;
+
+template <typename T, int SET, typename F>
 cudaError_t with_shape(int r, int g, F&& f)
 {
     if (r == 16) {
@@ -819,14 +828,23 @@ cudaError_t with_shape(int r, int g, F&& f)
             default: return cudaErrorInvalidValue;
         }
     }
-    if constexpr (sizeof(T) == 4 && !ONLY16) {
+    if constexpr (sizeof(T) == 4 && SET != kShapes16) {
         if (r == 9 && g == 4) return f.template run<9, 4>();
-        if (r == 20 && g == 2) return f.template run<20, 2>();
-        if (r == 12 && g == 4) return f.template run<12, 4>();
         if (r == 15 && g == 4) return f.template run<15, 4>();
         if (r == 9 && g == 8) return f.template run<9, 8>();
-        if (r == 20 && g == 4) return f.template run<20, 4>();
-        if (r == 24 && g == 4) return f.template run<24, 4>();
+        if constexpr (SET == kShapesYZ) {
+            if (r == 20 && g == 2) return f.template run<20, 2>();
+            if (r == 12 && g == 4) return f.template run<12, 4>();
+            if (r == 20 && g == 4) return f.template run<20, 4>();
+            if (r == 24 && g == 4) return f.template run<24, 4>();
+        } else {
+            if (r == 5 && g == 8) return f.template run<5, 8>();
+            if (r == 6 && g == 8) return f.template run<6, 8>();
+            if (r == 8 && g == 8) return f.template run<8, 8>();
+            if (r == 10 && g == 8) return f.template run<10, 8>();
+            if (r == 12 && g == 8) return f.template run<12, 8>();
+            if (r == 4 && g == 8) return f.template run<4, 8>();
+        }
     }
     return cudaErrorInvalidValue;
 }
@@ -856,7 +874,7 @@ struct XLaunch {
 template <typename T>
 cudaError_t dispatch_x(const PoissonArgs<T>& a, bool fwd, cudaStream_t st, bool prepare = false)
 {
-    return with_shape<T>(a.rx, a.gx, XLaunch<T>{a, fwd, st, prepare});
+    return with_shape<T, kShapesX>(a.rx, a.gx, XLaunch<T>{a, fwd, st, prepare});
 }
 
 template <typename T, int RY, int GY>
@@ -887,7 +905,7 @@ struct YLaunch {
             return YZLaunch<T, RY, GY>{a, st, prepare}.template run<RY, GY>();
         } else {
             if (a.rz != 16) return cudaErrorInvalidValue;
-            return with_shape<T, true>(16, a.gz, YZLaunch<T, RY, GY>{a, st, prepare});
+            return with_shape<T, kShapes16>(16, a.gz, YZLaunch<T, RY, GY>{a, st, prepare});
         }
     }
 };
@@ -895,7 +913,7 @@ struct YLaunch {
 template <typename T>
 cudaError_t dispatch_yz(const PoissonArgs<T>& a, cudaStream_t st, bool prepare = false)
 {
-    return with_shape<T>(a.ry, a.gy, YLaunch<T>{a, st, prepare});
+    return with_shape<T, kShapesYZ>(a.ry, a.gy, YLaunch<T>{a, st, prepare});
 }
 
 }  // namespace
@@ -906,7 +924,7 @@ bool RegFft<T>::eligible(int nx, int ny, int nz)
     if (nx % 2) return false;
     constexpr bool fp32 = sizeof(T) == 4;
     int rx, gx, ry, gy, rz, gz;
-    if (!reg_shape(nx / 2, fp32, &rx, &gx) || !reg_shape(ny, fp32, &ry, &gy) || !reg_shape(nz, fp32, &rz, &gz))
+    if (!reg_shape(nx / 2, fp32, &rx, &gx, true) || !reg_shape(ny, fp32, &ry, &gy) || !reg_shape(nz, fp32, &rz, &gz))
         return false;
     if (x_smem<T>(nx / 2, gx, nx / 2 + 15) > kRegSmemLimit) return false;
     // 2-3-5 lengths in y or z: square planes that fit whole (no tile mode); 16 G lengths: tiles when they do not
@@ -921,7 +939,7 @@ void RegFft<T>::configure(PoissonArgs<T>& a)
     a.reg = 0;
     if (!eligible(a.nx, a.ny, a.nz)) return;
     constexpr bool fp32 = sizeof(T) == 4;
-    reg_shape(a.M, fp32, &a.rx, &a.gx);
+    reg_shape(a.M, fp32, &a.rx, &a.gx, true);
     reg_shape(a.ny, fp32, &a.ry, &a.gy);
     reg_shape(a.nz, fp32, &a.rz, &a.gz);
     const int esz = (int)sizeof(typename CxT<T>::type);

@@ -15,7 +15,7 @@ from gpu_helpers import FIELD_NAMES, gpu_grid, load_state, rel_l2, require_gpu, 
 
 pytestmark = pytest.mark.gpu
 
-# (nx, ny, nz): G of x (nx / 32), y and z (n / 16)
+# (nx, ny, nz): G of x (nx / 32), y and z (n / 16); in FP32 the x lengths 32 and 64 run as 4 x 8 and 8 x 8
 SHAPES = [(32, 16, 16),      # 1 1 1
           (64, 32, 64),      # 2 2 4
           (128, 64, 32),     # 4 4 2
