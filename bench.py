@@ -651,10 +651,13 @@ def e2e_run(room, precision, steps, stream, per_step=False):
     t0 = time.perf_counter()
     g = native.Grid(room.nx, room.ny, room.nz, room.lx, room.ly, room.lz, nu=1.6e-5, dt=room.dt,
                     precision=precision, stream=stream.cuda_stream, history_capacity=max(16, steps))
+    t_create = time.perf_counter()
     g.set_mask(beta)
     g.set_inflow(S, (room.u_in, 0.0, 0.0), 0.0)
     g.set_region(region)
     g.set_field("c", c0)
+    g.sync()
+    t_upload = time.perf_counter()
     if per_step:
         hist = []
         for _ in range(steps):
@@ -663,6 +666,7 @@ def e2e_run(room, precision, steps, stream, per_step=False):
     else:
         g.step(steps, reduce_every=1)
         hist = g.history(steps)
+    t_steps = time.perf_counter()
     for name, out in zip(("u", "v", "w", "c", "p"), outs):
         native.lib().vf_read_field(g._h, native.FIELDS[name], native.C.c_void_p(out.ctypes.data), 0,
                                    native.VF_HOST)
@@ -676,7 +680,10 @@ def e2e_run(room, precision, steps, stream, per_step=False):
     if per_step:
         what += "; each step launched alone and its record read back (a host wait) before the next"
     return {"value": n * steps / el / 1e9, "unit": UNIT, "h2d_bytes_per_step": h2d / steps,
-            "d2h_bytes_per_step": d2h / steps, "seconds": el, "steps": steps, "records_read": len(hist),
+            "d2h_bytes_per_step": d2h / steps, "seconds": el,
+            "seconds_by_part": {"create_grid": t_create - t0, "upload_inputs": t_upload - t_create,
+                                "steps_and_records": t_steps - t_upload, "read_fields": t0 + el - t_steps},
+            "steps": steps, "records_read": len(hist),
             "last_record_step": hist[-1]["step"] if hist else None, "what": what}
 
 

@@ -253,20 +253,21 @@ __global__ void __launch_bounds__(x_threads<T>()) k_reg_x_inv(PoissonArgs<T> A)
     C* tw = reinterpret_cast<C*>(smem_raw);
     C* twr = tw + M;
     C* rowbuf = twr + (M + 1);
-    stage_table(tw, A.twx, M);
-    stage_table(twr, A.twr, M + 1);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int gi = group_of<GX>(lane), t = member_of<GX>(lane);
     const int b = warp * P + gi;
     const int rows = A.ny * A.nz, row = blockIdx.x * B + b;
     const bool act = row < rows;
     // the pairs (X_k, X_{M-k}) of this thread, k = t + GX i: straight from the plane layout with all loads in
-    // flight together, or (rows of 256 frequencies) gathered first for the CTA's B rows into a frequency-major stage
+    // flight together (the twiddle tables are staged after them, so that their latencies overlap), or (rows of 256
+    // frequencies) gathered first for the CTA's B rows into a frequency-major stage
     constexpr bool STAGED = GX == 16;
     constexpr int SB = B + 1;
     C* stage = rowbuf + B * SPX;
     C xk[RX / 2 + 1], xm[RX / 2 + 1];
     if (STAGED) {
+        stage_table(tw, A.twx, M);
+        stage_table(twr, A.twr, M + 1);
         const C* __restrict__ in = reinterpret_cast<const C*>(A.spec);
         const int row0 = blockIdx.x * B;
         for (int it0 = threadIdx.x; it0 < M * B; it0 += 8 * NT) {
@@ -299,6 +300,8 @@ __global__ void __launch_bounds__(x_threads<T>()) k_reg_x_inv(PoissonArgs<T> A)
             xk[i] = ok ? spec[(long long)k * rows] : mk<C>(T(0), T(0));
             xm[i] = ok && k > 0 ? spec[(long long)(M - k) * rows] : mk<C>(T(0), T(0));
         }
+        stage_table(tw, A.twx, M);
+        stage_table(twr, A.twr, M + 1);
         __syncthreads();   // tables staged
     }
     C* rb = rowbuf + b * SPX;
@@ -359,22 +362,27 @@ __global__ void __launch_bounds__((yz_bound<T, RY, GY, RZ, GZ>())) k_reg_yz_solv
     C* plane = reinterpret_cast<C*>(smem_raw);
     C* twy = plane + (NZ + 1) * SP;
     C* twz = twy + NY;
-    stage_table(twy, A.twy, NY);
-    stage_table(twz, A.twz, NZ);
     const int kx = blockIdx.x;
     C* g = reinterpret_cast<C*>(A.spec) + (long long)kx * NY * NZ;
-    __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    // y forward: a group per z row, global memory -> registers -> shared plane (slots)
+    // y forward: a group per z row, global memory -> registers -> shared plane (slots); the first row's loads are
+    // issued before the twiddle tables are staged, so that their latencies overlap
     {
         constexpr int P = 32 / GY;
         const int gi = group_of<GY>(lane), t = member_of<GY>(lane);
+        C v[SY::V];
+        auto load_row = [&](int z) {
+#pragma unroll
+            for (int m = 0; m < RY; ++m) v[m] = z < NZ ? g[z * NY + t + GY * m] : mk<C>(T(0), T(0));
+        };
+        load_row(warp * P + gi);
+        stage_table(twy, A.twy, NY);
+        stage_table(twz, A.twz, NZ);
+        __syncthreads();
         for (int z0 = warp * P; z0 < NZ; z0 += nwarps * P) {
             const int z = z0 + gi;
             const bool act = z < NZ;
-            C v[SY::V];
-#pragma unroll
-            for (int m = 0; m < RY; ++m) v[m] = act ? g[z * NY + t + GY * m] : mk<C>(T(0), T(0));
+            if (z0 != warp * P) load_row(z);
             C* row = plane + (act ? z : NZ) * SP;
             auto buf = [row](int e) -> C& { return row[e]; };
             reg_fwd<C, RY, GY>(v, t, twy, buf);
