@@ -286,13 +286,23 @@ class Batch:
         pb, mem, kb = _pointer(beta, np.uint8, n)
         ps = _pointer(S, np.uint8, n) if S is not None else (None, mem, None)
         pr = _pointer(room, np.uint8, n) if room is not None else (None, mem, None)
-        pc = _pointer(c0, np.float64, n) if c0 is not None else (None, mem, None)
+        c0_is64 = True   # float32 values (host or device) pass as they are, anything else as float64
+        if c0 is None:
+            pc = (None, mem, None)
+        elif _is_tensor(c0) and c0.is_cuda:
+            import torch
+            c0_is64 = c0.dtype != torch.float32
+            pc = _pointer(c0, np.float64 if c0_is64 else np.float32, n)
+        else:
+            c0 = np.asarray(c0)
+            c0_is64 = c0.dtype != np.float32
+            pc = _pointer(c0, np.float64 if c0_is64 else np.float32, n)
         if len({p[1] for p in (ps, pr, pc)} | {mem}) != 1:
             raise ValueError("beta, S, room and c0 must all be host arrays or all CUDA tensors")
         us = (C.c_double * 3)(*u_set)
         slot = C.c_int32()
-        rc = lib().vf_batch_add(self._h, C.byref(desc), pb, ps[0], pr[0], us, float(c_set), pc[0], 1, int(steps),
-                                mem, C.byref(slot))
+        rc = lib().vf_batch_add(self._h, C.byref(desc), pb, ps[0], pr[0], us, float(c_set), pc[0],
+                                1 if c0_is64 else 0, int(steps), mem, C.byref(slot))
         self._check(rc, "vf_batch_add")
         self._desc[slot.value] = desc
         return slot.value

@@ -64,9 +64,10 @@ class Room:
     def cells(self):
         return self.nx * self.ny * self.nz
 
-    def initial_c(self):
-        """Stale air c = 1 in fluid cells, 0 in solids and in the forcing region."""
-        return (self.beta.astype(np.float64) * (1.0 - self.S.astype(np.float64)))
+    def initial_c(self, dtype=np.float64):
+        """Stale air c = 1 in fluid cells, 0 in solids and in the forcing region (exact 0 / 1 in any dtype: an FP32
+        grid can take float32, half the bytes to form and upload)."""
+        return self.beta.astype(dtype) * (np.asarray(1.0, dtype) - self.S.astype(dtype))
 
 
 def _empty_box(nx, ny, nz, wall):

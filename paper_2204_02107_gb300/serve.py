@@ -76,36 +76,51 @@ class Server:
         """Serve a trace (dicts from ``rooms.request_trace``); returns the list of Results in completion order.
 
         realtime=True: a request becomes visible at its arrival time on the wall clock; False: all requests are
-        visible at once (arrival times still define latency)."""
+        visible at once (arrival times still define latency).
+
+        Admission overlaps the GPU: a chunk of batch steps is launched first, then the waiting requests are admitted
+        into the free slots while it runs (a new room's uploads go through its own stream, never behind the running
+        rooms), and they join the batch from the next chunk on."""
         pending = collections.deque(sorted(requests, key=lambda r: r["arrival_s"]))
         waiting = collections.deque()
         active = {}                               # slot -> (request, room, start time)
         results = []
         t0 = time.perf_counter()
         clock = lambda: time.perf_counter() - t0
-        while pending or waiting or active:
+        c_dtype = np.float32 if self.precision != "fp64" else np.float64
+
+        def arrivals():
             now = clock()
             while pending and (not realtime or pending[0]["arrival_s"] <= now):
                 req = pending.popleft()
                 waiting.append((req, rooms.request_room(req)))
-            # admit in arrival order while slots and memory allow
+
+        def admit():
+            # in arrival order while slots and memory allow
             while waiting:
                 req, room = waiting[0]
                 desc = native.room_desc(room, precision=self.precision, history_capacity=max(16, req["steps"]))
                 try:
                     slot = self.batch.add(desc, room.beta, room.S, (room.u_in, 0.0, 0.0), 0.0, req["steps"],
-                                          room=room.room, c0=room.initial_c())
+                                          room=room.room, c0=room.initial_c(c_dtype))
                 except native.VentflowError as e:
                     if e.code == native.VF_ENOMEM and active:
                         break                     # wait for running rooms to free memory
                     raise
                 waiting.popleft()
                 active[slot] = (req, room, clock())
+
+        while pending or waiting or active:
+            arrivals()
             if not active:
-                if pending:
-                    time.sleep(max(0.0, min(0.05, pending[0]["arrival_s"] - clock())))
-                continue
-            self.batch.step(self.chunk)
+                admit()
+                if not active:
+                    if pending:
+                        time.sleep(max(0.0, min(0.05, pending[0]["arrival_s"] - clock())))
+                    continue
+            self.batch.step(self.chunk)           # launched; the GPU runs it while the host admits
+            arrivals()
+            admit()
             for slot in self.batch.poll():        # waits for the chunk
                 req, room, start = active.pop(slot)
                 results.append(room_result(req, self.batch.grid(slot), room, req["arrival_s"], start, clock()))

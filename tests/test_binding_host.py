@@ -104,6 +104,25 @@ def test_batch_add_refuses_mixed_host_and_device_inputs(monkeypatch):
     host = __import__("numpy").ones(n, dtype="uint8")
     with pytest.raises(ValueError):
         b.add(desc, host, host, (1.0, 0.0, 0.0), 0.0, 10, room=host, c0=FakeCudaTensor(n))
-    with pytest.raises(TypeError):                 # a device c0 must be float64 (the call passes is_fp64 = 1)
-        b.add(desc, FakeCudaTensor(n, "uint8"), None, (1.0, 0.0, 0.0), 0.0, 10, c0=FakeCudaTensor(n, "float32"))
+    with pytest.raises(TypeError):                 # a device c0 must be float64 or float32
+        b.add(desc, FakeCudaTensor(n, "uint8"), None, (1.0, 0.0, 0.0), 0.0, 10, c0=FakeCudaTensor(n, "int32"))
     assert calls == []
+
+
+def test_batch_add_passes_the_element_type_of_c0(monkeypatch):
+    """a float32 c0 (host or device) reaches the library as float32 (c0_is_fp64 = 0), anything else as float64"""
+    np = __import__("numpy")
+    calls = []
+    b = native.Batch.__new__(native.Batch)
+    b._h, b._desc = None, {}
+    monkeypatch.setattr(native, "lib", lambda: type("L", (), {"vf_batch_add": lambda *a: calls.append(a) or 0})())
+    desc = native.VfGridDesc()
+    desc.nx, desc.ny, desc.nz = 8, 8, 8
+    n = 512
+    host = np.ones(n, dtype="uint8")
+    b.add(desc, host, host, (1.0, 0.0, 0.0), 0.0, 10, room=host, c0=np.ones(n, dtype=np.float32))
+    b.add(desc, host, host, (1.0, 0.0, 0.0), 0.0, 10, room=host, c0=np.ones(n))
+    dev = FakeCudaTensor(n, "uint8")
+    b.add(desc, dev, None, (1.0, 0.0, 0.0), 0.0, 10, c0=FakeCudaTensor(n, "float32"))
+    b.add(desc, dev, None, (1.0, 0.0, 0.0), 0.0, 10, c0=FakeCudaTensor(n, "float64"))
+    assert [c[9] for c in calls] == [0, 1, 0, 1]   # the c0_is_fp64 argument (after the bound stand-in)
